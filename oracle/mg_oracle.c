@@ -1,0 +1,823 @@
+/*
+ * mg_oracle.c -- CPU oracle for the Mixture Graph hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the GPU library computes.  Only the test-suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header, table or helper with the CUDA library.
+ *
+ * Arithmetic: exact integers (uint64) for mixtures, node keys and histograms;
+ * IEEE fp64 for colours.  Every function cites the passage of the paper it
+ * follows:
+ *   Eq. 4 (Sec. 3.1)       normalised histogram mipmap
+ *   Eq. 5-8 (Sec. 3.2)     factorisation into binary lerps, the DAG
+ *   Sec. 3.3               re-use (pruning) of identical nodes
+ *   Sec. 3.4, Fig. 5       topological level of every node
+ *   Sec. 3.4, Sec. 4       colour propagation, paletted lookup
+ *   Sec. 3.6, Algorithm 1  footprint assembly of a box query
+ *
+ * Readings of the paper taken here (the paper is silent or ambiguous):
+ *   R1 border normalisation: N counts children in support (Eq. 4), so a level
+ *      l mixture is stored as integers c = 8^l * H, with c_parent =
+ *      (8/N) * sum(c_child), exact because N is 1, 2, 4 or 8.
+ *   R2 sources are the segment IDs 0..S-1 (0-based).
+ *   R3 pair choice: the balanced positional pairing.  The entries of a mixture
+ *      are sorted by segment ID; each round lerps positions (0,1),(2,3),...
+ *      and carries an odd last entry to the end of the next round's list,
+ *      until one entry remains.  (The paper lets any pair be picked.)
+ *   R4 a node is the key (p, q, a, b): the lerp (a*p + b*q)/(a+b) of its two
+ *      predecessors with coprime integer weights a, b >= 1.  Identical keys are
+ *      one node (exact ratios, no quantiser).
+ *   R5 canonical node IDs: sources keep their segment ID; internal nodes are
+ *      numbered S, S+1, ... in ascending (depth, p', q', a, b), where p', q'
+ *      are the canonical IDs of the predecessors.
+ *   R6 Algorithm 1: "lzcnt(x)" is floor(log2 x); tzcnt(0) is infinite; the
+ *      sample position advances by the block size after each block.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdio.h>
+
+#define MGO_MAX_LEVELS 40
+#define MGO_NONE 0xFFFFFFFFu
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 4 (Sec. 3.1): resolution of every level, rounding up at each level    */
+/* until the level with 1^3 voxels.                                          */
+/* ------------------------------------------------------------------------ */
+int mgo_level_dims(int64_t nx, int64_t ny, int64_t nz, int64_t *dims_out, int max_levels)
+{
+    int64_t d[3] = {nx, ny, nz};
+    int L = 0;
+    if (nx < 1 || ny < 1 || nz < 1) return -1;
+    for (;;) {
+        if (L >= max_levels) return -1;
+        dims_out[3 * L + 0] = d[0];
+        dims_out[3 * L + 1] = d[1];
+        dims_out[3 * L + 2] = d[2];
+        L++;
+        if (d[0] == 1 && d[1] == 1 && d[2] == 1) break;
+        for (int k = 0; k < 3; k++) d[k] = (d[k] + 1) / 2;
+    }
+    return L;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mixture lists of one level: per voxel a list of (segment id, count),      */
+/* sorted by id, with count = 8^l * H (reading R1).                          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t d[3];
+    int64_t nv;       /* voxels */
+    int64_t nnz;      /* entries */
+    uint64_t *off;    /* nv + 1 */
+    uint32_t *ids;    /* nnz */
+    uint64_t *cnt;    /* nnz */
+} mgo_lists;
+
+static void lists_free(mgo_lists *m)
+{
+    free(m->off); free(m->ids); free(m->cnt);
+    memset(m, 0, sizeof(*m));
+}
+
+static uint32_t vol_id(const void *vol, int id_bytes, int64_t i)
+{
+    if (id_bytes == 2) return ((const uint16_t *)vol)[i];
+    return ((const uint32_t *)vol)[i];
+}
+
+/* Level 0: H(v,0) is the unit vector of the voxel's segment ID (Eq. 4). */
+static int lists_level0(const void *vol, int id_bytes, int64_t nx, int64_t ny, int64_t nz, mgo_lists *m)
+{
+    m->d[0] = nx; m->d[1] = ny; m->d[2] = nz;
+    m->nv = nx * ny * nz;
+    m->nnz = m->nv;
+    m->off = (uint64_t *)malloc((size_t)(m->nv + 1) * sizeof(uint64_t));
+    m->ids = (uint32_t *)malloc((size_t)m->nv * sizeof(uint32_t));
+    m->cnt = (uint64_t *)malloc((size_t)m->nv * sizeof(uint64_t));
+    if (!m->off || !m->ids || !m->cnt) return -1;
+    for (int64_t i = 0; i < m->nv; i++) {
+        m->off[i] = (uint64_t)i;
+        m->ids[i] = vol_id(vol, id_bytes, i);
+        m->cnt[i] = 1;
+    }
+    m->off[m->nv] = (uint64_t)m->nv;
+    return 0;
+}
+
+typedef struct { uint32_t id; uint64_t c; } pair_ic;
+
+static int cmp_pair_ic(const void *x, const void *y)
+{
+    const pair_ic *a = (const pair_ic *)x, *b = (const pair_ic *)y;
+    return (a->id > b->id) - (a->id < b->id);
+}
+
+/* Eq. 4: the parent mixture is the average of the children in its support,
+ * N of them.  In the integer form (R1): c_parent = (8/N) * sum of children. */
+static int lists_next(const mgo_lists *in, mgo_lists *out)
+{
+    int64_t dn[3];
+    for (int k = 0; k < 3; k++) dn[k] = (in->d[k] + 1) / 2;
+    out->d[0] = dn[0]; out->d[1] = dn[1]; out->d[2] = dn[2];
+    out->nv = dn[0] * dn[1] * dn[2];
+    /* entries never grow from one level to the next */
+    out->off = (uint64_t *)malloc((size_t)(out->nv + 1) * sizeof(uint64_t));
+    out->ids = (uint32_t *)malloc((size_t)(in->nnz > 0 ? in->nnz : 1) * sizeof(uint32_t));
+    out->cnt = (uint64_t *)malloc((size_t)(in->nnz > 0 ? in->nnz : 1) * sizeof(uint64_t));
+    if (!out->off || !out->ids || !out->cnt) return -1;
+    size_t cap = 64;
+    pair_ic *tmp = (pair_ic *)malloc(cap * sizeof(pair_ic));
+    if (!tmp) return -1;
+    int64_t w = 0;
+    for (int64_t Z = 0; Z < dn[2]; Z++)
+    for (int64_t Y = 0; Y < dn[1]; Y++)
+    for (int64_t X = 0; X < dn[0]; X++) {
+        int64_t v = (Z * dn[1] + Y) * dn[0] + X;
+        out->off[v] = (uint64_t)w;
+        size_t n = 0;
+        int N = 0;
+        for (int k = 0; k < 2; k++)
+        for (int j = 0; j < 2; j++)
+        for (int i = 0; i < 2; i++) {
+            int64_t x = 2 * X + i, y = 2 * Y + j, z = 2 * Z + k;
+            if (x >= in->d[0] || y >= in->d[1] || z >= in->d[2]) continue;
+            N++;
+            int64_t c = (z * in->d[1] + y) * in->d[0] + x;
+            for (uint64_t e = in->off[c]; e < in->off[c + 1]; e++) {
+                if (n == cap) {
+                    cap *= 2;
+                    pair_ic *t2 = (pair_ic *)realloc(tmp, cap * sizeof(pair_ic));
+                    if (!t2) { free(tmp); return -1; }
+                    tmp = t2;
+                }
+                tmp[n].id = in->ids[e];
+                tmp[n].c = in->cnt[e];
+                n++;
+            }
+        }
+        qsort(tmp, n, sizeof(pair_ic), cmp_pair_ic);
+        uint64_t scale = (uint64_t)(8 / N);
+        for (size_t e = 0; e < n;) {
+            uint32_t id = tmp[e].id;
+            uint64_t s = 0;
+            while (e < n && tmp[e].id == id) { s += tmp[e].c; e++; }
+            out->ids[w] = id;
+            out->cnt[w] = s * scale;
+            w++;
+        }
+    }
+    out->off[out->nv] = (uint64_t)w;
+    out->nnz = w;
+    free(tmp);
+    return 0;
+}
+
+/* Mixture lists of one level of the volume, for tests: returns a heap block
+ * the caller copies out and frees with mgo_level_release. */
+typedef struct {
+    int64_t nv, nnz;
+    uint64_t *off;
+    uint32_t *ids;
+    uint64_t *cnt;
+} mgo_level_out;
+
+int mgo_mixtures(const void *vol, int id_bytes, int64_t nx, int64_t ny, int64_t nz,
+                 int level, mgo_level_out *out)
+{
+    mgo_lists cur, nxt;
+    memset(&cur, 0, sizeof(cur));
+    if (lists_level0(vol, id_bytes, nx, ny, nz, &cur)) return -1;
+    for (int l = 0; l < level; l++) {
+        memset(&nxt, 0, sizeof(nxt));
+        if (lists_next(&cur, &nxt)) { lists_free(&cur); return -1; }
+        lists_free(&cur);
+        cur = nxt;
+    }
+    out->nv = cur.nv; out->nnz = cur.nnz;
+    out->off = cur.off; out->ids = cur.ids; out->cnt = cur.cnt;
+    return 0;
+}
+
+void mgo_level_release(mgo_level_out *out)
+{
+    free(out->off); free(out->ids); free(out->cnt);
+    memset(out, 0, sizeof(*out));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.2-3.3: factorisation into binary lerps with re-use of identical     */
+/* nodes.  Plain open-addressing map from key (p, q, a, b) to a temporary     */
+/* node number in order of creation.                                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    /* node arrays, indexed by temporary number; sources are 0..S-1 */
+    uint32_t *p, *q;
+    uint64_t *a, *b;
+    int32_t *depth;
+    int64_t n, cap;
+    /* map */
+    int64_t *slot;    /* -1 = empty, else node number */
+    int64_t nslot;    /* power of two */
+} mgo_table;
+
+static uint64_t mix64(uint64_t x)
+{
+    x ^= x >> 33; x *= 0xff51afd7ed558ccdULL;
+    x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ULL;
+    x ^= x >> 33;
+    return x;
+}
+
+static uint64_t key_hash(uint32_t p, uint32_t q, uint64_t a, uint64_t b)
+{
+    uint64_t h = mix64(((uint64_t)p << 32) | q);
+    h = mix64(h ^ a);
+    h = mix64(h ^ (b * 0x9e3779b97f4a7c15ULL));
+    return h;
+}
+
+static int table_grow_nodes(mgo_table *t)
+{
+    int64_t nc = t->cap ? t->cap * 2 : 1024;
+    uint32_t *np_ = (uint32_t *)realloc(t->p, (size_t)nc * sizeof(uint32_t));
+    if (!np_) return -1;
+    t->p = np_;
+    uint32_t *nq = (uint32_t *)realloc(t->q, (size_t)nc * sizeof(uint32_t));
+    if (!nq) return -1;
+    t->q = nq;
+    uint64_t *na = (uint64_t *)realloc(t->a, (size_t)nc * sizeof(uint64_t));
+    if (!na) return -1;
+    t->a = na;
+    uint64_t *nb = (uint64_t *)realloc(t->b, (size_t)nc * sizeof(uint64_t));
+    if (!nb) return -1;
+    t->b = nb;
+    int32_t *nd = (int32_t *)realloc(t->depth, (size_t)nc * sizeof(int32_t));
+    if (!nd) return -1;
+    t->depth = nd;
+    t->cap = nc;
+    return 0;
+}
+
+static int table_rehash(mgo_table *t, int64_t nslot)
+{
+    int64_t *s = (int64_t *)malloc((size_t)nslot * sizeof(int64_t));
+    if (!s) return -1;
+    for (int64_t i = 0; i < nslot; i++) s[i] = -1;
+    free(t->slot);
+    t->slot = s;
+    t->nslot = nslot;
+    return 0;
+}
+
+static int table_init(mgo_table *t, uint32_t S)
+{
+    memset(t, 0, sizeof(*t));
+    while (t->cap < (int64_t)S + 1) if (table_grow_nodes(t)) return -1;
+    for (uint32_t s = 0; s < S; s++) {
+        t->p[s] = MGO_NONE; t->q[s] = MGO_NONE; t->a[s] = 0; t->b[s] = 0; t->depth[s] = 0;
+    }
+    t->n = S;
+    return table_rehash(t, 1024);
+}
+
+static void table_free(mgo_table *t)
+{
+    free(t->p); free(t->q); free(t->a); free(t->b); free(t->depth); free(t->slot);
+    memset(t, 0, sizeof(*t));
+}
+
+static void table_insert_slot(mgo_table *t, int64_t node)
+{
+    uint64_t h = key_hash(t->p[node], t->q[node], t->a[node], t->b[node]);
+    int64_t m = t->nslot - 1;
+    int64_t i = (int64_t)(h & (uint64_t)m);
+    while (t->slot[i] >= 0) i = (i + 1) & m;
+    t->slot[i] = node;
+}
+
+static uint64_t gcd_u64(uint64_t x, uint64_t y)
+{
+    while (y) { uint64_t r = x % y; x = y; y = r; }
+    return x;
+}
+
+/* Eq. 5-6: the lerp of the entries (p, wp) and (q, wq) with the reduced ratio
+ * a:b = wp:wq; an identical key already in the table is re-used (Sec. 3.3). */
+static int64_t table_get(mgo_table *t, uint32_t p, uint64_t wp, uint32_t q, uint64_t wq)
+{
+    uint64_t g = gcd_u64(wp, wq);
+    uint64_t a = wp / g, b = wq / g;
+    uint64_t h = key_hash(p, q, a, b);
+    int64_t m = t->nslot - 1;
+    int64_t i = (int64_t)(h & (uint64_t)m);
+    while (t->slot[i] >= 0) {
+        int64_t k = t->slot[i];
+        if (t->p[k] == p && t->q[k] == q && t->a[k] == a && t->b[k] == b) return k;
+        i = (i + 1) & m;
+    }
+    if (t->n == t->cap) if (table_grow_nodes(t)) return -1;
+    int64_t k = t->n++;
+    t->p[k] = p; t->q[k] = q; t->a[k] = a; t->b[k] = b;
+    /* Sec. 3.4: topological level = max(level of predecessors) + 1 */
+    int32_t dp = t->depth[p], dq = t->depth[q];
+    t->depth[k] = (dp > dq ? dp : dq) + 1;
+    t->slot[i] = k;
+    if (2 * (t->n) > t->nslot) {
+        if (table_rehash(t, t->nslot * 2)) return -1;
+        for (int64_t j = 0; j < t->n; j++) if (t->p[j] != MGO_NONE) table_insert_slot(t, j);
+    }
+    return k;
+}
+
+/* Reading R3: factorise one mixture (entries sorted by id) with the balanced
+ * positional pairing; returns the node representing the whole mixture. */
+static int64_t factor_one(mgo_table *t, const uint32_t *ids, const uint64_t *cnt, int64_t n,
+                          uint32_t *node_buf, uint64_t *w_buf)
+{
+    for (int64_t k = 0; k < n; k++) { node_buf[k] = ids[k]; w_buf[k] = cnt[k]; }
+    while (n > 1) {
+        int64_t m = 0;
+        for (int64_t k = 0; k + 1 < n; k += 2) {
+            int64_t nd = table_get(t, node_buf[k], w_buf[k], node_buf[k + 1], w_buf[k + 1]);
+            if (nd < 0) return -1;
+            uint64_t w = w_buf[k] + w_buf[k + 1];
+            node_buf[m] = (uint32_t)nd;
+            w_buf[m] = w;
+            m++;
+        }
+        if (n & 1) { node_buf[m] = node_buf[n - 1]; w_buf[m] = w_buf[n - 1]; m++; }
+        n = m;
+    }
+    return node_buf[0];
+}
+
+/* ------------------------------------------------------------------------ */
+/* The whole graph (Sec. 3.2-3.4).                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    uint32_t S;
+    int L;
+    int64_t dims[MGO_MAX_LEVELS * 3];
+    int64_t N;          /* nodes including sources */
+    int D;              /* topological depth */
+    uint32_t *p, *q;    /* canonical order */
+    uint64_t *a, *b;
+    int32_t *depth;
+    int64_t *bucket;    /* D + 2 offsets: bucket d = [bucket[d], bucket[d+1]) */
+    uint32_t **mip;     /* per level, canonical node ID of every voxel */
+    int64_t max_nnz;    /* longest mixture list of any voxel */
+    int64_t pairs;      /* sum over voxels of (nnz - 1) */
+    int64_t *canon;     /* build-time only: temporary number -> canonical ID */
+} mgo_graph;
+
+typedef struct {
+    uint32_t cp, cq;
+    uint64_t a, b;
+    int64_t tmp;
+} relabel_key;
+
+static int cmp_relabel(const void *x, const void *y)
+{
+    const relabel_key *u = (const relabel_key *)x, *v = (const relabel_key *)y;
+    if (u->cp != v->cp) return u->cp < v->cp ? -1 : 1;
+    if (u->cq != v->cq) return u->cq < v->cq ? -1 : 1;
+    if (u->a != v->a) return u->a < v->a ? -1 : 1;
+    if (u->b != v->b) return u->b < v->b ? -1 : 1;
+    return 0;
+}
+
+/* Reading R5: canonical numbering, depth by depth.  Fills the node arrays,
+ * bucket offsets and g->canon (temporary number -> canonical ID). */
+static int relabel(mgo_graph *g, mgo_table *t)
+{
+    uint32_t S = g->S;
+    int D = 0;
+    for (int64_t k = S; k < t->n; k++) if (t->depth[k] > D) D = t->depth[k];
+    g->D = D;
+    g->N = t->n;
+    size_t n1 = (size_t)(t->n > 0 ? t->n : 1);
+    g->canon = (int64_t *)malloc(n1 * sizeof(int64_t));
+    g->bucket = (int64_t *)malloc((size_t)(D + 2) * sizeof(int64_t));
+    g->p = (uint32_t *)malloc(n1 * sizeof(uint32_t));
+    g->q = (uint32_t *)malloc(n1 * sizeof(uint32_t));
+    g->a = (uint64_t *)malloc(n1 * sizeof(uint64_t));
+    g->b = (uint64_t *)malloc(n1 * sizeof(uint64_t));
+    g->depth = (int32_t *)malloc(n1 * sizeof(int32_t));
+    relabel_key *keys = (relabel_key *)malloc(n1 * sizeof(relabel_key));
+    if (!g->canon || !g->bucket || !g->p || !g->q || !g->a || !g->b || !g->depth || !keys) {
+        free(keys);
+        return -1;
+    }
+    for (uint32_t s = 0; s < S; s++) {
+        g->canon[s] = s;
+        g->p[s] = MGO_NONE; g->q[s] = MGO_NONE; g->a[s] = 0; g->b[s] = 0; g->depth[s] = 0;
+    }
+    g->bucket[0] = 0;
+    g->bucket[1] = S;
+    int64_t next = S;
+    for (int d = 1; d <= D; d++) {
+        int64_t m = 0;
+        for (int64_t k = S; k < t->n; k++) {
+            if (t->depth[k] != d) continue;
+            keys[m].cp = (uint32_t)g->canon[t->p[k]];
+            keys[m].cq = (uint32_t)g->canon[t->q[k]];
+            keys[m].a = t->a[k];
+            keys[m].b = t->b[k];
+            keys[m].tmp = k;
+            m++;
+        }
+        qsort(keys, (size_t)m, sizeof(relabel_key), cmp_relabel);
+        for (int64_t i = 0; i < m; i++) {
+            int64_t c = next + i;
+            g->canon[keys[i].tmp] = c;
+            g->p[c] = keys[i].cp; g->q[c] = keys[i].cq;
+            g->a[c] = keys[i].a; g->b[c] = keys[i].b;
+            g->depth[c] = d;
+        }
+        next += m;
+        g->bucket[d + 1] = next;
+    }
+    free(keys);
+    return 0;
+}
+
+void mgo_graph_free(mgo_graph *g)
+{
+    if (!g) return;
+    free(g->p); free(g->q); free(g->a); free(g->b); free(g->depth); free(g->bucket);
+    free(g->canon);
+    if (g->mip) for (int l = 0; l < g->L; l++) free(g->mip[l]);
+    free(g->mip);
+    free(g);
+}
+
+mgo_graph *mgo_build(const void *vol, int id_bytes, int64_t nx, int64_t ny, int64_t nz, uint32_t S)
+{
+    mgo_graph *g = (mgo_graph *)calloc(1, sizeof(mgo_graph));
+    if (!g) return NULL;
+    g->S = S;
+    g->L = mgo_level_dims(nx, ny, nz, g->dims, MGO_MAX_LEVELS);
+    if (g->L < 1) { free(g); return NULL; }
+    int64_t V0 = nx * ny * nz;
+    for (int64_t i = 0; i < V0; i++) if (vol_id(vol, id_bytes, i) >= S) { free(g); return NULL; }
+    g->mip = (uint32_t **)calloc((size_t)g->L, sizeof(uint32_t *));
+    mgo_table t;
+    if (table_init(&t, S)) { mgo_graph_free(g); return NULL; }
+
+    /* level 0: the mip ID is the segment ID (Sec. 3.4, lossless level 0) */
+    g->mip[0] = (uint32_t *)malloc((size_t)V0 * sizeof(uint32_t));
+    for (int64_t i = 0; i < V0; i++) g->mip[0][i] = vol_id(vol, id_bytes, i);
+
+    mgo_lists cur, nxt;
+    memset(&cur, 0, sizeof(cur));
+    lists_level0(vol, id_bytes, nx, ny, nz, &cur);
+    g->max_nnz = 1;
+    int64_t bufcap = 16;
+    uint32_t *nbuf = (uint32_t *)malloc((size_t)bufcap * sizeof(uint32_t));
+    uint64_t *wbuf = (uint64_t *)malloc((size_t)bufcap * sizeof(uint64_t));
+    for (int l = 1; l < g->L; l++) {
+        memset(&nxt, 0, sizeof(nxt));
+        if (lists_next(&cur, &nxt)) { table_free(&t); mgo_graph_free(g); return NULL; }
+        lists_free(&cur);
+        cur = nxt;
+        g->mip[l] = (uint32_t *)malloc((size_t)cur.nv * sizeof(uint32_t));
+        for (int64_t v = 0; v < cur.nv; v++) {
+            int64_t n = (int64_t)(cur.off[v + 1] - cur.off[v]);
+            if (n > g->max_nnz) g->max_nnz = n;
+            g->pairs += n - 1;
+            if (n > bufcap) {
+                bufcap = n;
+                nbuf = (uint32_t *)realloc(nbuf, (size_t)bufcap * sizeof(uint32_t));
+                wbuf = (uint64_t *)realloc(wbuf, (size_t)bufcap * sizeof(uint64_t));
+            }
+            int64_t root = factor_one(&t, cur.ids + cur.off[v], cur.cnt + cur.off[v], n, nbuf, wbuf);
+            if (root < 0) { table_free(&t); mgo_graph_free(g); return NULL; }
+            g->mip[l][v] = (uint32_t)root;
+        }
+    }
+    lists_free(&cur);
+    free(nbuf); free(wbuf);
+
+    if (relabel(g, &t)) { table_free(&t); mgo_graph_free(g); return NULL; }
+    for (int l = 1; l < g->L; l++) {
+        int64_t nv = g->dims[3 * l] * g->dims[3 * l + 1] * g->dims[3 * l + 2];
+        for (int64_t v = 0; v < nv; v++) g->mip[l][v] = (uint32_t)g->canon[g->mip[l][v]];
+    }
+    free(g->canon); g->canon = NULL;
+    table_free(&t);
+    return g;
+}
+
+/* Factorise M given mixtures (CSR lists sorted by id, integer weights) with
+ * the same rule and numbering; roots[m] receives the canonical node of list m.
+ * Used to run the paper's worked examples (Fig. 2-4) through the oracle. */
+mgo_graph *mgo_factor_lists(const uint64_t *off, const uint32_t *ids, const uint64_t *cnt, int64_t M,
+                            uint32_t S, uint32_t *roots)
+{
+    mgo_graph *g = (mgo_graph *)calloc(1, sizeof(mgo_graph));
+    if (!g) return NULL;
+    g->S = S;
+    g->L = 0;
+    mgo_table t;
+    if (table_init(&t, S)) { free(g); return NULL; }
+    int64_t cap = 1;
+    for (int64_t m = 0; m < M; m++) {
+        int64_t n = (int64_t)(off[m + 1] - off[m]);
+        if (n > cap) cap = n;
+    }
+    uint32_t *nbuf = (uint32_t *)malloc((size_t)cap * sizeof(uint32_t));
+    uint64_t *wbuf = (uint64_t *)malloc((size_t)cap * sizeof(uint64_t));
+    for (int64_t m = 0; m < M; m++) {
+        int64_t n = (int64_t)(off[m + 1] - off[m]);
+        int64_t r = factor_one(&t, ids + off[m], cnt + off[m], n, nbuf, wbuf);
+        roots[m] = (uint32_t)r;
+    }
+    free(nbuf); free(wbuf);
+    if (relabel(g, &t)) { table_free(&t); mgo_graph_free(g); return NULL; }
+    for (int64_t m = 0; m < M; m++) roots[m] = (uint32_t)g->canon[roots[m]];
+    free(g->canon); g->canon = NULL;
+    table_free(&t);
+    return g;
+}
+
+/* Sec. 3.4: topological level of every node of a node table whose nodes come
+ * after their predecessors: sources 0, else max(level of p, level of q) + 1,
+ * in one linear scan. */
+void mgo_depths(const uint32_t *p, const uint32_t *q, int64_t N, uint32_t S, int32_t *depth)
+{
+    for (int64_t k = 0; k < N; k++) {
+        if ((uint32_t)k < S) { depth[k] = 0; continue; }
+        int32_t dp = depth[p[k]], dq = depth[q[k]];
+        depth[k] = (dp > dq ? dp : dq) + 1;
+    }
+}
+
+/* accessors for the Python wrapper */
+int64_t mgo_graph_nodes(const mgo_graph *g) { return g->N; }
+int mgo_graph_depth(const mgo_graph *g) { return g->D; }
+int mgo_graph_levels(const mgo_graph *g) { return g->L; }
+int64_t mgo_graph_max_nnz(const mgo_graph *g) { return g->max_nnz; }
+int64_t mgo_graph_pairs(const mgo_graph *g) { return g->pairs; }
+void mgo_graph_dims(const mgo_graph *g, int64_t *dims)
+{
+    memcpy(dims, g->dims, (size_t)g->L * 3 * sizeof(int64_t));
+}
+void mgo_graph_nodes_copy(const mgo_graph *g, uint32_t *p, uint32_t *q, uint64_t *a, uint64_t *b,
+                          int32_t *depth)
+{
+    memcpy(p, g->p, (size_t)g->N * sizeof(uint32_t));
+    memcpy(q, g->q, (size_t)g->N * sizeof(uint32_t));
+    memcpy(a, g->a, (size_t)g->N * sizeof(uint64_t));
+    memcpy(b, g->b, (size_t)g->N * sizeof(uint64_t));
+    memcpy(depth, g->depth, (size_t)g->N * sizeof(int32_t));
+}
+void mgo_graph_buckets_copy(const mgo_graph *g, int64_t *off)
+{
+    memcpy(off, g->bucket, (size_t)(g->D + 2) * sizeof(int64_t));
+}
+void mgo_graph_mip_copy(const mgo_graph *g, int level, uint32_t *out)
+{
+    int64_t nv = g->dims[3 * level] * g->dims[3 * level + 1] * g->dims[3 * level + 2];
+    memcpy(out, g->mip[level], (size_t)nv * sizeof(uint32_t));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact expansion of one node (Sec. 3.2: a node's mixture is given by its    */
+/* tree of lerps).  Pushes the integer total T from `node` to the sources:    */
+/* the predecessors of (p, q, a, b) receive T*a/(a+b) and T*b/(a+b).  Any     */
+/* node table that represents integer mixtures keeps every division exact;    */
+/* returns -1 when one is not.  out is a dense histogram of S counters.       */
+/* ------------------------------------------------------------------------ */
+int mgo_expand(const uint32_t *p, const uint32_t *q, const uint64_t *a, const uint64_t *b,
+               uint32_t S, uint32_t node, uint64_t T, uint64_t *out)
+{
+    size_t cap = 64, n = 0;
+    uint32_t *sn = (uint32_t *)malloc(cap * sizeof(uint32_t));
+    uint64_t *sw = (uint64_t *)malloc(cap * sizeof(uint64_t));
+    sn[n] = node; sw[n] = T; n++;
+    int rc = 0;
+    while (n) {
+        n--;
+        uint32_t k = sn[n];
+        uint64_t w = sw[n];
+        if (k < S) { out[k] += w; continue; }
+        uint64_t s = a[k] + b[k];
+        if (s == 0 || w % s) { rc = -1; break; }
+        uint64_t t = w / s;
+        if (n + 2 > cap) {
+            cap *= 2;
+            sn = (uint32_t *)realloc(sn, cap * sizeof(uint32_t));
+            sw = (uint64_t *)realloc(sw, cap * sizeof(uint64_t));
+        }
+        sn[n] = p[k]; sw[n] = t * a[k]; n++;
+        sn[n] = q[k]; sw[n] = t * b[k]; n++;
+    }
+    free(sn); free(sw);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.4 / Sec. 4: colour propagation over the node table in topological   */
+/* (ID) order, fp64: val[s] = TF[s]; val[n] = (a*val[p] + b*val[q])/(a+b).    */
+/* ------------------------------------------------------------------------ */
+void mgo_propagate(const uint32_t *p, const uint32_t *q, const uint64_t *a, const uint64_t *b,
+                   int64_t N, uint32_t S, const double *tf, int C, double *val)
+{
+    for (uint32_t s = 0; s < S; s++)
+        for (int c = 0; c < C; c++) val[(int64_t)s * C + c] = tf[(int64_t)s * C + c];
+    for (int64_t k = S; k < N; k++) {
+        double wa = (double)a[k], wb = (double)b[k];
+        for (int c = 0; c < C; c++)
+            val[k * C + c] = (wa * val[(int64_t)p[k] * C + c] + wb * val[(int64_t)q[k] * C + c]) / (wa + wb);
+    }
+}
+
+/* Direct colour of every voxel of one level: sum_i H_i * TF(i), fp64, from
+ * the integer mixture lists (count / 8^l). */
+void mgo_direct_colors(const uint64_t *off, const uint32_t *ids, const uint64_t *cnt, int64_t nv,
+                       const double *tf, int C, double *out)
+{
+    for (int64_t v = 0; v < nv; v++) {
+        uint64_t tot = 0;
+        for (uint64_t e = off[v]; e < off[v + 1]; e++) tot += cnt[e];
+        for (int c = 0; c < C; c++) {
+            double s = 0.0;
+            for (uint64_t e = off[v]; e < off[v + 1]; e++)
+                s += (double)cnt[e] * tf[(int64_t)ids[e] * C + c];
+            out[v * C + c] = s / (double)tot;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Box histogram by brute force (the plain definition of a sub-volume query, */
+/* Sec. 3.6): count the level-0 IDs inside the box clipped to the volume.    */
+/* Box = (x, y, z, dx, dy, dz); out is Q x S, zeroed here.                   */
+/* ------------------------------------------------------------------------ */
+void mgo_box_hist(const void *vol, int id_bytes, int64_t nx, int64_t ny, int64_t nz, uint32_t S,
+                  const int32_t *boxes, int64_t Q, uint32_t *out)
+{
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t qi = 0; qi < Q; qi++) {
+        const int32_t *bx = boxes + 6 * qi;
+        uint32_t *h = out + qi * (int64_t)S;
+        for (uint32_t s = 0; s < S; s++) h[s] = 0;
+        int64_t x1 = bx[0] + (int64_t)bx[3]; if (x1 > nx) x1 = nx;
+        int64_t y1 = bx[1] + (int64_t)bx[4]; if (y1 > ny) y1 = ny;
+        int64_t z1 = bx[2] + (int64_t)bx[5]; if (z1 > nz) z1 = nz;
+        for (int64_t z = bx[2]; z < z1; z++)
+            for (int64_t y = bx[1]; y < y1; y++)
+                for (int64_t x = bx[0]; x < x1; x++)
+                    h[vol_id(vol, id_bytes, (z * ny + y) * nx + x)]++;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 (Sec. 3.6): footprint assembly.                               */
+/* ------------------------------------------------------------------------ */
+static int floor_log2_u64(uint64_t x)
+{
+    int r = -1;
+    while (x) { x >>= 1; r++; }
+    return r;
+}
+
+static int ctz_or_inf(uint64_t x)
+{
+    if (x == 0) return 1000;          /* tzcnt(0) is taken as infinite (R6) */
+    int r = 0;
+    while (!(x & 1)) { x >>= 1; r++; }
+    return r;
+}
+
+/* footprint_1d: aligned power-of-two steps covering [i, i+di) clipped to dim */
+int mgo_footprint_1d(int64_t i, int64_t di, int64_t dim, int32_t *r)
+{
+    int n = 0;
+    di = ((i + di) < dim ? (i + di) : dim) - i;
+    while (di > 0) {
+        int a = floor_log2_u64((uint64_t)di);
+        int b = ctz_or_inf((uint64_t)i);
+        int l = a < b ? a : b;
+        r[n++] = l;
+        di -= (int64_t)1 << l;
+        i += (int64_t)1 << l;
+    }
+    return n;
+}
+
+/* Enumerate the cubes of one box: for every cube, its level and level-l voxel
+ * coordinates.  Returns the number of cubes; writes at most `cap` of them
+ * (cubes may be NULL to only count). */
+int64_t mgo_fa_cubes(const int32_t *box, int64_t nx, int64_t ny, int64_t nz,
+                     int32_t *cubes /* 4 per cube: l, x, y, z */, int64_t cap)
+{
+    int32_t Lx[80], Ly[80], Lz[80];
+    int nxr = mgo_footprint_1d(box[0], box[3], nx, Lx);
+    int nyr = mgo_footprint_1d(box[1], box[4], ny, Ly);
+    int nzr = mgo_footprint_1d(box[2], box[5], nz, Lz);
+    int64_t qx, qy, qz = box[2];
+    int64_t n = 0;
+    for (int k = 0; k < nzr; k++) {
+        qy = box[1];
+        for (int j = 0; j < nyr; j++) {
+            qx = box[0];
+            for (int i = 0; i < nxr; i++) {
+                int l = Lx[i];
+                if (Ly[j] < l) l = Ly[j];
+                if (Lz[k] < l) l = Lz[k];
+                int64_t ex = (int64_t)1 << (Lx[i] - l);
+                int64_t ey = (int64_t)1 << (Ly[j] - l);
+                int64_t ez = (int64_t)1 << (Lz[k] - l);
+                for (int64_t w = 0; w < ez; w++)
+                    for (int64_t v = 0; v < ey; v++)
+                        for (int64_t u = 0; u < ex; u++) {
+                            if (cubes && n < cap) {
+                                cubes[4 * n + 0] = l;
+                                cubes[4 * n + 1] = (int32_t)((qx >> l) + u);
+                                cubes[4 * n + 2] = (int32_t)((qy >> l) + v);
+                                cubes[4 * n + 3] = (int32_t)((qz >> l) + w);
+                            }
+                            n++;
+                        }
+                qx += (int64_t)1 << Lx[i];
+            }
+            qy += (int64_t)1 << Ly[j];
+        }
+        qz += (int64_t)1 << Lz[k];
+    }
+    return n;
+}
+
+/* Box histogram by footprint assembly over an oracle graph: every cube at
+ * level l contributes 8^l through its mip node, pushed exactly to the sources.
+ * Returns -1 if an inexact division is met.  out is Q x S, zeroed here. */
+int mgo_fa_query(const mgo_graph *g, const int32_t *boxes, int64_t Q, uint32_t *out)
+{
+    uint32_t S = g->S;
+    uint64_t *acc = (uint64_t *)malloc((size_t)S * sizeof(uint64_t));
+    int rc = 0;
+    for (int64_t qi = 0; qi < Q && rc == 0; qi++) {
+        const int32_t *bx = boxes + 6 * qi;
+        memset(acc, 0, (size_t)S * sizeof(uint64_t));
+        int64_t nc = mgo_fa_cubes(bx, g->dims[0], g->dims[1], g->dims[2], NULL, 0);
+        int32_t *cubes = (int32_t *)malloc((size_t)(nc > 0 ? nc : 1) * 4 * sizeof(int32_t));
+        mgo_fa_cubes(bx, g->dims[0], g->dims[1], g->dims[2], cubes, nc);
+        for (int64_t c = 0; c < nc && rc == 0; c++) {
+            int l = cubes[4 * c];
+            const int64_t *dl = g->dims + 3 * l;
+            int64_t v = ((int64_t)cubes[4 * c + 3] * dl[1] + cubes[4 * c + 2]) * dl[0] + cubes[4 * c + 1];
+            uint64_t w = (uint64_t)1 << (3 * l);
+            rc = mgo_expand(g->p, g->q, g->a, g->b, S, g->mip[l][v], w, acc);
+        }
+        free(cubes);
+        for (uint32_t s = 0; s < S; s++) out[qi * (int64_t)S + s] = (uint32_t)acc[s];
+    }
+    free(acc);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ray-sample lookup (Sec. 4): nearest voxel of the level nearest to the     */
+/* sample's LOD.  The level and voxel index are decided in fp32, the           */
+/* precision of the samples.  Sample = (x, y, z, lod) in level-0 voxel units. */
+/* ------------------------------------------------------------------------ */
+static int64_t floor_coord(float x, int64_t d0)
+{
+    /* clamp to [0, d0] in fp32 (NaN goes to 0), then floor; for x >= 0 the
+     * truncating conversion is the floor */
+    float xc = x;
+    if (!(xc >= 0.0f)) xc = 0.0f;
+    if (xc > (float)d0) xc = (float)d0;
+    return (int64_t)xc;
+}
+
+static int sample_level(float lod, int L)
+{
+    float t = lod + 0.5f;               /* round to the nearest level, fp32 */
+    if (!(t >= 0.0f)) return 0;
+    if (t >= (float)(L - 1)) return L - 1;
+    return (int)t;
+}
+
+/* For every sample: its level and the linear index of its voxel in that
+ * level (x fastest). */
+void mgo_sample_voxels(const int64_t *dims, int L, const float *samples, int64_t P,
+                       int32_t *level_out, int64_t *voxel_out)
+{
+    for (int64_t i = 0; i < P; i++) {
+        const float *s = samples + 4 * i;
+        int l = sample_level(s[3], L);
+        const int64_t *dl = dims + 3 * l;
+        int64_t v[3];
+        for (int k = 0; k < 3; k++) {
+            int64_t c = floor_coord(s[k], dims[k]) >> l;
+            v[k] = c < dl[k] - 1 ? c : dl[k] - 1;
+        }
+        level_out[i] = l;
+        voxel_out[i] = (v[2] * dl[1] + v[1]) * dl[0] + v[0];
+    }
+}

@@ -1,0 +1,387 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each expected value is printed
+in the paper (tests/golden/*.json, cited there), worked by hand from the
+paper's definitions, a closed form, an invariant, or a brute-force count by a
+different code path.
+"""
+from fractions import Fraction
+from math import gcd
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_02702_gb300 import synth
+from tests.conftest import golden
+
+
+def F(s):
+    return Fraction(s)
+
+
+# --------------------------------------------------------------------------
+# Eq. 4 / Table 2: mip geometry
+# --------------------------------------------------------------------------
+def test_table2_voxel_totals_and_levels():
+    g = golden("table2_mip_geometry.json")
+    for ds in g["datasets"]:
+        dims = oracle.level_dims(*ds["resolution"])
+        assert dims.shape[0] == ds["mip_levels"], ds["name"]
+        total = int(np.prod(dims, axis=1).sum())
+        printed = ds["voxels_million"].replace(",", "")
+        decimals = len(printed.split(".")[1]) if "." in printed else 0
+        # the paper truncates (1,195,445,766 -> 1,195) or rounds to its digits
+        assert abs(total / 1e6 - float(printed)) < 10 ** -decimals, (ds["name"], total)
+        assert tuple(dims[-1]) == (1, 1, 1)
+
+
+def test_level_dims_round_up():
+    d = oracle.level_dims(5, 1, 3)
+    assert d.tolist() == [[5, 1, 3], [3, 1, 2], [2, 1, 1], [1, 1, 1]]
+    assert oracle.level_dims(1, 1, 1).tolist() == [[1, 1, 1]]
+
+
+# --------------------------------------------------------------------------
+# Eq. 4: mixtures, hand-worked border cases and invariants
+# --------------------------------------------------------------------------
+def _vol_from_case(case):
+    nx, ny, nz = case["dims"]
+    if "ids" in case:
+        return np.array(case["ids"], np.uint16).reshape(nz, ny, nx)
+    v = np.zeros((nz, ny, nx), np.uint16)
+    x, y, z = case["ids_corner_one"]
+    v[z, y, x] = 1
+    return v
+
+
+def test_eq4_hand_worked_border_cases():
+    g = golden("eq4_border_mixtures.json")
+    for case in g["cases"]:
+        vol = _vol_from_case(case)
+        for lev, voxels in case["levels"].items():
+            off, ids, cnt = oracle.mixtures(vol, int(lev))
+            assert off.shape[0] - 1 == len(voxels)
+            for v, entries in enumerate(voxels):
+                got = [[int(i), int(c)] for i, c in zip(ids[off[v]:off[v + 1]], cnt[off[v]:off[v + 1]])]
+                assert got == entries, (case["dims"], lev, v)
+        if "level1_corner_voxel" in case:
+            off, ids, cnt = oracle.mixtures(vol, 1)
+            v = 7  # (1,1,1) in a 2x2x2 level
+            got = [[int(i), int(c)] for i, c in zip(ids[off[v]:off[v + 1]], cnt[off[v]:off[v + 1]])]
+            assert got == case["level1_corner_voxel"]
+
+
+def test_eq1_eq2_invariants_and_interior_counts():
+    vol = synth.make_volume(1, dims=(24, 20, 18), S=16)
+    dims = oracle.level_dims(24, 20, 18)
+    for l in range(dims.shape[0]):
+        off, ids, cnt = oracle.mixtures(vol, l)
+        nx, ny, nz = dims[l]
+        assert off.shape[0] - 1 == nx * ny * nz
+        for v in range(nx * ny * nz):
+            e = slice(off[v], off[v + 1])
+            assert off[v + 1] > off[v]
+            assert int(cnt[e].sum()) == 8 ** l                       # Eq. 1 (x 8^l)
+            assert (cnt[e] >= 1).all()                                # Eq. 2
+            assert (np.diff(ids[e].astype(np.int64)) > 0).all()       # sorted, unique
+        # interior voxels (whole 2^l footprint inside): raw counts of level-0 IDs
+        s = 2 ** l
+        for Z in range(nz):
+            for Y in range(ny):
+                for X in range(nx):
+                    if (X + 1) * s > 24 or (Y + 1) * s > 20 or (Z + 1) * s > 18:
+                        continue
+                    sub = vol[Z * s:(Z + 1) * s, Y * s:(Y + 1) * s, X * s:(X + 1) * s].ravel()
+                    bc = np.bincount(sub, minlength=16)
+                    v = (Z * ny + Y) * nx + X
+                    e = slice(off[v], off[v + 1])
+                    dense = np.zeros(16, np.int64)
+                    dense[ids[e]] = cnt[e]
+                    assert (dense == bc).all()
+
+
+def test_level0_is_lossless():
+    vol = synth.make_volume(1, dims=(9, 7, 5), S=10)
+    off, ids, cnt = oracle.mixtures(vol, 0)
+    assert (np.diff(off) == 1).all() and (cnt == 1).all()
+    assert (ids == vol.ravel()).all()
+    g = oracle.Graph(vol, 10)
+    assert (g.mip(0) == vol).all()
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.2-3.3: factorisation, Fig. 2 / Fig. 3 / Fig. 4
+# --------------------------------------------------------------------------
+def _paper_table_fig3():
+    """The Fig. 2/3 tree as an oracle node table (sources 0..3 = e1..e4)."""
+    g = golden("fig2_fig3_factorization.json")
+    name_to_id = {str(i + 1): i for i in range(4)}
+    p, q, a, b = [oracle.NONE] * 4, [oracle.NONE] * 4, [0] * 4, [0] * 4
+    for name in ("5", "6", "7"):
+        nd = g["nodes"][name]
+        wi, wj = F(nd["edge_weight"][0]), F(nd["edge_weight"][1])
+        assert wi + wj == 1
+        den = wi.denominator * wj.denominator // gcd(wi.denominator, wj.denominator)
+        name_to_id[name] = len(p)
+        p.append(name_to_id[str(nd["pred"][0])])
+        q.append(name_to_id[str(nd["pred"][1])])
+        a.append(int(wi * den))
+        b.append(int(wj * den))
+    return g, name_to_id, np.array(p), np.array(q), np.array(a), np.array(b)
+
+
+def test_fig2_fig3_expansion():
+    g, ids, p, q, a, b = _paper_table_fig3()
+    for name, expect in g["expanded"].items():
+        fr = [F(x) for x in expect]
+        den = 1
+        for x in fr:
+            den = den * x.denominator // gcd(den, x.denominator)
+        out = oracle.expand(p, q, a, b, 4, ids[name], den)
+        assert [Fraction(int(v), den) for v in out] == fr, name
+    # Sec. 3.4: levels of the chain
+    assert oracle.depths(p, q, 4).tolist() == [0, 0, 0, 0, 1, 2, 3]
+
+
+def test_fig2_propagation_of_unit_vectors():
+    g, ids, p, q, a, b = _paper_table_fig3()
+    val = oracle.propagate(p, q, a, b, 4, np.eye(4))
+    m = [float(F(x)) for x in g["mixture"]]
+    assert np.allclose(val[ids["7"]], m, rtol=0, atol=1e-15)
+
+
+def test_fig4_reuse_of_lambda5():
+    g = golden("fig4_dag.json")
+    lists = []
+    for mix in g["mixtures"]:
+        fr = [F(x) for x in mix]
+        lists.append([(i, int(x * 10)) for i, x in enumerate(fr)])
+    G, roots = oracle.factor_lists(lists, 4)
+    # exactly one node mixes e1 and e2 at 1:2 and both mixtures use it
+    sh = g["shared_node"]
+    wi, wj = F(sh["edge_weight"][0]), F(sh["edge_weight"][1])
+    key = (sh["pred"][0] - 1, sh["pred"][1] - 1, int(wi * 3), int(wj * 3))
+    hits = [k for k in range(G.N) if (G.p[k], G.q[k], G.a[k], G.b[k]) == key]
+    assert len(hits) == 1
+    lam5 = hits[0]
+    # m' = 3/5 lambda_5 + 2/5 lambda_8, lambda_8 = 1/4 e3 + 3/4 e4
+    r1 = int(roots[1])
+    assert G.p[r1] == lam5 and (G.a[r1], G.b[r1]) == (3, 2)
+    l8 = int(G.q[r1])
+    assert (G.p[l8], G.q[l8], G.a[l8], G.b[l8]) == (2, 3, 1, 3)
+    # m reaches lambda_5 through its root's left subtree
+    r0 = int(roots[0])
+    assert G.p[r0] == lam5
+    for r, lst in zip(roots, lists):
+        out = oracle.expand(G.p, G.q, G.a, G.b, 4, int(r), 10)
+        assert out.tolist() == [w for _, w in lst]
+
+
+def test_fig5_topological_levels():
+    g = golden("fig5_topological_levels.json")
+    names = g["node_names"]
+    idx = {n: i for i, n in enumerate(names)}
+    S = g["sources"]
+    p = np.full(len(names), oracle.NONE, np.uint32)
+    q = np.full(len(names), oracle.NONE, np.uint32)
+    for n, (u, v) in g["edges_into"].items():
+        p[idx[n]], q[idx[n]] = idx[u], idx[v]
+    lev = oracle.depths(p, q, S)
+    assert lev.tolist() == g["levels"]
+    # the deferrable node: its successors' minimum level bounds its window
+    node = idx[g["deferrable"]["node"]]
+    succ_levels = [lev[idx[n]] for n, pr in g["edges_into"].items() if names[node] in pr]
+    assert list(range(lev[node], min(succ_levels))) == g["deferrable"]["may_run_with_levels"]
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.2-3.4 on whole volumes: pruning keeps every mixture, table structure
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,S", [((16, 16, 16), 8), ((13, 9, 11), 12), ((1, 1, 40), 5)])
+def test_graph_expansion_equals_mixtures(dims, S):
+    vol = synth.make_volume(1, dims=dims, S=S)
+    g = oracle.Graph(vol, S)
+    for l in range(g.L):
+        off, ids, cnt = oracle.mixtures(vol, l)
+        mip = g.mip(l).ravel()
+        for v in range(mip.shape[0]):
+            out = oracle.expand(g.p, g.q, g.a, g.b, S, int(mip[v]), 8 ** l)
+            dense = np.zeros(S, np.uint64)
+            dense[ids[off[v]:off[v + 1]]] = cnt[off[v]:off[v + 1]]
+            assert (out == dense).all(), (l, v)
+
+
+def test_graph_table_structure():
+    vol = synth.make_volume(1, dims=(32, 24, 20), S=20)
+    g = oracle.Graph(vol, 20)
+    S = g.S
+    k = np.arange(S, g.N)
+    # Eq. 8: predecessors come first
+    assert (g.p[S:] < k).all() and (g.q[S:] < k).all()
+    # reduced ratios
+    assert (g.a[S:] >= 1).all() and (g.b[S:] >= 1).all()
+    assert all(gcd(int(x), int(y)) == 1 for x, y in zip(g.a[S:], g.b[S:]))
+    # Sec. 3.4 levels and buckets
+    assert (g.depth == oracle.depths(g.p, g.q, S)).all()
+    assert g.bucket[0] == 0 and g.bucket[1] == S and g.bucket[-1] == g.N
+    for d in range(1, g.D + 1):
+        assert (g.depth[g.bucket[d]:g.bucket[d + 1]] == d).all()
+    # canonical order inside each bucket, and unique keys (pruning)
+    keys = list(zip(g.depth[S:], g.p[S:], g.q[S:], g.a[S:], g.b[S:]))
+    assert keys == sorted(keys)
+    assert len(set(keys)) == len(keys)
+
+
+def test_two_segment_node_count_is_distinct_ratios():
+    """With two segments every mixed voxel is one lerp of the two sources, so
+    the number of internal nodes is the number of distinct reduced ratios."""
+    vol = np.zeros((20, 20, 20), np.uint16)
+    zz, yy, xx = np.meshgrid(np.arange(20), np.arange(20), np.arange(20), indexing="ij")
+    vol[(3 * xx + 5 * yy + 7 * zz) > 150] = 1
+    g = oracle.Graph(vol, 2)
+    ratios = set()
+    for l in range(1, g.L):
+        off, ids, cnt = oracle.mixtures(vol, l)
+        for v in range(off.shape[0] - 1):
+            if off[v + 1] - off[v] == 2:
+                c0, c1 = int(cnt[off[v]]), int(cnt[off[v] + 1])
+                t = gcd(c0, c1)
+                ratios.add((c0 // t, c1 // t))
+    assert g.N - 2 == len(ratios)
+    assert g.D == 1
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.4 / Sec. 4: forward propagation equals the direct convex combination
+# --------------------------------------------------------------------------
+def test_propagation_equals_direct_sum():
+    vol = synth.make_volume(1, dims=(20, 18, 16), S=30)
+    g = oracle.Graph(vol, 30)
+    tf = synth.make_tf(1, 30, 4).astype(np.float64)
+    val = oracle.propagate(g.p, g.q, g.a, g.b, 30, tf)
+    for l in range(g.L):
+        direct = oracle.direct_colors(vol, l, tf)
+        got = val[g.mip(l).ravel()]
+        assert np.allclose(got, direct, rtol=1e-12, atol=1e-14)
+
+
+def test_unit_vector_tf_gives_mixtures():
+    vol = synth.make_volume(1, dims=(12, 12, 12), S=9)
+    g = oracle.Graph(vol, 9)
+    val = oracle.propagate(g.p, g.q, g.a, g.b, 9, np.eye(9))
+    for l in range(g.L):
+        off, ids, cnt = oracle.mixtures(vol, l)
+        mip = g.mip(l).ravel()
+        for v in range(mip.shape[0]):
+            dense = np.zeros(9)
+            dense[ids[off[v]:off[v + 1]]] = cnt[off[v]:off[v + 1]] / 8.0 ** l
+            assert np.allclose(val[mip[v]], dense, rtol=0, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.6: brute-force histograms, footprint assembly
+# --------------------------------------------------------------------------
+def test_box_hist_brute_force_and_clipping():
+    vol = synth.make_volume(1, dims=(17, 13, 11), S=7)
+    rng = np.random.default_rng(5)
+    boxes = []
+    for _ in range(200):
+        o = [rng.integers(0, n) for n in (17, 13, 11)]
+        s = [rng.integers(1, 2 * n) for n in (17, 13, 11)]   # often past the border
+        boxes.append(o + s)
+    boxes = np.array(boxes, np.int32)
+    h = oracle.box_hist(vol, 7, boxes)
+    for bx, row in zip(boxes, h):
+        x, y, z, dx, dy, dz = bx
+        sub = vol[z:z + dz, y:y + dy, x:x + dx]
+        assert (np.bincount(sub.ravel(), minlength=7) == row).all()
+        assert row.sum() == sub.size
+
+
+def test_fig6_footprint_example():
+    g = golden("fig6_footprint.json")
+    assert oracle.footprint_1d(g["x_range"][0], g["x_range"][1], 1 << 20) == g["x_levels"]
+    assert oracle.footprint_1d(g["y_range"][0], g["y_range"][1], 1 << 20) == g["y_levels"]
+    box = [g["x_range"][0], g["y_range"][0], 0, g["x_range"][1], g["y_range"][1], 4]
+    cubes = oracle.fa_cubes(box, 64, 64, 64)
+    per = {int(l): int(c) for l, c in zip(*np.unique(cubes[:, 0], return_counts=True))}
+    sq = {int(k): v for k, v in g["squares_per_level"].items()}
+    assert per == {l: n * 2 ** (2 - l) for l, n in sq.items()}
+
+
+def test_footprint_1d_hand_cases():
+    assert oracle.footprint_1d(0, 16, 100) == [4]
+    assert oracle.footprint_1d(1, 512, 4096) == [0, 1, 2, 3, 4, 5, 6, 7, 8, 0]
+    assert oracle.footprint_1d(5, 100, 8) == [0, 1]            # clipped to [5, 8)
+    assert oracle.footprint_1d(0, 7, 7) == [2, 1, 0]
+    assert oracle.footprint_1d(6, 1, 7) == [0]
+
+
+def test_fa_cubes_tile_the_clipped_box():
+    dims = (23, 17, 14)
+    rng = np.random.default_rng(11)
+    for _ in range(150):
+        o = [int(rng.integers(0, n)) for n in dims]
+        s = [int(rng.integers(1, n + 6)) for n in dims]
+        box = o + s
+        cubes = oracle.fa_cubes(box, *dims)
+        mark = np.zeros(dims[::-1], np.int32)
+        for l, x, y, z in cubes:
+            e = 1 << l
+            assert x * e >= o[0] and y * e >= o[1] and z * e >= o[2]
+            mark[z * e:(z + 1) * e, y * e:(y + 1) * e, x * e:(x + 1) * e] += 1
+        want = np.zeros_like(mark)
+        want[o[2]:o[2] + s[2], o[1]:o[1] + s[1], o[0]:o[0] + s[0]] = 1
+        assert (mark == want).all(), box
+
+
+def test_fa_query_equals_brute_force():
+    vol = synth.make_volume(1)
+    g = oracle.Graph(vol, 64)
+    boxes = synth.make_boxes(1, Q=300)
+    assert (g.fa_query(boxes) == oracle.box_hist(vol, 64, boxes)).all()
+
+
+def test_table3_saved_arithmetic():
+    g = golden("table3_fetches.json")
+    for ds, fetches in g["fetches"].items():
+        for size, f, saved in zip(g["sizes"], fetches, g["saved_percent"][ds]):
+            mult = 1000.0 if f.endswith("K") else 1.0
+            digits = f.rstrip("K")
+            dec = len(digits.split(".")[1]) if "." in digits else 0
+            half = 0.5 * 10 ** -dec * mult
+            lo = 100 * (1 - (float(digits) * mult + half) / size ** 3)
+            hi = 100 * (1 - (float(digits) * mult - half) / size ** 3)
+            s = float(saved)
+            assert lo - 0.006 <= s <= hi + 0.006, (ds, size)
+
+
+def test_table3_fetch_counts_sanity_band():
+    """Randomly aligned cubic regions: mean fetch count within +-25% of the
+    paper's range (the paper's sampling is not specified: a band, not a pin)."""
+    g = golden("table3_fetches.json")
+    rng = np.random.default_rng(3)
+    big = 4096
+    for si, size in enumerate(g["sizes"]):
+        vals = []
+        for ds in g["fetches"].values():
+            f = ds[si]
+            vals.append(float(f.rstrip("K")) * (1000.0 if f.endswith("K") else 1.0))
+        n = 400 if size <= 64 else 60
+        counts = [oracle.fa_count([int(rng.integers(0, big - size)) for _ in range(3)] + [size] * 3,
+                                  big, big, big) for _ in range(n)]
+        m = float(np.mean(counts))
+        assert 0.75 * min(vals) <= m <= 1.25 * max(vals), (size, m, vals)
+
+
+def test_sec4_sample_lookup_hand_cases():
+    g = golden("sec4_sample_lookup.json")
+    dims = oracle.level_dims(*g["dims"])
+    smp = np.array([[float(x) for x in s["xyzl"]] for s in g["samples"]], np.float32)
+    lev, vox = oracle.sample_voxels(dims, smp)
+    for s, l, v in zip(g["samples"], lev, vox):
+        assert l == s["level"]
+        nx, ny, _ = dims[l]
+        x, y, z = s["voxel"]
+        assert v == (z * ny + y) * nx + x, s
