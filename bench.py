@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""Benchmark of the Mixture Graph hot path on GB300.
+
+One step = one pass of the served hot path over one batch of synthetic input:
+  A4  propagate one RGBA fp32 transfer function through the whole graph,
+  A6-A8  answer one batch of box-histogram queries (exact u32 histograms,
+      persistent batched launch),
+  A5  look up one 1920x1080 frame of ray samples in the propagated palette.
+The graph build (A1-A3, the paper's offline encoder) runs once per volume
+before the timed region and is reported as build_ms.
+
+value = box-histogram queries per second over whole steps (all ranks).
+e2e   = the same through the public API with host buffers: boxes, TF and
+        samples copied host->device and histograms and looked-up colours
+        copied back inside the timed region.
+--impl reference times the CPU oracle (brute-force counting) on bounded
+samples of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2009_02702_gb300 import synth  # noqa: E402
+
+METRIC = "box-histogram queries/s & TF propagations/s (HBM GB/s vs peak); p99 latency"
+UNIT = "queries/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--queries", type=int, default=0)
+    ap.add_argument("--schedule", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_config(cfg_index, Q, args):
+    cfg = synth.CONFIGS[cfg_index]
+    nx, ny, nz = cfg["dims"]
+    return {"workload": "%s (synthetic, seeded; stands in for the paper's volume)" % cfg["name"],
+            "volume": "%dx%dx%d uint16" % (nx, ny, nz), "segments": cfg["S"],
+            "queries_per_step": Q, "box_sides": "%s 1..%d" % (cfg["box"], cfg["box_max"]),
+            "hist": "exact u32, dense Q x S", "schedule": args.schedule,
+            "tf": "RGBA fp32", "samples_per_step": 1920 * 1080,
+            "l2": "flushed between steps (write of a 512 MiB buffer)"}
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes of a query batch (footprint assembly, counted on the host)
+# --------------------------------------------------------------------------
+def _runs(i, di, dim):
+    r = []
+    di = min(i + di, dim) - i
+    while di > 0:
+        a = di.bit_length() - 1
+        b = (i & -i).bit_length() - 1 if i else 63
+        l = min(a, b)
+        r.append(l)
+        di -= 1 << l
+        i += 1 << l
+    return np.array(r, np.int64)
+
+
+def cube_levels(boxes, dims):
+    """Number of footprint-assembly cubes per mip level over all boxes."""
+    out = np.zeros(40, np.int64)
+    for b in boxes:
+        lx = _runs(int(b[0]), int(b[3]), dims[0])
+        ly = _runs(int(b[1]), int(b[4]), dims[1])
+        lz = _runs(int(b[2]), int(b[5]), dims[2])
+        L3 = lx[None, None, :] + ly[None, :, None] + lz[:, None, None]
+        lmin = np.minimum(np.minimum(lx[None, None, :], ly[None, :, None]), lz[:, None, None])
+        cnt = np.left_shift(1, L3 - 3 * lmin)
+        out += np.bincount(lmin.ravel(), weights=cnt.ravel(), minlength=40).astype(np.int64)[:40]
+    return out
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2009_02702_gb300 import mg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg_i = args.config
+    cfg = synth.CONFIGS[cfg_i]
+    S = cfg["S"]
+    Q = args.queries or cfg["queries"]
+    dims = cfg["dims"]
+
+    vol = synth.make_volume(cfg_i, device=dev)
+    torch.cuda.synchronize()
+    g = mg.mg_build(vol, S)
+    info = g.info
+    del vol
+    boxes_h = synth.make_boxes(cfg_i, Q=Q, stream_offset=rank)
+    tf_h = synth.make_tf(cfg_i, S, 4)
+    smp_h = synth.make_samples(cfg_i)
+    P = smp_h.shape[0]
+    boxes = torch.from_numpy(boxes_h).to(dev)
+    tf = torch.from_numpy(tf_h).to(dev)
+    smp = torch.from_numpy(smp_h).to(dev)
+    vals = torch.empty((g.N, 4), dtype=torch.float32, device=dev)
+    hist = torch.empty((Q, S), dtype=torch.uint32, device=dev)
+    look = torch.empty((P, 4), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    qkw = dict(schedule=args.schedule, chunk_cubes=args.chunk, block_threads=args.threads)
+
+    def step(timing=False):
+        mg.mg_propagate_tf(g, tf, out=vals)
+        mg.mg_query_boxes(g, boxes, out=hist, timing=timing, **qkw)
+        mg.mg_render_lookup(g, vals, smp, out=look)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    mg.mg_sync_status(g)
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    qmain = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        e = ev[k]
+        e[0].record(stream)
+        mg.mg_propagate_tf(g, tf, out=vals)
+        e[1].record(stream)
+        mg.mg_query_boxes(g, boxes, out=hist, timing=True, **qkw)
+        e[2].record(stream)
+        mg.mg_render_lookup(g, vals, smp, out=look)
+        e[3].record(stream)
+        qmain.append(mg.mg_query_timing(g))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    mg.mg_sync_status(g)
+    step_ms = np.array([e[0].elapsed_time(e[3]) for e in ev])
+    prop_ms = np.array([e[0].elapsed_time(e[1]) for e in ev])
+    query_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
+    look_ms = np.array([e[2].elapsed_time(e[3]) for e in ev])
+    main_ms = np.array([t[1] for t in qmain])
+    tot_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    value = world * Q / (ms_per_step / 1e3)
+
+    # algorithmic bytes of the query kernel: box in, cube IDs (uint16 at level
+    # 0, uint32 above), dense histogram out
+    lv = cube_levels(boxes_h, dims)
+    cubes = int(lv.sum())
+    id0 = 2 if S <= 65536 else 4
+    q_bytes = 24 * Q + id0 * int(lv[0]) + 4 * int(lv[1:].sum()) + 4 * Q * S
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        peak = float(peaks["hbm_gbs"])
+        peak_src = "measured"
+    except Exception:
+        peak, peak_src = 6800.0, "fallback"
+    achieved = q_bytes / (float(np.mean(main_ms)) / 1e3) / 1e9
+    n_int = info["num_nodes"] - S
+    prop_bytes = 28 * n_int + 16 * S
+    prop_gbs = prop_bytes / (float(np.mean(prop_ms)) / 1e3) / 1e9
+    look_bytes = 52 * P
+    look_gbs = look_bytes / (float(np.mean(look_ms)) / 1e3) / 1e9
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        boxes_p = torch.from_numpy(boxes_h).pin_memory()
+        tf_p = torch.from_numpy(tf_h).pin_memory()
+        smp_p = torch.from_numpy(smp_h).pin_memory()
+        hist_p = torch.empty((Q, S), dtype=torch.uint32).pin_memory()
+        look_p = torch.empty((P, 4), dtype=torch.float32).pin_memory()
+        boxes_d = torch.empty_like(boxes)
+        tf_d = torch.empty_like(tf)
+        smp_d = torch.empty_like(smp)
+
+        def e2e_step():
+            boxes_d.copy_(boxes_p, non_blocking=True)
+            tf_d.copy_(tf_p, non_blocking=True)
+            smp_d.copy_(smp_p, non_blocking=True)
+            mg.mg_propagate_tf(g, tf_d, out=vals)
+            mg.mg_query_boxes(g, boxes_d, out=hist, **qkw)
+            mg.mg_render_lookup(g, vals, smp_d, out=look)
+            hist_p.copy_(hist, non_blocking=True)
+            look_p.copy_(look, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            ee[k][0].record(stream)
+            e2e_step()
+            ee[k][1].record(stream)
+        torch.cuda.synchronize()
+        e_ms = float(np.sum([a.elapsed_time(b) for a, b in ee]))
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * Q / (e_ms / args.steps / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(boxes_h.nbytes + tf_h.nbytes + smp_h.nbytes),
+               "d2h_bytes_per_step": int(Q * S * 4 + P * 16), "ms_per_step": e_ms / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg_i, boxes_h, args.cpu_seconds)
+
+    launches_prop = 1 + sum(1 for d in range(1, info["depth"] + 1) if info["bucket"][d + 1] > info["bucket"][d])
+    launches_query = 1 if args.schedule == "batched" else Q
+    launches_query += 8 + (0 if args.schedule == "batched" else -8)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 counts / f32 colours", "data": "synthetic",
+        "config": workload_config(cfg_i, Q, args),
+        "tf_propagations_per_s": 1e3 / float(np.mean(prop_ms)),
+        "samples_per_s": P / (float(np.mean(look_ms)) / 1e3),
+        "latency_ms": {"step_p50": float(np.percentile(step_ms, 50)), "step_p99": float(np.percentile(step_ms, 99)),
+                       "query_batch_p50": float(np.percentile(query_ms, 50)),
+                       "query_batch_p99": float(np.percentile(query_ms, 99)),
+                       "propagate_p50": float(np.percentile(prop_ms, 50)),
+                       "propagate_p99": float(np.percentile(prop_ms, 99)),
+                       "lookup_p50": float(np.percentile(look_ms, 50))},
+        "stages_ms": {"propagate": float(np.mean(prop_ms)), "query": float(np.mean(query_ms)),
+                      "query_plan": float(np.mean([t[0] for t in qmain])), "query_main": float(np.mean(main_ms)),
+                      "query_output": float(np.mean([t[2] for t in qmain])), "lookup": float(np.mean(look_ms))},
+        "roofline": {"bound": "hbm", "kernel": "query_batched_kernel" if args.schedule == "batched" else
+                     "query_plain_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src + " hbm_gbs (copy, burst)",
+                     "traffic": None, "algorithmic_bytes_per_launch": q_bytes, "cubes_per_launch": cubes},
+        "other_kernels": {"propagate_gbs": prop_gbs, "propagate_frac": prop_gbs / peak,
+                          "propagate_bytes": prop_bytes, "lookup_gbs": look_gbs, "lookup_frac": look_gbs / peak},
+        "graph": {"nodes": info["num_nodes"], "depth": info["depth"], "levels": info["levels"],
+                  "build_ms": info["build_ms"], "device_bytes": info["device_bytes"],
+                  "max_list": info["max_list"], "pairs": info["pairs"]},
+        "e2e": e2e,
+        "gpu_launches": args.steps * (launches_prop + launches_query + 1),
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (reported baseline and the reference arm)
+# --------------------------------------------------------------------------
+def _host_volume(cfg_i):
+    return synth.make_volume(cfg_i, device="cpu")
+
+
+def cpu_baseline(cfg_i, boxes, seconds, vol=None):
+    import oracle
+    cfg = synth.CONFIGS[cfg_i]
+    if vol is None:
+        vol = _host_volume(cfg_i)
+    n = min(50, len(boxes))
+    t0 = time.perf_counter()
+    oracle.box_hist(vol, cfg["S"], boxes[:n])
+    dt = time.perf_counter() - t0
+    n2 = int(min(len(boxes), max(n, n * seconds / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.box_hist(vol, cfg["S"], boxes[:n2])
+    dt2 = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n2 / dt2, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of the step's %d boxes, brute-force level-0 counting (OpenMP over boxes), %.1f s"
+                      % (n2, len(boxes), dt2)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg_i = args.config
+    cfg = synth.CONFIGS[cfg_i]
+    Q = args.queries or cfg["queries"]
+    import oracle
+    vol = _host_volume(cfg_i)
+    boxes = synth.make_boxes(cfg_i, Q=Q)
+    # size one step to ~6 s of host work
+    t0 = time.perf_counter()
+    oracle.box_hist(vol, cfg["S"], boxes[:40])
+    dt = time.perf_counter() - t0
+    n = int(min(Q, max(40, 40 * 6.0 / max(dt, 1e-6))))
+    times = []
+    for k in range(max(args.warmup, 3) + args.steps):
+        sl = boxes[(k * n) % Q:][:n]
+        if len(sl) < n:
+            sl = boxes[:n]
+        t0 = time.perf_counter()
+        oracle.box_hist(vol, cfg["S"], sl)
+        if k >= max(args.warmup, 3):
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = n / (ms / 1e3)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = "%d of the %d boxes per step, brute-force level-0 counting (OpenMP over boxes)" % (n, Q)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 counts", "data": "synthetic", "impl": "reference",
+            "config": workload_config(cfg_i, Q, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

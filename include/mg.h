@@ -1,0 +1,239 @@
+/*
+ * mg.h -- C-ABI of the GB300 Mixture Graph library (libmg.so).
+ *
+ * The Mixture Graph (Al-Thelaya, Agus, Schneider, "The Mixture Graph -- A Data
+ * Structure for Compressing, Rendering, and Querying Segmentation Histograms",
+ * IEEE Vis 2020) factorises the normalised histogram mipmap of a segmentation
+ * volume into binary lerps between segment IDs, so that
+ *   - a transfer function on the segments becomes a colour per mipmap voxel by
+ *     one forward pass over the lerp DAG (Sec. 3.4, Sec. 4), and
+ *   - the segment histogram of a box becomes a footprint of coarse mipmap
+ *     samples whose weights are pushed back through the DAG (Sec. 3.6).
+ *
+ * Conventions for every call:
+ *   - Array arguments are device pointers unless a name ends in _host.  The
+ *     caller owns them; the library never frees or keeps them.
+ *   - Every call is asynchronous on `stream` unless its comment says it
+ *     synchronises.  Calls return mg_status and never abort, throw or exit; a
+ *     message for the last failure of the calling thread is in mg_last_error().
+ *   - Argument errors that the host can see are returned before any launch.
+ *     Errors only the device can see (an ID >= num_segments, a malformed box,
+ *     an inexact integer push) set the graph's device status word, which
+ *     mg_sync_status() reads and clears.
+ *   - Volumes are x-fastest: voxel (x, y, z) is element (z*ny + y)*nx + x.
+ *     Each axis is at most 65535 voxels and nx*ny*nz < 2^32.
+ *   - Node IDs: sources 0..S-1 are the segment IDs; internal nodes S..N-1 are
+ *     numbered by ascending (topological level, p, q, a, b), so a node's
+ *     predecessors always have smaller IDs (Eq. 8) and nodes of one level are
+ *     contiguous (Sec. 3.4).
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MG_API __attribute__((visibility("default")))
+#else
+#define MG_API
+#endif
+
+/* cudaStream_t without requiring the CUDA headers */
+typedef struct CUstream_st *mg_stream;
+
+#define MG_MAX_LEVELS 32
+#define MG_MAX_DEPTH 64
+#define MG_NO_NODE 0xFFFFFFFFu
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_INVALID_ARG = 1,  /* bad argument, or bad input data seen on the device */
+    MG_ERR_OOM = 2,          /* the allocator returned NULL */
+    MG_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    MG_ERR_TIMEOUT = 4,      /* a bounded device-side wait expired */
+    MG_ERR_CAPACITY = 5,     /* sparse output larger than the caller's capacity */
+    MG_ERR_UNSUPPORTED = 6,  /* size or option outside what this build supports */
+    MG_ERR_INEXACT = 7       /* an integer push met a weight not divisible by a+b */
+} mg_status;
+
+typedef enum { MG_F32 = 0, MG_F16 = 1, MG_BF16 = 2 } mg_dtype;
+
+typedef struct mg_graph mg_graph;   /* opaque, library-owned */
+
+/* Device memory for the graph and for per-call scratch.  alloc returns a
+ * device pointer usable in stream order on `stream` (NULL = out of memory);
+ * free releases it in stream order.  Pass NULL to mg_build to use
+ * cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+    void *ctx;
+    void *(*alloc)(void *ctx, size_t bytes, mg_stream stream);
+    void (*free)(void *ctx, void *ptr, size_t bytes, mg_stream stream);
+} mg_allocator;
+
+typedef struct {
+    int id_bytes;      /* 2: ids are uint16, 4: ids are uint32 */
+    int reserved[7];   /* zero */
+} mg_build_opts;
+
+typedef struct {
+    uint32_t num_segments;                    /* S: sources */
+    int levels;                               /* L: mip levels, level 0 = input */
+    int depth;                                /* D: topological depth */
+    int64_t num_nodes;                        /* N: sources + internal nodes */
+    int64_t dims[MG_MAX_LEVELS][3];           /* per-level (x, y, z) resolution */
+    int64_t bucket[MG_MAX_DEPTH + 2];         /* nodes of level d: [bucket[d], bucket[d+1]) */
+    int64_t max_list;                         /* longest mixture of any voxel */
+    int64_t pairs;                            /* sum over voxels of (entries - 1) */
+    int64_t device_bytes;                     /* bytes the graph holds on the device */
+    double build_ms;                          /* wall time of mg_build */
+} mg_graph_info;
+
+/*
+ * mg_build -- build the Mixture Graph of a segmentation volume.
+ *   Sec. 3.1 (Eq. 4): normalised histogram mipmap, average-of-eight with N =
+ *     children in support at the borders, levels rounding up to 1^3; held as
+ *     integer weights 8^l * H.
+ *   Sec. 3.2 (Eq. 5-7): each mixture with more than one entry is factorised
+ *     into binary lerps.  Pair choice: the entries, sorted by segment ID, are
+ *     lerped pairwise (0,1),(2,3),... per round, an odd last entry carried,
+ *     until one remains.
+ *   Sec. 3.3: identical lerps (same predecessors, same reduced integer ratio
+ *     a:b) are one node, so no voxel's mixture changes (exact, no quantiser).
+ *   Sec. 3.4 / Fig. 5: topological levels; nodes renumbered canonically.
+ * ids: nx*ny*nz segment IDs (uint16 or uint32 per opts->id_bytes), each
+ *   < num_segments (else MG_ERR_INVALID_ARG after the build's sync).
+ * allocator: may be NULL (cudaMallocAsync).  It is copied into the graph and
+ *   used for the graph's memory and for scratch of later calls.
+ * Synchronises `stream` several times (level sizes are data dependent).
+ * On success *out owns its device memory until mg_free.
+ */
+MG_API mg_status mg_build(const void *ids, int64_t nx, int64_t ny, int64_t nz,
+                          uint32_t num_segments, const mg_build_opts *opts,
+                          const mg_allocator *allocator, mg_stream stream, mg_graph **out);
+
+/* Sizes and level geometry of a built graph (host only, no device work). */
+MG_API mg_status mg_graph_info_get(const mg_graph *g, mg_graph_info *info);
+
+/* Copy the node table to caller buffers (host or device, any may be NULL):
+ * p[N], q[N] predecessors (MG_NO_NODE for sources), a[N], b[N] the coprime
+ * weights of p and q (0 for sources).  Node n is the lerp (a*p + b*q)/(a+b),
+ * Eq. 5-7.  Synchronises `stream`. */
+MG_API mg_status mg_graph_copy_nodes(const mg_graph *g, uint32_t *p, uint32_t *q, uint64_t *a,
+                                     uint64_t *b, mg_stream stream);
+
+/* Copy the node ID of every voxel of one level (dims[level], x fastest) to a
+ * caller buffer (host or device).  Level 0 gives the segment IDs (lossless,
+ * Sec. 3.4).  Synchronises `stream`. */
+MG_API mg_status mg_graph_copy_mip(const mg_graph *g, int level, uint32_t *dst, mg_stream stream);
+
+/*
+ * mg_propagate_tf -- forward transfer-function propagation (Sec. 3.4, Sec. 4,
+ * Sec. 5.2 "Color lookup table").
+ *   vals[s] = tf[s] for sources; for every internal node, level by level,
+ *   vals[n] = (1 - alpha_n) * vals[p] + alpha_n * vals[q], alpha_n = b/(a+b),
+ *   computed in fp32.  The colour of mipmap voxel v at level l is then
+ *   vals[node ID of v] (a paletted lookup).
+ * tf: S x C fp32, row-major.  C in 1..16.
+ * storage: dtype of vals (MG_F32, MG_F16 or MG_BF16).  For 16-bit storage the
+ *   node weights are read as 16-bit too (alpha <= 1/2 kept by swapping p and q,
+ *   the interpolation symmetry of Sec. 3.7); arithmetic stays fp32.
+ * vals: N x C in `storage`, caller-owned, fully overwritten.
+ */
+MG_API mg_status mg_propagate_tf(mg_graph *g, const float *tf, int C, mg_dtype storage, void *vals,
+                                 mg_stream stream);
+
+/* Query output forms. */
+typedef enum { MG_HIST_U32 = 0, MG_HIST_F32 = 1 } mg_hist_type;
+typedef enum { MG_LAYOUT_DENSE = 0, MG_LAYOUT_CSR = 1 } mg_layout;
+typedef enum { MG_SCHED_BATCHED = 0, MG_SCHED_PLAIN = 1 } mg_schedule;
+
+typedef struct {
+    int hist_type;      /* MG_HIST_U32: exact integer push; MG_HIST_F32: fp32 push */
+    int layout;         /* MG_LAYOUT_DENSE or MG_LAYOUT_CSR */
+    int alpha_dtype;    /* fp32 push only: node weights read as MG_F32, MG_F16 or MG_BF16 */
+    int schedule;       /* MG_SCHED_BATCHED: persistent work queue over cube chunks;
+                           MG_SCHED_PLAIN: one launch per query, one CTA (baseline) */
+    int chunk_cubes;    /* batched: cubes per work item (0 = tuned default) */
+    int block_threads;  /* batched: threads per CTA, 128/256/512 (0 = tuned default) */
+    int timing;         /* nonzero: record CUDA events around the plan, main and output
+                           stages on `stream` (read them with mg_query_timing) */
+    int reserved;       /* zero */
+} mg_query_opts;
+
+/*
+ * mg_query_boxes -- segment histograms of axis-aligned boxes (Sec. 3.6).
+ *   Each box (x, y, z, dx, dy, dz) covers [x, x+dx) x [y, y+dy) x [z, z+dz),
+ *   clipped to the volume.  It needs 0 <= x < nx (likewise y, z) and dx, dy,
+ *   dz >= 1; a box that breaks this sets MG_ERR_INVALID_ARG in the status word
+ *   and its histogram is left zero.
+ *   Footprint assembly (Algorithm 1): each axis range splits into aligned
+ *   power-of-two runs; every block of their tensor product is tiled by cubes
+ *   of its shortest side 2^l, one level-l voxel each, weight 8^l.  The weight
+ *   is pushed from the voxel's node to the sources in descending topological
+ *   order: p receives W*a/(a+b), q receives W*b/(a+b).  Every cube lies inside
+ *   the box, so with MG_HIST_U32 the histogram equals the count of level-0 IDs
+ *   in the clipped box exactly.
+ * boxes: Q x 6 int32.  Q >= 0 (Q = 0 writes only offsets[0] = 0 in CSR).
+ * Dense layout: out is Q x S (uint32 or fp32), fully overwritten; seg and
+ *   offsets are unused; out_capacity >= Q*S elements.
+ * CSR layout: offsets[Q+1] (uint64), seg[nnz] (uint32) and out[nnz] hold each
+ *   query's non-zero segments in ascending order.  If nnz > out_capacity the
+ *   call returns MG_ERR_CAPACITY with *out_required = nnz and offsets written.
+ *   CSR synchronises `stream` once to read nnz.
+ * Scratch is allocated from the graph's allocator and released in stream
+ * order before return.
+ */
+MG_API mg_status mg_query_boxes(const mg_graph *g, const int32_t *boxes, int64_t Q,
+                                const mg_query_opts *opts, void *out, size_t out_capacity,
+                                uint32_t *seg, uint64_t *offsets, size_t *out_required,
+                                mg_stream stream);
+
+/* Stage durations of the last mg_query_boxes call on this graph made with
+ * opts->timing set: plan (footprint plan and scans), main (the histogram
+ * kernel or, for MG_SCHED_PLAIN, all per-box launches) and output (dense fp32
+ * or CSR finalisation), in milliseconds from CUDA events on that call's
+ * stream.  Waits for the call's last event.  Returns MG_ERR_INVALID_ARG if no
+ * timed call was made. */
+MG_API mg_status mg_query_timing(const mg_graph *g, float *plan_ms, float *main_ms, float *output_ms);
+
+/* Number of footprint-assembly cubes (mipmap fetches) of each box, uint64[Q]
+ * (the "fetches" of Table 3).  Boxes as for mg_query_boxes. */
+MG_API mg_status mg_count_cubes(const mg_graph *g, const int32_t *boxes, int64_t Q, uint64_t *cubes,
+                                mg_stream stream);
+
+/*
+ * mg_render_lookup -- ray-sample node lookup (Sec. 4: rendering from the graph
+ * is a paletted lookup).  Sample i = (x, y, z, lod) in level-0 voxel units.
+ *   level = floor(lod + 1/2) in fp32, clamped to [0, L-1] (NaN: 0);
+ *   voxel = floor of each coordinate clamped to [0, dim] (NaN: 0), shifted
+ *           right by level and clamped to the level's last voxel;
+ *   out[i] = vals[node ID of that voxel] (C values of dtype, copied exactly).
+ * samples: P x 4 fp32.  vals: N x C in dtype (from mg_propagate_tf).
+ * out: P x C in dtype.
+ */
+MG_API mg_status mg_render_lookup(const mg_graph *g, const void *vals, int C, mg_dtype dtype,
+                                  const float *samples, int64_t P, void *out, mg_stream stream);
+
+/* Synchronise `stream`, read and clear the graph's device status word.
+ * Returns MG_OK or the first error recorded by an earlier call's kernels. */
+MG_API mg_status mg_sync_status(mg_graph *g, mg_stream stream);
+
+/* Release the graph's device memory (stream-ordered on the build stream's
+ * allocator semantics; synchronises the device first).  NULL is ignored. */
+MG_API void mg_free(mg_graph *g);
+
+/* Message of the calling thread's last failed call ("" if none). */
+MG_API const char *mg_last_error(void);
+
+/* Library version string. */
+MG_API const char *mg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

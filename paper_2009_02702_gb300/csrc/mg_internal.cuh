@@ -1,0 +1,190 @@
+// mg_internal.cuh -- internal declarations shared by the libmg translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+
+#include "mg.h"
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// status word bits set by kernels (read by mg_sync_status)
+// ---------------------------------------------------------------------------
+enum : unsigned {
+    kStatBadInput = 1u << 0,   // ID >= S, malformed box
+    kStatCapacity = 1u << 1,   // node table or hash full
+    kStatTimeout = 1u << 2,    // bounded wait expired
+    kStatInexact = 1u << 3,    // integer push met W % (a+b) != 0
+};
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;   // no predecessor
+constexpr uint32_t kDead = 0xFFFFFFFEu;   // node slot lost a publication race
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+mg_status fail(mg_status st, const std::string& msg);
+mg_status cuda_fail(cudaError_t e, const char* what);
+
+#define MG_CUDA(call)                                            \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return ::mg::cuda_fail(e_, #call); \
+    } while (0)
+
+#define MG_TRY(call)                         \
+    do {                                     \
+        mg_status s_ = (call);               \
+        if (s_ != MG_OK) return s_;          \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// memory through the caller's allocator (or cudaMallocAsync)
+// ---------------------------------------------------------------------------
+struct Alloc {
+    mg_allocator a{};
+    bool custom = false;
+    void* get(size_t bytes, cudaStream_t s) const;
+    void put(void* p, size_t bytes, cudaStream_t s) const;
+};
+
+// RAII scratch buffer released in stream order
+struct Buf {
+    const Alloc* al = nullptr;
+    cudaStream_t s = nullptr;
+    void* p = nullptr;
+    size_t bytes = 0;
+    Buf() = default;
+    Buf(const Buf&) = delete;
+    Buf& operator=(const Buf&) = delete;
+    Buf(Buf&& o) noexcept { *this = static_cast<Buf&&>(o); }
+    Buf& operator=(Buf&& o) noexcept {
+        release();
+        al = o.al; s = o.s; p = o.p; bytes = o.bytes;
+        o.p = nullptr; o.bytes = 0;
+        return *this;
+    }
+    ~Buf() { release(); }
+    mg_status alloc(const Alloc* a, size_t n, cudaStream_t st);
+    void release();
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// the graph
+// ---------------------------------------------------------------------------
+struct LevelGeom {
+    int L;
+    int32_t dims[MG_MAX_LEVELS][3];
+    int64_t off[MG_MAX_LEVELS];   // offset of level l (l >= 1) in the concatenated mip array
+};
+
+}  // namespace mg
+
+struct mg_graph {
+    mg::Alloc al;
+    int device = 0;
+    uint32_t S = 0;
+    int L = 0;
+    int D = 0;
+    int64_t N = 0;
+    mg::LevelGeom geom{};
+    int64_t bucket[MG_MAX_DEPTH + 2] = {};
+    int64_t max_list = 0, pairs = 0;
+    double build_ms = 0.0;
+
+    // level 0: segment IDs (uint16 when S <= 65536, else uint32)
+    int id0_bytes = 2;
+    mg::Buf mip0;
+    // levels 1..L-1 concatenated, uint32 node IDs
+    mg::Buf mip;
+    // node table, canonical order, N entries
+    mg::Buf pq;       // uint2 (p, q); (kNone, kNone) for sources
+    mg::Buf ab;       // ulonglong2 (a, b) exact coprime weights
+    mg::Buf ab32;     // uint2 (a, b) when a+b < 2^32, else (0, 0)
+    mg::Buf alpha;    // float b/(a+b)
+    mg::Buf alpha16;  // lazily: signed __half alpha, swap flag in the sign
+    mg::Buf alphab16; // lazily: signed __nv_bfloat16 alpha, swap flag in the sign
+    mg::Buf status;   // unsigned int status word
+    // events of the last timed query call: plan start, main start, main end, output end
+    cudaEvent_t qev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool qev_valid = false;
+    ~mg_graph() {
+        for (auto& e : qev)
+            if (e) cudaEventDestroy(e);
+    }
+
+    int64_t device_bytes() const;
+};
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// device primitives (mg_prims.cu)
+// ---------------------------------------------------------------------------
+// exclusive scan of n elements; if total != nullptr, writes the sum there (device)
+mg_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total,
+                             const Alloc& al, cudaStream_t s);
+mg_status scan_exclusive_u64(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* total,
+                             const Alloc& al, cudaStream_t s);
+// stable LSD radix sort of (key, value) by key bits [0, bits); result in keys/vals
+mg_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, const Alloc& al,
+                           cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// stages
+// ---------------------------------------------------------------------------
+mg_status build_graph(mg_graph* g, const void* ids, int id_bytes, int64_t nx, int64_t ny, int64_t nz,
+                      cudaStream_t s);
+mg_status propagate(mg_graph* g, const float* tf, int C, mg_dtype storage, void* vals, cudaStream_t s);
+mg_status ensure_alpha16(mg_graph* g, mg_dtype dt, cudaStream_t s);
+mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const mg_query_opts& o,
+                      void* out, size_t cap, uint32_t* seg, uint64_t* offsets, size_t* required,
+                      cudaStream_t s);
+mg_status query_timing(const mg_graph* g, float* plan_ms, float* main_ms, float* out_ms);
+mg_status count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64_t* cubes,
+                      cudaStream_t s);
+mg_status render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dt, const float* samples,
+                        int64_t P, void* out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint8_t ld_relaxed_u8(const uint8_t* p) {
+    uint16_t v;
+    asm volatile("ld.relaxed.gpu.global.u8 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
+    return (uint8_t)v;
+}
+__device__ __forceinline__ void set_status(unsigned* st, unsigned bit) {
+    if (st) atomicOr(st, bit);
+}
+
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 30) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+}  // namespace mg

@@ -1,0 +1,183 @@
+// mg_propagate.cu -- forward transfer-function propagation (Sec. 3.4, Sec. 4).
+//
+// Sources take the TF row of their segment; then, one launch per topological
+// level (nodes of a level are contiguous and independent), every node lerps
+// the rows of its two predecessors:  v = v_p + alpha * (v_q - v_p), fp32.
+// Node records are SoA: (p, q) as one 8-byte load, alpha as 4 (or 2) bytes;
+// value rows are gathered as one vector load per predecessor.
+#include "mg_internal.cuh"
+
+namespace mg {
+namespace {
+
+template <typename T> struct Cvt;
+template <> struct Cvt<float> {
+    static __device__ __forceinline__ float to(float x) { return x; }
+    static __device__ __forceinline__ float from(float x) { return x; }
+};
+template <> struct Cvt<__half> {
+    static __device__ __forceinline__ float to(__half x) { return __half2float(x); }
+    static __device__ __forceinline__ __half from(float x) { return __float2half_rn(x); }
+};
+template <> struct Cvt<__nv_bfloat16> {
+    static __device__ __forceinline__ float to(__nv_bfloat16 x) { return __bfloat162float(x); }
+    static __device__ __forceinline__ __nv_bfloat16 from(float x) { return __float2bfloat16_rn(x); }
+};
+
+// load / store one row of C values (vectorised when the row is 8 or 16 bytes)
+template <typename ST, int C>
+__device__ __forceinline__ void load_row(const ST* __restrict__ base, int64_t row, float (&v)[C]) {
+    const ST* r = base + row * C;
+    if constexpr (sizeof(ST) * C == 16) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(r));
+        const ST* e = reinterpret_cast<const ST*>(&u);
+#pragma unroll
+        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(e[c]);
+    } else if constexpr (sizeof(ST) * C == 8) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(r));
+        const ST* e = reinterpret_cast<const ST*>(&u);
+#pragma unroll
+        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(e[c]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(r[c]);
+    }
+}
+
+template <typename ST, int C>
+__device__ __forceinline__ void store_row(ST* __restrict__ base, int64_t row, const float (&v)[C]) {
+    ST* r = base + row * C;
+    if constexpr (sizeof(ST) * C == 16 || sizeof(ST) * C == 8) {
+        ST e[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) e[c] = Cvt<ST>::from(v[c]);
+        if constexpr (sizeof(ST) * C == 16)
+            *reinterpret_cast<uint4*>(r) = *reinterpret_cast<const uint4*>(e);
+        else
+            *reinterpret_cast<uint2*>(r) = *reinterpret_cast<const uint2*>(e);
+    } else {
+#pragma unroll
+        for (int c = 0; c < C; c++) r[c] = Cvt<ST>::from(v[c]);
+    }
+}
+
+template <typename ST, int C>
+__global__ void sources_kernel(const float* __restrict__ tf, uint32_t S, ST* __restrict__ vals) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+        float v[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) v[c] = tf[s * C + c];
+        store_row<ST, C>(vals, s, v);
+    }
+}
+
+// node weight: fp32 alpha, or a signed 16-bit alpha whose sign says p and q
+// are swapped (alpha <= 1/2 after the swap; interpolation symmetry, Sec. 3.7)
+template <typename ST> struct Weight {
+    using T = ST;
+};
+template <> struct Weight<float> {
+    using T = float;
+};
+
+template <typename ST, int C>
+__global__ void level_kernel(const uint2* __restrict__ pq, const typename Weight<ST>::T* __restrict__ alpha,
+                             int64_t lo, int64_t hi, ST* __restrict__ vals) {
+    const int64_t n = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= hi) return;
+    const uint2 e = __ldg(pq + n);
+    uint32_t p = e.x, q = e.y;
+    float al = Cvt<typename Weight<ST>::T>::to(alpha[n]);
+    if (al < 0.f) {
+        al = -al;
+        const uint32_t t = p;
+        p = q;
+        q = t;
+    }
+    float vp[C], vq[C], out[C];
+    load_row<ST, C>(vals, p, vp);
+    load_row<ST, C>(vals, q, vq);
+#pragma unroll
+    for (int c = 0; c < C; c++) out[c] = fmaf(al, vq[c] - vp[c], vp[c]);
+    store_row<ST, C>(vals, n, out);
+}
+
+__global__ void alpha16_kernel(const ulonglong2* __restrict__ ab, int64_t N, uint32_t S, int bf16,
+                               void* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (i >= (int64_t)S) {
+            const ulonglong2 w = ab[i];
+            const double s = (double)w.x + (double)w.y;
+            // alpha = b/(a+b); above 1/2 store -(a/(a+b)) meaning "swap p and q"
+            v = (w.y <= w.x) ? (float)((double)w.y / s) : -(float)((double)w.x / s);
+        }
+        if (bf16)
+            static_cast<__nv_bfloat16*>(out)[i] = __float2bfloat16_rn(v);
+        else
+            static_cast<__half*>(out)[i] = __float2half_rn(v);
+    }
+}
+
+template <typename ST, int C>
+mg_status run(const mg_graph* g, const float* tf, const void* alpha, ST* vals, cudaStream_t s) {
+    sources_kernel<ST, C><<<grid_for(g->S, 256, 152 * 16), 256, 0, s>>>(tf, g->S, vals);
+    MG_CUDA(cudaGetLastError());
+    using W = typename Weight<ST>::T;
+    for (int d = 1; d <= g->D; d++) {
+        const int64_t lo = g->bucket[d], hi = g->bucket[d + 1];
+        if (hi <= lo) continue;
+        level_kernel<ST, C><<<grid_for(hi - lo, 256), 256, 0, s>>>(g->pq.as<uint2>(), static_cast<const W*>(alpha),
+                                                                   lo, hi, vals);
+        MG_CUDA(cudaGetLastError());
+    }
+    return MG_OK;
+}
+
+template <typename ST>
+mg_status dispatch_c(const mg_graph* g, const float* tf, int C, const void* alpha, void* vals, cudaStream_t s) {
+    ST* v = static_cast<ST*>(vals);
+    switch (C) {
+        case 1: return run<ST, 1>(g, tf, alpha, v, s);
+        case 2: return run<ST, 2>(g, tf, alpha, v, s);
+        case 3: return run<ST, 3>(g, tf, alpha, v, s);
+        case 4: return run<ST, 4>(g, tf, alpha, v, s);
+        case 5: return run<ST, 5>(g, tf, alpha, v, s);
+        case 6: return run<ST, 6>(g, tf, alpha, v, s);
+        case 7: return run<ST, 7>(g, tf, alpha, v, s);
+        case 8: return run<ST, 8>(g, tf, alpha, v, s);
+        case 12: return run<ST, 12>(g, tf, alpha, v, s);
+        case 16: return run<ST, 16>(g, tf, alpha, v, s);
+        default: break;
+    }
+    return fail(MG_ERR_UNSUPPORTED, "channel count C must be 1-8, 12 or 16");
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+mg_status ensure_alpha16(mg_graph* g, mg_dtype dt, cudaStream_t s) {
+    Buf& b = dt == MG_BF16 ? g->alphab16 : g->alpha16;
+    if (b.p) return MG_OK;
+    MG_TRY(b.alloc(&g->al, (size_t)g->N * 2, s));
+    alpha16_kernel<<<grid_for(g->N, 256, 152 * 32), 256, 0, s>>>(g->ab.as<ulonglong2>(), g->N, g->S, dt == MG_BF16,
+                                                                b.p);
+    MG_CUDA(cudaGetLastError());
+    MG_CUDA(cudaStreamSynchronize(s));
+    b.s = nullptr;
+    return MG_OK;
+}
+
+mg_status propagate(mg_graph* g, const float* tf, int C, mg_dtype storage, void* vals, cudaStream_t s) {
+    const size_t esz = storage == MG_F32 ? 4 : 2;
+    const size_t row = esz * (size_t)C;
+    if ((row == 16 || row == 8) && !aligned(vals, row))
+        return fail(MG_ERR_INVALID_ARG, "vals must be aligned to its row size");
+    if (storage == MG_F32) return dispatch_c<float>(g, tf, C, g->alpha.p, vals, s);
+    MG_TRY(ensure_alpha16(g, storage, s));
+    if (storage == MG_F16) return dispatch_c<__half>(g, tf, C, g->alpha16.p, vals, s);
+    return dispatch_c<__nv_bfloat16>(g, tf, C, g->alphab16.p, vals, s);
+}
+
+}  // namespace mg

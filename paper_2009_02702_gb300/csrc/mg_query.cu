@@ -1,0 +1,778 @@
+// mg_query.cu -- segment histograms of boxes: footprint assembly (Sec. 3.6,
+// Algorithm 1) and the reverse weight push through the Mixture Graph.
+//
+// Plan (one warp per box): clip the box, split each axis range into aligned
+// power-of-two runs (footprint_1d), count the blocks of the runs' tensor
+// product and the cubes tiling them (a block of run levels (lx, ly, lz) sits at
+// level l = min and holds 2^(lx-l) * 2^(ly-l) * 2^(lz-l) cubes), then write one
+// 12-byte record per block: first cube index, level-l origin, level and log2
+// extents.  Blocks follow Algorithm 1's loop order (z, y, x).
+//
+// Main (persistent CTAs, MG_SCHED_BATCHED): a global ticket hands out chunks of
+// `chunk` consecutive cubes of one box.  Each thread takes a cube, finds its
+// block (per-warp binary search, then a short walk), reads the cube's node ID
+// from the level's ID array, and the warp merges equal (level, node) pairs
+// with __match_any_sync.  One lane per group adds the group weight
+// (count * 8^l): a source goes straight into the CTA's shared-memory
+// histogram; an internal node is pushed down its lerp tree (p gets
+// W*a/(a+b), q gets W*b/(a+b), exact u32 arithmetic) into the same histogram.
+// At the end of a chunk the touched bins are added to the box's row in global
+// memory -- the only global atomics.
+//
+// MG_SCHED_PLAIN is the baseline: one launch and one CTA per box, walking the
+// blocks in order.
+#include "mg_internal.cuh"
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+namespace mg {
+namespace {
+
+constexpr int kMaxRuns = 40;
+constexpr int kMaxStack = 64;
+constexpr uint32_t kMaxSharedSegments = 32768;
+constexpr uint32_t kMaxPushSteps = 1u << 24;   // a valid table never needs this many
+
+struct Geom {
+    int L;
+    int id0_bytes;
+    uint32_t S;
+    int32_t dims[MG_MAX_LEVELS][3];
+    int64_t off[MG_MAX_LEVELS];
+};
+
+struct Blk {
+    uint32_t start;   // first cube of the block within its box
+    uint16_t x, y, z; // origin in level-l voxels
+    uint16_t meta;    // l | ex << 4 | ey << 8 | ez << 12 (log2 extents in cubes)
+};
+
+Geom make_geom(const mg_graph* g) {
+    Geom G;
+    G.L = g->L;
+    G.id0_bytes = g->id0_bytes;
+    G.S = g->S;
+    for (int l = 0; l < MG_MAX_LEVELS; l++) {
+        for (int k = 0; k < 3; k++) G.dims[l][k] = g->geom.dims[l][k];
+        G.off[l] = g->geom.off[l];
+    }
+    return G;
+}
+
+// Algorithm 1, footprint_1d: aligned power-of-two steps covering [i, i+di)
+// clipped to [0, dim); tzcnt(0) is infinite.
+__device__ __forceinline__ int footprint_1d(int64_t i, int64_t di, int64_t dim, uint8_t* r, int32_t* start) {
+    int n = 0;
+    di = min(i + di, dim) - i;
+    while (di > 0 && n < kMaxRuns) {
+        const int a = 63 - __clzll(di);
+        const int b = i == 0 ? 63 : __ffsll(i) - 1;
+        const int l = min(a, b);
+        r[n] = (uint8_t)l;
+        start[n] = (int32_t)i;
+        n++;
+        di -= (int64_t)1 << l;
+        i += (int64_t)1 << l;
+    }
+    return n;
+}
+
+__device__ __forceinline__ bool box_ok(const int32_t* b, const Geom& G) {
+    return b[0] >= 0 && b[0] < G.dims[0][0] && b[1] >= 0 && b[1] < G.dims[0][1] && b[2] >= 0 &&
+           b[2] < G.dims[0][2] && b[3] >= 1 && b[4] >= 1 && b[5] >= 1;
+}
+
+struct Runs {
+    uint8_t lx[kMaxRuns], ly[kMaxRuns], lz[kMaxRuns];
+    int32_t sx[kMaxRuns], sy[kMaxRuns], sz[kMaxRuns];
+    int nx, ny, nz;
+};
+
+__device__ __forceinline__ void make_runs(const int32_t* b, const Geom& G, Runs& R) {
+    R.nx = footprint_1d(b[0], b[3], G.dims[0][0], R.lx, R.sx);
+    R.ny = footprint_1d(b[1], b[4], G.dims[0][1], R.ly, R.sy);
+    R.nz = footprint_1d(b[2], b[5], G.dims[0][2], R.lz, R.sz);
+}
+
+__device__ __forceinline__ uint32_t block_cubes(int lx, int ly, int lz) {
+    const int l = min(lx, min(ly, lz));
+    return 1u << (lx + ly + lz - 3 * l);
+}
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+__global__ void plan_count_kernel(Geom G, const int32_t* __restrict__ boxes, int64_t Q, uint32_t chunk,
+                                  uint32_t* __restrict__ nblk, uint64_t* __restrict__ ncube,
+                                  uint64_t* __restrict__ nchunk, unsigned* __restrict__ status) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= Q) return;
+    int32_t b[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
+    if (!box_ok(b, G)) {
+        if (lane == 0) {
+            set_status(status, kStatBadInput);
+            if (nblk) nblk[q] = 0;
+            ncube[q] = 0;
+            if (nchunk) nchunk[q] = 0;
+        }
+        return;
+    }
+    Runs R;
+    make_runs(b, G, R);
+    uint64_t cubes = 0;
+    const int npairs = R.ny * R.nz;
+    for (int pr = lane; pr < npairs; pr += 32) {
+        const int j = pr % R.ny, k = pr / R.ny;
+        for (int i = 0; i < R.nx; i++) cubes += block_cubes(R.lx[i], R.ly[j], R.lz[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cubes += __shfl_xor_sync(0xffffffffu, cubes, o);
+    if (lane == 0) {
+        if (nblk) nblk[q] = (uint32_t)(R.nx * R.ny * R.nz);
+        ncube[q] = cubes;
+        if (nchunk) nchunk[q] = (cubes + chunk - 1) / chunk;
+    }
+}
+
+__global__ void plan_write_kernel(Geom G, const int32_t* __restrict__ boxes, int64_t Q,
+                                  const uint64_t* __restrict__ blk_off, Blk* __restrict__ blk) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= Q) return;
+    int32_t b[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
+    if (!box_ok(b, G)) return;
+    Runs R;
+    make_runs(b, G, R);
+    const uint64_t base = blk_off[q];
+    const int npairs = R.ny * R.nz;
+    uint32_t running = 0;
+    for (int pbase = 0; pbase < npairs; pbase += 32) {
+        const int pr = pbase + lane;
+        const bool valid = pr < npairs;
+        const int j = valid ? pr % R.ny : 0, k = valid ? pr / R.ny : 0;
+        uint32_t row = 0;
+        if (valid)
+            for (int i = 0; i < R.nx; i++) row += block_cubes(R.lx[i], R.ly[j], R.lz[k]);
+        // exclusive warp scan of the row totals
+        uint32_t incl = row;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (valid) {
+            uint32_t start = running + incl - row;
+            for (int i = 0; i < R.nx; i++) {
+                const int lx = R.lx[i], ly = R.ly[j], lz = R.lz[k];
+                const int l = min(lx, min(ly, lz));
+                Blk r;
+                r.start = start;
+                r.x = (uint16_t)(R.sx[i] >> l);
+                r.y = (uint16_t)(R.sy[j] >> l);
+                r.z = (uint16_t)(R.sz[k] >> l);
+                r.meta = (uint16_t)(l | (lx - l) << 4 | (ly - l) << 8 | (lz - l) << 12);
+                blk[base + (uint64_t)pr * R.nx + i] = r;
+                start += 1u << (lx + ly + lz - 3 * l);
+            }
+        }
+        running += tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory histogram of one chunk
+// ---------------------------------------------------------------------------
+template <bool FP>
+struct Hist {
+    uint32_t* h;        // S integer bins
+    float* hf;          // S fractional bins (fp32 push)
+    uint16_t* touched;  // bins to flush
+    uint32_t* ntouched;
+
+    __device__ __forceinline__ void add_int(uint32_t s, uint32_t w) const {
+        if (atomicAdd(h + s, w) == 0u) touched[atomicAdd(ntouched, 1u)] = (uint16_t)s;
+    }
+    __device__ __forceinline__ void add_frac(uint32_t s, float w) const {
+        if (atomicAdd(hf + s, w) == 0.f) touched[atomicAdd(ntouched, 1u)] = (uint16_t)s;
+    }
+};
+
+template <typename AT> struct AlphaCvt;
+template <> struct AlphaCvt<float> {
+    static __device__ __forceinline__ float to(float x) { return x; }
+};
+template <> struct AlphaCvt<__half> {
+    static __device__ __forceinline__ float to(__half x) { return __half2float(x); }
+};
+template <> struct AlphaCvt<__nv_bfloat16> {
+    static __device__ __forceinline__ float to(__nv_bfloat16 x) { return __bfloat162float(x); }
+};
+
+struct PushArgs {
+    const uint2* pq;
+    const uint2* ab32;
+    const void* alpha;
+    uint32_t S;
+    unsigned* status;
+};
+
+// exact integer push of weight W from node n (Sec. 3.6 with the lerp tree of
+// Sec. 3.2): depth-first, one branch kept in registers, the other stacked
+template <bool FP>
+__device__ void push_int(const PushArgs& P, const Hist<FP>& H, uint32_t n, uint32_t w) {
+    uint32_t sn[kMaxStack], sw[kMaxStack];
+    int sp = 0;
+    for (uint32_t step = 0;; step++) {
+        if (step >= kMaxPushSteps) {
+            set_status(P.status, kStatInexact);
+            return;
+        }
+        if (n < P.S) {
+            H.add_int(n, w);
+            if (sp == 0) return;
+            --sp;
+            n = sn[sp];
+            w = sw[sp];
+            continue;
+        }
+        const uint2 e = __ldg(P.pq + n);
+        const uint2 ab = __ldg(P.ab32 + n);
+        const uint32_t s = ab.x + ab.y;
+        const uint32_t k = s ? w / s : 0u;
+        if (s == 0 || k * s != w || sp >= kMaxStack) {
+            set_status(P.status, kStatInexact);
+            if (sp == 0) return;
+            --sp;
+            n = sn[sp];
+            w = sw[sp];
+            continue;
+        }
+        sn[sp] = e.y;
+        sw[sp] = k * ab.y;
+        sp++;
+        n = e.x;
+        w = k * ab.x;
+    }
+}
+
+// fp32 push: q receives W*alpha, p the rest
+template <typename AT>
+__device__ void push_frac(const PushArgs& P, const Hist<true>& H, uint32_t n, float w) {
+    uint32_t sn[kMaxStack];
+    float sw[kMaxStack];
+    int sp = 0;
+    const AT* alpha = static_cast<const AT*>(P.alpha);
+    for (uint32_t step = 0;; step++) {
+        if (step >= kMaxPushSteps) {
+            set_status(P.status, kStatInexact);
+            return;
+        }
+        if (n < P.S) {
+            H.add_frac(n, w);
+            if (sp == 0) return;
+            --sp;
+            n = sn[sp];
+            w = sw[sp];
+            continue;
+        }
+        const uint2 e = __ldg(P.pq + n);
+        float al = AlphaCvt<AT>::to(alpha[n]);
+        uint32_t p = e.x, q = e.y;
+        if (al < 0.f) {   // 16-bit weights: sign = p and q swapped, |alpha| <= 1/2
+            al = -al;
+            p = e.y;
+            q = e.x;
+        }
+        if (sp >= kMaxStack) {
+            set_status(P.status, kStatInexact);
+            return;
+        }
+        const float wq = w * al;
+        sn[sp] = q;
+        sw[sp] = wq;
+        sp++;
+        n = p;
+        w = w - wq;
+    }
+}
+
+// read the node ID of cube (block b, offset o)
+__device__ __forceinline__ uint32_t cube_node(const Geom& G, const void* __restrict__ mip0,
+                                              const uint32_t* __restrict__ mip, const Blk& B, uint32_t o, int& l) {
+    l = B.meta & 15;
+    const int ex = (B.meta >> 4) & 15, ey = (B.meta >> 8) & 15;
+    const uint32_t u = o & ((1u << ex) - 1u);
+    const uint32_t v = (o >> ex) & ((1u << ey) - 1u);
+    const uint32_t w = o >> (ex + ey);
+    const int64_t X = B.x + u, Y = B.y + v, Z = B.z + w;
+    const int64_t idx = (Z * G.dims[l][1] + Y) * G.dims[l][0] + X;
+    if (l == 0)
+        return G.id0_bytes == 2 ? (uint32_t)__ldg(static_cast<const uint16_t*>(mip0) + idx)
+                                : __ldg(static_cast<const uint32_t*>(mip0) + idx);
+    return __ldg(mip + G.off[l] + idx);
+}
+
+// one warp-aggregated contribution of cube node `id` at level l
+template <bool FP, typename AT>
+__device__ __forceinline__ void accumulate(const PushArgs& P, const Hist<FP>& H, bool valid, uint32_t id, int l) {
+    const uint64_t key = valid ? ((uint64_t)l << 32 | id) : ~0ull;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    if (!valid || lane != __ffs(peers) - 1) return;
+    const uint32_t W = (uint32_t)__popc(peers) << (3 * l);
+    if (id < P.S) {
+        H.add_int(id, W);
+    } else if constexpr (FP) {
+        push_frac<AT>(P, H, id, (float)W);
+    } else {
+        push_int<FP>(P, H, id, W);
+    }
+}
+
+template <bool FP>
+__device__ __forceinline__ Hist<FP> carve(uint8_t* smem, uint32_t S, uint32_t* ntouched) {
+    Hist<FP> H;
+    H.h = reinterpret_cast<uint32_t*>(smem);
+    H.hf = FP ? reinterpret_cast<float*>(H.h + S) : nullptr;
+    H.touched = reinterpret_cast<uint16_t*>(FP ? reinterpret_cast<uint8_t*>(H.hf + S)
+                                               : reinterpret_cast<uint8_t*>(H.h + S));
+    H.ntouched = ntouched;
+    return H;
+}
+
+template <bool FP>
+__device__ __forceinline__ void flush(const Hist<FP>& H, uint32_t S, int64_t q, uint32_t* __restrict__ acc,
+                                      float* __restrict__ accf) {
+    // With the fp32 push a bin can be listed twice (once when its integer part
+    // and once when its fractional part became non-zero), so bins are read and
+    // cleared in one atomic step: the second reader sees zero.
+    const uint32_t n = *H.ntouched;
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+        const uint32_t s = H.touched[t];
+        const uint32_t v = FP ? atomicExch(H.h + s, 0u) : H.h[s];
+        if (!FP) H.h[s] = 0;
+        if (v) atomicAdd(acc + q * S + s, v);
+        if constexpr (FP) {
+            const float f = atomicExch(H.hf + s, 0.f);
+            if (f != 0.f) atomicAdd(accf + q * S + s, f);
+        }
+    }
+}
+
+struct MainArgs {
+    Geom G;
+    const void* mip0;
+    const uint32_t* mip;
+    PushArgs P;
+    const Blk* blk;
+    const uint64_t* blk_off;
+    const uint64_t* ncube;
+    const uint64_t* chunk_off;
+    int64_t Q;
+    uint32_t chunk;
+    unsigned long long* ticket;
+    uint32_t* acc;
+    float* accf;
+};
+
+template <bool FP, typename AT>
+__global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ uint32_t s_ntouched;
+    __shared__ unsigned long long s_chunk;
+    __shared__ int64_t s_q;
+    const uint32_t S = A.P.S;
+    const Hist<FP> H = carve<FP>(smem, S, &s_ntouched);
+    for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+        H.h[i] = 0;
+        if constexpr (FP) H.hf[i] = 0.f;
+    }
+    if (threadIdx.x == 0) s_ntouched = 0;
+    const unsigned long long total = A.chunk_off[A.Q];
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long c = atomicAdd(A.ticket, 1ull);
+            s_chunk = c;
+            if (c < total) {
+                // last box whose first chunk is <= c
+                int64_t lo = 0, hi = A.Q;   // chunk_off[lo] <= c < chunk_off[hi]
+                while (hi - lo > 1) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (A.chunk_off[mid] <= c) lo = mid;
+                    else hi = mid;
+                }
+                s_q = lo;
+            }
+        }
+        __syncthreads();
+        const unsigned long long c = s_chunk;
+        if (c >= total) break;
+        const int64_t q = s_q;
+        const uint64_t c0 = (c - A.chunk_off[q]) * A.chunk;
+        const uint64_t c1 = min(c0 + A.chunk, A.ncube[q]);
+        const uint64_t b0 = A.blk_off[q], b1 = A.blk_off[q + 1];
+        for (uint64_t base = c0; base < c1; base += blockDim.x) {
+            const uint64_t cube = base + threadIdx.x;
+            const bool valid = cube < c1;
+            // the warp's first cube: binary search for its block
+            uint64_t bw = b0;
+            if (lane == 0) {
+                const uint64_t first = base + (threadIdx.x & ~31u);
+                uint64_t lo = b0, hi = b1;   // blk[lo].start <= first < blk[hi].start
+                while (hi - lo > 1) {
+                    const uint64_t mid = (lo + hi) >> 1;
+                    if (__ldg(&A.blk[mid].start) <= first) lo = mid;
+                    else hi = mid;
+                }
+                bw = lo;
+            }
+            bw = __shfl_sync(0xffffffffu, bw, 0);
+            uint32_t id = 0;
+            int l = 0;
+            if (valid) {
+                uint64_t bb = bw;
+                while (bb + 1 < b1 && __ldg(&A.blk[bb + 1].start) <= cube) bb++;
+                const Blk B = A.blk[bb];
+                id = cube_node(A.G, A.mip0, A.mip, B, (uint32_t)(cube - B.start), l);
+            }
+            accumulate<FP, AT>(A.P, H, valid, id, l);
+        }
+        __syncthreads();
+        flush<FP>(H, S, q, A.acc, A.accf);
+        __syncthreads();
+        if (threadIdx.x == 0) s_ntouched = 0;
+    }
+}
+
+// baseline: one CTA per box, one launch per box, blocks walked in order
+template <bool FP, typename AT>
+__global__ void __launch_bounds__(256) query_plain_kernel(MainArgs A, const int32_t* __restrict__ boxes, int64_t q) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ uint32_t s_ntouched;
+    __shared__ Runs R;
+    const uint32_t S = A.P.S;
+    const Hist<FP> H = carve<FP>(smem, S, &s_ntouched);
+    for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+        H.h[i] = 0;
+        if constexpr (FP) H.hf[i] = 0.f;
+    }
+    int32_t b[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
+    if (!box_ok(b, A.G)) {
+        if (threadIdx.x == 0) set_status(A.P.status, kStatBadInput);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        s_ntouched = 0;
+        make_runs(b, A.G, R);
+    }
+    __syncthreads();
+    for (int k = 0; k < R.nz; k++)
+        for (int j = 0; j < R.ny; j++)
+            for (int i = 0; i < R.nx; i++) {
+                const int lx = R.lx[i], ly = R.ly[j], lz = R.lz[k];
+                const int l = min(lx, min(ly, lz));
+                Blk B;
+                B.start = 0;
+                B.x = (uint16_t)(R.sx[i] >> l);
+                B.y = (uint16_t)(R.sy[j] >> l);
+                B.z = (uint16_t)(R.sz[k] >> l);
+                B.meta = (uint16_t)(l | (lx - l) << 4 | (ly - l) << 8 | (lz - l) << 12);
+                const uint32_t n = 1u << (lx + ly + lz - 3 * l);
+                for (uint32_t base = 0; base < n; base += blockDim.x) {
+                    const uint32_t o = base + threadIdx.x;
+                    const bool valid = o < n;
+                    uint32_t id = 0;
+                    int lv = 0;
+                    if (valid) id = cube_node(A.G, A.mip0, A.mip, B, o, lv);
+                    accumulate<FP, AT>(A.P, H, valid, id, lv);
+                }
+            }
+    __syncthreads();
+    flush<FP>(H, S, q, A.acc, A.accf);
+}
+
+// ---------------------------------------------------------------------------
+// finalisation
+// ---------------------------------------------------------------------------
+__global__ void dense_f32_kernel(const uint32_t* __restrict__ acc, float* __restrict__ out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)acc[i] + out[i];
+}
+
+template <bool FP>
+__global__ void csr_count_kernel(const uint32_t* __restrict__ acc, const float* __restrict__ accf, int64_t Q,
+                                 uint32_t S, uint64_t* __restrict__ cnt) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= Q) return;
+    uint64_t c = 0;
+    for (uint32_t s = lane; s < S; s += 32) {
+        bool nz = acc[q * S + s] != 0;
+        if constexpr (FP) nz = nz || accf[q * S + s] != 0.f;
+        c += nz;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[q] = c;
+}
+
+template <bool FP>
+__global__ void csr_write_kernel(const uint32_t* __restrict__ acc, const float* __restrict__ accf, int64_t Q,
+                                 uint32_t S, const uint64_t* __restrict__ off, uint32_t* __restrict__ seg,
+                                 void* __restrict__ out) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= Q) return;
+    uint64_t pos = off[q];
+    for (uint32_t sb = 0; sb < S; sb += 32) {
+        const uint32_t s = sb + lane;
+        uint32_t v = 0;
+        float f = 0.f;
+        bool nz = false;
+        if (s < S) {
+            v = acc[q * S + s];
+            nz = v != 0;
+            if constexpr (FP) {
+                f = accf[q * S + s];
+                nz = nz || f != 0.f;
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, nz);
+        if (nz) {
+            const uint64_t o = pos + __popc(m & ((1u << lane) - 1u));
+            seg[o] = s;
+            if constexpr (FP) static_cast<float*>(out)[o] = (float)v + f;
+            else static_cast<uint32_t*>(out)[o] = v;
+        }
+        pos += __popc(m);
+    }
+}
+
+__global__ void widen_kernel(const uint32_t* __restrict__ a, uint64_t* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+}
+
+int sm_count(int dev) {
+    static std::mutex mu;
+    static std::vector<int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1, 0);
+    if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
+    return cache[dev] ? cache[dev] : 1;
+}
+
+template <typename K>
+mg_status prepare_kernel(K kernel, size_t smem) {
+    MG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return MG_OK;
+}
+
+template <bool FP, typename AT>
+mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts& o, const int32_t* boxes,
+                      size_t smem, int threads, cudaStream_t s) {
+    if (o.schedule == MG_SCHED_PLAIN) {
+        auto k = query_plain_kernel<FP, AT>;
+        MG_TRY(prepare_kernel(k, smem));
+        for (int64_t q = 0; q < A.Q; q++) {
+            k<<<1, 256, smem, s>>>(A, boxes, q);
+        }
+        MG_CUDA(cudaGetLastError());
+        return MG_OK;
+    }
+    auto k = query_batched_kernel<FP, AT>;
+    MG_TRY(prepare_kernel(k, smem));
+    int per_sm = 0;
+    MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
+    if (per_sm < 1) return fail(MG_ERR_UNSUPPORTED, "query kernel does not fit on an SM");
+    const int grid = per_sm * sm_count(g->device);
+    k<<<grid, threads, smem, s>>>(A);
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+}  // namespace
+
+mg_status count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64_t* cubes, cudaStream_t s) {
+    const Geom G = make_geom(g);
+    plan_count_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, 1, nullptr, cubes, nullptr,
+                                                            g->status.as<unsigned>());
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const mg_query_opts& o, void* out,
+                      size_t cap, uint32_t* seg, uint64_t* offsets, size_t* required, cudaStream_t s) {
+    const Alloc& al = g->al;
+    const uint32_t S = g->S;
+    const bool FP = o.hist_type == MG_HIST_F32;
+    const bool csr = o.layout == MG_LAYOUT_CSR;
+    if (S > kMaxSharedSegments) return fail(MG_ERR_UNSUPPORTED, "more than 32768 segments");
+    if (required) *required = 0;
+    if (Q == 0) {
+        if (csr) MG_CUDA(cudaMemsetAsync(offsets, 0, sizeof(uint64_t), s));
+        return MG_OK;
+    }
+    if (FP && o.alpha_dtype != MG_F32) MG_TRY(ensure_alpha16(const_cast<mg_graph*>(g), (mg_dtype)o.alpha_dtype, s));
+    const uint32_t chunk = o.chunk_cubes > 0 ? (uint32_t)o.chunk_cubes : 4096u;
+    const int threads = o.block_threads > 0 ? o.block_threads : 256;
+    const Geom G = make_geom(g);
+    unsigned* status = g->status.as<unsigned>();
+    mg_graph* gm = const_cast<mg_graph*>(g);
+    const bool timed = o.timing != 0;
+    if (timed) {
+        for (auto& e : gm->qev)
+            if (!e) MG_CUDA(cudaEventCreate(&e));
+        gm->qev_valid = false;
+        MG_CUDA(cudaEventRecord(gm->qev[0], s));
+    }
+
+    // accumulators: the dense u32 output itself, else scratch
+    Buf acc_b, accf_b;
+    uint32_t* acc = nullptr;
+    float* accf = nullptr;
+    const size_t cells = (size_t)Q * S;
+    if (!csr && !FP) {
+        acc = static_cast<uint32_t*>(out);
+    } else {
+        MG_TRY(acc_b.alloc(&al, cells * 4, s));
+        acc = acc_b.as<uint32_t>();
+    }
+    if (FP) {
+        if (!csr) {
+            accf = static_cast<float*>(out);
+        } else {
+            MG_TRY(accf_b.alloc(&al, cells * 4, s));
+            accf = accf_b.as<float>();
+        }
+        MG_CUDA(cudaMemsetAsync(accf, 0, cells * 4, s));
+    }
+    MG_CUDA(cudaMemsetAsync(acc, 0, cells * 4, s));
+
+    MainArgs A;
+    A.G = G;
+    A.mip0 = g->mip0.p;
+    A.mip = g->mip.as<uint32_t>();
+    A.P.pq = g->pq.as<uint2>();
+    A.P.ab32 = g->ab32.as<uint2>();
+    A.P.alpha = o.alpha_dtype == MG_F16 ? g->alpha16.p : o.alpha_dtype == MG_BF16 ? g->alphab16.p : g->alpha.p;
+    A.P.S = S;
+    A.P.status = status;
+    A.Q = Q;
+    A.chunk = chunk;
+    A.acc = acc;
+    A.accf = accf;
+    A.blk = nullptr;
+    A.blk_off = nullptr;
+    A.ncube = nullptr;
+    A.chunk_off = nullptr;
+    A.ticket = nullptr;
+
+    const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + (size_t)S * 2 * (FP ? 2 : 1) + 16;
+    if (smem > 220 * 1024) return fail(MG_ERR_UNSUPPORTED, "too many segments for the shared-memory histogram");
+    Buf nblk, ncube, nchunk, blk_off, chunk_off, blk, ticket;
+    if (o.schedule == MG_SCHED_BATCHED) {
+        MG_TRY(nblk.alloc(&al, (size_t)Q * 4, s));
+        MG_TRY(ncube.alloc(&al, (size_t)Q * 8, s));
+        MG_TRY(nchunk.alloc(&al, (size_t)Q * 8, s));
+        MG_TRY(blk_off.alloc(&al, (size_t)(Q + 1) * 8, s));
+        MG_TRY(chunk_off.alloc(&al, (size_t)(Q + 1) * 8, s));
+        MG_TRY(ticket.alloc(&al, 8, s));
+        plan_count_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, chunk, nblk.as<uint32_t>(),
+                                                                ncube.as<uint64_t>(), nchunk.as<uint64_t>(),
+                                                                status);
+        MG_CUDA(cudaGetLastError());
+        // block offsets are 64-bit sums of the 32-bit per-box counts
+        MG_TRY(scan_exclusive_u64(nchunk.as<uint64_t>(), chunk_off.as<uint64_t>(), Q,
+                                  chunk_off.as<uint64_t>() + Q, al, s));
+        {
+            Buf nb64;
+            MG_TRY(nb64.alloc(&al, (size_t)Q * 8, s));
+            widen_kernel<<<grid_for(Q, 256, 152 * 64), 256, 0, s>>>(nblk.as<uint32_t>(), nb64.as<uint64_t>(), Q);
+            MG_CUDA(cudaGetLastError());
+            MG_TRY(scan_exclusive_u64(nb64.as<uint64_t>(), blk_off.as<uint64_t>(), Q, blk_off.as<uint64_t>() + Q, al,
+                                      s));
+        }
+        uint64_t nblocks = 0;
+        MG_CUDA(cudaMemcpyAsync(&nblocks, blk_off.as<uint64_t>() + Q, 8, cudaMemcpyDeviceToHost, s));
+        MG_CUDA(cudaStreamSynchronize(s));
+        MG_TRY(blk.alloc(&al, (size_t)std::max<uint64_t>(nblocks, 1) * sizeof(Blk), s));
+        plan_write_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>());
+        MG_CUDA(cudaGetLastError());
+        MG_CUDA(cudaMemsetAsync(ticket.p, 0, 8, s));
+        A.blk = blk.as<Blk>();
+        A.blk_off = blk_off.as<uint64_t>();
+        A.ncube = ncube.as<uint64_t>();
+        A.chunk_off = chunk_off.as<uint64_t>();
+        A.ticket = ticket.as<unsigned long long>();
+    }
+    if (timed) MG_CUDA(cudaEventRecord(gm->qev[1], s));
+    if (FP) {
+        if (o.alpha_dtype == MG_F16) MG_TRY((launch_main<true, __half>(g, A, o, boxes, smem, threads, s)));
+        else if (o.alpha_dtype == MG_BF16) MG_TRY((launch_main<true, __nv_bfloat16>(g, A, o, boxes, smem, threads, s)));
+        else MG_TRY((launch_main<true, float>(g, A, o, boxes, smem, threads, s)));
+    } else {
+        MG_TRY((launch_main<false, float>(g, A, o, boxes, smem, threads, s)));
+    }
+
+    if (timed) MG_CUDA(cudaEventRecord(gm->qev[2], s));
+    if (!csr) {
+        if (FP) {
+            dense_f32_kernel<<<grid_for((int64_t)cells, 256, 152 * 64), 256, 0, s>>>(acc, accf, (int64_t)cells);
+            MG_CUDA(cudaGetLastError());
+        }
+        if (timed) {
+            MG_CUDA(cudaEventRecord(gm->qev[3], s));
+            gm->qev_valid = true;
+        }
+        return MG_OK;
+    }
+    // CSR: count, scan, capacity check, write
+    Buf cnt;
+    MG_TRY(cnt.alloc(&al, (size_t)Q * 8, s));
+    if (FP)
+        csr_count_kernel<true><<<grid_for(Q * 32, 256), 256, 0, s>>>(acc, accf, Q, S, cnt.as<uint64_t>());
+    else
+        csr_count_kernel<false><<<grid_for(Q * 32, 256), 256, 0, s>>>(acc, accf, Q, S, cnt.as<uint64_t>());
+    MG_CUDA(cudaGetLastError());
+    MG_TRY(scan_exclusive_u64(cnt.as<uint64_t>(), offsets, Q, offsets + Q, al, s));
+    uint64_t nnz = 0;
+    MG_CUDA(cudaMemcpyAsync(&nnz, offsets + Q, 8, cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    if (required) *required = (size_t)nnz;
+    if (nnz > cap) return fail(MG_ERR_CAPACITY, "CSR output needs " + std::to_string(nnz) + " entries");
+    if (FP)
+        csr_write_kernel<true><<<grid_for(Q * 32, 256), 256, 0, s>>>(acc, accf, Q, S, offsets, seg, out);
+    else
+        csr_write_kernel<false><<<grid_for(Q * 32, 256), 256, 0, s>>>(acc, accf, Q, S, offsets, seg, out);
+    MG_CUDA(cudaGetLastError());
+    if (timed) {
+        MG_CUDA(cudaEventRecord(gm->qev[3], s));
+        gm->qev_valid = true;
+    }
+    return MG_OK;
+}
+
+mg_status query_timing(const mg_graph* g, float* plan_ms, float* main_ms, float* out_ms) {
+    if (!g->qev_valid) return fail(MG_ERR_INVALID_ARG, "no timed query call on this graph");
+    MG_CUDA(cudaEventSynchronize(g->qev[3]));
+    float t[3];
+    for (int i = 0; i < 3; i++) MG_CUDA(cudaEventElapsedTime(&t[i], g->qev[i], g->qev[i + 1]));
+    if (plan_ms) *plan_ms = t[0];
+    if (main_ms) *main_ms = t[1];
+    if (out_ms) *out_ms = t[2];
+    return MG_OK;
+}
+
+}  // namespace mg

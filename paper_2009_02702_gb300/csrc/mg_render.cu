@@ -1,0 +1,90 @@
+// mg_render.cu -- ray-sample node lookup (Sec. 4: rendering from the Mixture
+// Graph is a paletted lookup).  One thread per sample: pick the level nearest
+// to the sample's LOD, the voxel containing the sample at that level, read its
+// node ID and copy the node's value row.  The level and voxel are decided in
+// fp32, the precision of the samples.
+#include "mg_internal.cuh"
+
+namespace mg {
+namespace {
+
+struct Geom {
+    int L;
+    int id0_bytes;
+    int32_t dims[MG_MAX_LEVELS][3];
+    int64_t off[MG_MAX_LEVELS];
+};
+
+__device__ __forceinline__ int64_t floor_coord(float x, int32_t d0) {
+    float xc = x;
+    if (!(xc >= 0.f)) xc = 0.f;                  // negatives and NaN
+    if (xc > (float)d0) xc = (float)d0;
+    return (int64_t)xc;                         // truncation is the floor for xc >= 0
+}
+
+template <typename RowT>
+__global__ void lookup_kernel(Geom G, const void* __restrict__ mip0, const uint32_t* __restrict__ mip,
+                              const float4* __restrict__ samples, int64_t P, const RowT* __restrict__ vals,
+                              int words, RowT* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const float4 smp = __ldg(samples + i);
+    const float t = smp.w + 0.5f;                 // nearest level
+    int l;
+    if (!(t >= 0.f)) l = 0;
+    else if (t >= (float)(G.L - 1)) l = G.L - 1;
+    else l = (int)t;
+    int64_t v[3];
+    const float c[3] = {smp.x, smp.y, smp.z};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int64_t x = floor_coord(c[k], G.dims[0][k]) >> l;
+        v[k] = min(x, (int64_t)G.dims[l][k] - 1);
+    }
+    const int64_t idx = (v[2] * G.dims[l][1] + v[1]) * G.dims[l][0] + v[0];
+    uint32_t node;
+    if (l == 0)
+        node = G.id0_bytes == 2 ? (uint32_t)__ldg(static_cast<const uint16_t*>(mip0) + idx)
+                                : __ldg(static_cast<const uint32_t*>(mip0) + idx);
+    else
+        node = __ldg(mip + G.off[l] + idx);
+    const RowT* src = vals + (int64_t)node * words;
+    RowT* dst = out + i * words;
+    for (int w = 0; w < words; w++) dst[w] = __ldg(src + w);
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+mg_status render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dt, const float* samples, int64_t P,
+                        void* out, cudaStream_t s) {
+    if (!aligned(samples, 16)) return fail(MG_ERR_INVALID_ARG, "samples must be 16-byte aligned");
+    Geom G;
+    G.L = g->L;
+    G.id0_bytes = g->id0_bytes;
+    for (int l = 0; l < MG_MAX_LEVELS; l++) {
+        for (int k = 0; k < 3; k++) G.dims[l][k] = g->geom.dims[l][k];
+        G.off[l] = g->geom.off[l];
+    }
+    const size_t row = (size_t)C * (dt == MG_F32 ? 4 : 2);
+    const unsigned grid = grid_for(P, 256);
+    const float4* sm = reinterpret_cast<const float4*>(samples);
+    const uint32_t* mip = g->mip.as<uint32_t>();
+    if (row % 16 == 0 && aligned(vals, 16) && aligned(out, 16))
+        lookup_kernel<uint4><<<grid, 256, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint4*)vals, (int)(row / 16),
+                                                  (uint4*)out);
+    else if (row % 8 == 0 && aligned(vals, 8) && aligned(out, 8))
+        lookup_kernel<uint2><<<grid, 256, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint2*)vals, (int)(row / 8),
+                                                  (uint2*)out);
+    else if (row % 4 == 0 && aligned(vals, 4) && aligned(out, 4))
+        lookup_kernel<uint32_t><<<grid, 256, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint32_t*)vals,
+                                                     (int)(row / 4), (uint32_t*)out);
+    else
+        lookup_kernel<uint16_t><<<grid, 256, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint16_t*)vals,
+                                                     (int)(row / 2), (uint16_t*)out);
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+}  // namespace mg

@@ -56,7 +56,7 @@ __global__ void voronoi_kernel(int64_t nx, int64_t ny, int64_t nz, const int64_t
 
 }  // namespace
 
-extern "C" int mgs_voronoi_dev(int64_t nx, int64_t ny, int64_t nz, const int64_t* seeds2_dev,
+extern "C" __attribute__((visibility("default"))) int mgs_voronoi_dev(int64_t nx, int64_t ny, int64_t nz, const int64_t* seeds2_dev,
                                const int64_t* weight_dev, int64_t K, const int64_t* metric_host,
                                int out_bytes, void* out_dev, cudaStream_t stream)
 {

@@ -1,0 +1,342 @@
+"""Thin Python binding of libmg (the C-ABI declared in include/mg.h).
+
+Each function carries the name of the C entry point it marshals arguments
+for; all computation happens in the library's CUDA kernels.  PyTorch supplies
+device memory (tensors, and the caching allocator behind the library's
+allocator callback) and streams.  There is no fallback: if the compiled
+library is missing, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmg.so")
+
+MG_OK, MG_ERR_INVALID_ARG, MG_ERR_OOM, MG_ERR_CUDA = 0, 1, 2, 3
+MG_ERR_TIMEOUT, MG_ERR_CAPACITY, MG_ERR_UNSUPPORTED, MG_ERR_INEXACT = 4, 5, 6, 7
+MG_F32, MG_F16, MG_BF16 = 0, 1, 2
+MG_HIST_U32, MG_HIST_F32 = 0, 1
+MG_LAYOUT_DENSE, MG_LAYOUT_CSR = 0, 1
+MG_SCHED_BATCHED, MG_SCHED_PLAIN = 0, 1
+MG_MAX_LEVELS, MG_MAX_DEPTH = 32, 64
+MG_NO_NODE = 0xFFFFFFFF
+
+_DTYPES = {"f32": (MG_F32, torch.float32), "f16": (MG_F16, torch.float16), "bf16": (MG_BF16, torch.bfloat16)}
+_TORCH_TO_MG = {torch.float32: MG_F32, torch.float16: MG_F16, torch.bfloat16: MG_BF16}
+
+# names of every symbol include/mg.h declares (checked by the CPU tests)
+EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_copy_mip", "mg_propagate_tf",
+           "mg_query_boxes", "mg_query_timing", "mg_count_cubes", "mg_render_lookup", "mg_sync_status", "mg_free",
+           "mg_last_error", "mg_version")
+
+
+class MGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("mg status %d: %s" % (status, msg))
+        self.status = status
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class mg_allocator(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN)]
+
+
+class mg_build_opts(ctypes.Structure):
+    _fields_ = [("id_bytes", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class mg_graph_info(ctypes.Structure):
+    _fields_ = [("num_segments", ctypes.c_uint32), ("levels", ctypes.c_int), ("depth", ctypes.c_int),
+                ("num_nodes", ctypes.c_int64), ("dims", (ctypes.c_int64 * 3) * MG_MAX_LEVELS),
+                ("bucket", ctypes.c_int64 * (MG_MAX_DEPTH + 2)), ("max_list", ctypes.c_int64),
+                ("pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double)]
+
+
+class mg_query_opts(ctypes.Structure):
+    _fields_ = [("hist_type", ctypes.c_int), ("layout", ctypes.c_int), ("alpha_dtype", ctypes.c_int),
+                ("schedule", ctypes.c_int), ("chunk_cubes", ctypes.c_int), ("block_threads", ctypes.c_int),
+                ("timing", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libmg.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmg.so is not built (%s): run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32, st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int
+        L.mg_build.argtypes = [P, i64, i64, i64, ctypes.c_uint32, ctypes.POINTER(mg_build_opts),
+                               ctypes.POINTER(mg_allocator), P, ctypes.POINTER(P)]
+        L.mg_build.restype = st
+        L.mg_graph_info_get.argtypes = [P, ctypes.POINTER(mg_graph_info)]
+        L.mg_graph_info_get.restype = st
+        L.mg_graph_copy_nodes.argtypes = [P, P, P, P, P, P]
+        L.mg_graph_copy_nodes.restype = st
+        L.mg_graph_copy_mip.argtypes = [P, i32, P, P]
+        L.mg_graph_copy_mip.restype = st
+        L.mg_propagate_tf.argtypes = [P, P, i32, i32, P, P]
+        L.mg_propagate_tf.restype = st
+        L.mg_query_boxes.argtypes = [P, P, i64, ctypes.POINTER(mg_query_opts), P, ctypes.c_size_t, P, P,
+                                     ctypes.POINTER(ctypes.c_size_t), P]
+        L.mg_query_boxes.restype = st
+        L.mg_query_timing.argtypes = [P, P, P, P]
+        L.mg_query_timing.restype = st
+        L.mg_count_cubes.argtypes = [P, P, i64, P, P]
+        L.mg_count_cubes.restype = st
+        L.mg_render_lookup.argtypes = [P, P, i32, i32, P, i64, P, P]
+        L.mg_render_lookup.restype = st
+        L.mg_sync_status.argtypes = [P, P]
+        L.mg_sync_status.restype = st
+        L.mg_free.argtypes = [P]
+        L.mg_free.restype = None
+        L.mg_last_error.argtypes = []
+        L.mg_last_error.restype = ctypes.c_char_p
+        L.mg_version.argtypes = []
+        L.mg_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def mg_last_error() -> str:
+    return lib().mg_last_error().decode()
+
+
+def mg_version() -> str:
+    return lib().mg_version().decode()
+
+
+def _check(st: int):
+    if st != MG_OK:
+        raise MGError(st, mg_last_error())
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# --------------------------------------------------------------------------
+# allocator callback backed by torch's caching allocator
+# --------------------------------------------------------------------------
+def _torch_alloc(ctx, nbytes, stream):
+    try:
+        dev = int(ctx or 0)
+        return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+    except Exception:
+        return None
+
+
+def _torch_free(ctx, ptr, nbytes, stream):
+    try:
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:
+        pass
+
+
+_ALLOC_CB = ALLOC_FN(_torch_alloc)
+_FREE_CB = FREE_FN(_torch_free)
+
+
+def torch_allocator(device: int) -> mg_allocator:
+    return mg_allocator(ctypes.c_void_p(device), _ALLOC_CB, _FREE_CB)
+
+
+# --------------------------------------------------------------------------
+# entry points
+# --------------------------------------------------------------------------
+class Graph:
+    """Owns an mg_graph handle (released by mg_free)."""
+
+    def __init__(self, handle: int, device: int, allocator):
+        self.handle = handle
+        self.device = device
+        self._allocator = allocator   # keeps the callback struct alive
+        self.info = mg_graph_info_get(self)
+
+    @property
+    def S(self):
+        return self.info["num_segments"]
+
+    @property
+    def N(self):
+        return self.info["num_nodes"]
+
+    def close(self):
+        if self.handle:
+            mg_free(self)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mg_build(ids: torch.Tensor, num_segments: int, stream=None, use_torch_allocator: bool = True) -> Graph:
+    """Build the Mixture Graph of a (nz, ny, nx) uint16/uint32/int32 ID volume on the GPU."""
+    if not ids.is_cuda or ids.dim() != 3:
+        raise ValueError("ids must be a 3-D CUDA tensor (z, y, x)")
+    ids = ids.contiguous()
+    if ids.dtype == torch.uint16:
+        nb = 2
+    elif ids.dtype in (torch.uint32, torch.int32):
+        nb = 4
+    else:
+        raise TypeError("ids must be uint16, uint32 or int32")
+    nz, ny, nx = ids.shape
+    opts = mg_build_opts(nb)
+    dev = ids.device.index if ids.device.index is not None else torch.cuda.current_device()
+    alloc = torch_allocator(dev) if use_torch_allocator else None
+    h = ctypes.c_void_p()
+    with torch.cuda.device(dev):
+        st = lib().mg_build(ids.data_ptr(), nx, ny, nz, num_segments, ctypes.byref(opts),
+                            ctypes.byref(alloc) if alloc is not None else None, _stream(stream),
+                            ctypes.byref(h))
+    _check(st)
+    return Graph(h.value, dev, alloc)
+
+
+def mg_graph_info_get(g: Graph) -> dict:
+    info = mg_graph_info()
+    _check(lib().mg_graph_info_get(g.handle, ctypes.byref(info)))
+    L, D = info.levels, info.depth
+    return dict(num_segments=info.num_segments, levels=L, depth=D, num_nodes=info.num_nodes,
+                dims=[tuple(info.dims[l][k] for k in range(3)) for l in range(L)],
+                bucket=[info.bucket[d] for d in range(D + 2)], max_list=info.max_list, pairs=info.pairs,
+                device_bytes=info.device_bytes, build_ms=info.build_ms)
+
+
+def mg_graph_copy_nodes(g: Graph, stream=None):
+    """(p, q, a, b) numpy arrays of the canonical node table."""
+    import numpy as np
+    N = g.N
+    p = np.zeros(N, np.uint32); q = np.zeros(N, np.uint32)
+    a = np.zeros(N, np.uint64); b = np.zeros(N, np.uint64)
+    _check(lib().mg_graph_copy_nodes(g.handle, p.ctypes.data, q.ctypes.data, a.ctypes.data, b.ctypes.data,
+                                     _stream(stream)))
+    return p, q, a, b
+
+
+def mg_graph_copy_mip(g: Graph, level: int, stream=None):
+    """Node IDs of one level, numpy uint32 array (z, y, x)."""
+    import numpy as np
+    nx, ny, nz = g.info["dims"][level]
+    out = np.zeros((nz, ny, nx), np.uint32)
+    _check(lib().mg_graph_copy_mip(g.handle, level, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def mg_propagate_tf(g: Graph, tf: torch.Tensor, storage: str = "f32", out: torch.Tensor = None,
+                    stream=None) -> torch.Tensor:
+    """Node values (N, C) in `storage` dtype from an (S, C) fp32 CUDA transfer function."""
+    if not tf.is_cuda or tf.dtype != torch.float32 or tf.dim() != 2 or tf.shape[0] != g.S:
+        raise ValueError("tf must be a CUDA float32 tensor of shape (S, C)")
+    tf = tf.contiguous()
+    code, dt = _DTYPES[storage]
+    C = tf.shape[1]
+    if out is None:
+        out = torch.empty((g.N, C), dtype=dt, device=tf.device)
+    _check(lib().mg_propagate_tf(g.handle, tf.data_ptr(), C, code, out.data_ptr(), _stream(stream)))
+    return out
+
+
+def mg_query_boxes(g: Graph, boxes: torch.Tensor, hist: str = "u32", layout: str = "dense",
+                   alpha: str = "f32", schedule: str = "batched", chunk_cubes: int = 0,
+                   block_threads: int = 0, out=None, capacity: int = None, timing: bool = False,
+                   stream=None):
+    """Segment histograms of (Q, 6) int32 boxes.
+
+    dense: returns a (Q, S) uint32 (hist='u32') or float32 tensor.
+    csr:   returns (offsets uint64 (Q+1), seg uint32 (nnz), values (nnz))."""
+    if not boxes.is_cuda or boxes.dtype != torch.int32 or boxes.dim() != 2 or boxes.shape[1] != 6:
+        raise ValueError("boxes must be a CUDA int32 tensor of shape (Q, 6)")
+    boxes = boxes.contiguous()
+    Q = boxes.shape[0]
+    o = mg_query_opts()
+    o.hist_type = MG_HIST_F32 if hist == "f32" else MG_HIST_U32
+    o.layout = MG_LAYOUT_CSR if layout == "csr" else MG_LAYOUT_DENSE
+    o.alpha_dtype = _DTYPES[alpha][0]
+    o.schedule = MG_SCHED_PLAIN if schedule == "plain" else MG_SCHED_BATCHED
+    o.chunk_cubes = chunk_cubes
+    o.block_threads = block_threads
+    o.timing = 1 if timing else 0
+    vdt = torch.float32 if hist == "f32" else torch.uint32
+    req = ctypes.c_size_t(0)
+    dev = boxes.device
+    if layout != "csr":
+        if out is None:
+            out = torch.empty((Q, g.S), dtype=vdt, device=dev)
+        _check(lib().mg_query_boxes(g.handle, boxes.data_ptr(), Q, ctypes.byref(o), out.data_ptr(),
+                                    out.numel(), None, None, ctypes.byref(req), _stream(stream)))
+        return out
+    offsets = torch.empty(Q + 1, dtype=torch.uint64, device=dev)
+    cap = int(capacity) if capacity is not None else 0
+    for _ in range(2):
+        seg = torch.empty(max(cap, 1), dtype=torch.uint32, device=dev)
+        vals = torch.empty(max(cap, 1), dtype=vdt, device=dev)
+        st = lib().mg_query_boxes(g.handle, boxes.data_ptr(), Q, ctypes.byref(o), vals.data_ptr(), cap,
+                                  seg.data_ptr(), offsets.data_ptr(), ctypes.byref(req), _stream(stream))
+        if st == MG_ERR_CAPACITY and capacity is None:
+            cap = int(req.value)
+            continue
+        _check(st)
+        n = int(req.value)
+        return offsets, seg[:n], vals[:n]
+    raise MGError(MG_ERR_CAPACITY, mg_last_error())
+
+
+def mg_query_timing(g: Graph):
+    """(plan_ms, main_ms, output_ms) of the last query call made with timing=True."""
+    t = [ctypes.c_float(), ctypes.c_float(), ctypes.c_float()]
+    _check(lib().mg_query_timing(g.handle, *[ctypes.byref(x) for x in t]))
+    return tuple(x.value for x in t)
+
+
+def mg_count_cubes(g: Graph, boxes: torch.Tensor, stream=None) -> torch.Tensor:
+    """Footprint-assembly cube (fetch) count per box, uint64 (Q,)."""
+    boxes = boxes.contiguous()
+    out = torch.empty(boxes.shape[0], dtype=torch.uint64, device=boxes.device)
+    _check(lib().mg_count_cubes(g.handle, boxes.data_ptr(), boxes.shape[0], out.data_ptr(), _stream(stream)))
+    return out
+
+
+def mg_render_lookup(g: Graph, vals: torch.Tensor, samples: torch.Tensor, out: torch.Tensor = None,
+                     stream=None) -> torch.Tensor:
+    """Value row of the node under every (x, y, z, lod) sample, (P, C) in vals' dtype."""
+    if samples.dtype != torch.float32 or samples.dim() != 2 or samples.shape[1] != 4:
+        raise ValueError("samples must be float32 of shape (P, 4)")
+    samples = samples.contiguous()
+    C = vals.shape[1]
+    if out is None:
+        out = torch.empty((samples.shape[0], C), dtype=vals.dtype, device=vals.device)
+    _check(lib().mg_render_lookup(g.handle, vals.data_ptr(), C, _TORCH_TO_MG[vals.dtype], samples.data_ptr(),
+                                  samples.shape[0], out.data_ptr(), _stream(stream)))
+    return out
+
+
+def mg_sync_status(g: Graph, stream=None):
+    """Synchronise and raise MGError if a kernel recorded an error."""
+    _check(lib().mg_sync_status(g.handle, _stream(stream)))
+
+
+def mg_free(g: Graph):
+    lib().mg_free(g.handle)

@@ -1,0 +1,73 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports
+every entry point include/mg.h declares, and rejects bad arguments on the host
+before any launch."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from tests.conftest import ROOT
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "mg.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"MG_API\s+[\w\s\*]+?\b(mg_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2009_02702_gb300 import build as b
+    b.build_mg()
+    from paper_2009_02702_gb300 import mg
+    return mg.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("mg_build", "mg_propagate_tf", "mg_query_boxes", "mg_render_lookup", "mg_free", "mg_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2009_02702_gb300 import mg
+    names = _declared()
+    assert sorted(mg.EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_host_argument_checks(lib):
+    from paper_2009_02702_gb300 import mg
+    h = ctypes.c_void_p()
+    opts = mg.mg_build_opts(2)
+    # NULL ids, bad dims, bad id width: rejected before touching the device
+    assert lib.mg_build(None, 4, 4, 4, 3, ctypes.byref(opts), None, None, ctypes.byref(h)) == mg.MG_ERR_INVALID_ARG
+    assert "ids" in mg.mg_last_error()
+    assert lib.mg_build(ctypes.c_void_p(16), 0, 4, 4, 3, ctypes.byref(opts), None, None,
+                        ctypes.byref(h)) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_build(ctypes.c_void_p(16), 70000, 4, 4, 3, ctypes.byref(opts), None, None,
+                        ctypes.byref(h)) == mg.MG_ERR_UNSUPPORTED
+    bad = mg.mg_build_opts(3)
+    assert lib.mg_build(ctypes.c_void_p(16), 4, 4, 4, 3, ctypes.byref(bad), None, None,
+                        ctypes.byref(h)) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_build(ctypes.c_void_p(16), 4, 4, 4, 0, ctypes.byref(opts), None, None,
+                        ctypes.byref(h)) == mg.MG_ERR_INVALID_ARG
+    # NULL graph
+    o = mg.mg_query_opts()
+    assert lib.mg_query_boxes(None, None, 0, ctypes.byref(o), None, 0, None, None, None, None) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_propagate_tf(None, None, 4, 0, None, None) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_render_lookup(None, None, 4, 0, None, 0, None, None) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_count_cubes(None, None, 0, None, None) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_sync_status(None, None) == mg.MG_ERR_INVALID_ARG
+    lib.mg_free(None)
+    assert mg.mg_version().startswith("mixgraph-gb300")
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2009_02702_gb300 import mg
+    monkeypatch.setattr(mg, "_lib", None)
+    monkeypatch.setattr(mg, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        mg.lib()

@@ -1,0 +1,248 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+Integers (mip IDs, node table, node counts, depth, box histograms, cube
+counts) must match bit for bit.  Floating point: |x - ref| <= 1e-5 |ref| or,
+for |ref| < 1e-2, |x - ref| <= 1e-7, structural zeros exact (the stated FP32
+tolerance); 16-bit storage is held to the bound its rounding allows.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_02702_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL, ATOL_SMALL = 1e-5, 1e-7
+
+
+def fp32_close(x, ref):
+    x = np.asarray(x, np.float64)
+    ref = np.asarray(ref, np.float64)
+    tol = np.where(np.abs(ref) < 1e-2, ATOL_SMALL, RTOL * np.abs(ref))
+    ok = (np.abs(x - ref) <= tol) & ((ref != 0) | (x == 0))
+    return bool(ok.all()), float(np.max(np.abs(x - ref)) if x.size else 0.0)
+
+
+@pytest.fixture(scope="module")
+def mg():
+    from paper_2009_02702_gb300 import mg as _mg
+    _mg.lib()
+    return _mg
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def build_pair(mg, vol, S, ids_dtype=None):
+    t = torch.from_numpy(vol.astype(np.int32) if ids_dtype == "i32" else vol).to(dev())
+    return mg.mg_build(t, S), oracle.Graph(vol, S)
+
+
+VOLUMES = [
+    ("cfg1-64^3", lambda: synth.make_volume(1), 64),
+    ("ragged-37x29x23", lambda: synth.make_volume(1, dims=(37, 29, 23), S=24), 24),
+    ("thin-130x7x3", lambda: synth.make_volume(1, dims=(130, 7, 3), S=50), 50),
+    ("line-1x1x40", lambda: synth.make_volume(1, dims=(1, 1, 40), S=5), 5),
+    ("one-voxel", lambda: np.array([[[2]]], np.uint16), 3),
+    ("one-segment", lambda: np.zeros((17, 9, 12), np.uint16), 1),
+    ("many-segments-40^3-s3000", lambda: synth.make_volume(1, dims=(40, 40, 40), S=3000), 3000),
+    ("aniso-48x40x20", lambda: synth.make_volume(3, dims=(48, 40, 20), S=30), 30),
+    ("powerlaw-45x33x27", lambda: synth.make_volume(2, dims=(45, 33, 27), S=40), 40),
+]
+
+
+@pytest.mark.parametrize("name,make,S", VOLUMES, ids=[v[0] for v in VOLUMES])
+def test_build_bit_exact(mg, name, make, S):
+    vol = make()
+    g, og = build_pair(mg, vol, S)
+    assert g.N == og.N and g.info["depth"] == og.D and g.info["levels"] == og.L
+    assert g.info["bucket"] == og.bucket.tolist()
+    assert g.info["max_list"] == og.max_nnz and g.info["pairs"] == og.pairs
+    p, q, a, b = mg.mg_graph_copy_nodes(g)
+    assert (p == og.p[: og.N]).all() and (q == og.q[: og.N]).all()
+    assert (a == og.a[: og.N]).all() and (b == og.b[: og.N]).all()
+    for level in range(og.L):
+        assert (mg.mg_graph_copy_mip(g, level) == og.mip(level)).all(), level
+    g.close()
+
+
+def test_build_uint32_ids(mg):
+    vol = synth.make_volume(1, dims=(33, 20, 17), S=70)
+    g = mg.mg_build(torch.from_numpy(vol.astype(np.int32)).to(dev()), 70)
+    og = oracle.Graph(vol, 70)
+    assert g.N == og.N
+    for level in range(og.L):
+        assert (mg.mg_graph_copy_mip(g, level) == og.mip(level)).all()
+
+
+def test_build_rejects_id_out_of_range(mg):
+    vol = synth.make_volume(1, dims=(16, 16, 16), S=10)
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_build(torch.from_numpy(vol).to(dev()), 9)
+    assert e.value.status == mg.MG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("C", [1, 3, 4, 16])
+def test_propagate_fp32(mg, C):
+    vol = synth.make_volume(1, dims=(37, 29, 23), S=24)
+    g, og = build_pair(mg, vol, 24)
+    tf = synth.make_tf(1, 24, C)
+    vals = mg.mg_propagate_tf(g, torch.from_numpy(tf).to(dev())).cpu().numpy()
+    ref = oracle.propagate(og.p, og.q, og.a, og.b, 24, tf.astype(np.float64))
+    ok, err = fp32_close(vals, ref)
+    assert ok, err
+    # every voxel's colour is the direct convex combination (Sec. 3.4)
+    for level in range(og.L):
+        direct = oracle.direct_colors(vol, level, tf.astype(np.float64))
+        ok, err = fp32_close(vals[og.mip(level).ravel()], direct)
+        assert ok, (level, err)
+
+
+@pytest.mark.parametrize("storage,u", [("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_propagate_16bit_storage_error_bound(mg, storage, u):
+    vol = synth.make_volume(1)
+    g, og = build_pair(mg, vol, 64)
+    tf = synth.make_tf(1, 64, 4)
+    vals = mg.mg_propagate_tf(g, torch.from_numpy(tf).to(dev()), storage=storage).float().cpu().numpy()
+    ref = oracle.propagate(og.p, og.q, og.a, og.b, 64, tf.astype(np.float64))
+    err = np.abs(vals - ref).max()
+    # each level rounds the stored value (u) and the stored weight (u)
+    bound = (2 * og.D + 1) * u
+    assert err <= bound, (err, bound)
+
+
+def _boxes_cfg1(Q=1000):
+    return synth.make_boxes(1, Q=Q)
+
+
+@pytest.mark.parametrize("schedule,chunk,threads", [("batched", 0, 0), ("batched", 64, 128), ("batched", 1000, 512),
+                                                    ("plain", 0, 0)])
+def test_query_u32_exact(mg, schedule, chunk, threads):
+    vol = synth.make_volume(1)
+    g = mg.mg_build(torch.from_numpy(vol).to(dev()), 64)
+    boxes = _boxes_cfg1(1000 if schedule == "batched" else 150)
+    h = mg.mg_query_boxes(g, torch.from_numpy(boxes).to(dev()), schedule=schedule, chunk_cubes=chunk,
+                          block_threads=threads).cpu().numpy()
+    mg.mg_sync_status(g)
+    ref = oracle.box_hist(vol, 64, boxes)
+    assert np.array_equal(h, ref)
+
+
+def test_query_csr_u32(mg):
+    vol = synth.make_volume(1, dims=(37, 29, 23), S=24)
+    g = mg.mg_build(torch.from_numpy(vol).to(dev()), 24)
+    boxes = synth.make_boxes(1, Q=300, dims=(37, 29, 23), box_max=40)
+    off, seg, val = mg.mg_query_boxes(g, torch.from_numpy(boxes).to(dev()), layout="csr")
+    off, seg, val = off.cpu().numpy(), seg.cpu().numpy(), val.cpu().numpy()
+    ref = oracle.box_hist(vol, 24, boxes)
+    for i in range(len(boxes)):
+        nzs = np.nonzero(ref[i])[0]
+        assert (seg[off[i]:off[i + 1]] == nzs).all()
+        assert (val[off[i]:off[i + 1]] == ref[i][nzs]).all()
+    # too small a capacity reports the size needed
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_query_boxes(g, torch.from_numpy(boxes).to(dev()), layout="csr", capacity=3)
+    assert e.value.status == mg.MG_ERR_CAPACITY
+
+
+@pytest.mark.parametrize("layout", ["dense", "csr"])
+def test_query_fp32(mg, layout):
+    vol = synth.make_volume(1)
+    g = mg.mg_build(torch.from_numpy(vol).to(dev()), 64)
+    boxes = _boxes_cfg1()
+    ref = oracle.box_hist(vol, 64, boxes).astype(np.float64)
+    if layout == "dense":
+        h = mg.mg_query_boxes(g, torch.from_numpy(boxes).to(dev()), hist="f32").cpu().numpy()
+    else:
+        off, seg, val = [t.cpu().numpy() for t in mg.mg_query_boxes(g, torch.from_numpy(boxes).to(dev()),
+                                                                     hist="f32", layout="csr")]
+        h = np.zeros_like(ref)
+        for i in range(len(boxes)):
+            h[i, seg[off[i]:off[i + 1]]] = val[off[i]:off[i + 1]]
+    ok, err = fp32_close(h, ref)
+    assert ok, err
+
+
+@pytest.mark.parametrize("alpha,u", [("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_query_16bit_weights_error_bound(mg, alpha, u):
+    vol = synth.make_volume(1)
+    g, og = build_pair(mg, vol, 64)
+    boxes = _boxes_cfg1(400)
+    ref = oracle.box_hist(vol, 64, boxes).astype(np.float64)
+    h = mg.mg_query_boxes(g, torch.from_numpy(boxes).to(dev()), hist="f32", alpha=alpha).cpu().numpy()
+    vol_q = np.prod(boxes[:, 3:].astype(np.float64), axis=1)
+    l1 = np.abs(h - ref).sum(axis=1)
+    # every pushed unit of weight crosses at most D rounded weights
+    assert (l1 <= 1.5 * og.D * u * vol_q + 1e-3).all(), float((l1 / vol_q).max())
+    assert np.allclose(h.sum(axis=1), vol_q, rtol=1e-5)
+
+
+def test_count_cubes(mg):
+    vol = synth.make_volume(1)
+    g = mg.mg_build(torch.from_numpy(vol).to(dev()), 64)
+    boxes = _boxes_cfg1(500)
+    c = mg.mg_count_cubes(g, torch.from_numpy(boxes).to(dev())).cpu().numpy()
+    ref = np.array([oracle.fa_count(b, 64, 64, 64) for b in boxes], np.uint64)
+    assert np.array_equal(c, ref)
+
+
+def test_query_edge_cases(mg):
+    vol = synth.make_volume(1, dims=(19, 13, 11), S=12)
+    g = mg.mg_build(torch.from_numpy(vol).to(dev()), 12)
+    boxes = np.array([[0, 0, 0, 19, 13, 11],      # whole volume
+                      [18, 12, 10, 1, 1, 1],      # last voxel
+                      [5, 3, 2, 100, 100, 100],   # clipped at the far faces
+                      [0, 0, 0, 1, 1, 1],
+                      [7, 0, 4, 1, 13, 1]], np.int32)
+    h = mg.mg_query_boxes(g, torch.from_numpy(boxes).to(dev())).cpu().numpy()
+    assert np.array_equal(h, oracle.box_hist(vol, 12, boxes))
+    # empty batch
+    e = mg.mg_query_boxes(g, torch.zeros((0, 6), dtype=torch.int32, device=dev()))
+    assert e.shape == (0, 12)
+    off, seg, val = mg.mg_query_boxes(g, torch.zeros((0, 6), dtype=torch.int32, device=dev()), layout="csr")
+    assert off.cpu().numpy().tolist() == [0]
+    # malformed boxes are reported through the status word, their rows stay zero
+    bad = np.array([[0, 0, 0, 2, 2, 2], [19, 0, 0, 1, 1, 1], [0, 0, 0, 0, 1, 1], [-1, 0, 0, 1, 1, 1]], np.int32)
+    h = mg.mg_query_boxes(g, torch.from_numpy(bad).to(dev())).cpu().numpy()
+    with pytest.raises(mg.MGError) as ei:
+        mg.mg_sync_status(g)
+    assert ei.value.status == mg.MG_ERR_INVALID_ARG
+    assert np.array_equal(h[0], oracle.box_hist(vol, 12, bad[:1])[0])
+    assert (h[1:] == 0).all()
+    mg.mg_sync_status(g)   # cleared
+
+
+def test_render_lookup(mg):
+    dims = (37, 29, 23)
+    vol = synth.make_volume(1, dims=dims, S=24)
+    g, og = build_pair(mg, vol, 24)
+    tf = synth.make_tf(1, 24, 4)
+    vals_t = mg.mg_propagate_tf(g, torch.from_numpy(tf).to(dev()))
+    smp = synth.make_samples(1, dims=dims, width=160, height=90)
+    smp[:7] = [[0, 0, 0, 0], [-3, 40, 1e9, 2.49], [np.nan, 5, 5, np.nan], [36.99, 28.99, 22.99, -1],
+               [18.5, 14.5, 11.5, 100], [36.5, 28.5, 22.5, 1.5], [1e-8, 1e-8, 1e-8, 0.5]]
+    out = mg.mg_render_lookup(g, vals_t, torch.from_numpy(smp).to(dev())).cpu().numpy()
+    vals = vals_t.cpu().numpy()
+    lev, vox = oracle.sample_voxels(og.dims, smp)
+    nodes = np.array([og.mip(int(l)).ravel()[v] for l, v in zip(lev, vox)])
+    assert np.array_equal(out, vals[nodes])
+    # and the colour is the direct convex combination of that voxel
+    direct = {l: oracle.direct_colors(vol, l, tf.astype(np.float64)) for l in set(lev.tolist())}
+    ref = np.stack([direct[int(l)][v] for l, v in zip(lev, vox)])
+    ok, err = fp32_close(out, ref)
+    assert ok, err
+    # bf16 values are copied bit for bit
+    vb = mg.mg_propagate_tf(g, torch.from_numpy(tf).to(dev()), storage="bf16")
+    ob = mg.mg_render_lookup(g, vb, torch.from_numpy(smp).to(dev()))
+    assert torch.equal(ob.cpu(), vb.cpu()[torch.from_numpy(nodes.astype(np.int64))])
+
+
+@pytest.mark.parametrize("cfg,dims,S", [(1, (64, 64, 64), 64), (2, (45, 33, 27), 40), (3, (48, 40, 20), 30)])
+def test_generators_agree(cfg, dims, S):
+    """The GPU volume generator reproduces the host generator bit for bit."""
+    host = synth.make_volume(cfg, dims=dims, S=S)
+    gpu = synth.make_volume(cfg, device="cuda", dims=dims, S=S).cpu().numpy()
+    assert np.array_equal(host, gpu)
