@@ -376,6 +376,8 @@ struct MainArgs {
     const uint64_t* blk_off;
     const uint64_t* ncube;
     const uint64_t* chunk_off;
+    const uint32_t* chunk_q;     // box of every chunk
+    unsigned long long total_chunks;
     int64_t Q;
     uint32_t chunk;
     unsigned long long* ticket;
@@ -383,68 +385,126 @@ struct MainArgs {
     float* accf;
 };
 
+constexpr int kQueue = 64;   // pending internal-node pushes per warp
+
+// push up to 32 queued (node, weight) entries, one per lane, then move the
+// rest to the front of the queue
+template <bool FP, typename AT>
+__device__ __forceinline__ void drain(const PushArgs& P, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
+                                      uint32_t& qc) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t take = min(qc, 32u);
+    if ((uint32_t)lane < take) {
+        const uint32_t n = qn[lane], w = qw[lane];
+        if constexpr (FP) push_frac<AT>(P, H, n, (float)w);
+        else push_int<FP>(P, H, n, w);
+    }
+    __syncwarp();
+    const uint32_t rest = qc - take;
+    uint32_t tn = 0, tw = 0;
+    if ((uint32_t)lane < rest) {
+        tn = qn[32 + lane];
+        tw = qw[32 + lane];
+    }
+    __syncwarp();
+    if ((uint32_t)lane < rest) {
+        qn[lane] = tn;
+        qw[lane] = tw;
+    }
+    __syncwarp();
+    qc = rest;
+}
+
 template <bool FP, typename AT>
 __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t s_ntouched;
     __shared__ unsigned long long s_chunk;
-    __shared__ int64_t s_q;
+    __shared__ uint32_t s_q;
     const uint32_t S = A.P.S;
     const Hist<FP> H = carve<FP>(smem, S, &s_ntouched);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // per-warp queues follow the touched list
+    const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
+    uint8_t* qbase = reinterpret_cast<uint8_t*>(H.touched) + ((touched_bytes + 15) & ~(size_t)15);
+    uint32_t* qn = reinterpret_cast<uint32_t*>(qbase) + warp * 2 * kQueue;
+    uint32_t* qw = qn + kQueue;
     for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
         H.h[i] = 0;
         if constexpr (FP) H.hf[i] = 0.f;
     }
     if (threadIdx.x == 0) s_ntouched = 0;
-    const unsigned long long total = A.chunk_off[A.Q];
-    const int lane = threadIdx.x & 31;
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned long long c = atomicAdd(A.ticket, 1ull);
             s_chunk = c;
-            if (c < total) {
-                // last box whose first chunk is <= c
-                int64_t lo = 0, hi = A.Q;   // chunk_off[lo] <= c < chunk_off[hi]
-                while (hi - lo > 1) {
-                    const int64_t mid = (lo + hi) >> 1;
-                    if (A.chunk_off[mid] <= c) lo = mid;
-                    else hi = mid;
-                }
-                s_q = lo;
-            }
+            if (c < A.total_chunks) s_q = A.chunk_q[c];
         }
         __syncthreads();
         const unsigned long long c = s_chunk;
-        if (c >= total) break;
+        if (c >= A.total_chunks) break;
         const int64_t q = s_q;
         const uint64_t c0 = (c - A.chunk_off[q]) * A.chunk;
         const uint64_t c1 = min(c0 + A.chunk, A.ncube[q]);
         const uint64_t b0 = A.blk_off[q], b1 = A.blk_off[q + 1];
-        for (uint64_t base = c0; base < c1; base += blockDim.x) {
-            const uint64_t cube = base + threadIdx.x;
-            const bool valid = cube < c1;
-            // the warp's first cube: binary search for its block
-            uint64_t bw = b0;
-            if (lane == 0) {
-                const uint64_t first = base + (threadIdx.x & ~31u);
-                uint64_t lo = b0, hi = b1;   // blk[lo].start <= first < blk[hi].start
+        // each warp takes a contiguous span of the chunk's cubes
+        const uint64_t span = (((c1 - c0) + nw - 1) / nw + 31) & ~31ull;
+        const uint64_t w0 = c0 + warp * span, w1 = min(w0 + span, c1);
+        if (w0 < w1) {
+            uint64_t b = b0;
+            if (lane == 0) {   // block of the span's first cube
+                uint64_t lo = b0, hi = b1;   // blk[lo].start <= w0 < blk[hi].start
                 while (hi - lo > 1) {
                     const uint64_t mid = (lo + hi) >> 1;
-                    if (__ldg(&A.blk[mid].start) <= first) lo = mid;
+                    if (__ldg(&A.blk[mid].start) <= w0) lo = mid;
                     else hi = mid;
                 }
-                bw = lo;
+                b = lo;
             }
-            bw = __shfl_sync(0xffffffffu, bw, 0);
-            uint32_t id = 0;
-            int l = 0;
-            if (valid) {
-                uint64_t bb = bw;
-                while (bb + 1 < b1 && __ldg(&A.blk[bb + 1].start) <= cube) bb++;
-                const Blk B = A.blk[bb];
-                id = cube_node(A.G, A.mip0, A.mip, B, (uint32_t)(cube - B.start), l);
+            b = __shfl_sync(0xffffffffu, b, 0);
+            uint32_t qc = 0;
+            const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);   // lanes <= this one
+            for (uint64_t base = w0; base < w1; base += 32) {
+                const uint64_t cube = base + lane;
+                const bool valid = cube < w1;
+                // block of every lane: lane k >= 1 marks where block b+k begins
+                uint32_t bit = 0;
+                if (lane > 0 && b + lane < b1) {
+                    const uint64_t t = (uint64_t)__ldg(&A.blk[b + lane].start) - base;
+                    if (t < 32) bit = 1u << t;
+                }
+                const unsigned M = __reduce_or_sync(0xffffffffu, bit);
+                uint32_t id = 0;
+                int l = 0;
+                if (valid) {
+                    const Blk B = A.blk[b + __popc(M & le)];
+                    id = cube_node(A.G, A.mip0, A.mip, B, (uint32_t)(cube - B.start), l);
+                }
+                // runs of equal (level, node) in adjacent lanes add once
+                const uint64_t key = valid ? ((uint64_t)l << 32 | id) : ~0ull;
+                const uint64_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+                const bool head = valid && (lane == 0 || key != prev);
+                const unsigned heads = __ballot_sync(0xffffffffu, head);
+                const int nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+                const unsigned after = heads & ~le;
+                const int end = min(after ? __ffs(after) - 1 : 32, nvalid);
+                const uint32_t W = (uint32_t)(end - lane) << (3 * l);
+                const bool internal = head && id >= S;
+                if (head && !internal) H.add_int(id, W);
+                const unsigned im = __ballot_sync(0xffffffffu, internal);
+                if (internal) {
+                    const uint32_t pos = qc + __popc(im & ((1u << lane) - 1u));
+                    qn[pos] = id;
+                    qw[pos] = W;
+                }
+                qc += __popc(im);
+                __syncwarp();
+                if (qc >= 32) drain<FP, AT>(A.P, H, qn, qw, qc);
+                // advance to the block of cube base + 32
+                b += __popc(M);
+                if (b + 1 < b1 && __ldg(&A.blk[b + 1].start) <= base + 32) b++;
             }
-            accumulate<FP, AT>(A.P, H, valid, id, l);
+            if (qc) drain<FP, AT>(A.P, H, qn, qw, qc);
         }
         __syncthreads();
         flush<FP>(H, S, q, A.acc, A.accf);
@@ -557,6 +617,13 @@ __global__ void csr_write_kernel(const uint32_t* __restrict__ acc, const float* 
         }
         pos += __popc(m);
     }
+}
+
+__global__ void chunk_map_kernel(const uint64_t* __restrict__ chunk_off, int64_t Q, uint32_t* __restrict__ chunk_q) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= Q) return;
+    for (uint64_t c = chunk_off[q] + lane; c < chunk_off[q + 1]; c += 32) chunk_q[c] = (uint32_t)q;
 }
 
 __global__ void widen_kernel(const uint32_t* __restrict__ a, uint64_t* __restrict__ b, int64_t n) {
@@ -677,11 +744,15 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
     A.blk_off = nullptr;
     A.ncube = nullptr;
     A.chunk_off = nullptr;
+    A.chunk_q = nullptr;
+    A.total_chunks = 0;
     A.ticket = nullptr;
 
-    const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + (size_t)S * 2 * (FP ? 2 : 1) + 16;
+    const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
+    const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + ((touched_bytes + 15) & ~(size_t)15) +
+                        (size_t)(threads / 32) * 2 * kQueue * 4 + 16;
     if (smem > 220 * 1024) return fail(MG_ERR_UNSUPPORTED, "too many segments for the shared-memory histogram");
-    Buf nblk, ncube, nchunk, blk_off, chunk_off, blk, ticket;
+    Buf nblk, ncube, nchunk, blk_off, chunk_off, blk, ticket, chunk_q;
     if (o.schedule == MG_SCHED_BATCHED) {
         MG_TRY(nblk.alloc(&al, (size_t)Q * 4, s));
         MG_TRY(ncube.alloc(&al, (size_t)Q * 8, s));
@@ -704,12 +775,19 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
             MG_TRY(scan_exclusive_u64(nb64.as<uint64_t>(), blk_off.as<uint64_t>(), Q, blk_off.as<uint64_t>() + Q, al,
                                       s));
         }
-        uint64_t nblocks = 0;
-        MG_CUDA(cudaMemcpyAsync(&nblocks, blk_off.as<uint64_t>() + Q, 8, cudaMemcpyDeviceToHost, s));
+        uint64_t totals[2] = {0, 0};   // blocks, chunks
+        MG_CUDA(cudaMemcpyAsync(&totals[0], blk_off.as<uint64_t>() + Q, 8, cudaMemcpyDeviceToHost, s));
+        MG_CUDA(cudaMemcpyAsync(&totals[1], chunk_off.as<uint64_t>() + Q, 8, cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaStreamSynchronize(s));
-        MG_TRY(blk.alloc(&al, (size_t)std::max<uint64_t>(nblocks, 1) * sizeof(Blk), s));
+        if (totals[1] >= (1ull << 32)) return fail(MG_ERR_UNSUPPORTED, "more than 2^32 work chunks");
+        MG_TRY(blk.alloc(&al, (size_t)std::max<uint64_t>(totals[0], 1) * sizeof(Blk), s));
+        MG_TRY(chunk_q.alloc(&al, (size_t)std::max<uint64_t>(totals[1], 1) * 4, s));
         plan_write_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>());
         MG_CUDA(cudaGetLastError());
+        chunk_map_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(chunk_off.as<uint64_t>(), Q, chunk_q.as<uint32_t>());
+        MG_CUDA(cudaGetLastError());
+        A.chunk_q = chunk_q.as<uint32_t>();
+        A.total_chunks = totals[1];
         MG_CUDA(cudaMemsetAsync(ticket.p, 0, 8, s));
         A.blk = blk.as<Blk>();
         A.blk_off = blk_off.as<uint64_t>();
