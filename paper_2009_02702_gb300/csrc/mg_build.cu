@@ -496,6 +496,26 @@ __global__ void weights_kernel(const ulonglong2* __restrict__ ab, int64_t N, uin
 }
 
 // ---------------------------------------------------------------------------
+// axis-major copies: copy 1 orders (y, z, x), copy 2 orders (z, x, y)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void transpose_copy_kernel(const T* __restrict__ src, T* __restrict__ dst, Dims3 d, int copy) {
+    const int64_t n = nvox(d);
+    const int32_t d0 = copy == 1 ? d.y : d.z, d1 = copy == 1 ? d.z : d.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = i % d0, r = i / d0;
+        const int64_t sc = r % d1, t = r / d1;
+        int64_t x, y, z;
+        if (copy == 1) {
+            y = f; z = sc; x = t;
+        } else {
+            z = f; x = sc; y = t;
+        }
+        dst[i] = src[(z * d.y + y) * d.x + x];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
 struct HostTable {
@@ -812,6 +832,26 @@ mg_status build_graph(mg_graph* g, const void* ids, int id_bytes, int64_t nx, in
     if (total_hi > 0) {
         remap_kernel<<<grid_n(total_hi), 256, 0, s>>>(g->mip.as<uint32_t>(), total_hi, canon.as<uint32_t>(), status);
         MG_CUDA(cudaGetLastError());
+    }
+    // axis-major copies for the query path
+    for (int c = 0; c < 2; c++) {
+        const Dims3 d0 = dims_of(0);
+        MG_TRY(g->mip0x[c].alloc(&al, (size_t)V0 * g->id0_bytes, s));
+        if (g->id0_bytes == 2)
+            transpose_copy_kernel<uint16_t><<<grid_n(V0), 256, 0, s>>>(g->mip0.as<uint16_t>(), g->mip0x[c].as<uint16_t>(),
+                                                                       d0, c + 1);
+        else
+            transpose_copy_kernel<uint32_t><<<grid_n(V0), 256, 0, s>>>(g->mip0.as<uint32_t>(), g->mip0x[c].as<uint32_t>(),
+                                                                       d0, c + 1);
+        MG_CUDA(cudaGetLastError());
+        if (total_hi > 0) {
+            MG_TRY(g->mipx[c].alloc(&al, (size_t)total_hi * 4, s));
+            for (int l = 1; l < L; l++) {
+                transpose_copy_kernel<uint32_t><<<grid_n(nvox(dims_of(l))), 256, 0, s>>>(
+                    g->mip.as<uint32_t>() + G.off[l], g->mipx[c].as<uint32_t>() + G.off[l], dims_of(l), c + 1);
+                MG_CUDA(cudaGetLastError());
+            }
+        }
     }
     MG_TRY(g->ab32.alloc(&al, (size_t)N * sizeof(uint2), s));
     MG_TRY(g->alpha.alloc(&al, (size_t)N * sizeof(float), s));

@@ -104,6 +104,12 @@ struct mg_graph {
     mg::Buf mip0;
     // levels 1..L-1 concatenated, uint32 node IDs
     mg::Buf mip;
+    // axis-major copies of the same IDs for box queries: copy 1 is y-fastest
+    // (order y, z, x), copy 2 is z-fastest (order z, x, y); copy 0 is the
+    // x-fastest array above.  A footprint block reads the copy whose fastest
+    // axis is its longest side.
+    mg::Buf mip0x[2];
+    mg::Buf mipx[2];
     // node table, canonical order, N entries
     mg::Buf pq;       // uint2 (p, q); (kNone, kNone) for sources
     mg::Buf ab;       // ulonglong2 (a, b) exact coprime weights

@@ -5,16 +5,21 @@
 // power-of-two runs (footprint_1d), count the blocks of the runs' tensor
 // product and the cubes tiling them (a block of run levels (lx, ly, lz) sits at
 // level l = min and holds 2^(lx-l) * 2^(ly-l) * 2^(lz-l) cubes), then write one
-// 12-byte record per block: first cube index, level-l origin, level and log2
-// extents.  Blocks follow Algorithm 1's loop order (z, y, x).
+// 12-byte record per block: first cube index, the index of its first cube in
+// the level's ID array, level, and log2 extents.  Blocks follow Algorithm 1's
+// loop order (z, y, x).  Every level is stored three times (x-, y- and
+// z-fastest); a block reads the copy whose fastest axis is its longest side,
+// so even a one-voxel-thick slab reads contiguous IDs.
 //
 // Main (persistent CTAs, MG_SCHED_BATCHED): a global ticket hands out chunks of
-// `chunk` consecutive cubes of one box.  Each thread takes a cube, finds its
-// block (per-warp binary search, then a short walk), reads the cube's node ID
-// from the level's ID array, and the warp merges equal (level, node) pairs
-// with __match_any_sync.  One lane per group adds the group weight
-// (count * 8^l): a source goes straight into the CTA's shared-memory
-// histogram; an internal node is pushed down its lerp tree (p gets
+// `chunk` consecutive cubes of one box; each warp of the CTA takes a
+// contiguous span of the chunk.  While 32 or more cubes of the current block
+// remain, the warp walks the block directly (one ID per lane, 32-bit index
+// arithmetic); the last few cubes of a block go with the next block's first
+// ones through a ballot that tells each lane its block.  Adjacent lanes with
+// the same (level, node) merge into one contribution of count * 8^l.  A
+// source adds it to the CTA's shared-memory histogram; an internal node is
+// queued per warp and pushed down its lerp tree 32 at a time (p gets
 // W*a/(a+b), q gets W*b/(a+b), exact u32 arithmetic) into the same histogram.
 // At the end of a chunk the touched bins are added to the box's row in global
 // memory -- the only global atomics.
@@ -41,12 +46,20 @@ struct Geom {
     uint32_t S;
     int32_t dims[MG_MAX_LEVELS][3];
     int64_t off[MG_MAX_LEVELS];
+    // strides of the second and third axis of each copy (copy 0: x, y, z;
+    // copy 1: y, z, x; copy 2: z, x, y)
+    uint32_t st1[MG_MAX_LEVELS][3], st2[MG_MAX_LEVELS][3];
+};
+
+struct Ids {
+    const void* l0[3];       // level 0 copies (uint16 or uint32)
+    const uint32_t* hi[3];   // levels >= 1 copies, concatenated at Geom::off
 };
 
 struct Blk {
     uint32_t start;   // first cube of the block within its box
-    uint16_t x, y, z; // origin in level-l voxels
-    uint16_t meta;    // l | ex << 4 | ey << 8 | ez << 12 (log2 extents in cubes)
+    uint32_t base;    // index of the block's first cube in its copy of level l
+    uint32_t meta;    // l | copy << 5 | e0 << 7 | e1 << 12 | e2 << 17 (log2 extents, copy axis order)
 };
 
 Geom make_geom(const mg_graph* g) {
@@ -57,8 +70,49 @@ Geom make_geom(const mg_graph* g) {
     for (int l = 0; l < MG_MAX_LEVELS; l++) {
         for (int k = 0; k < 3; k++) G.dims[l][k] = g->geom.dims[l][k];
         G.off[l] = g->geom.off[l];
+        const uint32_t dx = (uint32_t)G.dims[l][0], dy = (uint32_t)G.dims[l][1], dz = (uint32_t)G.dims[l][2];
+        G.st1[l][0] = dx; G.st2[l][0] = dx * dy;
+        G.st1[l][1] = dy; G.st2[l][1] = dy * dz;
+        G.st1[l][2] = dz; G.st2[l][2] = dz * dx;
     }
     return G;
+}
+
+Ids make_ids(const mg_graph* g) {
+    Ids I;
+    I.l0[0] = g->mip0.p;
+    I.l0[1] = g->mip0x[0].p;
+    I.l0[2] = g->mip0x[1].p;
+    I.hi[0] = g->mip.as<uint32_t>();
+    I.hi[1] = g->mipx[0].as<uint32_t>();
+    I.hi[2] = g->mipx[1].as<uint32_t>();
+    return I;
+}
+
+// block of run levels (lx, ly, lz) whose origin is the level-0 voxel (x0, y0, z0)
+__device__ __forceinline__ Blk make_blk(const Geom& G, uint32_t start, int32_t x0, int32_t y0, int32_t z0, int lx,
+                                        int ly, int lz) {
+    const int l = min(lx, min(ly, lz));
+    const int ex = lx - l, ey = ly - l, ez = lz - l;
+    const uint32_t X = (uint32_t)x0 >> l, Y = (uint32_t)y0 >> l, Z = (uint32_t)z0 >> l;
+    const uint32_t dx = (uint32_t)G.dims[l][0], dy = (uint32_t)G.dims[l][1], dz = (uint32_t)G.dims[l][2];
+    int c, e0, e1, e2;
+    uint32_t base;
+    if (ex >= ey && ex >= ez) {
+        c = 0; e0 = ex; e1 = ey; e2 = ez;
+        base = (Z * dy + Y) * dx + X;
+    } else if (ey >= ez) {
+        c = 1; e0 = ey; e1 = ez; e2 = ex;
+        base = (X * dz + Z) * dy + Y;
+    } else {
+        c = 2; e0 = ez; e1 = ex; e2 = ey;
+        base = (Y * dx + X) * dz + Z;
+    }
+    Blk B;
+    B.start = start;
+    B.base = base;
+    B.meta = (uint32_t)(l | c << 5 | e0 << 7 | e1 << 12 | e2 << 17);
+    return B;
 }
 
 // Algorithm 1, footprint_1d: aligned power-of-two steps covering [i, i+di)
@@ -171,16 +225,9 @@ __global__ void plan_write_kernel(Geom G, const int32_t* __restrict__ boxes, int
         if (valid) {
             uint32_t start = running + incl - row;
             for (int i = 0; i < R.nx; i++) {
-                const int lx = R.lx[i], ly = R.ly[j], lz = R.lz[k];
-                const int l = min(lx, min(ly, lz));
-                Blk r;
-                r.start = start;
-                r.x = (uint16_t)(R.sx[i] >> l);
-                r.y = (uint16_t)(R.sy[j] >> l);
-                r.z = (uint16_t)(R.sz[k] >> l);
-                r.meta = (uint16_t)(l | (lx - l) << 4 | (ly - l) << 8 | (lz - l) << 12);
-                blk[base + (uint64_t)pr * R.nx + i] = r;
-                start += 1u << (lx + ly + lz - 3 * l);
+                blk[base + (uint64_t)pr * R.nx + i] = make_blk(G, start, R.sx[i], R.sy[j], R.sz[k], R.lx[i], R.ly[j],
+                                                               R.lz[k]);
+                start += block_cubes(R.lx[i], R.ly[j], R.lz[k]);
             }
         }
         running += tot;
@@ -194,16 +241,30 @@ template <bool FP>
 struct Hist {
     uint32_t* h;        // S integer bins
     float* hf;          // S fractional bins (fp32 push)
-    uint16_t* touched;  // bins to flush
+    uint16_t* touched;  // bins to flush (when tracking)
     uint32_t* ntouched;
+    bool track;         // false: the flush scans all S bins, adds need no return value
 
     __device__ __forceinline__ void add_int(uint32_t s, uint32_t w) const {
-        if (atomicAdd(h + s, w) == 0u) touched[atomicAdd(ntouched, 1u)] = (uint16_t)s;
+        if (track) {
+            if (atomicAdd(h + s, w) == 0u) touched[atomicAdd(ntouched, 1u)] = (uint16_t)s;
+        } else {
+            atomicAdd(h + s, w);
+        }
     }
     __device__ __forceinline__ void add_frac(uint32_t s, float w) const {
-        if (atomicAdd(hf + s, w) == 0.f) touched[atomicAdd(ntouched, 1u)] = (uint16_t)s;
+        if (track) {
+            if (atomicAdd(hf + s, w) == 0.f) touched[atomicAdd(ntouched, 1u)] = (uint16_t)s;
+        } else {
+            atomicAdd(hf + s, w);
+        }
     }
 };
+
+// segment counts up to this are flushed by scanning every bin
+constexpr uint32_t kScanFlushMax = 2048;
+// segment counts up to this get one histogram per warp
+constexpr uint32_t kWarpHistMax = 2048;
 
 template <typename AT> struct AlphaCvt;
 template <> struct AlphaCvt<float> {
@@ -304,20 +365,21 @@ __device__ void push_frac(const PushArgs& P, const Hist<true>& H, uint32_t n, fl
     }
 }
 
-// read the node ID of cube (block b, offset o)
-__device__ __forceinline__ uint32_t cube_node(const Geom& G, const void* __restrict__ mip0,
-                                              const uint32_t* __restrict__ mip, const Blk& B, uint32_t o, int& l) {
-    l = B.meta & 15;
-    const int ex = (B.meta >> 4) & 15, ey = (B.meta >> 8) & 15;
-    const uint32_t u = o & ((1u << ex) - 1u);
-    const uint32_t v = (o >> ex) & ((1u << ey) - 1u);
-    const uint32_t w = o >> (ex + ey);
-    const int64_t X = B.x + u, Y = B.y + v, Z = B.z + w;
-    const int64_t idx = (Z * G.dims[l][1] + Y) * G.dims[l][0] + X;
+__device__ __forceinline__ uint32_t read_id(const Geom& G, const Ids& I, int l, int c, uint32_t idx) {
     if (l == 0)
-        return G.id0_bytes == 2 ? (uint32_t)__ldg(static_cast<const uint16_t*>(mip0) + idx)
-                                : __ldg(static_cast<const uint32_t*>(mip0) + idx);
-    return __ldg(mip + G.off[l] + idx);
+        return G.id0_bytes == 2 ? (uint32_t)__ldg(static_cast<const uint16_t*>(I.l0[c]) + idx)
+                                : __ldg(static_cast<const uint32_t*>(I.l0[c]) + idx);
+    return __ldg(I.hi[c] + G.off[l] + idx);
+}
+
+// node ID of cube o of block B
+__device__ __forceinline__ uint32_t cube_node(const Geom& G, const Ids& I, const Blk& B, uint32_t o, int& l) {
+    l = B.meta & 31;
+    const int c = (B.meta >> 5) & 3, e0 = (B.meta >> 7) & 31, e1 = (B.meta >> 12) & 31;
+    const uint32_t f = o & ((1u << e0) - 1u);
+    const uint32_t sc = (o >> e0) & ((1u << e1) - 1u);
+    const uint32_t t = o >> (e0 + e1);
+    return read_id(G, I, l, c, B.base + f + sc * G.st1[l][c] + t * G.st2[l][c]);
 }
 
 // one warp-aggregated contribution of cube node `id` at level l
@@ -345,6 +407,7 @@ __device__ __forceinline__ Hist<FP> carve(uint8_t* smem, uint32_t S, uint32_t* n
     H.touched = reinterpret_cast<uint16_t*>(FP ? reinterpret_cast<uint8_t*>(H.hf + S)
                                                : reinterpret_cast<uint8_t*>(H.h + S));
     H.ntouched = ntouched;
+    H.track = S > kScanFlushMax;
     return H;
 }
 
@@ -354,6 +417,23 @@ __device__ __forceinline__ void flush(const Hist<FP>& H, uint32_t S, int64_t q, 
     // With the fp32 push a bin can be listed twice (once when its integer part
     // and once when its fractional part became non-zero), so bins are read and
     // cleared in one atomic step: the second reader sees zero.
+    if (!H.track) {
+        for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
+            const uint32_t v = H.h[s];
+            if (v) {
+                H.h[s] = 0;
+                atomicAdd(acc + q * S + s, v);
+            }
+            if constexpr (FP) {
+                const float f = H.hf[s];
+                if (f != 0.f) {
+                    H.hf[s] = 0.f;
+                    atomicAdd(accf + q * S + s, f);
+                }
+            }
+        }
+        return;
+    }
     const uint32_t n = *H.ntouched;
     for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
         const uint32_t s = H.touched[t];
@@ -369,14 +449,14 @@ __device__ __forceinline__ void flush(const Hist<FP>& H, uint32_t S, int64_t q, 
 
 struct MainArgs {
     Geom G;
-    const void* mip0;
-    const uint32_t* mip;
+    Ids I;
     PushArgs P;
     const Blk* blk;
     const uint64_t* blk_off;
     const uint64_t* ncube;
     const uint64_t* chunk_off;
     const uint32_t* chunk_q;     // box of every chunk
+    const uint32_t* chunk_b;     // block holding every chunk's first cube
     unsigned long long total_chunks;
     int64_t Q;
     uint32_t chunk;
@@ -390,8 +470,8 @@ constexpr int kQueue = 64;   // pending internal-node pushes per warp
 // push up to 32 queued (node, weight) entries, one per lane, then move the
 // rest to the front of the queue
 template <bool FP, typename AT>
-__device__ __forceinline__ void drain(const PushArgs& P, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
-                                      uint32_t& qc) {
+__device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
+                                   uint32_t& qc) {
     const int lane = threadIdx.x & 31;
     const uint32_t take = min(qc, 32u);
     if ((uint32_t)lane < take) {
@@ -415,12 +495,208 @@ __device__ __forceinline__ void drain(const PushArgs& P, const Hist<FP>& H, uint
     qc = rest;
 }
 
+// lanes with `pred` add weight W to node `id`: a source into the shared
+// histogram, an internal node into the warp's push queue (drained at 32)
+template <bool FP, typename AT>
+__device__ __forceinline__ void add_heads(const PushArgs& P, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
+                                          uint32_t& qc, bool pred, uint32_t id, uint32_t W) {
+    const int lane = threadIdx.x & 31;
+    const bool internal = pred && id >= P.S;
+    if (pred && !internal) H.add_int(id, W);
+    const unsigned im = __ballot_sync(0xffffffffu, internal);
+    if (im) {
+        if (internal) {
+            const uint32_t pos = qc + __popc(im & ((1u << lane) - 1u));
+            qn[pos] = id;
+            qw[pos] = W;
+        }
+        qc += __popc(im);
+        __syncwarp();
+        if (qc >= 32) drain<FP, AT>(P, H, qn, qw, qc);
+    }
+}
+
+// contribution of one group of (up to) 32 cubes, one per lane; valid lanes
+// are a prefix.  Adjacent lanes with equal (level, node) add once.
+template <bool FP, typename AT>
+__device__ __forceinline__ void add_group(const PushArgs& P, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
+                                          uint32_t& qc, bool valid, uint32_t id, int l, unsigned le) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t pid = __shfl_up_sync(0xffffffffu, id, 1);
+    const int pl = __shfl_up_sync(0xffffffffu, l, 1);
+    const bool head = valid && (lane == 0 || id != pid || l != pl);
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const int nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+    const unsigned after = heads & ~le;
+    const int end = min(after ? __ffs(after) - 1 : 32, nvalid);
+    add_heads<FP, AT>(P, H, qn, qw, qc, head, id, (uint32_t)(end - lane) << (3 * l));
+}
+
+// groups of 32 consecutive cubes of one block, all lanes valid.  Every lane
+// keeps a run (node rid, rcnt cubes) of its own cubes -- lane i sees cubes
+// i, i+32, i+64, ..., which inside a segment carry the same node -- and adds
+// it only when its node changes.  Level-0 IDs are segments (sources, weight
+// 1 each), so that loop is a load, a compare and an increment per cube; at
+// higher levels a finished run may be an internal node, queued warp-wide.
+template <bool FP, typename AT, typename IT, bool L0>
+__device__ __forceinline__ void block_groups(const PushArgs& P, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
+                                             uint32_t& qc, const IT* __restrict__ ids, uint32_t o, uint32_t groups,
+                                             int e0, int e1, uint32_t s1, uint32_t s2, int l) {
+    const uint32_t m0 = (1u << e0) - 1u, m1 = (1u << e1) - 1u;
+    const int sh = e0 + e1, w3 = 3 * l;
+    uint32_t rid = kNone, rcnt = 0;
+    for (uint32_t gi = 0; gi < groups; gi += 4, o += 128) {
+        const uint32_t n4 = min(4u, groups - gi);
+        uint32_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t oo = o + 32u * u;
+            v[u] = (uint32_t)u < n4 ? (uint32_t)__ldg(ids + (oo & m0) + ((oo >> e0) & m1) * s1 + (oo >> sh) * s2)
+                                    : rid;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if ((uint32_t)u >= n4) break;
+            const uint32_t x = v[u];
+            const bool change = x != rid;
+            if constexpr (L0) {
+                if (change && rcnt) H.add_int(rid, rcnt);
+            } else {
+                add_heads<FP, AT>(P, H, qn, qw, qc, change && rcnt != 0, rid, rcnt << w3);
+            }
+            rcnt = change ? 1u : rcnt + 1u;
+            rid = x;
+        }
+    }
+    if constexpr (L0) {
+        if (rcnt) H.add_int(rid, rcnt);
+    } else {
+        add_heads<FP, AT>(P, H, qn, qw, qc, rcnt != 0, rid, rcnt << w3);
+    }
+}
+
+// cubes [w0, w1) of box q by one warp; b is the block holding cube w0.
+// Returns the block holding the last cube processed.
+template <bool FP, typename AT>
+__device__ __forceinline__ uint64_t process_span(const MainArgs& A, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
+                                                 uint32_t& qc, uint32_t w0, uint32_t w1, uint64_t b, uint64_t b1,
+                                                 uint32_t ncube, unsigned le) {
+    const int lane = threadIdx.x & 31;
+    uint32_t cur = w0;   // invariant: cube `cur` lies in block b
+    while (cur < w1) {
+        const Blk B = A.blk[b];
+        const uint32_t bend = b + 1 < b1 ? __ldg(&A.blk[b + 1].start) : ncube;
+        const uint32_t hi = min(bend, w1);
+        if (hi - cur >= 32) {
+            // whole groups of 32 cubes of block b
+            const int l = B.meta & 31, cp = (B.meta >> 5) & 3;
+            const int e0 = (B.meta >> 7) & 31, e1 = (B.meta >> 12) & 31;
+            const uint32_t groups = (hi - cur) >> 5;
+            const uint32_t o = cur - B.start + lane;
+            const uint32_t s1 = A.G.st1[l][cp], s2 = A.G.st2[l][cp];
+            if (l == 0 && A.G.id0_bytes == 2)
+                block_groups<FP, AT, uint16_t, true>(A.P, H, qn, qw, qc,
+                                                     static_cast<const uint16_t*>(A.I.l0[cp]) + B.base, o, groups, e0,
+                                                     e1, s1, s2, 0);
+            else if (l == 0)
+                block_groups<FP, AT, uint32_t, true>(A.P, H, qn, qw, qc,
+                                                     static_cast<const uint32_t*>(A.I.l0[cp]) + B.base, o, groups, e0,
+                                                     e1, s1, s2, 0);
+            else
+                block_groups<FP, AT, uint32_t, false>(A.P, H, qn, qw, qc, A.I.hi[cp] + A.G.off[l] + B.base, o, groups,
+                                                      e0, e1, s1, s2, l);
+            cur += groups << 5;
+            if (cur == bend && b + 1 < b1) b++;
+        } else {
+            // the next (up to) 32 cubes may span several blocks: lane k >= 1
+            // marks where block b+k begins, each lane counts the marks at or
+            // before it
+            const uint32_t cube = cur + lane;
+            const bool valid = cube < w1;
+            uint32_t bit = 0;
+            if (lane > 0 && b + lane < b1) {
+                const uint32_t t = __ldg(&A.blk[b + lane].start) - cur;
+                if (t < 32) bit = 1u << t;
+            }
+            const unsigned M = __reduce_or_sync(0xffffffffu, bit);
+            uint32_t id = 0;
+            int l = 0;
+            if (valid) {
+                const Blk Bl = A.blk[b + __popc(M & le)];
+                id = cube_node(A.G, A.I, Bl, cube - Bl.start, l);
+            }
+            add_group<FP, AT>(A.P, H, qn, qw, qc, valid, id, l, le);
+            b += __popc(M);   // block of cube cur + 31
+            cur = min(cur + 32, w1);
+            if (cur < w1 && b + 1 < b1 && __ldg(&A.blk[b + 1].start) <= cur) b++;
+        }
+    }
+    return b;
+}
+
+// Few segments: every warp owns a histogram in shared memory and takes whole
+// chunks from the global ticket, so warps never wait for each other.
+template <bool FP, typename AT>
+__global__ void __launch_bounds__(512) query_warp_kernel(MainArgs A) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint32_t S = A.P.S;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t per_warp = (size_t)S * 4 * (FP ? 2 : 1) + 2 * kQueue * 4;
+    uint8_t* mine = smem + warp * per_warp;
+    Hist<FP> H;
+    H.h = reinterpret_cast<uint32_t*>(mine);
+    H.hf = FP ? reinterpret_cast<float*>(H.h + S) : nullptr;
+    H.touched = nullptr;
+    H.ntouched = nullptr;
+    H.track = false;
+    uint32_t* qn = reinterpret_cast<uint32_t*>(mine + (size_t)S * 4 * (FP ? 2 : 1));
+    uint32_t* qw = qn + kQueue;
+    const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    for (uint32_t i = lane; i < S; i += 32) {
+        H.h[i] = 0;
+        if constexpr (FP) H.hf[i] = 0.f;
+    }
+    __syncwarp();
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(A.ticket, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= A.total_chunks) break;
+        const uint32_t q = __ldg(A.chunk_q + c);
+        const uint32_t ncube = (uint32_t)A.ncube[q];
+        const uint32_t c0 = (uint32_t)(c - A.chunk_off[q]) * A.chunk;
+        const uint32_t c1 = min(c0 + A.chunk, ncube);
+        uint32_t qc = 0;
+        process_span<FP, AT>(A, H, qn, qw, qc, c0, c1, __ldg(A.chunk_b + c), A.blk_off[q + 1], ncube, le);
+        if (qc) drain<FP, AT>(A.P, H, qn, qw, qc);
+        __syncwarp();
+        for (uint32_t s = lane; s < S; s += 32) {
+            const uint32_t v = H.h[s];
+            if (v) {
+                H.h[s] = 0;
+                atomicAdd(A.acc + (size_t)q * S + s, v);
+            }
+            if constexpr (FP) {
+                const float f = H.hf[s];
+                if (f != 0.f) {
+                    H.hf[s] = 0.f;
+                    atomicAdd(A.accf + (size_t)q * S + s, f);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Many segments: one histogram per CTA; the CTA takes a chunk and its warps
+// take sub-spans of it (about two each) from a shared counter.
 template <bool FP, typename AT>
 __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t s_ntouched;
     __shared__ unsigned long long s_chunk;
     __shared__ uint32_t s_q;
+    __shared__ uint32_t s_next;
     const uint32_t S = A.P.S;
     const Hist<FP> H = carve<FP>(smem, S, &s_ntouched);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -429,6 +705,7 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
     uint8_t* qbase = reinterpret_cast<uint8_t*>(H.touched) + ((touched_bytes + 15) & ~(size_t)15);
     uint32_t* qn = reinterpret_cast<uint32_t*>(qbase) + warp * 2 * kQueue;
     uint32_t* qw = qn + kQueue;
+    const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);   // lanes <= this one
     for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
         H.h[i] = 0;
         if constexpr (FP) H.hf[i] = 0.f;
@@ -438,22 +715,30 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
         if (threadIdx.x == 0) {
             const unsigned long long c = atomicAdd(A.ticket, 1ull);
             s_chunk = c;
+            s_next = 0;
             if (c < A.total_chunks) s_q = A.chunk_q[c];
         }
         __syncthreads();
         const unsigned long long c = s_chunk;
         if (c >= A.total_chunks) break;
-        const int64_t q = s_q;
-        const uint64_t c0 = (c - A.chunk_off[q]) * A.chunk;
-        const uint64_t c1 = min(c0 + A.chunk, A.ncube[q]);
-        const uint64_t b0 = A.blk_off[q], b1 = A.blk_off[q + 1];
-        // each warp takes a contiguous span of the chunk's cubes
-        const uint64_t span = (((c1 - c0) + nw - 1) / nw + 31) & ~31ull;
-        const uint64_t w0 = c0 + warp * span, w1 = min(w0 + span, c1);
-        if (w0 < w1) {
-            uint64_t b = b0;
-            if (lane == 0) {   // block of the span's first cube
-                uint64_t lo = b0, hi = b1;   // blk[lo].start <= w0 < blk[hi].start
+        const uint32_t q = s_q;
+        const uint32_t ncube = (uint32_t)A.ncube[q];
+        const uint32_t c0 = (uint32_t)(c - A.chunk_off[q]) * A.chunk;
+        const uint32_t c1 = min(c0 + A.chunk, ncube);
+        const uint64_t b1 = A.blk_off[q + 1];
+        const uint32_t sub = max(32u, (((c1 - c0) + 2 * nw - 1) / (2 * nw) + 31) & ~31u);
+        uint64_t bhint = __ldg(A.chunk_b + c);   // a warp's sub-spans only move forward
+        uint32_t qc = 0;
+        for (;;) {
+            uint32_t k = 0;
+            if (lane == 0) k = atomicAdd(&s_next, 1u);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if ((uint64_t)k * sub >= (uint64_t)(c1 - c0)) break;
+            const uint32_t w0 = c0 + k * sub;
+            const uint32_t w1 = min(w0 + sub, c1);
+            uint64_t b = bhint;
+            if (lane == 0) {   // block of the sub-span's first cube
+                uint64_t lo = bhint, hi = b1;   // blk[lo].start <= w0 < blk[hi].start
                 while (hi - lo > 1) {
                     const uint64_t mid = (lo + hi) >> 1;
                     if (__ldg(&A.blk[mid].start) <= w0) lo = mid;
@@ -462,50 +747,9 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
                 b = lo;
             }
             b = __shfl_sync(0xffffffffu, b, 0);
-            uint32_t qc = 0;
-            const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);   // lanes <= this one
-            for (uint64_t base = w0; base < w1; base += 32) {
-                const uint64_t cube = base + lane;
-                const bool valid = cube < w1;
-                // block of every lane: lane k >= 1 marks where block b+k begins
-                uint32_t bit = 0;
-                if (lane > 0 && b + lane < b1) {
-                    const uint64_t t = (uint64_t)__ldg(&A.blk[b + lane].start) - base;
-                    if (t < 32) bit = 1u << t;
-                }
-                const unsigned M = __reduce_or_sync(0xffffffffu, bit);
-                uint32_t id = 0;
-                int l = 0;
-                if (valid) {
-                    const Blk B = A.blk[b + __popc(M & le)];
-                    id = cube_node(A.G, A.mip0, A.mip, B, (uint32_t)(cube - B.start), l);
-                }
-                // runs of equal (level, node) in adjacent lanes add once
-                const uint64_t key = valid ? ((uint64_t)l << 32 | id) : ~0ull;
-                const uint64_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-                const bool head = valid && (lane == 0 || key != prev);
-                const unsigned heads = __ballot_sync(0xffffffffu, head);
-                const int nvalid = __popc(__ballot_sync(0xffffffffu, valid));
-                const unsigned after = heads & ~le;
-                const int end = min(after ? __ffs(after) - 1 : 32, nvalid);
-                const uint32_t W = (uint32_t)(end - lane) << (3 * l);
-                const bool internal = head && id >= S;
-                if (head && !internal) H.add_int(id, W);
-                const unsigned im = __ballot_sync(0xffffffffu, internal);
-                if (internal) {
-                    const uint32_t pos = qc + __popc(im & ((1u << lane) - 1u));
-                    qn[pos] = id;
-                    qw[pos] = W;
-                }
-                qc += __popc(im);
-                __syncwarp();
-                if (qc >= 32) drain<FP, AT>(A.P, H, qn, qw, qc);
-                // advance to the block of cube base + 32
-                b += __popc(M);
-                if (b + 1 < b1 && __ldg(&A.blk[b + 1].start) <= base + 32) b++;
-            }
-            if (qc) drain<FP, AT>(A.P, H, qn, qw, qc);
+            bhint = process_span<FP, AT>(A, H, qn, qw, qc, w0, w1, b, b1, ncube, le);
         }
+        if (qc) drain<FP, AT>(A.P, H, qn, qw, qc);
         __syncthreads();
         flush<FP>(H, S, q, A.acc, A.accf);
         __syncthreads();
@@ -540,21 +784,14 @@ __global__ void __launch_bounds__(256) query_plain_kernel(MainArgs A, const int3
     for (int k = 0; k < R.nz; k++)
         for (int j = 0; j < R.ny; j++)
             for (int i = 0; i < R.nx; i++) {
-                const int lx = R.lx[i], ly = R.ly[j], lz = R.lz[k];
-                const int l = min(lx, min(ly, lz));
-                Blk B;
-                B.start = 0;
-                B.x = (uint16_t)(R.sx[i] >> l);
-                B.y = (uint16_t)(R.sy[j] >> l);
-                B.z = (uint16_t)(R.sz[k] >> l);
-                B.meta = (uint16_t)(l | (lx - l) << 4 | (ly - l) << 8 | (lz - l) << 12);
-                const uint32_t n = 1u << (lx + ly + lz - 3 * l);
+                const Blk B = make_blk(A.G, 0, R.sx[i], R.sy[j], R.sz[k], R.lx[i], R.ly[j], R.lz[k]);
+                const uint32_t n = block_cubes(R.lx[i], R.ly[j], R.lz[k]);
                 for (uint32_t base = 0; base < n; base += blockDim.x) {
                     const uint32_t o = base + threadIdx.x;
                     const bool valid = o < n;
                     uint32_t id = 0;
                     int lv = 0;
-                    if (valid) id = cube_node(A.G, A.mip0, A.mip, B, o, lv);
+                    if (valid) id = cube_node(A.G, A.I, B, o, lv);
                     accumulate<FP, AT>(A.P, H, valid, id, lv);
                 }
             }
@@ -619,11 +856,25 @@ __global__ void csr_write_kernel(const uint32_t* __restrict__ acc, const float* 
     }
 }
 
-__global__ void chunk_map_kernel(const uint64_t* __restrict__ chunk_off, int64_t Q, uint32_t* __restrict__ chunk_q) {
+// box and first block of every chunk
+__global__ void chunk_map_kernel(const uint64_t* __restrict__ chunk_off, const uint64_t* __restrict__ blk_off,
+                                 const Blk* __restrict__ blk, int64_t Q, uint32_t chunk, uint32_t* __restrict__ chunk_q,
+                                 uint32_t* __restrict__ chunk_b) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (q >= Q) return;
-    for (uint64_t c = chunk_off[q] + lane; c < chunk_off[q + 1]; c += 32) chunk_q[c] = (uint32_t)q;
+    const uint64_t b0 = blk_off[q], b1 = blk_off[q + 1];
+    for (uint64_t c = chunk_off[q] + lane; c < chunk_off[q + 1]; c += 32) {
+        chunk_q[c] = (uint32_t)q;
+        const uint32_t first = (uint32_t)(c - chunk_off[q]) * chunk;
+        uint64_t lo = b0, hi = b1;   // blk[lo].start <= first < blk[hi].start
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (blk[mid].start <= first) lo = mid;
+            else hi = mid;
+        }
+        chunk_b[c] = (uint32_t)lo;
+    }
 }
 
 __global__ void widen_kernel(const uint32_t* __restrict__ a, uint64_t* __restrict__ b, int64_t n) {
@@ -658,13 +909,17 @@ mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts&
         MG_CUDA(cudaGetLastError());
         return MG_OK;
     }
-    auto k = query_batched_kernel<FP, AT>;
-    MG_TRY(prepare_kernel(k, smem));
+    // few segments: a private histogram per warp; else one per CTA
+    const size_t per_warp = (size_t)g->S * 4 * (FP ? 2 : 1) + 2 * kQueue * 4;
+    const bool warp_mode = g->S <= kWarpHistMax && per_warp * (threads / 32) <= 96 * 1024;
+    auto k = warp_mode ? query_warp_kernel<FP, AT> : query_batched_kernel<FP, AT>;
+    const size_t sm = warp_mode ? per_warp * (threads / 32) : smem;
+    MG_TRY(prepare_kernel(k, sm));
     int per_sm = 0;
-    MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
+    MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, sm));
     if (per_sm < 1) return fail(MG_ERR_UNSUPPORTED, "query kernel does not fit on an SM");
     const int grid = per_sm * sm_count(g->device);
-    k<<<grid, threads, smem, s>>>(A);
+    k<<<grid, threads, sm, s>>>(A);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
@@ -692,7 +947,7 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
         return MG_OK;
     }
     if (FP && o.alpha_dtype != MG_F32) MG_TRY(ensure_alpha16(const_cast<mg_graph*>(g), (mg_dtype)o.alpha_dtype, s));
-    const uint32_t chunk = o.chunk_cubes > 0 ? (uint32_t)o.chunk_cubes : 4096u;
+    const uint32_t chunk = o.chunk_cubes > 0 ? (uint32_t)o.chunk_cubes : 16384u;
     const int threads = o.block_threads > 0 ? o.block_threads : 256;
     const Geom G = make_geom(g);
     unsigned* status = g->status.as<unsigned>();
@@ -729,8 +984,7 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
 
     MainArgs A;
     A.G = G;
-    A.mip0 = g->mip0.p;
-    A.mip = g->mip.as<uint32_t>();
+    A.I = make_ids(g);
     A.P.pq = g->pq.as<uint2>();
     A.P.ab32 = g->ab32.as<uint2>();
     A.P.alpha = o.alpha_dtype == MG_F16 ? g->alpha16.p : o.alpha_dtype == MG_BF16 ? g->alphab16.p : g->alpha.p;
@@ -745,6 +999,7 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
     A.ncube = nullptr;
     A.chunk_off = nullptr;
     A.chunk_q = nullptr;
+    A.chunk_b = nullptr;
     A.total_chunks = 0;
     A.ticket = nullptr;
 
@@ -752,7 +1007,7 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
     const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + ((touched_bytes + 15) & ~(size_t)15) +
                         (size_t)(threads / 32) * 2 * kQueue * 4 + 16;
     if (smem > 220 * 1024) return fail(MG_ERR_UNSUPPORTED, "too many segments for the shared-memory histogram");
-    Buf nblk, ncube, nchunk, blk_off, chunk_off, blk, ticket, chunk_q;
+    Buf nblk, ncube, nchunk, blk_off, chunk_off, blk, ticket, chunk_q, chunk_b;
     if (o.schedule == MG_SCHED_BATCHED) {
         MG_TRY(nblk.alloc(&al, (size_t)Q * 4, s));
         MG_TRY(ncube.alloc(&al, (size_t)Q * 8, s));
@@ -779,14 +1034,19 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
         MG_CUDA(cudaMemcpyAsync(&totals[0], blk_off.as<uint64_t>() + Q, 8, cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaMemcpyAsync(&totals[1], chunk_off.as<uint64_t>() + Q, 8, cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaStreamSynchronize(s));
-        if (totals[1] >= (1ull << 32)) return fail(MG_ERR_UNSUPPORTED, "more than 2^32 work chunks");
+        if (totals[0] >= (1ull << 32) || totals[1] >= (1ull << 32))
+            return fail(MG_ERR_UNSUPPORTED, "more than 2^32 footprint blocks or work chunks in one call");
         MG_TRY(blk.alloc(&al, (size_t)std::max<uint64_t>(totals[0], 1) * sizeof(Blk), s));
         MG_TRY(chunk_q.alloc(&al, (size_t)std::max<uint64_t>(totals[1], 1) * 4, s));
+        MG_TRY(chunk_b.alloc(&al, (size_t)std::max<uint64_t>(totals[1], 1) * 4, s));
         plan_write_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>());
         MG_CUDA(cudaGetLastError());
-        chunk_map_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(chunk_off.as<uint64_t>(), Q, chunk_q.as<uint32_t>());
+        chunk_map_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(chunk_off.as<uint64_t>(), blk_off.as<uint64_t>(),
+                                                               blk.as<Blk>(), Q, chunk, chunk_q.as<uint32_t>(),
+                                                               chunk_b.as<uint32_t>());
         MG_CUDA(cudaGetLastError());
         A.chunk_q = chunk_q.as<uint32_t>();
+        A.chunk_b = chunk_b.as<uint32_t>();
         A.total_chunks = totals[1];
         MG_CUDA(cudaMemsetAsync(ticket.p, 0, 8, s));
         A.blk = blk.as<Blk>();
