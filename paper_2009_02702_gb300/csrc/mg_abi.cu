@@ -86,6 +86,54 @@ void Buf::release() {
     bytes = 0;
 }
 
+namespace {
+void* arena_alloc(void* ctx, size_t bytes, mg_stream s) {
+    Arena* a = static_cast<Arena*>(ctx);
+    const size_t n = (bytes + 255) & ~(size_t)255;
+    if (a->buf.p && a->used + n <= a->buf.bytes) {
+        void* p = static_cast<char*>(a->buf.p) + a->used;
+        a->used += n;
+        if (a->used > a->need) a->need = a->used;
+        return p;
+    }
+    if (a->used + n > a->need) a->need = a->used + n;
+    return a->fallback->get(bytes, reinterpret_cast<cudaStream_t>(s));
+}
+
+void arena_free(void* ctx, void* p, size_t bytes, mg_stream s) {
+    Arena* a = static_cast<Arena*>(ctx);
+    char* lo = static_cast<char*>(a->buf.p);
+    if (lo && static_cast<char*>(p) >= lo && static_cast<char*>(p) < lo + a->buf.bytes) return;
+    a->fallback->put(p, bytes, reinterpret_cast<cudaStream_t>(s));
+}
+}  // namespace
+
+mg_status arena_begin(mg_graph* g, cudaStream_t s, Arena** out) {
+    std::lock_guard<std::mutex> lk(g->arena_mu);
+    auto& slot = g->arenas[s];
+    if (!slot) {
+        slot.reset(new (std::nothrow) Arena());
+        if (!slot) return fail(MG_ERR_OOM, "host allocation failed");
+        slot->fallback = &g->al;
+        slot->view.a.ctx = slot.get();
+        slot->view.a.alloc = arena_alloc;
+        slot->view.a.free = arena_free;
+        slot->view.custom = true;
+        if (cudaMallocHost(&slot->pinned, 8 * sizeof(uint64_t)) != cudaSuccess) {
+            cudaGetLastError();
+            slot->pinned = nullptr;
+        }
+    }
+    Arena* a = slot.get();
+    if (a->need > a->buf.bytes) {
+        a->buf.release();   // stream-ordered after the previous call on s
+        MG_TRY(a->buf.alloc(&g->al, a->need + a->need / 4, s));
+    }
+    a->used = 0;
+    *out = a;
+    return MG_OK;
+}
+
 mg_status sync_status(mg_graph* g, cudaStream_t s) {
     MG_CUDA(cudaStreamSynchronize(s));
     unsigned bits = 0;
@@ -149,6 +197,7 @@ MG_API mg_status mg_build(const void* ids, int64_t nx, int64_t ny, int64_t nz, u
         return st;
     }
     g->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+
     // graph buffers are released on the legacy stream after a device sync
     for (Buf* b : {&g->mip0, &g->mip, &g->mip0x[0], &g->mip0x[1], &g->mipx[0], &g->mipx[1], &g->pq, &g->ab,
                    &g->ab32, &g->alpha, &g->status})
@@ -318,6 +367,7 @@ MG_API void mg_free(mg_graph* g) {
     if (!g) return;
     DeviceGuard dg(g->device);
     cudaDeviceSynchronize();
+    for (auto& kv : g->arenas) kv.second->buf.s = nullptr;   // the device is idle; the call streams may be gone
     delete g;
 }
 

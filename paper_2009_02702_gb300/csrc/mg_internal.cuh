@@ -6,6 +6,9 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstddef>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <string>
 
 #include "mg.h"
@@ -76,6 +79,21 @@ struct Buf {
     template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Scratch arena for the calls made on one stream: bump allocation from one
+// buffer, reset at the start of every call.  What does not fit comes from the
+// graph's allocator; the next call on the stream grows the buffer to the
+// high-water mark.  Calls on one stream run in order, so reuse is safe.
+struct Arena {
+    Buf buf;
+    size_t used = 0, need = 0;
+    const Alloc* fallback = nullptr;
+    Alloc view;                  // an Alloc whose alloc/free go through this arena
+    uint64_t* pinned = nullptr;  // 8 pinned host words for readbacks on this stream
+    ~Arena() {
+        if (pinned) cudaFreeHost(pinned);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // the graph
 // ---------------------------------------------------------------------------
@@ -118,6 +136,9 @@ struct mg_graph {
     mg::Buf alpha16;  // lazily: signed __half alpha, swap flag in the sign
     mg::Buf alphab16; // lazily: signed __nv_bfloat16 alpha, swap flag in the sign
     mg::Buf status;   // unsigned int status word
+    // per-stream scratch arenas of query calls
+    std::mutex arena_mu;
+    std::map<cudaStream_t, std::unique_ptr<mg::Arena>> arenas;
     // events of the last timed query call: plan start, main start, main end, output end
     cudaEvent_t qev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool qev_valid = false;
@@ -154,6 +175,8 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
                       void* out, size_t cap, uint32_t* seg, uint64_t* offsets, size_t* required,
                       cudaStream_t s);
 mg_status query_timing(const mg_graph* g, float* plan_ms, float* main_ms, float* out_ms);
+// the arena of `s` on graph g, reset for a new call (grown if the last call overflowed)
+mg_status arena_begin(mg_graph* g, cudaStream_t s, Arena** out);
 mg_status count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64_t* cubes,
                       cudaStream_t s);
 mg_status render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dt, const float* samples,

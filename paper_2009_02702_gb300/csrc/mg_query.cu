@@ -911,7 +911,7 @@ mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts&
     }
     // few segments: a private histogram per warp; else one per CTA
     const size_t per_warp = (size_t)g->S * 4 * (FP ? 2 : 1) + 2 * kQueue * 4;
-    const bool warp_mode = g->S <= kWarpHistMax && per_warp * (threads / 32) <= 96 * 1024;
+    const bool warp_mode = g->S <= kWarpHistMax && threads <= 256 && per_warp * (threads / 32) <= 96 * 1024;
     auto k = warp_mode ? query_warp_kernel<FP, AT> : query_batched_kernel<FP, AT>;
     const size_t sm = warp_mode ? per_warp * (threads / 32) : smem;
     MG_TRY(prepare_kernel(k, sm));
@@ -936,7 +936,9 @@ mg_status count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64
 
 mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const mg_query_opts& o, void* out,
                       size_t cap, uint32_t* seg, uint64_t* offsets, size_t* required, cudaStream_t s) {
-    const Alloc& al = g->al;
+    Arena* arena = nullptr;
+    MG_TRY(arena_begin(const_cast<mg_graph*>(g), s, &arena));
+    const Alloc& al = arena->view;
     const uint32_t S = g->S;
     const bool FP = o.hist_type == MG_HIST_F32;
     const bool csr = o.layout == MG_LAYOUT_CSR;
@@ -947,7 +949,7 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
         return MG_OK;
     }
     if (FP && o.alpha_dtype != MG_F32) MG_TRY(ensure_alpha16(const_cast<mg_graph*>(g), (mg_dtype)o.alpha_dtype, s));
-    const uint32_t chunk = o.chunk_cubes > 0 ? (uint32_t)o.chunk_cubes : 16384u;
+    const uint32_t chunk = o.chunk_cubes > 0 ? (uint32_t)o.chunk_cubes : 2048u;
     const int threads = o.block_threads > 0 ? o.block_threads : 256;
     const Geom G = make_geom(g);
     unsigned* status = g->status.as<unsigned>();
@@ -1030,7 +1032,8 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
             MG_TRY(scan_exclusive_u64(nb64.as<uint64_t>(), blk_off.as<uint64_t>(), Q, blk_off.as<uint64_t>() + Q, al,
                                       s));
         }
-        uint64_t totals[2] = {0, 0};   // blocks, chunks
+        uint64_t local[2] = {0, 0};
+        uint64_t* totals = arena->pinned ? arena->pinned : local;   // blocks, chunks
         MG_CUDA(cudaMemcpyAsync(&totals[0], blk_off.as<uint64_t>() + Q, 8, cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaMemcpyAsync(&totals[1], chunk_off.as<uint64_t>() + Q, 8, cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaStreamSynchronize(s));
@@ -1085,9 +1088,11 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
         csr_count_kernel<false><<<grid_for(Q * 32, 256), 256, 0, s>>>(acc, accf, Q, S, cnt.as<uint64_t>());
     MG_CUDA(cudaGetLastError());
     MG_TRY(scan_exclusive_u64(cnt.as<uint64_t>(), offsets, Q, offsets + Q, al, s));
-    uint64_t nnz = 0;
-    MG_CUDA(cudaMemcpyAsync(&nnz, offsets + Q, 8, cudaMemcpyDeviceToHost, s));
+    uint64_t nnz_local = 0;
+    uint64_t* nnz_p = arena->pinned ? arena->pinned + 2 : &nnz_local;
+    MG_CUDA(cudaMemcpyAsync(nnz_p, offsets + Q, 8, cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaStreamSynchronize(s));
+    const uint64_t nnz = *nnz_p;
     if (required) *required = (size_t)nnz;
     if (nnz > cap) return fail(MG_ERR_CAPACITY, "CSR output needs " + std::to_string(nnz) + " entries");
     if (FP)
