@@ -193,6 +193,30 @@ MG_API mg_status mg_query_boxes(const mg_graph *g, const int32_t *boxes, int64_t
                                 uint32_t *seg, uint64_t *offsets, size_t *out_required,
                                 mg_stream stream);
 
+/*
+ * mg_query_boxes_noalloc -- the exact box histograms of mg_query_boxes
+ * (uint32 counts, dense Q x S layout, batched schedule, default tuning) for
+ * callers that must not allocate device memory: real-time frame loops that
+ * cannot absorb an allocation's latency or failure in the middle of a frame,
+ * engines whose memory manager reserves the whole device up front and lets no
+ * library allocate, and services held to a fixed memory budget.  The paper has
+ * no counterpart; this is a deployment aid.
+ * Its scratch is a 64 MiB array compiled into the library (every GPU that
+ * loads libmg holds it until the process exits), so the call allocates
+ * nothing.  A batch must fit it: up to about 500,000 boxes, and footprint
+ * blocks and chunks of at most 32 MiB (12 bytes per block, 8 per chunk);
+ * larger batches return MG_ERR_CAPACITY before any histogram is written, with
+ * the limit in mg_last_error() -- split them.
+ * The first call on a device looks up the array's device address (so make
+ * it before any stream capture).  All calls share the one array and leave
+ * their scratch in it: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.
+ * out: Q x S uint32, fully overwritten.  Synchronises `stream` once (the
+ * footprint size depends on the boxes).  Errors as for mg_query_boxes.
+ */
+MG_API mg_status mg_query_boxes_noalloc(const mg_graph *g, const int32_t *boxes, int64_t Q, uint32_t *out,
+                                        size_t out_capacity, mg_stream stream);
+
 /* Stage durations of the last mg_query_boxes call on this graph made with
  * opts->timing set: plan (footprint plan and scans), main (the histogram
  * kernel or, for MG_SCHED_PLAIN, all per-box launches) and output (dense fp32

@@ -934,11 +934,13 @@ mg_status count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64
     return MG_OK;
 }
 
-mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const mg_query_opts& o, void* out,
-                      size_t cap, uint32_t* seg, uint64_t* offsets, size_t* required, cudaStream_t s) {
-    Arena* arena = nullptr;
-    MG_TRY(arena_begin(const_cast<mg_graph*>(g), s, &arena));
-    const Alloc& al = arena->view;
+namespace {
+
+// Scratch comes from `al`; `words` are two host words for readbacks; `room`,
+// when not null, returns the bytes `al` can still hand out (fixed pools).
+mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, const mg_query_opts& o, void* out,
+                           size_t cap, uint32_t* seg, uint64_t* offsets, size_t* required, cudaStream_t s,
+                           const Alloc& al, uint64_t* words, size_t (*room)(const Alloc&)) {
     const uint32_t S = g->S;
     const bool FP = o.hist_type == MG_HIST_F32;
     const bool csr = o.layout == MG_LAYOUT_CSR;
@@ -1032,13 +1034,20 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
             MG_TRY(scan_exclusive_u64(nb64.as<uint64_t>(), blk_off.as<uint64_t>(), Q, blk_off.as<uint64_t>() + Q, al,
                                       s));
         }
-        uint64_t local[2] = {0, 0};
-        uint64_t* totals = arena->pinned ? arena->pinned : local;   // blocks, chunks
+        uint64_t* totals = words;   // blocks, chunks
         MG_CUDA(cudaMemcpyAsync(&totals[0], blk_off.as<uint64_t>() + Q, 8, cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaMemcpyAsync(&totals[1], chunk_off.as<uint64_t>() + Q, 8, cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaStreamSynchronize(s));
         if (totals[0] >= (1ull << 32) || totals[1] >= (1ull << 32))
             return fail(MG_ERR_UNSUPPORTED, "more than 2^32 footprint blocks or work chunks in one call");
+        if (room) {
+            const size_t need = (((size_t)std::max<uint64_t>(totals[0], 1) * sizeof(Blk) + 255) & ~(size_t)255) +
+                                2 * (((size_t)std::max<uint64_t>(totals[1], 1) * 4 + 255) & ~(size_t)255);
+            if (need > room(al))
+                return fail(MG_ERR_CAPACITY, "these boxes need " + std::to_string(need >> 10) +
+                                                 " KiB of footprint scratch; " + std::to_string(room(al) >> 10) +
+                                                 " KiB of the fixed scratch remain: split the batch");
+        }
         MG_TRY(blk.alloc(&al, (size_t)std::max<uint64_t>(totals[0], 1) * sizeof(Blk), s));
         MG_TRY(chunk_q.alloc(&al, (size_t)std::max<uint64_t>(totals[1], 1) * 4, s));
         MG_TRY(chunk_b.alloc(&al, (size_t)std::max<uint64_t>(totals[1], 1) * 4, s));
@@ -1088,8 +1097,7 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
         csr_count_kernel<false><<<grid_for(Q * 32, 256), 256, 0, s>>>(acc, accf, Q, S, cnt.as<uint64_t>());
     MG_CUDA(cudaGetLastError());
     MG_TRY(scan_exclusive_u64(cnt.as<uint64_t>(), offsets, Q, offsets + Q, al, s));
-    uint64_t nnz_local = 0;
-    uint64_t* nnz_p = arena->pinned ? arena->pinned + 2 : &nnz_local;
+    uint64_t* nnz_p = words;
     MG_CUDA(cudaMemcpyAsync(nnz_p, offsets + Q, 8, cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaStreamSynchronize(s));
     const uint64_t nnz = *nnz_p;
@@ -1107,6 +1115,17 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
     return MG_OK;
 }
 
+}  // namespace
+
+mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const mg_query_opts& o, void* out,
+                      size_t cap, uint32_t* seg, uint64_t* offsets, size_t* required, cudaStream_t s) {
+    Arena* arena = nullptr;
+    MG_TRY(arena_begin(const_cast<mg_graph*>(g), s, &arena));
+    uint64_t local[2] = {0, 0};
+    return query_boxes_impl(g, boxes, Q, o, out, cap, seg, offsets, required, s, arena->view,
+                            arena->pinned ? arena->pinned : local, nullptr);
+}
+
 mg_status query_timing(const mg_graph* g, float* plan_ms, float* main_ms, float* out_ms) {
     if (!g->qev_valid) return fail(MG_ERR_INVALID_ARG, "no timed query call on this graph");
     MG_CUDA(cudaEventSynchronize(g->qev[3]));
@@ -1119,3 +1138,104 @@ mg_status query_timing(const mg_graph* g, float* plan_ms, float* main_ms, float*
 }
 
 }  // namespace mg
+
+// ---------------------------------------------------------------------------
+// Box histograms for callers that cannot allocate device memory: the same
+// exact dense query with its scratch in a fixed array compiled into the
+// library instead of memory from the allocator.
+// ---------------------------------------------------------------------------
+namespace mg {
+namespace {
+
+// Fixed scratch of mg_query_boxes_noalloc.  Every GPU that loads the library
+// holds these 64 MiB until the process exits.
+constexpr size_t kNoAllocBytes = 64ull << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};   // device address of the array, per device
+
+// Host code only knows a stand-in for the array's name; the device address is
+// looked up once per device, with that device current.
+mg_status noalloc_scratch(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= 256) return fail(MG_ERR_UNSUPPORTED, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(fixed query scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    return MG_OK;
+}
+
+// bump allocation from the fixed array for one call
+struct Pool {
+    unsigned char* base;
+    size_t cap, used;
+};
+
+void* pool_alloc(void* ctx, size_t bytes, mg_stream) {
+    Pool* pl = static_cast<Pool*>(ctx);
+    const size_t n = (bytes + 255) & ~(size_t)255;
+    if (pl->used + n > pl->cap) return nullptr;
+    void* p = pl->base + pl->used;
+    pl->used += n;
+    return p;
+}
+
+void pool_free(void*, void*, size_t, mg_stream) {}
+
+size_t pool_room(const Alloc& al) {
+    const Pool* pl = static_cast<const Pool*>(al.a.ctx);
+    return pl->cap - pl->used;
+}
+
+size_t rounded(size_t n) { return (n + 255) & ~(size_t)255; }
+
+// scratch of the per-box plan arrays and their scans, before the footprint blocks
+size_t per_box_scratch(int64_t Q) {
+    const size_t q = (size_t)Q;
+    const size_t parts = rounded(8 * ((q + 2047) / 2048)) * 2;   // one scan level's partial sums
+    return rounded(4 * q) + 5 * rounded(8 * (q + 1)) + rounded(8) + 2 * (parts + 2 * rounded(8)) + 4096;
+}
+
+}  // namespace
+}  // namespace mg
+
+extern "C" MG_API mg_status mg_query_boxes_noalloc(const mg_graph* g, const int32_t* boxes, int64_t Q, uint32_t* out,
+                                                   size_t out_capacity, mg_stream stream) {
+    using namespace mg;
+    if (!g) return fail(MG_ERR_INVALID_ARG, "graph is NULL");
+    if (Q < 0) return fail(MG_ERR_INVALID_ARG, "Q must be >= 0");
+    if (Q == 0) return MG_OK;
+    if (!boxes || !out) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    if ((uint64_t)out_capacity < (uint64_t)Q * g->S) return fail(MG_ERR_INVALID_ARG, "out_capacity must be >= Q*S");
+    if (g->S > kMaxSharedSegments) return fail(MG_ERR_UNSUPPORTED, "more than 32768 segments");
+    if (per_box_scratch(Q) > kNoAllocBytes / 2) {
+        int64_t qmax = 1;
+        while (per_box_scratch(qmax * 2) <= kNoAllocBytes / 2) qmax *= 2;
+        return fail(MG_ERR_CAPACITY, "at most about " + std::to_string(qmax) +
+                                         " boxes fit the fixed query scratch in one call: split the batch");
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != g->device) MG_CUDA(cudaSetDevice(g->device));
+    unsigned char* base = nullptr;
+    mg_status st = noalloc_scratch(g->device, &base);
+    if (st == MG_OK) {
+        Pool pool{base, kNoAllocBytes, 0};
+        Alloc al;
+        al.a.ctx = &pool;
+        al.a.alloc = pool_alloc;
+        al.a.free = pool_free;
+        al.custom = true;
+        mg_query_opts o{};   // exact uint32 counts, dense, batched, default tuning
+        uint64_t words[2] = {0, 0};
+        st = query_boxes_impl(g, boxes, Q, o, out, out_capacity, nullptr, nullptr, nullptr,
+                              reinterpret_cast<cudaStream_t>(stream), al, words, pool_room);
+    }
+    if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
+    return st;
+}

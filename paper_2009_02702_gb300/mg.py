@@ -31,7 +31,7 @@ _TORCH_TO_MG = {torch.float32: MG_F32, torch.float16: MG_F16, torch.bfloat16: MG
 
 # names of every symbol include/mg.h declares (checked by the CPU tests)
 EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_copy_mip", "mg_propagate_tf",
-           "mg_query_boxes", "mg_query_timing", "mg_count_cubes", "mg_render_lookup", "mg_sync_status", "mg_free",
+           "mg_query_boxes", "mg_query_boxes_noalloc", "mg_query_timing", "mg_count_cubes", "mg_render_lookup", "mg_sync_status", "mg_free",
            "mg_last_error", "mg_version")
 
 
@@ -94,6 +94,8 @@ def lib():
         L.mg_query_boxes.argtypes = [P, P, i64, ctypes.POINTER(mg_query_opts), P, ctypes.c_size_t, P, P,
                                      ctypes.POINTER(ctypes.c_size_t), P]
         L.mg_query_boxes.restype = st
+        L.mg_query_boxes_noalloc.argtypes = [P, P, i64, P, ctypes.c_size_t, P]
+        L.mg_query_boxes_noalloc.restype = st
         L.mg_query_timing.argtypes = [P, P, P, P]
         L.mg_query_timing.restype = st
         L.mg_count_cubes.argtypes = [P, P, i64, P, P]
@@ -302,6 +304,20 @@ def mg_query_boxes(g: Graph, boxes: torch.Tensor, hist: str = "u32", layout: str
         n = int(req.value)
         return offsets, seg[:n], vals[:n]
     raise MGError(MG_ERR_CAPACITY, mg_last_error())
+
+
+def mg_query_boxes_noalloc(g: Graph, boxes: torch.Tensor, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """Exact dense (Q, S) uint32 histograms with the library's fixed scratch:
+    for callers that must not allocate device memory (the output is theirs)."""
+    if not boxes.is_cuda or boxes.dtype != torch.int32 or boxes.dim() != 2 or boxes.shape[1] != 6:
+        raise ValueError("boxes must be a CUDA int32 tensor of shape (Q, 6)")
+    boxes = boxes.contiguous()
+    Q = boxes.shape[0]
+    if out is None:
+        out = torch.empty((Q, g.S), dtype=torch.uint32, device=boxes.device)
+    _check(lib().mg_query_boxes_noalloc(g.handle, boxes.data_ptr(), Q, out.data_ptr(), out.numel(),
+                                        _stream(stream)))
+    return out
 
 
 def mg_query_timing(g: Graph):
