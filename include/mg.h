@@ -150,14 +150,16 @@ MG_API mg_status mg_propagate_tf(mg_graph *g, const float *tf, int C, mg_dtype s
 /* Query output forms. */
 typedef enum { MG_HIST_U32 = 0, MG_HIST_F32 = 1 } mg_hist_type;
 typedef enum { MG_LAYOUT_DENSE = 0, MG_LAYOUT_CSR = 1 } mg_layout;
-typedef enum { MG_SCHED_BATCHED = 0, MG_SCHED_PLAIN = 1 } mg_schedule;
+typedef enum { MG_SCHED_BATCHED = 0, MG_SCHED_PLAIN = 1, MG_SCHED_NAIVE = 2 } mg_schedule;
 
 typedef struct {
     int hist_type;      /* MG_HIST_U32: exact integer push; MG_HIST_F32: fp32 push */
     int layout;         /* MG_LAYOUT_DENSE or MG_LAYOUT_CSR */
     int alpha_dtype;    /* fp32 push only: node weights read as MG_F32, MG_F16 or MG_BF16 */
     int schedule;       /* MG_SCHED_BATCHED: persistent work queue over cube chunks;
-                           MG_SCHED_PLAIN: one launch per query, one CTA (baseline) */
+                           MG_SCHED_PLAIN: one launch per query, one CTA (baseline);
+                           MG_SCHED_NAIVE: no footprint assembly, every level-0 voxel
+                           of the box counted (brute-force baseline, same results) */
     int chunk_cubes;    /* batched: cubes per work item (0 = tuned default) */
     int block_threads;  /* batched: threads per CTA, 128/256/512 (0 = tuned default) */
     int timing;         /* nonzero: record CUDA events around the plan, main and output
@@ -224,6 +226,40 @@ MG_API mg_status mg_query_boxes_noalloc(const mg_graph *g, const int32_t *boxes,
  * stream.  Waits for the call's last event.  Returns MG_ERR_INVALID_ARG if no
  * timed call was made. */
 MG_API mg_status mg_query_timing(const mg_graph *g, float *plan_ms, float *main_ms, float *output_ms);
+
+/*
+ * Query plans: the batched pipeline of mg_query_boxes for up to max_Q boxes,
+ * captured once as a CUDA graph with every buffer preallocated, so that a run
+ * is three copies and one graph launch, with no host synchronisation.
+ * opts: dense layout and batched schedule only; hist_type, alpha_dtype and the
+ *   launch shape (0 = the graph's tuned shape, else the defaults) as for
+ *   mg_query_boxes.
+ * max_blocks, max_chunks: footprint blocks and work chunks one run may need
+ *   (0 = 1024 and 256 per box).  A run whose boxes need more writes zero
+ *   histograms and sets MG_ERR_CAPACITY in the status word (mg_sync_status).
+ * The plan holds its memory (from the graph's allocator) until
+ * mg_query_plan_free; runs of one plan share it, so runs of one plan on
+ * different streams must not overlap.
+ */
+typedef struct mg_query_plan mg_query_plan;
+MG_API mg_status mg_query_plan_create(mg_graph *g, int64_t max_Q, const mg_query_opts *opts, int64_t max_blocks,
+                                      int64_t max_chunks, mg_query_plan **out);
+/* boxes: Q x 6 int32 (device), 0 <= Q <= max_Q; out: Q x S (uint32 or fp32). */
+MG_API mg_status mg_query_plan_run(mg_query_plan *p, const int32_t *boxes, int64_t Q, void *out, size_t out_capacity,
+                                   mg_stream stream);
+MG_API void mg_query_plan_free(mg_query_plan *p);
+
+/* Autotuner of the batched query: times every work-chunk size in
+ * {1024, 2048, 4096, 8192} cubes with CTAs of 128 and 256 threads on the
+ * given batch (dense layout; opts->hist_type and alpha_dtype as the caller
+ * will use them), writes the fastest into opts->chunk_cubes/block_threads and
+ * keeps it in the graph for later calls and plans that leave them 0.
+ * *best_ms (may be NULL) receives the fastest time of one call.
+ * Synchronises `stream`. */
+MG_API mg_status mg_query_autotune(mg_graph *g, const int32_t *boxes, int64_t Q, mg_query_opts *opts,
+                                   float *best_ms, mg_stream stream);
+/* Record a tuned launch shape for a histogram type (e.g. from a cache file). */
+MG_API mg_status mg_query_set_tuning(mg_graph *g, int hist_type, int chunk_cubes, int block_threads);
 
 /* Number of footprint-assembly cubes (mipmap fetches) of each box, uint64[Q]
  * (the "fetches" of Table 3).  Boxes as for mg_query_boxes. */

@@ -307,8 +307,8 @@ MG_API mg_status mg_query_boxes(const mg_graph* g, const int32_t* boxes, int64_t
         return fail(MG_ERR_INVALID_ARG, "alpha_dtype must be MG_F32, MG_F16 or MG_BF16");
     if (o.hist_type == MG_HIST_U32 && o.alpha_dtype != MG_F32)
         return fail(MG_ERR_INVALID_ARG, "16-bit weights apply to the fp32 push only");
-    if (o.schedule != MG_SCHED_BATCHED && o.schedule != MG_SCHED_PLAIN)
-        return fail(MG_ERR_INVALID_ARG, "schedule must be MG_SCHED_BATCHED or MG_SCHED_PLAIN");
+    if (o.schedule != MG_SCHED_BATCHED && o.schedule != MG_SCHED_PLAIN && o.schedule != MG_SCHED_NAIVE)
+        return fail(MG_ERR_INVALID_ARG, "schedule must be MG_SCHED_BATCHED, MG_SCHED_PLAIN or MG_SCHED_NAIVE");
     if (o.chunk_cubes < 0 || o.block_threads < 0) return fail(MG_ERR_INVALID_ARG, "negative tuning option");
     if (o.block_threads && o.block_threads != 128 && o.block_threads != 256 && o.block_threads != 512)
         return fail(MG_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");

@@ -136,6 +136,9 @@ struct mg_graph {
     mg::Buf alpha16;  // lazily: signed __half alpha, swap flag in the sign
     mg::Buf alphab16; // lazily: signed __nv_bfloat16 alpha, swap flag in the sign
     mg::Buf status;   // unsigned int status word
+    // launch shape chosen by mg_query_autotune, per histogram type (0 = none yet)
+    int tuned_chunk[2] = {0, 0};
+    int tuned_threads[2] = {0, 0};
     // per-stream scratch arenas of query calls
     std::mutex arena_mu;
     std::map<cudaStream_t, std::unique_ptr<mg::Arena>> arenas;

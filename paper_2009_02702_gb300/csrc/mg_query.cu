@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 namespace mg {
@@ -155,15 +156,39 @@ __device__ __forceinline__ uint32_t block_cubes(int lx, int ly, int lz) {
     return 1u << (lx + ly + lz - 3 * l);
 }
 
+// Batch size and capacities read on the device, for query plans replayed as
+// CUDA graphs: the launches cover Q boxes, *Qd of them are live, and the
+// footprint must fit the plan's buffers.  Qd == nullptr: all Q are live and
+// the buffers were sized for this batch.
+struct Lim {
+    const int64_t* Qd;
+    uint64_t cap_blocks, cap_chunks;
+};
+
+__device__ __forceinline__ int64_t live_q(const Lim& lim, int64_t Q) { return lim.Qd ? *lim.Qd : Q; }
+
+__device__ __forceinline__ bool over_cap(const Lim& lim, const uint64_t* blk_off, const uint64_t* chunk_off,
+                                         int64_t Qe) {
+    return lim.Qd && (blk_off[Qe] > lim.cap_blocks || chunk_off[Qe] > lim.cap_chunks);
+}
+
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------
 __global__ void plan_count_kernel(Geom G, const int32_t* __restrict__ boxes, int64_t Q, uint32_t chunk,
                                   uint32_t* __restrict__ nblk, uint64_t* __restrict__ ncube,
-                                  uint64_t* __restrict__ nchunk, unsigned* __restrict__ status) {
+                                  uint64_t* __restrict__ nchunk, unsigned* __restrict__ status, Lim lim) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (q >= Q) return;
+    if (q >= live_q(lim, Q)) {
+        if (lane == 0) {
+            if (nblk) nblk[q] = 0;
+            ncube[q] = 0;
+            if (nchunk) nchunk[q] = 0;
+        }
+        return;
+    }
     int32_t b[6];
 #pragma unroll
     for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
@@ -194,10 +219,12 @@ __global__ void plan_count_kernel(Geom G, const int32_t* __restrict__ boxes, int
 }
 
 __global__ void plan_write_kernel(Geom G, const int32_t* __restrict__ boxes, int64_t Q,
-                                  const uint64_t* __restrict__ blk_off, Blk* __restrict__ blk) {
+                                  const uint64_t* __restrict__ blk_off, Blk* __restrict__ blk, Lim lim,
+                                  const uint64_t* __restrict__ chunk_off) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (q >= Q) return;
+    const int64_t Qe = live_q(lim, Q);
+    if (q >= Qe || over_cap(lim, blk_off, chunk_off, Qe)) return;
     int32_t b[6];
 #pragma unroll
     for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
@@ -458,6 +485,7 @@ struct MainArgs {
     const uint32_t* chunk_q;     // box of every chunk
     const uint32_t* chunk_b;     // block holding every chunk's first cube
     unsigned long long total_chunks;
+    Lim lim;                     // device-side batch size (plans)
     int64_t Q;
     uint32_t chunk;
     unsigned long long* ticket;
@@ -466,6 +494,14 @@ struct MainArgs {
 };
 
 constexpr int kQueue = 64;   // pending internal-node pushes per warp
+
+// chunks of the launch: known on the host, or (plans) read on the device,
+// zero when the batch overflows the plan's buffers
+__device__ __forceinline__ unsigned long long main_total(const MainArgs& A) {
+    if (!A.lim.Qd) return A.total_chunks;
+    const int64_t Qe = *A.lim.Qd;
+    return over_cap(A.lim, A.blk_off, A.chunk_off, Qe) ? 0ull : A.chunk_off[Qe];
+}
 
 // push up to 32 queued (node, weight) entries, one per lane, then move the
 // rest to the front of the queue
@@ -657,11 +693,12 @@ __global__ void __launch_bounds__(512) query_warp_kernel(MainArgs A) {
         if constexpr (FP) H.hf[i] = 0.f;
     }
     __syncwarp();
+    const unsigned long long total = main_total(A);
     for (;;) {
         unsigned long long c = 0;
         if (lane == 0) c = atomicAdd(A.ticket, 1ull);
         c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= A.total_chunks) break;
+        if (c >= total) break;
         const uint32_t q = __ldg(A.chunk_q + c);
         const uint32_t ncube = (uint32_t)A.ncube[q];
         const uint32_t c0 = (uint32_t)(c - A.chunk_off[q]) * A.chunk;
@@ -711,16 +748,17 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
         if constexpr (FP) H.hf[i] = 0.f;
     }
     if (threadIdx.x == 0) s_ntouched = 0;
+    const unsigned long long total = main_total(A);
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned long long c = atomicAdd(A.ticket, 1ull);
             s_chunk = c;
             s_next = 0;
-            if (c < A.total_chunks) s_q = A.chunk_q[c];
+            if (c < total) s_q = A.chunk_q[c];
         }
         __syncthreads();
         const unsigned long long c = s_chunk;
-        if (c >= A.total_chunks) break;
+        if (c >= total) break;
         const uint32_t q = s_q;
         const uint32_t ncube = (uint32_t)A.ncube[q];
         const uint32_t c0 = (uint32_t)(c - A.chunk_off[q]) * A.chunk;
@@ -799,9 +837,70 @@ __global__ void __launch_bounds__(256) query_plain_kernel(MainArgs A, const int3
     flush<FP>(H, S, q, A.acc, A.accf);
 }
 
+// Naive baseline: one CTA per box counts every level-0 voxel of the clipped
+// box into a shared histogram (rows read x-fastest, whole-warp runs of one
+// segment added once).  No mipmap, no graph: the brute force the footprint
+// assembly is measured against.
+template <bool FP>
+__global__ void __launch_bounds__(256) query_naive_kernel(Geom G, const void* __restrict__ ids0,
+                                                          const int32_t* __restrict__ boxes, int64_t Q,
+                                                          uint32_t* __restrict__ acc, float* __restrict__ accf,
+                                                          unsigned* __restrict__ status) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t* h = reinterpret_cast<uint32_t*>(smem);
+    const uint32_t S = G.S;
+    const int lane = threadIdx.x & 31;
+    for (int64_t q = blockIdx.x; q < Q; q += gridDim.x) {
+        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) h[i] = 0;
+        __syncthreads();
+        int32_t b[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
+        if (!box_ok(b, G)) {
+            if (threadIdx.x == 0) set_status(status, kStatBadInput);
+            continue;   // uniform across the CTA
+        }
+        const int64_t nx = G.dims[0][0], ny = G.dims[0][1];
+        const int64_t dx = min((int64_t)b[0] + b[3], nx) - b[0];
+        const int64_t dy = min((int64_t)b[1] + b[4], ny) - b[1];
+        const int64_t dz = min((int64_t)b[2] + b[5], (int64_t)G.dims[0][2]) - b[2];
+        const int64_t n = dx * dy * dz;
+        for (int64_t base = 0; base < n; base += blockDim.x) {
+            const int64_t v = base + threadIdx.x;
+            const bool valid = v < n;
+            uint32_t id = 0;
+            if (valid) {
+                const int64_t x = b[0] + v % dx, y = b[1] + (v / dx) % dy, z = b[2] + v / (dx * dy);
+                const int64_t idx = (z * ny + y) * nx + x;
+                id = G.id0_bytes == 2 ? (uint32_t)__ldg(static_cast<const uint16_t*>(ids0) + idx)
+                                      : __ldg(static_cast<const uint32_t*>(ids0) + idx);
+            }
+            const uint32_t first = __shfl_sync(0xffffffffu, id, 0);
+            if (__all_sync(0xffffffffu, valid && id == first)) {
+                if (lane == 0) atomicAdd(h + first, 32u);
+            } else if (valid) {
+                atomicAdd(h + id, 1u);
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+            if (FP) accf[q * S + i] = (float)h[i];
+            else acc[q * S + i] = h[i];
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // finalisation
 // ---------------------------------------------------------------------------
+__global__ void dense_f32_rows_kernel(const uint32_t* __restrict__ acc, float* __restrict__ out,
+                                      const int64_t* __restrict__ Qd, int64_t S) {
+    const int64_t n = *Qd * S;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)acc[i] + out[i];
+}
+
 __global__ void dense_f32_kernel(const uint32_t* __restrict__ acc, float* __restrict__ out, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (float)acc[i] + out[i];
@@ -859,10 +958,11 @@ __global__ void csr_write_kernel(const uint32_t* __restrict__ acc, const float* 
 // box and first block of every chunk
 __global__ void chunk_map_kernel(const uint64_t* __restrict__ chunk_off, const uint64_t* __restrict__ blk_off,
                                  const Blk* __restrict__ blk, int64_t Q, uint32_t chunk, uint32_t* __restrict__ chunk_q,
-                                 uint32_t* __restrict__ chunk_b) {
+                                 uint32_t* __restrict__ chunk_b, Lim lim) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (q >= Q) return;
+    const int64_t Qe = live_q(lim, Q);
+    if (q >= Qe || over_cap(lim, blk_off, chunk_off, Qe)) return;
     const uint64_t b0 = blk_off[q], b1 = blk_off[q + 1];
     for (uint64_t c = chunk_off[q] + lane; c < chunk_off[q + 1]; c += 32) {
         chunk_q[c] = (uint32_t)q;
@@ -875,6 +975,21 @@ __global__ void chunk_map_kernel(const uint64_t* __restrict__ chunk_off, const u
         }
         chunk_b[c] = (uint32_t)lo;
     }
+}
+
+// a plan's batch needs more footprint blocks or chunks than it holds
+__global__ void plan_check_kernel(const uint64_t* __restrict__ blk_off, const uint64_t* __restrict__ chunk_off, Lim lim,
+                                  unsigned* __restrict__ status) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && over_cap(lim, blk_off, chunk_off, *lim.Qd))
+        set_status(status, kStatCapacity);
+}
+
+// zero the first *Qd rows of S counters (plans); n = rows * S bound
+template <typename T>
+__global__ void zero_rows_kernel(T* __restrict__ a, const int64_t* __restrict__ Qd, int64_t S) {
+    const int64_t n = *Qd * S;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = T(0);
 }
 
 __global__ void widen_kernel(const uint32_t* __restrict__ a, uint64_t* __restrict__ b, int64_t n) {
@@ -900,6 +1015,17 @@ mg_status prepare_kernel(K kernel, size_t smem) {
 template <bool FP, typename AT>
 mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts& o, const int32_t* boxes,
                       size_t smem, int threads, cudaStream_t s) {
+    if (o.schedule == MG_SCHED_NAIVE) {
+        auto k = query_naive_kernel<FP>;
+        const size_t sm = (size_t)g->S * 4;
+        MG_TRY(prepare_kernel(k, sm));
+        int per_sm = 0;
+        MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, sm));
+        const int64_t grid = std::min<int64_t>(A.Q, (int64_t)std::max(per_sm, 1) * sm_count(g->device));
+        k<<<(unsigned)grid, 256, sm, s>>>(A.G, A.I.l0[0], boxes, A.Q, A.acc, A.accf, A.P.status);
+        MG_CUDA(cudaGetLastError());
+        return MG_OK;
+    }
     if (o.schedule == MG_SCHED_PLAIN) {
         auto k = query_plain_kernel<FP, AT>;
         MG_TRY(prepare_kernel(k, smem));
@@ -929,7 +1055,7 @@ mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts&
 mg_status count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64_t* cubes, cudaStream_t s) {
     const Geom G = make_geom(g);
     plan_count_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, 1, nullptr, cubes, nullptr,
-                                                            g->status.as<unsigned>());
+                                                            g->status.as<unsigned>(), Lim{nullptr, 0, 0});
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
@@ -951,8 +1077,9 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
         return MG_OK;
     }
     if (FP && o.alpha_dtype != MG_F32) MG_TRY(ensure_alpha16(const_cast<mg_graph*>(g), (mg_dtype)o.alpha_dtype, s));
-    const uint32_t chunk = o.chunk_cubes > 0 ? (uint32_t)o.chunk_cubes : 2048u;
-    const int threads = o.block_threads > 0 ? o.block_threads : 256;
+    const int tuned_c = g->tuned_chunk[FP ? 1 : 0], tuned_t = g->tuned_threads[FP ? 1 : 0];
+    const uint32_t chunk = o.chunk_cubes > 0 ? (uint32_t)o.chunk_cubes : tuned_c > 0 ? (uint32_t)tuned_c : 2048u;
+    const int threads = o.block_threads > 0 ? o.block_threads : tuned_t > 0 ? tuned_t : 256;
     const Geom G = make_geom(g);
     unsigned* status = g->status.as<unsigned>();
     mg_graph* gm = const_cast<mg_graph*>(g);
@@ -1005,6 +1132,7 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
     A.chunk_q = nullptr;
     A.chunk_b = nullptr;
     A.total_chunks = 0;
+    A.lim = Lim{nullptr, 0, 0};
     A.ticket = nullptr;
 
     const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
@@ -1021,7 +1149,7 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
         MG_TRY(ticket.alloc(&al, 8, s));
         plan_count_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, chunk, nblk.as<uint32_t>(),
                                                                 ncube.as<uint64_t>(), nchunk.as<uint64_t>(),
-                                                                status);
+                                                                status, Lim{nullptr, 0, 0});
         MG_CUDA(cudaGetLastError());
         // block offsets are 64-bit sums of the 32-bit per-box counts
         MG_TRY(scan_exclusive_u64(nchunk.as<uint64_t>(), chunk_off.as<uint64_t>(), Q,
@@ -1051,11 +1179,12 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
         MG_TRY(blk.alloc(&al, (size_t)std::max<uint64_t>(totals[0], 1) * sizeof(Blk), s));
         MG_TRY(chunk_q.alloc(&al, (size_t)std::max<uint64_t>(totals[1], 1) * 4, s));
         MG_TRY(chunk_b.alloc(&al, (size_t)std::max<uint64_t>(totals[1], 1) * 4, s));
-        plan_write_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>());
+        plan_write_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>(),
+                                                                Lim{nullptr, 0, 0}, chunk_off.as<uint64_t>());
         MG_CUDA(cudaGetLastError());
         chunk_map_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(chunk_off.as<uint64_t>(), blk_off.as<uint64_t>(),
                                                                blk.as<Blk>(), Q, chunk, chunk_q.as<uint32_t>(),
-                                                               chunk_b.as<uint32_t>());
+                                                               chunk_b.as<uint32_t>(), Lim{nullptr, 0, 0});
         MG_CUDA(cudaGetLastError());
         A.chunk_q = chunk_q.as<uint32_t>();
         A.chunk_b = chunk_b.as<uint32_t>();
@@ -1238,4 +1367,326 @@ extern "C" MG_API mg_status mg_query_boxes_noalloc(const mg_graph* g, const int3
     }
     if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// Query plans: the whole batched pipeline for up to max_Q boxes captured once
+// as a CUDA graph, with every buffer preallocated; a run copies the boxes in,
+// replays the graph and copies the histograms out, with no host sync.
+// ---------------------------------------------------------------------------
+struct mg_query_plan {
+    mg_graph* g = nullptr;
+    int64_t max_Q = 0;
+    bool fp = false;
+    uint32_t chunk = 0;
+    int threads = 0;
+    uint64_t cap_blocks = 0, cap_chunks = 0;
+    mg::Buf pool;
+    mg::Pool bump{nullptr, 0, 0};
+    int32_t* boxes = nullptr;
+    int64_t* Qd = nullptr;
+    void* result = nullptr;   // max_Q x S, uint32 or fp32
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~mg_query_plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
+
+namespace mg {
+namespace {
+
+template <bool FP, typename AT>
+mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
+    const mg_graph* g = p->g;
+    const int64_t Q = p->max_Q;
+    const uint32_t S = g->S;
+    const Geom G = make_geom(g);
+    unsigned* status = g->status.as<unsigned>();
+    const Lim lim{p->Qd, p->cap_blocks, p->cap_chunks};
+    Buf acc_b, nblk, ncube, nchunk, nb64, blk_off, chunk_off, blk, chunk_q, chunk_b, ticket;
+    uint32_t* acc = nullptr;
+    float* accf = nullptr;
+    if (FP) {
+        MG_TRY(acc_b.alloc(&al, (size_t)Q * S * 4, s));
+        acc = acc_b.as<uint32_t>();
+        accf = static_cast<float*>(p->result);
+    } else {
+        acc = static_cast<uint32_t*>(p->result);
+    }
+    MG_TRY(nblk.alloc(&al, (size_t)Q * 4, s));
+    MG_TRY(ncube.alloc(&al, (size_t)Q * 8, s));
+    MG_TRY(nchunk.alloc(&al, (size_t)Q * 8, s));
+    MG_TRY(nb64.alloc(&al, (size_t)Q * 8, s));
+    MG_TRY(blk_off.alloc(&al, (size_t)(Q + 1) * 8, s));
+    MG_TRY(chunk_off.alloc(&al, (size_t)(Q + 1) * 8, s));
+    MG_TRY(blk.alloc(&al, (size_t)p->cap_blocks * sizeof(Blk), s));
+    MG_TRY(chunk_q.alloc(&al, (size_t)p->cap_chunks * 4, s));
+    MG_TRY(chunk_b.alloc(&al, (size_t)p->cap_chunks * 4, s));
+    MG_TRY(ticket.alloc(&al, 8, s));
+
+    MG_CUDA(cudaMemsetAsync(ticket.p, 0, 8, s));
+    const unsigned zg = grid_for(Q * S, 256, 152 * 64);
+    zero_rows_kernel<uint32_t><<<zg, 256, 0, s>>>(acc, p->Qd, S);
+    if (FP) zero_rows_kernel<float><<<zg, 256, 0, s>>>(accf, p->Qd, S);
+    const unsigned wg = grid_for(Q * 32, 256);
+    plan_count_kernel<<<wg, 256, 0, s>>>(G, p->boxes, Q, p->chunk, nblk.as<uint32_t>(), ncube.as<uint64_t>(),
+                                         nchunk.as<uint64_t>(), status, lim);
+    MG_CUDA(cudaGetLastError());
+    MG_TRY(scan_exclusive_u64(nchunk.as<uint64_t>(), chunk_off.as<uint64_t>(), Q, chunk_off.as<uint64_t>() + Q, al, s));
+    widen_kernel<<<grid_for(Q, 256, 152 * 64), 256, 0, s>>>(nblk.as<uint32_t>(), nb64.as<uint64_t>(), Q);
+    MG_TRY(scan_exclusive_u64(nb64.as<uint64_t>(), blk_off.as<uint64_t>(), Q, blk_off.as<uint64_t>() + Q, al, s));
+    plan_check_kernel<<<1, 32, 0, s>>>(blk_off.as<uint64_t>(), chunk_off.as<uint64_t>(), lim, status);
+    plan_write_kernel<<<wg, 256, 0, s>>>(G, p->boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>(), lim,
+                                         chunk_off.as<uint64_t>());
+    chunk_map_kernel<<<wg, 256, 0, s>>>(chunk_off.as<uint64_t>(), blk_off.as<uint64_t>(), blk.as<Blk>(), Q, p->chunk,
+                                        chunk_q.as<uint32_t>(), chunk_b.as<uint32_t>(), lim);
+    MG_CUDA(cudaGetLastError());
+
+    MainArgs A;
+    A.G = G;
+    A.I = make_ids(g);
+    A.P.pq = g->pq.as<uint2>();
+    A.P.ab32 = g->ab32.as<uint2>();
+    A.P.alpha = std::is_same<AT, __half>::value ? g->alpha16.p : std::is_same<AT, __nv_bfloat16>::value ? g->alphab16.p
+                                                                                                          : g->alpha.p;
+    A.P.S = S;
+    A.P.status = status;
+    A.blk = blk.as<Blk>();
+    A.blk_off = blk_off.as<uint64_t>();
+    A.ncube = ncube.as<uint64_t>();
+    A.chunk_off = chunk_off.as<uint64_t>();
+    A.chunk_q = chunk_q.as<uint32_t>();
+    A.chunk_b = chunk_b.as<uint32_t>();
+    A.total_chunks = 0;
+    A.lim = lim;
+    A.Q = Q;
+    A.chunk = p->chunk;
+    A.ticket = ticket.as<unsigned long long>();
+    A.acc = acc;
+    A.accf = accf;
+    mg_query_opts o{};
+    o.hist_type = FP ? MG_HIST_F32 : MG_HIST_U32;
+    const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
+    const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + ((touched_bytes + 15) & ~(size_t)15) +
+                        (size_t)(p->threads / 32) * 2 * kQueue * 4 + 16;
+    MG_TRY((launch_main<FP, AT>(g, A, o, nullptr, smem, p->threads, s)));
+    if (FP) {
+        dense_f32_rows_kernel<<<zg, 256, 0, s>>>(acc, accf, p->Qd, S);
+        MG_CUDA(cudaGetLastError());
+    }
+    return MG_OK;
+}
+
+}  // namespace
+}  // namespace mg
+
+using mg::fail;
+
+extern "C" {
+
+MG_API mg_status mg_query_plan_create(mg_graph* g, int64_t max_Q, const mg_query_opts* opts, int64_t max_blocks,
+                                      int64_t max_chunks, mg_query_plan** out) {
+    using namespace mg;
+    if (!g || !out) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (max_Q < 1 || max_Q >= (1ll << 31)) return fail(MG_ERR_INVALID_ARG, "max_Q must be in 1..2^31-1");
+    if (max_blocks < 0 || max_chunks < 0) return fail(MG_ERR_INVALID_ARG, "negative capacity");
+    mg_query_opts o{};
+    if (opts) o = *opts;
+    if (o.layout != MG_LAYOUT_DENSE || o.schedule != MG_SCHED_BATCHED)
+        return fail(MG_ERR_UNSUPPORTED, "plans hold the dense layout and the batched schedule");
+    if (o.hist_type != MG_HIST_U32 && o.hist_type != MG_HIST_F32) return fail(MG_ERR_INVALID_ARG, "bad hist_type");
+    if (o.alpha_dtype != MG_F32 && (o.hist_type == MG_HIST_U32 || (o.alpha_dtype != MG_F16 && o.alpha_dtype != MG_BF16)))
+        return fail(MG_ERR_INVALID_ARG, "bad alpha_dtype");
+    if (o.block_threads && o.block_threads != 128 && o.block_threads != 256 && o.block_threads != 512)
+        return fail(MG_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
+    if (o.chunk_cubes < 0) return fail(MG_ERR_INVALID_ARG, "negative chunk_cubes");
+    if (g->S > kMaxSharedSegments) return fail(MG_ERR_UNSUPPORTED, "more than 32768 segments");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != g->device) MG_CUDA(cudaSetDevice(g->device));
+    std::unique_ptr<mg_query_plan> p(new (std::nothrow) mg_query_plan());
+    mg_status st = p ? MG_OK : fail(MG_ERR_OOM, "host allocation failed");
+    if (st == MG_OK) {
+        const bool FP = o.hist_type == MG_HIST_F32;
+        p->g = g;
+        p->max_Q = max_Q;
+        p->fp = FP;
+        const int tc = g->tuned_chunk[FP], tt = g->tuned_threads[FP];
+        p->chunk = o.chunk_cubes > 0 ? (uint32_t)o.chunk_cubes : tc > 0 ? (uint32_t)tc : 2048u;
+        p->threads = o.block_threads > 0 ? o.block_threads : tt > 0 ? tt : 256;
+        p->cap_blocks = max_blocks > 0 ? (uint64_t)max_blocks : (uint64_t)max_Q * 1024;
+        p->cap_chunks = max_chunks > 0 ? (uint64_t)max_chunks : (uint64_t)max_Q * 256;
+        if (p->cap_blocks >= (1ull << 32) || p->cap_chunks >= (1ull << 32))
+            st = fail(MG_ERR_UNSUPPORTED, "plan capacities must be below 2^32");
+    }
+    if (st == MG_OK) {
+        const size_t S = g->S, Q = (size_t)max_Q;
+        auto r = [](size_t n) { return (n + 255) & ~(size_t)255; };
+        const size_t parts = 4 * (r(8 * ((Q + 2047) / 2048)) + r(8 * ((Q + 2047) / 2048 / 2048 + 1)) + 2 * r(8));
+        const size_t bytes = r(Q * 24) + r(8) + r(Q * S * 4) * (p->fp ? 2 : 1) + r(4 * Q) + 3 * r(8 * Q) +
+                             2 * r(8 * (Q + 1)) + r(p->cap_blocks * sizeof(Blk)) + 2 * r(p->cap_chunks * 4) + r(8) +
+                             parts + 65536;
+        st = p->pool.alloc(&g->al, bytes, nullptr);
+        if (st == MG_OK) {
+            cudaError_t e = cudaStreamSynchronize(nullptr);
+            if (e != cudaSuccess) st = cuda_fail(e, "plan pool");
+            p->pool.s = nullptr;
+        }
+        if (st == MG_OK) {
+            p->bump = Pool{p->pool.as<unsigned char>(), p->pool.bytes, 0};
+            p->boxes = static_cast<int32_t*>(pool_alloc(&p->bump, Q * 24, nullptr));
+            p->Qd = static_cast<int64_t*>(pool_alloc(&p->bump, 8, nullptr));
+            p->result = pool_alloc(&p->bump, Q * S * 4, nullptr);
+        }
+    }
+    if (st == MG_OK && p->fp && o.alpha_dtype != MG_F32) st = ensure_alpha16(g, (mg_dtype)o.alpha_dtype, nullptr);
+    if (st == MG_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    if (st == MG_OK) {
+        // scratch comes from the plan's pool, so nothing is allocated while capturing
+        Alloc al;
+        al.a.ctx = &p->bump;
+        al.a.alloc = pool_alloc;
+        al.a.free = pool_free;
+        al.custom = true;
+        cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCapture");
+        if (st == MG_OK) {
+            if (!p->fp) st = plan_enqueue<false, float>(p.get(), al, p->cap_stream);
+            else if (o.alpha_dtype == MG_F16) st = plan_enqueue<true, __half>(p.get(), al, p->cap_stream);
+            else if (o.alpha_dtype == MG_BF16) st = plan_enqueue<true, __nv_bfloat16>(p.get(), al, p->cap_stream);
+            else st = plan_enqueue<true, float>(p.get(), al, p->cap_stream);
+            cudaGraph_t gr = nullptr;
+            e = cudaStreamEndCapture(p->cap_stream, &gr);
+            p->graph = gr;
+            if (st == MG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture");
+        }
+        if (st == MG_OK) {
+            e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+            if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphInstantiate");
+        }
+    }
+    if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
+    if (st != MG_OK) return st;
+    *out = p.release();
+    return MG_OK;
+}
+
+MG_API mg_status mg_query_plan_run(mg_query_plan* p, const int32_t* boxes, int64_t Q, void* out, size_t out_capacity,
+                                   mg_stream stream) {
+    using namespace mg;
+    if (!p) return fail(MG_ERR_INVALID_ARG, "plan is NULL");
+    if (Q < 0 || Q > p->max_Q) return fail(MG_ERR_INVALID_ARG, "Q must be in 0..max_Q");
+    if (Q == 0) return MG_OK;
+    if (!boxes || !out) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    if ((uint64_t)out_capacity < (uint64_t)Q * p->g->S) return fail(MG_ERR_INVALID_ARG, "out_capacity must be >= Q*S");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != p->g->device) MG_CUDA(cudaSetDevice(p->g->device));
+    const int64_t q = Q;   // pageable source: copied out before the call returns
+    mg_status st = MG_OK;
+    cudaError_t e = cudaMemcpyAsync(p->boxes, boxes, (size_t)Q * 24, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->Qd, &q, 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(p->exec, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, p->result, (size_t)Q * p->g->S * 4, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "mg_query_plan_run");
+    if (prev >= 0 && prev != p->g->device) cudaSetDevice(prev);
+    return st;
+}
+
+MG_API void mg_query_plan_free(mg_query_plan* p) {
+    if (!p) return;
+    const int dev = p->g->device;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+    cudaDeviceSynchronize();
+    delete p;
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner: time the batched query over work-chunk sizes and CTA sizes on the
+// caller's own batch and keep the fastest for later calls on this graph.
+// ---------------------------------------------------------------------------
+extern "C" MG_API mg_status mg_query_autotune(mg_graph* g, const int32_t* boxes, int64_t Q, mg_query_opts* opts,
+                                              float* best_ms, mg_stream stream) {
+    using namespace mg;
+    if (!g || !opts) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    if (Q < 1 || !boxes) return fail(MG_ERR_INVALID_ARG, "autotuning needs a non-empty batch");
+    if (opts->hist_type != MG_HIST_U32 && opts->hist_type != MG_HIST_F32) return fail(MG_ERR_INVALID_ARG, "bad hist_type");
+    const bool FP = opts->hist_type == MG_HIST_F32;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != g->device) MG_CUDA(cudaSetDevice(g->device));
+    mg_status st = MG_OK;
+    Buf outb;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best = 1e30f;
+    int best_c = 0, best_t = 0;
+    st = outb.alloc(&g->al, (size_t)Q * g->S * 4, s);
+    if (st == MG_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = fail(MG_ERR_CUDA, "cudaEventCreate");
+    const int chunks[] = {1024, 2048, 4096, 8192};
+    const int threads[] = {128, 256};
+    for (int ci = 0; st == MG_OK && ci < 4; ci++) {
+        for (int ti = 0; st == MG_OK && ti < 2; ti++) {
+            mg_query_opts o = *opts;
+            o.layout = MG_LAYOUT_DENSE;
+            o.schedule = MG_SCHED_BATCHED;
+            o.chunk_cubes = chunks[ci];
+            o.block_threads = threads[ti];
+            o.timing = 0;
+            float ms = 0.f;
+            for (int rep = 0; st == MG_OK && rep < 3; rep++) {   // first run warms up
+                cudaEventRecord(e0, s);
+                st = query_boxes(g, boxes, Q, o, outb.p, (size_t)Q * g->S, nullptr, nullptr, nullptr, s);
+                cudaEventRecord(e1, s);
+                if (st == MG_OK && cudaEventSynchronize(e1) != cudaSuccess) st = fail(MG_ERR_CUDA, "autotune sync");
+                float t = 0.f;
+                if (st == MG_OK) cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms += t;
+            }
+            if (st == MG_OK && ms < best) {
+                best = ms;
+                best_c = chunks[ci];
+                best_t = threads[ti];
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st == MG_OK) {
+        g->tuned_chunk[FP ? 1 : 0] = best_c;
+        g->tuned_threads[FP ? 1 : 0] = best_t;
+        opts->chunk_cubes = best_c;
+        opts->block_threads = best_t;
+        if (best_ms) *best_ms = best / 2.f;
+    }
+    if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
+    return st;
+}
+
+// Record a launch shape found earlier (for example, read from a cache file).
+extern "C" MG_API mg_status mg_query_set_tuning(mg_graph* g, int hist_type, int chunk_cubes, int block_threads) {
+    using namespace mg;
+    if (!g) return fail(MG_ERR_INVALID_ARG, "graph is NULL");
+    if (hist_type != MG_HIST_U32 && hist_type != MG_HIST_F32) return fail(MG_ERR_INVALID_ARG, "bad hist_type");
+    if (chunk_cubes < 0 || (block_threads && block_threads != 128 && block_threads != 256 && block_threads != 512))
+        return fail(MG_ERR_INVALID_ARG, "bad launch shape");
+    g->tuned_chunk[hist_type] = chunk_cubes;
+    g->tuned_threads[hist_type] = block_threads;
+    return MG_OK;
 }

@@ -22,7 +22,8 @@ MG_ERR_TIMEOUT, MG_ERR_CAPACITY, MG_ERR_UNSUPPORTED, MG_ERR_INEXACT = 4, 5, 6, 7
 MG_F32, MG_F16, MG_BF16 = 0, 1, 2
 MG_HIST_U32, MG_HIST_F32 = 0, 1
 MG_LAYOUT_DENSE, MG_LAYOUT_CSR = 0, 1
-MG_SCHED_BATCHED, MG_SCHED_PLAIN = 0, 1
+MG_SCHED_BATCHED, MG_SCHED_PLAIN, MG_SCHED_NAIVE = 0, 1, 2
+_SCHED = {"batched": MG_SCHED_BATCHED, "plain": MG_SCHED_PLAIN, "naive": MG_SCHED_NAIVE}
 MG_MAX_LEVELS, MG_MAX_DEPTH = 32, 64
 MG_NO_NODE = 0xFFFFFFFF
 
@@ -31,7 +32,9 @@ _TORCH_TO_MG = {torch.float32: MG_F32, torch.float16: MG_F16, torch.bfloat16: MG
 
 # names of every symbol include/mg.h declares (checked by the CPU tests)
 EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_copy_mip", "mg_propagate_tf",
-           "mg_query_boxes", "mg_query_boxes_noalloc", "mg_query_timing", "mg_count_cubes", "mg_render_lookup", "mg_sync_status", "mg_free",
+           "mg_query_boxes", "mg_query_boxes_noalloc", "mg_query_timing",
+           "mg_query_plan_create", "mg_query_plan_run", "mg_query_plan_free", "mg_query_autotune",
+           "mg_query_set_tuning", "mg_count_cubes", "mg_render_lookup", "mg_sync_status", "mg_free",
            "mg_last_error", "mg_version")
 
 
@@ -96,6 +99,16 @@ def lib():
         L.mg_query_boxes.restype = st
         L.mg_query_boxes_noalloc.argtypes = [P, P, i64, P, ctypes.c_size_t, P]
         L.mg_query_boxes_noalloc.restype = st
+        L.mg_query_plan_create.argtypes = [P, i64, ctypes.POINTER(mg_query_opts), i64, i64, ctypes.POINTER(P)]
+        L.mg_query_plan_create.restype = st
+        L.mg_query_plan_run.argtypes = [P, P, i64, P, ctypes.c_size_t, P]
+        L.mg_query_plan_run.restype = st
+        L.mg_query_plan_free.argtypes = [P]
+        L.mg_query_plan_free.restype = None
+        L.mg_query_autotune.argtypes = [P, P, i64, ctypes.POINTER(mg_query_opts), ctypes.POINTER(ctypes.c_float), P]
+        L.mg_query_autotune.restype = st
+        L.mg_query_set_tuning.argtypes = [P, i32, i32, i32]
+        L.mg_query_set_tuning.restype = st
         L.mg_query_timing.argtypes = [P, P, P, P]
         L.mg_query_timing.restype = st
         L.mg_count_cubes.argtypes = [P, P, i64, P, P]
@@ -277,7 +290,7 @@ def mg_query_boxes(g: Graph, boxes: torch.Tensor, hist: str = "u32", layout: str
     o.hist_type = MG_HIST_F32 if hist == "f32" else MG_HIST_U32
     o.layout = MG_LAYOUT_CSR if layout == "csr" else MG_LAYOUT_DENSE
     o.alpha_dtype = _DTYPES[alpha][0]
-    o.schedule = MG_SCHED_PLAIN if schedule == "plain" else MG_SCHED_BATCHED
+    o.schedule = _SCHED[schedule]
     o.chunk_cubes = chunk_cubes
     o.block_threads = block_threads
     o.timing = 1 if timing else 0
@@ -318,6 +331,93 @@ def mg_query_boxes_noalloc(g: Graph, boxes: torch.Tensor, out: torch.Tensor = No
     _check(lib().mg_query_boxes_noalloc(g.handle, boxes.data_ptr(), Q, out.data_ptr(), out.numel(),
                                         _stream(stream)))
     return out
+
+
+class QueryPlan:
+    """A captured batched query (mg_query_plan_*): one graph launch per batch."""
+
+    def __init__(self, g: Graph, max_Q: int, hist: str = "u32", alpha: str = "f32", chunk_cubes: int = 0,
+                 block_threads: int = 0, max_blocks: int = 0, max_chunks: int = 0):
+        o = mg_query_opts()
+        o.hist_type = MG_HIST_F32 if hist == "f32" else MG_HIST_U32
+        o.alpha_dtype = _DTYPES[alpha][0]
+        o.chunk_cubes = chunk_cubes
+        o.block_threads = block_threads
+        h = ctypes.c_void_p()
+        with torch.cuda.device(g.device):
+            _check(lib().mg_query_plan_create(g.handle, max_Q, ctypes.byref(o), max_blocks, max_chunks,
+                                              ctypes.byref(h)))
+        self.handle = h.value
+        self.graph = g
+        self.max_Q = max_Q
+        self.dtype = torch.float32 if hist == "f32" else torch.uint32
+
+    def run(self, boxes: torch.Tensor, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+        """mg_query_plan_run: (Q, S) histograms of (Q, 6) int32 CUDA boxes."""
+        boxes = boxes.contiguous()
+        Q = boxes.shape[0]
+        if out is None:
+            out = torch.empty((Q, self.graph.S), dtype=self.dtype, device=boxes.device)
+        _check(lib().mg_query_plan_run(self.handle, boxes.data_ptr(), Q, out.data_ptr(), out.numel(),
+                                       _stream(stream)))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().mg_query_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mg_query_plan_create(g: Graph, max_Q: int, **kw) -> QueryPlan:
+    return QueryPlan(g, max_Q, **kw)
+
+
+def mg_query_autotune(g: Graph, boxes: torch.Tensor, hist: str = "u32", alpha: str = "f32", cache: str = None,
+                      key: str = None, stream=None) -> dict:
+    """Choose the batched query's launch shape on this batch and keep it in the
+    graph.  With `cache` (a JSON file) and `key`, a shape found before under
+    the same GPU name and key is reused without timing."""
+    import json
+    dev = torch.cuda.get_device_name(g.device)
+    full_key = "%s|%s|%s" % (dev, key, hist) if key else None
+    ht = MG_HIST_F32 if hist == "f32" else MG_HIST_U32
+    if cache and full_key and os.path.exists(cache):
+        try:
+            with open(cache) as f:
+                hit = json.load(f).get(full_key)
+        except (OSError, ValueError):
+            hit = None
+        if hit:
+            _check(lib().mg_query_set_tuning(g.handle, ht, int(hit["chunk_cubes"]), int(hit["block_threads"])))
+            return dict(hit, cached=True)
+    boxes = boxes.contiguous()
+    o = mg_query_opts()
+    o.hist_type = ht
+    o.alpha_dtype = _DTYPES[alpha][0]
+    best = ctypes.c_float(0)
+    _check(lib().mg_query_autotune(g.handle, boxes.data_ptr(), boxes.shape[0], ctypes.byref(o), ctypes.byref(best),
+                                   _stream(stream)))
+    res = {"chunk_cubes": o.chunk_cubes, "block_threads": o.block_threads, "best_ms": best.value}
+    if cache and full_key:
+        data = {}
+        try:
+            with open(cache) as f:
+                data = json.load(f)
+        except (OSError, ValueError):
+            data = {}
+        data[full_key] = res
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        tmp = cache + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
+    return dict(res, cached=False)
 
 
 def mg_query_timing(g: Graph):

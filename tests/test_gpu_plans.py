@@ -1,0 +1,84 @@
+"""GPU parity of the captured query plans, the autotuner and the naive
+brute-force schedule against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_02702_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mg():
+    from paper_2009_02702_gb300 import mg as _mg
+    _mg.lib()
+    return _mg
+
+
+@pytest.fixture(scope="module")
+def cfg1(mg):
+    vol = synth.make_volume(1)
+    g = mg.mg_build(torch.from_numpy(vol).cuda(), 64)
+    return vol, g
+
+
+def test_plan_u32_matches_oracle_for_varying_batches(mg, cfg1):
+    vol, g = cfg1
+    plan = mg.QueryPlan(g, max_Q=800)
+    for k, Q in enumerate([800, 1, 333, 800, 57]):
+        boxes = synth.make_boxes(1, Q=Q, stream_offset=k)
+        h = plan.run(torch.from_numpy(boxes).cuda()).cpu().numpy()
+        mg.mg_sync_status(g)
+        assert np.array_equal(h, oracle.box_hist(vol, 64, boxes)), Q
+    assert plan.run(torch.zeros((0, 6), dtype=torch.int32, device="cuda")).shape == (0, 64)
+    plan.close()
+
+
+def test_plan_fp32_and_bf16(mg, cfg1):
+    vol, g = cfg1
+    boxes = synth.make_boxes(1, Q=300)
+    ref = oracle.box_hist(vol, 64, boxes).astype(np.float64)
+    for alpha, rtol in (("f32", 1e-5), ("bf16", None)):
+        plan = mg.QueryPlan(g, max_Q=300, hist="f32", alpha=alpha)
+        h = plan.run(torch.from_numpy(boxes).cuda()).cpu().numpy().astype(np.float64)
+        direct = mg.mg_query_boxes(g, torch.from_numpy(boxes).cuda(), hist="f32", alpha=alpha).cpu().numpy()
+        assert np.allclose(h, direct, rtol=1e-6, atol=1e-3)
+        if rtol:
+            tol = np.where(np.abs(ref) < 1e-2, 1e-7, rtol * np.abs(ref))
+            assert (np.abs(h - ref) <= tol).all()
+        plan.close()
+
+
+def test_plan_capacity_overflow_is_reported(mg, cfg1):
+    vol, g = cfg1
+    plan = mg.QueryPlan(g, max_Q=100, max_blocks=10, max_chunks=10)
+    boxes = synth.make_boxes(1, Q=100)
+    h = plan.run(torch.from_numpy(boxes).cuda()).cpu().numpy()
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_sync_status(g)
+    assert e.value.status == mg.MG_ERR_CAPACITY
+    assert (h == 0).all()
+    plan.close()
+
+
+def test_autotune_and_cache(mg, cfg1, tmp_path):
+    vol, g = cfg1
+    boxes = torch.from_numpy(synth.make_boxes(1, Q=500)).cuda()
+    cache = str(tmp_path / "tune.json")
+    r = mg.mg_query_autotune(g, boxes, cache=cache, key="cfg1")
+    assert r["chunk_cubes"] in (1024, 2048, 4096, 8192) and r["block_threads"] in (128, 256)
+    assert not r["cached"]
+    r2 = mg.mg_query_autotune(g, boxes, cache=cache, key="cfg1")
+    assert r2["cached"] and r2["chunk_cubes"] == r["chunk_cubes"]
+    h = mg.mg_query_boxes(g, boxes).cpu().numpy()   # uses the tuned shape
+    assert np.array_equal(h, oracle.box_hist(vol, 64, boxes.cpu().numpy()))
+
+
+@pytest.mark.parametrize("hist", ["u32", "f32"])
+def test_naive_schedule(mg, cfg1, hist):
+    vol, g = cfg1
+    boxes = synth.make_boxes(1, Q=200)
+    h = mg.mg_query_boxes(g, torch.from_numpy(boxes).cuda(), schedule="naive", hist=hist).cpu().numpy()
+    assert np.array_equal(h.astype(np.int64), oracle.box_hist(vol, 64, boxes).astype(np.int64))
