@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-plan", action="store_true", help="time direct calls instead of the captured plan")
+    ap.add_argument("--no-forms", action="store_true", help="skip the plain/naive/16-bit extra measurements")
     return ap.parse_args()
 
 
@@ -192,11 +194,23 @@ def run_ours(args):
     look = torch.empty((P, 4), dtype=torch.float32, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    tune = None
+    if args.schedule == "batched" and not args.chunk and not args.threads:
+        tune = mg.mg_query_autotune(g, boxes, cache=os.environ.get("MG_AUTOTUNE_CACHE"),
+                                    key="%s-Q%d" % (cfg["name"], Q))
     qkw = dict(schedule=args.schedule, chunk_cubes=args.chunk, block_threads=args.threads)
+    use_plan = args.schedule == "batched" and not args.no_plan
+    plan = mg.QueryPlan(g, max_Q=Q, chunk_cubes=args.chunk, block_threads=args.threads) if use_plan else None
+
+    def query(timing=False):
+        if plan is not None:
+            plan.run(boxes, out=hist)
+        else:
+            mg.mg_query_boxes(g, boxes, out=hist, timing=timing, **qkw)
 
     def step(timing=False):
         mg.mg_propagate_tf(g, tf, out=vals)
-        mg.mg_query_boxes(g, boxes, out=hist, timing=timing, **qkw)
+        query(timing)
         mg.mg_render_lookup(g, vals, smp, out=look)
 
     for _ in range(max(args.warmup, 3)):
@@ -219,17 +233,23 @@ def run_ours(args):
         e[0].record(stream)
         mg.mg_propagate_tf(g, tf, out=vals)
         e[1].record(stream)
-        mg.mg_query_boxes(g, boxes, out=hist, timing=True, **qkw)
+        query()
         e[2].record(stream)
         mg.mg_render_lookup(g, vals, smp, out=look)
         e[3].record(stream)
-        qmain.append(mg.mg_query_timing(g))
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     mg.mg_sync_status(g)
+    # stage split of the query (plan, histogram kernel, output) from CUDA events
+    # the library records on this stream, same launch shape, L2 flushed first
+    for k in range(args.steps):
+        flush.zero_()
+        mg.mg_query_boxes(g, boxes, out=hist, timing=True, **qkw)
+        qmain.append(mg.mg_query_timing(g))
+    torch.cuda.synchronize()
     step_ms = np.array([e[0].elapsed_time(e[3]) for e in ev])
     prop_ms = np.array([e[0].elapsed_time(e[1]) for e in ev])
     query_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
@@ -281,7 +301,10 @@ def run_ours(args):
             tf_d.copy_(tf_p, non_blocking=True)
             smp_d.copy_(smp_p, non_blocking=True)
             mg.mg_propagate_tf(g, tf_d, out=vals)
-            mg.mg_query_boxes(g, boxes_d, out=hist, **qkw)
+            if plan is not None:
+                plan.run(boxes_d, out=hist)
+            else:
+                mg.mg_query_boxes(g, boxes_d, out=hist, **qkw)
             mg.mg_render_lookup(g, vals, smp_d, out=look)
             hist_p.copy_(hist, non_blocking=True)
             look_p.copy_(look, non_blocking=True)
@@ -305,13 +328,20 @@ def run_ours(args):
                "h2d_bytes_per_step": int(boxes_h.nbytes + tf_h.nbytes + smp_h.nbytes),
                "d2h_bytes_per_step": int(Q * S * 4 + P * 16), "ms_per_step": e_ms / args.steps}
 
+    forms = None
+    if not args.no_forms:
+        forms = other_forms(mg, g, boxes, boxes_h, tf, vals, Q, S, dims, cfg_i, flush, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg_i, boxes_h, args.cpu_seconds)
 
     launches_prop = 1 + sum(1 for d in range(1, info["depth"] + 1) if info["bucket"][d + 1] > info["bucket"][d])
-    launches_query = 1 if args.schedule == "batched" else Q
-    launches_query += 8 + (0 if args.schedule == "batched" else -8)
+    nscan = 1 if Q <= 2048 else 3   # kernels of one device-wide scan of Q values
+    if args.schedule == "batched":
+        launches_query = 1 + 1 + 2 * nscan + 1 + 1 + 1 + 1 + 1   # zero, count, 2 scans, widen, check, write, map, main
+    else:
+        launches_query = Q
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -338,6 +368,9 @@ def run_ours(args):
                   "build_ms": info["build_ms"], "device_bytes": info["device_bytes"],
                   "max_list": info["max_list"], "pairs": info["pairs"]},
         "e2e": e2e,
+        "autotune": tune,
+        "query_path": "captured plan (one CUDA graph launch per batch)" if use_plan else "direct calls",
+        "forms": forms,
         "gpu_launches": args.steps * (launches_prop + launches_query + 1),
         "clocks": clk,
         "wall_s_timed": wall,
@@ -346,9 +379,86 @@ def run_ours(args):
         line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line))
+    if plan is not None:
+        plan.close()
     g.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# the other forms the workload is reported in
+# --------------------------------------------------------------------------
+def _time(fn, reps, flush, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def storage_errors(mg, g, tf, vol_h, dims, S, nsample=1500, seed=5):
+    """Max / mean |colour - fp64 direct sum| of node values stored in fp32,
+    fp16 and bf16, over sampled interior voxels of levels 1..5 (their mixture
+    is the count of level-0 IDs in the voxel's footprint)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    tf64 = tf.detach().cpu().numpy().astype(np.float64)
+    vals = {dt: mg.mg_propagate_tf(g, tf, storage=dt).float().cpu().numpy() for dt in ("f32", "f16", "bf16")}
+    mips = {}
+    errs = {dt: [] for dt in vals}
+    for _ in range(nsample):
+        l = int(rng.integers(1, 6))
+        e = 1 << l
+        X, Y, Z = [int(rng.integers(0, d // e)) for d in dims]
+        sub = vol_h[Z * e:(Z + 1) * e, Y * e:(Y + 1) * e, X * e:(X + 1) * e].ravel()
+        ref = np.bincount(sub, minlength=S).astype(np.float64) @ tf64 / sub.size
+        if l not in mips:
+            mips[l] = mg.mg_graph_copy_mip(g, l)
+        node = mips[l][Z, Y, X]
+        for dt, v in vals.items():
+            errs[dt].append(np.abs(v[node] - ref).max())
+    return {dt: {"max_abs": float(np.max(v)), "mean_abs": float(np.mean(v))} for dt, v in errs.items()}
+
+
+def other_forms(mg, g, boxes, boxes_h, tf, vals, Q, S, dims, cfg_i, flush, stream):
+    import torch
+    out = {}
+    hist = torch.empty((Q, S), dtype=torch.uint32, device=boxes.device)
+    histf = torch.empty((Q, S), dtype=torch.float32, device=boxes.device)
+    ms = _time(lambda: mg.mg_query_boxes(g, boxes, out=hist), 5, flush, stream)
+    out["batched_direct_u32"] = {"queries_per_s": Q / (ms / 1e3), "ms": ms}
+    ms = _time(lambda: mg.mg_query_boxes(g, boxes, out=histf, hist="f32"), 5, flush, stream)
+    out["batched_direct_f32"] = {"queries_per_s": Q / (ms / 1e3), "ms": ms}
+    n = min(Q, 1000)
+    sub = boxes[:n].contiguous()
+    hs = torch.empty((n, S), dtype=torch.float32, device=boxes.device)
+    ms = _time(lambda: mg.mg_query_boxes(g, sub, out=hs, hist="f32", schedule="plain"), 3, flush, stream)
+    out["plain_one_launch_per_box_f32"] = {"queries_per_s": n / (ms / 1e3), "ms": ms, "boxes": n}
+    hn = torch.empty((n, S), dtype=torch.uint32, device=boxes.device)
+    ms = _time(lambda: mg.mg_query_boxes(g, sub, out=hn, schedule="naive"), 3, flush, stream)
+    out["naive_gpu_level0_u32"] = {"queries_per_s": n / (ms / 1e3), "ms": ms, "boxes": n}
+    for alpha in ("f16", "bf16"):
+        ms = _time(lambda: mg.mg_query_boxes(g, boxes, out=histf, hist="f32", alpha=alpha), 5, flush, stream)
+        out["batched_direct_f32_alpha_%s" % alpha] = {"queries_per_s": Q / (ms / 1e3), "ms": ms}
+    # 16-bit storage of the propagated values (A9)
+    for dt in ("f16", "bf16"):
+        v16 = torch.empty((g.N, vals.shape[1]), dtype=torch.float16 if dt == "f16" else torch.bfloat16,
+                          device=vals.device)
+        ms = _time(lambda: mg.mg_propagate_tf(g, tf, storage=dt, out=v16), 10, flush, stream)
+        out["propagate_%s_ms" % dt] = ms
+    vol_h = synth.make_volume(cfg_i, device="cpu") if max(dims) <= 1024 else None
+    if vol_h is not None:
+        out["storage_error_vs_fp64"] = storage_errors(mg, g, tf, vol_h, dims, S)
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -1,11 +1,21 @@
 // mg_propagate.cu -- forward transfer-function propagation (Sec. 3.4, Sec. 4).
 //
-// Sources take the TF row of their segment; then, one launch per topological
-// level (nodes of a level are contiguous and independent), every node lerps
-// the rows of its two predecessors:  v = v_p + alpha * (v_q - v_p), fp32.
-// Node records are SoA: (p, q) as one 8-byte load, alpha as 4 (or 2) bytes;
-// value rows are gathered as one vector load per predecessor.
+// Sources take the TF row of their segment; then, level by level (nodes of a
+// level are contiguous and independent), every node lerps the rows of its two
+// predecessors:  v = v_p + alpha * (v_q - v_p), fp32.  Node records are SoA:
+// (p, q) as one 8-byte load, alpha as 4 (or 2) bytes; value rows are gathered
+// as one vector load per predecessor.
+//
+// One persistent launch covers all levels: CTAs take tiles of nodes from a
+// global ticket in level order, and a tile of level d first waits until every
+// tile of level d-1 has signalled (a per-level counter).  Tiles are handed out
+// in order, so every tile waited on belongs to a CTA that is already running:
+// the wait always ends.  It is bounded all the same; past the bound the
+// kernel records MG_ERR_TIMEOUT and returns.  Rows written in this launch are
+// read through L2 (ld.global.cg), never through the read-only cache.
 #include "mg_internal.cuh"
+
+#include <algorithm>
 
 namespace mg {
 namespace {
@@ -61,6 +71,32 @@ __device__ __forceinline__ void store_row(ST* __restrict__ base, int64_t row, co
     }
 }
 
+// the same row load through L2 only, for rows written earlier in this launch
+template <typename ST, int C>
+__device__ __forceinline__ void load_row_cg(const ST* __restrict__ base, int64_t row, float (&v)[C]) {
+    const ST* r = base + row * C;
+    if constexpr (sizeof(ST) * C == 16) {
+        const uint4 u = __ldcg(reinterpret_cast<const uint4*>(r));
+        const ST* e = reinterpret_cast<const ST*>(&u);
+#pragma unroll
+        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(e[c]);
+    } else if constexpr (sizeof(ST) * C == 8) {
+        const uint2 u = __ldcg(reinterpret_cast<const uint2*>(r));
+        const ST* e = reinterpret_cast<const ST*>(&u);
+#pragma unroll
+        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(e[c]);
+    } else if constexpr (sizeof(ST) == 4) {
+#pragma unroll
+        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(__ldcg(reinterpret_cast<const float*>(r) + c));
+    } else {
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            const unsigned short u = __ldcg(reinterpret_cast<const unsigned short*>(r) + c);
+            v[c] = Cvt<ST>::to(*reinterpret_cast<const ST*>(&u));
+        }
+    }
+}
+
 template <typename ST, int C>
 __global__ void sources_kernel(const float* __restrict__ tf, uint32_t S, ST* __restrict__ vals) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
@@ -102,6 +138,83 @@ __global__ void level_kernel(const uint2* __restrict__ pq, const typename Weight
     store_row<ST, C>(vals, n, out);
 }
 
+constexpr int kPropThreads = 256;
+constexpr int kPropTile = 1024;                 // nodes per tile
+constexpr unsigned kSpinLimit = 1u << 22;       // polls before a wait gives up
+
+struct PropTiles {
+    int levels;                                 // D + 1, level 0 = the sources
+    int64_t tile0[MG_MAX_DEPTH + 2];            // first tile of every level (+ end)
+    int64_t first[MG_MAX_DEPTH + 1];            // first node of every level
+    int64_t count[MG_MAX_DEPTH + 1];            // nodes of every level
+};
+
+template <typename ST, int C>
+__global__ void __launch_bounds__(kPropThreads) single_pass_kernel(PropTiles T, const uint2* __restrict__ pq,
+                                                                   const typename Weight<ST>::T* __restrict__ alpha,
+                                                                   const float* __restrict__ tf, ST* __restrict__ vals,
+                                                                   unsigned* __restrict__ done,
+                                                                   unsigned long long* __restrict__ ticket,
+                                                                   unsigned* __restrict__ status) {
+    __shared__ long long s_tile;
+    __shared__ int s_abort;
+    const long long total = T.tile0[T.levels];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_tile = (long long)atomicAdd(ticket, 1ull);
+            s_abort = 0;
+        }
+        __syncthreads();
+        const long long t = s_tile;
+        if (t >= total) break;
+        int d = 0;
+        while (t >= T.tile0[d + 1]) d++;
+        const int64_t lo = T.first[d] + (t - T.tile0[d]) * kPropTile;
+        const int64_t hi = min(lo + kPropTile, T.first[d] + T.count[d]);
+        if (d > 0 && threadIdx.x == 0) {
+            const unsigned need = (unsigned)(T.tile0[d] - T.tile0[d - 1]);
+            unsigned it = 0;
+            while (ld_acquire_u32(done + d - 1) < need) {
+                if (++it > kSpinLimit) {
+                    set_status(status, kStatTimeout);
+                    s_abort = 1;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        for (int64_t n = lo + threadIdx.x; n < hi; n += kPropThreads) {
+            float out[C];
+            if (d == 0) {
+#pragma unroll
+                for (int c = 0; c < C; c++) out[c] = tf[n * C + c];
+            } else {
+                const uint2 e = __ldg(pq + n);
+                uint32_t p = e.x, q = e.y;
+                float al = Cvt<typename Weight<ST>::T>::to(alpha[n]);
+                if (al < 0.f) {
+                    al = -al;
+                    p = e.y;
+                    q = e.x;
+                }
+                float vp[C], vq[C];
+                load_row_cg<ST, C>(vals, p, vp);
+                load_row_cg<ST, C>(vals, q, vq);
+#pragma unroll
+                for (int c = 0; c < C; c++) out[c] = fmaf(al, vq[c] - vp[c], vp[c]);
+            }
+            store_row<ST, C>(vals, n, out);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(done + d, 1u);
+        }
+    }
+}
+
 __global__ void alpha16_kernel(const ulonglong2* __restrict__ ab, int64_t N, uint32_t S, int bf16,
                                void* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -119,8 +232,46 @@ __global__ void alpha16_kernel(const ulonglong2* __restrict__ ab, int64_t N, uin
     }
 }
 
+int sm_count_prop(int dev) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
 template <typename ST, int C>
-mg_status run(const mg_graph* g, const float* tf, const void* alpha, ST* vals, cudaStream_t s) {
+mg_status run_single_pass(mg_graph* g, const float* tf, const void* alpha, ST* vals, cudaStream_t s) {
+    PropTiles T;
+    T.levels = g->D + 1;
+    int64_t tiles = 0;
+    for (int d = 0; d <= g->D; d++) {
+        T.tile0[d] = tiles;
+        T.first[d] = g->bucket[d];
+        T.count[d] = g->bucket[d + 1] - g->bucket[d];
+        tiles += (T.count[d] + kPropTile - 1) / kPropTile;
+    }
+    T.tile0[g->D + 1] = tiles;
+    Arena* arena = nullptr;
+    MG_TRY(arena_begin(g, s, &arena));
+    Buf sync;
+    MG_TRY(sync.alloc(&arena->view, (MG_MAX_DEPTH + 2) * sizeof(unsigned) + 16, s));
+    MG_CUDA(cudaMemsetAsync(sync.p, 0, (MG_MAX_DEPTH + 2) * sizeof(unsigned) + 16, s));
+    unsigned* done = sync.as<unsigned>();
+    auto* ticket = reinterpret_cast<unsigned long long*>(sync.as<unsigned char>() + (MG_MAX_DEPTH + 2) * sizeof(unsigned) +
+                                                        (8 - ((MG_MAX_DEPTH + 2) * sizeof(unsigned)) % 8) % 8);
+    using W = typename Weight<ST>::T;
+    auto k = single_pass_kernel<ST, C>;
+    int per_sm = 0;
+    MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kPropThreads, 0));
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)std::max(per_sm, 1) * sm_count_prop(g->device));
+    k<<<(unsigned)std::max<int64_t>(grid, 1), kPropThreads, 0, s>>>(T, g->pq.as<uint2>(), static_cast<const W*>(alpha),
+                                                                    tf, vals, done, ticket, g->status.as<unsigned>());
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+template <typename ST, int C>
+mg_status run(mg_graph* g, const float* tf, const void* alpha, ST* vals, cudaStream_t s) {
+    if (g->D + 1 <= MG_MAX_DEPTH) return run_single_pass<ST, C>(g, tf, alpha, vals, s);
     sources_kernel<ST, C><<<grid_for(g->S, 256, 152 * 16), 256, 0, s>>>(tf, g->S, vals);
     MG_CUDA(cudaGetLastError());
     using W = typename Weight<ST>::T;
@@ -135,7 +286,7 @@ mg_status run(const mg_graph* g, const float* tf, const void* alpha, ST* vals, c
 }
 
 template <typename ST>
-mg_status dispatch_c(const mg_graph* g, const float* tf, int C, const void* alpha, void* vals, cudaStream_t s) {
+mg_status dispatch_c(mg_graph* g, const float* tf, int C, const void* alpha, void* vals, cudaStream_t s) {
     ST* v = static_cast<ST*>(vals);
     switch (C) {
         case 1: return run<ST, 1>(g, tf, alpha, v, s);

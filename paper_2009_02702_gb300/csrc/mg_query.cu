@@ -151,6 +151,17 @@ __device__ __forceinline__ void make_runs(const int32_t* b, const Geom& G, Runs&
     R.nz = footprint_1d(b[2], b[5], G.dims[0][2], R.lz, R.sz);
 }
 
+// the runs of a warp's box, one axis per lane, into the warp's shared slot
+__device__ __forceinline__ void make_runs_warp(const int32_t* b, const Geom& G, Runs& R) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) R.nx = footprint_1d(b[0], b[3], G.dims[0][0], R.lx, R.sx);
+    else if (lane == 1) R.ny = footprint_1d(b[1], b[4], G.dims[0][1], R.ly, R.sy);
+    else if (lane == 2) R.nz = footprint_1d(b[2], b[5], G.dims[0][2], R.lz, R.sz);
+    __syncwarp();
+}
+
+constexpr int kPlanThreads = 256;   // plan kernels: one warp per box
+
 __device__ __forceinline__ uint32_t block_cubes(int lx, int ly, int lz) {
     const int l = min(lx, min(ly, lz));
     return 1u << (lx + ly + lz - 3 * l);
@@ -201,8 +212,9 @@ __global__ void plan_count_kernel(Geom G, const int32_t* __restrict__ boxes, int
         }
         return;
     }
-    Runs R;
-    make_runs(b, G, R);
+    __shared__ Runs wr[kPlanThreads / 32];
+    Runs& R = wr[threadIdx.x >> 5];
+    make_runs_warp(b, G, R);
     uint64_t cubes = 0;
     const int npairs = R.ny * R.nz;
     for (int pr = lane; pr < npairs; pr += 32) {
@@ -229,8 +241,9 @@ __global__ void plan_write_kernel(Geom G, const int32_t* __restrict__ boxes, int
 #pragma unroll
     for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
     if (!box_ok(b, G)) return;
-    Runs R;
-    make_runs(b, G, R);
+    __shared__ Runs wr[kPlanThreads / 32];
+    Runs& R = wr[threadIdx.x >> 5];
+    make_runs_warp(b, G, R);
     const uint64_t base = blk_off[q];
     const int npairs = R.ny * R.nz;
     uint32_t running = 0;
@@ -849,38 +862,37 @@ __global__ void __launch_bounds__(256) query_naive_kernel(Geom G, const void* __
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t* h = reinterpret_cast<uint32_t*>(smem);
     const uint32_t S = G.S;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t q = blockIdx.x; q < Q; q += gridDim.x) {
         for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) h[i] = 0;
         __syncthreads();
         int32_t b[6];
 #pragma unroll
         for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
-        if (!box_ok(b, G)) {
-            if (threadIdx.x == 0) set_status(status, kStatBadInput);
-            continue;   // uniform across the CTA
-        }
-        const int64_t nx = G.dims[0][0], ny = G.dims[0][1];
-        const int64_t dx = min((int64_t)b[0] + b[3], nx) - b[0];
-        const int64_t dy = min((int64_t)b[1] + b[4], ny) - b[1];
-        const int64_t dz = min((int64_t)b[2] + b[5], (int64_t)G.dims[0][2]) - b[2];
-        const int64_t n = dx * dy * dz;
-        for (int64_t base = 0; base < n; base += blockDim.x) {
-            const int64_t v = base + threadIdx.x;
-            const bool valid = v < n;
-            uint32_t id = 0;
-            if (valid) {
-                const int64_t x = b[0] + v % dx, y = b[1] + (v / dx) % dy, z = b[2] + v / (dx * dy);
-                const int64_t idx = (z * ny + y) * nx + x;
-                id = G.id0_bytes == 2 ? (uint32_t)__ldg(static_cast<const uint16_t*>(ids0) + idx)
-                                      : __ldg(static_cast<const uint32_t*>(ids0) + idx);
+        if (box_ok(b, G)) {
+            const int64_t nx = G.dims[0][0], ny = G.dims[0][1];
+            const int dx = (int)(min((int64_t)b[0] + b[3], nx) - b[0]);
+            const int dy = (int)(min((int64_t)b[1] + b[4], ny) - b[1]);
+            const int dz = (int)(min((int64_t)b[2] + b[5], (int64_t)G.dims[0][2]) - b[2]);
+            // warps take rows (y, z); lanes read along x; each lane keeps a run
+            for (int r = warp; r < dy * dz; r += nw) {
+                const int64_t row = ((int64_t)(b[2] + r / dy) * ny + b[1] + r % dy) * nx + b[0];
+                uint32_t rid = kNone, rcnt = 0;
+                for (int x = lane; x < dx; x += 32) {
+                    const uint32_t id = G.id0_bytes == 2 ? (uint32_t)__ldg(static_cast<const uint16_t*>(ids0) + row + x)
+                                                         : __ldg(static_cast<const uint32_t*>(ids0) + row + x);
+                    if (id != rid) {
+                        if (rcnt) atomicAdd(h + rid, rcnt);
+                        rid = id;
+                        rcnt = 1;
+                    } else {
+                        rcnt++;
+                    }
+                }
+                if (rcnt) atomicAdd(h + rid, rcnt);
             }
-            const uint32_t first = __shfl_sync(0xffffffffu, id, 0);
-            if (__all_sync(0xffffffffu, valid && id == first)) {
-                if (lane == 0) atomicAdd(h + first, 32u);
-            } else if (valid) {
-                atomicAdd(h + id, 1u);
-            }
+        } else if (threadIdx.x == 0) {
+            set_status(status, kStatBadInput);
         }
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
@@ -1054,7 +1066,7 @@ mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts&
 
 mg_status count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64_t* cubes, cudaStream_t s) {
     const Geom G = make_geom(g);
-    plan_count_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, 1, nullptr, cubes, nullptr,
+    plan_count_kernel<<<grid_for(Q * 32, kPlanThreads), kPlanThreads, 0, s>>>(G, boxes, Q, 1, nullptr, cubes, nullptr,
                                                             g->status.as<unsigned>(), Lim{nullptr, 0, 0});
     MG_CUDA(cudaGetLastError());
     return MG_OK;
@@ -1147,7 +1159,7 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
         MG_TRY(blk_off.alloc(&al, (size_t)(Q + 1) * 8, s));
         MG_TRY(chunk_off.alloc(&al, (size_t)(Q + 1) * 8, s));
         MG_TRY(ticket.alloc(&al, 8, s));
-        plan_count_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, chunk, nblk.as<uint32_t>(),
+        plan_count_kernel<<<grid_for(Q * 32, kPlanThreads), kPlanThreads, 0, s>>>(G, boxes, Q, chunk, nblk.as<uint32_t>(),
                                                                 ncube.as<uint64_t>(), nchunk.as<uint64_t>(),
                                                                 status, Lim{nullptr, 0, 0});
         MG_CUDA(cudaGetLastError());
@@ -1179,7 +1191,7 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
         MG_TRY(blk.alloc(&al, (size_t)std::max<uint64_t>(totals[0], 1) * sizeof(Blk), s));
         MG_TRY(chunk_q.alloc(&al, (size_t)std::max<uint64_t>(totals[1], 1) * 4, s));
         MG_TRY(chunk_b.alloc(&al, (size_t)std::max<uint64_t>(totals[1], 1) * 4, s));
-        plan_write_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(G, boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>(),
+        plan_write_kernel<<<grid_for(Q * 32, kPlanThreads), kPlanThreads, 0, s>>>(G, boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>(),
                                                                 Lim{nullptr, 0, 0}, chunk_off.as<uint64_t>());
         MG_CUDA(cudaGetLastError());
         chunk_map_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(chunk_off.as<uint64_t>(), blk_off.as<uint64_t>(),
