@@ -155,6 +155,22 @@ def cube_levels(boxes, dims):
     return out
 
 
+def measured_traffic(kernel, cfg_i, Q):
+    """DRAM bytes per launch from the committed ncu record, only while the
+    kernel's source is the one the counters were taken on (else None)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except (OSError, KeyError, ValueError):
+        return None
+    if sha != rec["sha256_16"] or cfg_i != 2 or Q != synth.CONFIGS[2]["queries"]:
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
@@ -278,6 +294,7 @@ def run_ours(args):
     except Exception:
         peak, peak_src = 6800.0, "fallback"
     achieved = q_bytes / (float(np.mean(main_ms)) / 1e3) / 1e9
+    traffic = measured_traffic("query_warp_kernel", cfg_i, Q)
     n_int = info["num_nodes"] - S
     prop_bytes = 28 * n_int + 16 * S
     prop_gbs = prop_bytes / (float(np.mean(prop_ms)) / 1e3) / 1e9
@@ -361,7 +378,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "query_batched_kernel" if args.schedule == "batched" else
                      "query_plain_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src + " hbm_gbs (copy, burst)",
-                     "traffic": None, "algorithmic_bytes_per_launch": q_bytes, "cubes_per_launch": cubes},
+                     "traffic": traffic, "algorithmic_bytes_per_launch": q_bytes, "cubes_per_launch": cubes},
         "other_kernels": {"propagate_gbs": prop_gbs, "propagate_frac": prop_gbs / peak,
                           "propagate_bytes": prop_bytes, "lookup_gbs": look_gbs, "lookup_frac": look_gbs / peak},
         "graph": {"nodes": info["num_nodes"], "depth": info["depth"], "levels": info["levels"],
