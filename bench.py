@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-plan", action="store_true", help="time direct calls instead of the captured plan")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain/naive/16-bit extra measurements")
+    ap.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving mix) measurement")
+    ap.add_argument("--serve-requests", type=int, default=0)
+    ap.add_argument("--serve-rate", type=float, default=0.0)
     return ap.parse_args()
 
 
@@ -349,6 +352,10 @@ def run_ours(args):
     if not args.no_forms:
         forms = other_forms(mg, g, boxes, boxes_h, tf, vals, Q, S, dims, cfg_i, flush, stream)
 
+    served = None
+    if not args.no_serve and rank == 0:
+        served = serving(mg, g, args, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg_i, boxes_h, args.cpu_seconds)
@@ -375,8 +382,8 @@ def run_ours(args):
         "stages_ms": {"propagate": float(np.mean(prop_ms)), "query": float(np.mean(query_ms)),
                       "query_plan": float(np.mean([t[0] for t in qmain])), "query_main": float(np.mean(main_ms)),
                       "query_output": float(np.mean([t[2] for t in qmain])), "lookup": float(np.mean(look_ms))},
-        "roofline": {"bound": "hbm", "kernel": "query_batched_kernel" if args.schedule == "batched" else
-                     "query_plain_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": ("query_warp_kernel" if S <= 2048 else "query_batched_kernel")
+                     if args.schedule == "batched" else "query_plain_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src + " hbm_gbs (copy, burst)",
                      "traffic": traffic, "algorithmic_bytes_per_launch": q_bytes, "cubes_per_launch": cubes},
         "other_kernels": {"propagate_gbs": prop_gbs, "propagate_frac": prop_gbs / peak,
@@ -388,6 +395,7 @@ def run_ours(args):
         "autotune": tune,
         "query_path": "captured plan (one CUDA graph launch per batch)" if use_plan else "direct calls",
         "forms": forms,
+        "serving": served,
         "gpu_launches": args.steps * (launches_prop + launches_query + 1),
         "clocks": clk,
         "wall_s_timed": wall,
@@ -475,6 +483,97 @@ def other_forms(mg, g, boxes, boxes_h, tf, vals, Q, S, dims, cfg_i, flush, strea
     vol_h = synth.make_volume(cfg_i, device="cpu") if max(dims) <= 1024 else None
     if vol_h is not None:
         out["storage_error_vs_fp64"] = storage_errors(mg, g, tf, vol_h, dims, S)
+    return out
+
+
+# --------------------------------------------------------------------------
+# the request loop under the serving mix (volumes of configs 1-3 resident)
+# --------------------------------------------------------------------------
+def _pct(x, q):
+    return float(np.percentile(x, q)) * 1e3 if len(x) else None
+
+
+def serving(mg, g2, args, dev):
+    """Replay the Poisson mix through the continuously batched server and
+    through the plain one-launch-per-box server (both fp32 histograms, so at
+    equal accuracy), at the offered rate and as one saturating burst."""
+    import torch
+    c5 = synth.CONFIGS[5]
+    n = args.serve_requests or c5["requests"]
+    rate = args.serve_rate or c5["rate"]
+    t0 = time.perf_counter()
+    graphs, meta = [], []
+    for ci in c5["volumes"]:
+        cfg = synth.CONFIGS[ci]
+        if ci == 2:
+            g = g2
+        else:
+            vol = synth.make_volume(ci, device=dev)
+            torch.cuda.synchronize()
+            g = mg.mg_build(vol, cfg["S"])
+            del vol
+        graphs.append(g)
+        meta.append(dict(cfg=ci, S=cfg["S"], dims=cfg["dims"], bmax=cfg["box_max"]))
+    build_s = time.perf_counter() - t0
+    arr, kind, vidx, boxes = synth.make_request_mix(n, rate, [m["dims"] for m in meta], [m["bmax"] for m in meta],
+                                                    c5["tf_frac"])
+    side = int(math.isqrt(c5["frame_samples"]))
+    frames = {v: [(synth.make_tf(5, m["S"], 4, frame=f),
+                   synth.make_samples(m["cfg"], width=side, height=side, frame=f)) for f in range(8)]
+              for v, m in enumerate(meta)}
+    reqs = []
+    for i in range(n):
+        v = int(vidx[i])
+        if kind[i] == 0:
+            reqs.append(dict(kind="box", volume=v, box=boxes[i], arrival=float(arr[i])))
+        else:
+            tf, smp = frames[v][i % 8]
+            reqs.append(dict(kind="tf", volume=v, tf=tf, samples=smp, arrival=float(arr[i])))
+    burst = [dict(r, arrival=0.0) for r in reqs]
+    is_box = np.array([r["kind"] == "box" for r in reqs])
+    out = {"workload": c5["name"], "requests": n, "offered_rate_hz": rate, "tf_fraction": c5["tf_frac"],
+           "frame_samples": side * side, "volumes": [synth.CONFIGS[m["cfg"]]["name"] for m in meta],
+           "hist": "f32 (both forms)", "volume_build_s": build_s}
+    for form, plain in (("batched", False), ("plain", True)):
+        srv = mg.Server(slots=4, max_batch=1024, hist="f32", storage="f32", max_samples=side * side, plain=plain)
+        for g in graphs:
+            srv.add_volume(g, 4)
+        srv.start()
+        res = {}
+        for mode, stream in (("offered", reqs), ("burst", burst)):
+            before = srv.stats()
+            results, lat, wall = srv.replay(stream)
+            after = srv.stats()
+            launches = after["box_launches"] - before["box_launches"]
+            nb = int(is_box.sum())
+            res[mode] = {"wall_s": wall, "queries_per_s": nb / wall, "requests_per_s": n / wall,
+                         "tf_frames_per_s": (n - nb) / wall,
+                         "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
+                         "box_p50_ms": _pct(lat[is_box], 50), "box_p99_ms": _pct(lat[is_box], 99),
+                         "tf_p50_ms": _pct(lat[~is_box], 50), "tf_p99_ms": _pct(lat[~is_box], 99),
+                         "mean_batch": nb / max(launches, 1), "box_launches": launches,
+                         "failed": after["failed"] - before["failed"]}
+            if form == "batched" and mode == "offered":
+                # served results against the same boxes queried alone (fp32 tolerance)
+                rng = np.random.default_rng(7)
+                pick = rng.choice(np.flatnonzero(is_box), size=min(200, int(is_box.sum())), replace=False)
+                ok = True
+                for i in pick:
+                    g = graphs[reqs[i]["volume"]]
+                    b = torch.from_numpy(np.asarray(reqs[i]["box"], np.int32).reshape(1, 6)).to(dev)
+                    ref = mg.mg_query_boxes(g, b, hist="f32").cpu().numpy()[0].astype(np.float64)
+                    got = results[i].astype(np.float64)
+                    ok &= bool(np.all(np.abs(got - ref) <= np.maximum(1e-5 * np.abs(ref), 1e-7)))
+                res[mode]["sampled_alone_match"] = {"boxes": int(len(pick)), "ok": ok}
+            del results
+        res["memory_admitted_bytes"] = srv.stats()["memory_admitted"]
+        srv.close()
+        out[form] = res
+    out["batched_over_plain_queries_per_s"] = {m: out["batched"][m]["queries_per_s"] / out["plain"][m]["queries_per_s"]
+                                               for m in ("offered", "burst")}
+    for g in graphs:
+        if g is not g2:
+            g.close()
     return out
 
 

@@ -58,7 +58,8 @@ typedef enum {
     MG_ERR_TIMEOUT = 4,      /* a bounded device-side wait expired */
     MG_ERR_CAPACITY = 5,     /* sparse output larger than the caller's capacity */
     MG_ERR_UNSUPPORTED = 6,  /* size or option outside what this build supports */
-    MG_ERR_INEXACT = 7       /* an integer push met a weight not divisible by a+b */
+    MG_ERR_INEXACT = 7,      /* an integer push met a weight not divisible by a+b */
+    MG_ERR_CANCELLED = 8     /* a request of the request loop was cancelled before launch */
 } mg_status;
 
 typedef enum { MG_F32 = 0, MG_F16 = 1, MG_BF16 = 2 } mg_dtype;
@@ -278,6 +279,116 @@ MG_API mg_status mg_count_cubes(const mg_graph *g, const int32_t *boxes, int64_t
  */
 MG_API mg_status mg_render_lookup(const mg_graph *g, const void *vals, int C, mg_dtype dtype,
                                   const float *samples, int64_t P, void *out, mg_stream stream);
+
+/*
+ * Request loop (serving).  A server keeps the graphs of several volumes
+ * resident on one GPU and runs box-histogram requests (Sec. 3.6) and
+ * TF-update frames (propagation, Sec. 3.5, then ray-sample lookups, Sec. 4)
+ * as they arrive.  A worker thread owns `slots` CUDA streams.  Whenever a
+ * slot is free it takes the oldest queued request; a box request takes with
+ * it every queued box of the same volume that still fits the slot's batch
+ * (max_batch boxes and the footprint capacity of the slot's captured query
+ * plan), and the whole batch runs as one plan launch; a TF frame runs alone.
+ * Requests that arrive while slots are busy join the next batch, so batches
+ * of different volumes overlap on the device (continuous batching).  The
+ * paper evaluates single queries; the loop is a deployment layer around its
+ * operations.
+ *
+ * Memory: every admitted volume gets, per slot, a query plan and staging
+ * buffers (device and pinned host) sized by the options.  A volume whose
+ * graph plus these buffers would take the server past memory_budget is not
+ * admitted (MG_ERR_CAPACITY), so resident volumes never compete for memory
+ * at run time.
+ */
+typedef struct mg_server mg_server;   /* opaque */
+
+typedef struct {
+    int slots;              /* concurrent streams (0 = 4; at most 64) */
+    int max_batch;          /* boxes per launch (0 = 1024; at most 2^20) */
+    int hist_type;          /* MG_HIST_U32 (exact counts) or MG_HIST_F32 */
+    int storage;            /* TF frames: node values as MG_F32, MG_F16 or MG_BF16 */
+    int64_t max_samples;    /* TF frames: ray samples per frame (0 = 65536) */
+    int64_t memory_budget;  /* bytes the admitted volumes may hold (0 = no limit) */
+    int plain;              /* 1: no batching, every box is its own one-CTA launch
+                               (the one-launch-per-query baseline under the same traffic) */
+    int reserved[5];        /* zero */
+} mg_server_opts;
+
+typedef enum { MG_REQ_BOX = 0, MG_REQ_TF = 1 } mg_request_kind;
+
+typedef struct {
+    int kind;               /* mg_request_kind */
+    int volume;             /* index returned by mg_server_add_volume */
+    int32_t box[6];         /* MG_REQ_BOX: (x, y, z, dx, dy, dz) as for mg_query_boxes */
+    const float *tf;        /* MG_REQ_TF: S x C fp32 transfer function (host) */
+    const float *samples;   /* MG_REQ_TF: P x 4 fp32 samples as for mg_render_lookup (host) */
+    int64_t P;              /* MG_REQ_TF: number of samples, 0..max_samples */
+    void *result;           /* host, may be NULL.  MG_REQ_BOX: S counts (uint32, or fp32 with
+                               MG_HIST_F32).  MG_REQ_TF: P x C values in the storage dtype */
+    double arrival_s;       /* mg_server_replay only: arrival time in seconds from its start */
+} mg_request;
+
+typedef struct {
+    int64_t box_requests;   /* completed box requests */
+    int64_t tf_requests;    /* completed TF frames */
+    int64_t box_launches;   /* box batches launched (plan runs, or plain launches) */
+    int64_t max_batch_seen; /* largest box batch */
+    int64_t cancelled;      /* requests cancelled before launch */
+    int64_t failed;         /* requests that completed with an error */
+    int64_t memory_admitted; /* bytes the admitted volumes hold (graphs, plans, buffers) */
+} mg_server_stats;
+
+/* Create a server on the current device.  opts may be NULL (defaults).
+ * Invalid options: MG_ERR_INVALID_ARG before any CUDA call. */
+MG_API mg_status mg_server_create(const mg_server_opts *opts, mg_server **out);
+
+/* Admit a volume: its graph g (built with mg_build, owned by the caller and
+ * kept alive until mg_server_free) and the channel count C (1-8, 12 or 16) of
+ * its TF frames.  Only before mg_server_start.  Allocates the volume's
+ * per-slot plans and buffers from g's allocator, runs each slot's scratch up
+ * to size (serving then allocates nothing) and synchronises the device.
+ * MG_ERR_CAPACITY if the budget does not hold it (nothing is kept).
+ * *volume = its index. */
+MG_API mg_status mg_server_add_volume(mg_server *sv, mg_graph *g, int C, int *volume);
+
+/* Start the worker thread.  Volumes cannot be added afterwards. */
+MG_API mg_status mg_server_start(mg_server *sv);
+
+/* Queue a request (thread-safe; before mg_server_start requests wait in the
+ * queue).  The request is copied; tf, samples and result must stay valid
+ * until it completes.  Checked on the host: volume,
+ * kind, box bounds (MG_ERR_INVALID_ARG), P <= max_samples, and a box whose
+ * footprint alone exceeds a slot's plan capacity (MG_ERR_CAPACITY).
+ * *ticket identifies it for mg_server_wait / mg_server_cancel. */
+MG_API mg_status mg_server_submit(mg_server *sv, const mg_request *r, uint64_t *ticket);
+
+/* Cancel a queued request: MG_OK if it had not been launched (its wait then
+ * returns MG_ERR_CANCELLED), MG_ERR_INVALID_ARG if it was already launched,
+ * done or unknown. */
+MG_API mg_status mg_server_cancel(mg_server *sv, uint64_t ticket);
+
+/* Wait for a request (thread-safe).  *latency_s (may be NULL) = seconds from
+ * its submission (or replay arrival) to its result being in host memory.
+ * Returns the request's status; MG_ERR_TIMEOUT if it is not done within
+ * timeout_s seconds (0 = no limit), leaving it queued or running. */
+MG_API mg_status mg_server_wait(mg_server *sv, uint64_t ticket, double timeout_s, double *latency_s);
+
+/* Replay a timed request stream: submits reqs[i] at reqs[i].arrival_s
+ * (non-decreasing, seconds from the start of the call) from the calling
+ * thread, then waits for all of them.  latency_s[i] (may be NULL) is measured
+ * from the scheduled arrival, so queueing behind a late submission counts.
+ * *wall_s (may be NULL) = seconds from the start to the last completion.
+ * Returns the first failing request's status (the rest still complete). */
+MG_API mg_status mg_server_replay(mg_server *sv, const mg_request *reqs, int64_t n, double *latency_s,
+                                  double *wall_s);
+
+/* Counters since creation. */
+MG_API mg_status mg_server_stats_get(mg_server *sv, mg_server_stats *stats);
+
+/* Stop the worker (queued requests complete with MG_ERR_CANCELLED), wait for
+ * launched work and release the server's memory.  The graphs stay the
+ * caller's.  NULL is ignored. */
+MG_API void mg_server_free(mg_server *sv);
 
 /* Synchronise `stream`, read and clear the graph's device status word.
  * Returns MG_OK or the first error recorded by an earlier call's kernels. */

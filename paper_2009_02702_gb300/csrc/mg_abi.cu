@@ -25,6 +25,8 @@ struct DeviceGuard {
     }
 };
 
+}  // namespace
+
 mg_status status_from_bits(unsigned bits) {
     if (bits & kStatBadInput) return fail(MG_ERR_INVALID_ARG, "device saw invalid input (ID >= num_segments or malformed box)");
     if (bits & kStatCapacity) return fail(MG_ERR_CAPACITY, "node table capacity exceeded on the device");
@@ -32,7 +34,6 @@ mg_status status_from_bits(unsigned bits) {
     if (bits & kStatInexact) return fail(MG_ERR_INEXACT, "integer push met a weight not divisible by a+b");
     return MG_OK;
 }
-}  // namespace
 
 void set_error(const std::string& msg) { t_err = msg; }
 
@@ -132,6 +133,14 @@ mg_status arena_begin(mg_graph* g, cudaStream_t s, Arena** out) {
     a->used = 0;
     *out = a;
     return MG_OK;
+}
+
+void arena_drop(mg_graph* g, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g->arena_mu);
+    auto it = g->arenas.find(s);
+    if (it == g->arenas.end()) return;
+    it->second->buf.s = nullptr;   // the caller has synchronised the device
+    g->arenas.erase(it);
 }
 
 mg_status sync_status(mg_graph* g, cudaStream_t s) {

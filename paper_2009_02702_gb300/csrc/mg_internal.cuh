@@ -34,6 +34,8 @@ constexpr uint32_t kDead = 0xFFFFFFFEu;   // node slot lost a publication race
 void set_error(const std::string& msg);
 mg_status fail(mg_status st, const std::string& msg);
 mg_status cuda_fail(cudaError_t e, const char* what);
+// the error of the first bit set in a device status word (MG_OK for 0)
+mg_status status_from_bits(unsigned bits);
 
 #define MG_CUDA(call)                                            \
     do {                                                         \
@@ -180,10 +182,25 @@ mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const 
 mg_status query_timing(const mg_graph* g, float* plan_ms, float* main_ms, float* out_ms);
 // the arena of `s` on graph g, reset for a new call (grown if the last call overflowed)
 mg_status arena_begin(mg_graph* g, cudaStream_t s, Arena** out);
+// release the arena of a stream that is about to be destroyed (device idle)
+void arena_drop(mg_graph* g, cudaStream_t s);
 mg_status count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64_t* cubes,
                       cudaStream_t s);
 mg_status render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dt, const float* samples,
                         int64_t P, void* out, cudaStream_t s);
+
+// A query plan's own buffers, executable graph and footprint capacities, for
+// the request loop, which stages boxes straight into them: a run is the boxes
+// in `boxes`, Q in `Qd`, a launch of `exec`, and Q x S values in `result`.
+struct PlanParts {
+    int32_t* boxes;
+    int64_t* Qd;
+    void* result;
+    cudaGraphExec_t exec;
+    uint32_t chunk;
+    uint64_t cap_blocks, cap_chunks;
+};
+PlanParts plan_parts(const mg_query_plan* p);
 
 // ---------------------------------------------------------------------------
 // small device helpers

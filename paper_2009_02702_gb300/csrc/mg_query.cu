@@ -1496,6 +1496,12 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
 }  // namespace
 }  // namespace mg
 
+namespace mg {
+PlanParts plan_parts(const mg_query_plan* p) {
+    return PlanParts{p->boxes, p->Qd, p->result, p->exec, p->chunk, p->cap_blocks, p->cap_chunks};
+}
+}  // namespace mg
+
 using mg::fail;
 
 extern "C" {

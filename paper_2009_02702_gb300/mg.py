@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmg.so")
 
 MG_OK, MG_ERR_INVALID_ARG, MG_ERR_OOM, MG_ERR_CUDA = 0, 1, 2, 3
 MG_ERR_TIMEOUT, MG_ERR_CAPACITY, MG_ERR_UNSUPPORTED, MG_ERR_INEXACT = 4, 5, 6, 7
+MG_ERR_CANCELLED = 8
+MG_REQ_BOX, MG_REQ_TF = 0, 1
 MG_F32, MG_F16, MG_BF16 = 0, 1, 2
 MG_HIST_U32, MG_HIST_F32 = 0, 1
 MG_LAYOUT_DENSE, MG_LAYOUT_CSR = 0, 1
@@ -34,8 +36,10 @@ _TORCH_TO_MG = {torch.float32: MG_F32, torch.float16: MG_F16, torch.bfloat16: MG
 EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_copy_mip", "mg_propagate_tf",
            "mg_query_boxes", "mg_query_boxes_noalloc", "mg_query_timing",
            "mg_query_plan_create", "mg_query_plan_run", "mg_query_plan_free", "mg_query_autotune",
-           "mg_query_set_tuning", "mg_count_cubes", "mg_render_lookup", "mg_sync_status", "mg_free",
-           "mg_last_error", "mg_version")
+           "mg_query_set_tuning", "mg_count_cubes", "mg_render_lookup",
+           "mg_server_create", "mg_server_add_volume", "mg_server_start", "mg_server_submit", "mg_server_cancel",
+           "mg_server_wait", "mg_server_replay", "mg_server_stats_get", "mg_server_free",
+           "mg_sync_status", "mg_free", "mg_last_error", "mg_version")
 
 
 class MGError(RuntimeError):
@@ -67,6 +71,23 @@ class mg_query_opts(ctypes.Structure):
     _fields_ = [("hist_type", ctypes.c_int), ("layout", ctypes.c_int), ("alpha_dtype", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("chunk_cubes", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("timing", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class mg_server_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("max_batch", ctypes.c_int), ("hist_type", ctypes.c_int),
+                ("storage", ctypes.c_int), ("max_samples", ctypes.c_int64), ("memory_budget", ctypes.c_int64),
+                ("plain", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+class mg_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("volume", ctypes.c_int), ("box", ctypes.c_int32 * 6),
+                ("tf", ctypes.c_void_p), ("samples", ctypes.c_void_p), ("P", ctypes.c_int64),
+                ("result", ctypes.c_void_p), ("arrival_s", ctypes.c_double)]
+
+
+class mg_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("box_requests", "tf_requests", "box_launches", "max_batch_seen",
+                                              "cancelled", "failed", "memory_admitted")]
 
 
 _lib = None
@@ -115,6 +136,24 @@ def lib():
         L.mg_count_cubes.restype = st
         L.mg_render_lookup.argtypes = [P, P, i32, i32, P, i64, P, P]
         L.mg_render_lookup.restype = st
+        L.mg_server_create.argtypes = [ctypes.POINTER(mg_server_opts), ctypes.POINTER(P)]
+        L.mg_server_create.restype = st
+        L.mg_server_add_volume.argtypes = [P, P, i32, ctypes.POINTER(ctypes.c_int)]
+        L.mg_server_add_volume.restype = st
+        L.mg_server_start.argtypes = [P]
+        L.mg_server_start.restype = st
+        L.mg_server_submit.argtypes = [P, ctypes.POINTER(mg_request), ctypes.POINTER(ctypes.c_uint64)]
+        L.mg_server_submit.restype = st
+        L.mg_server_cancel.argtypes = [P, ctypes.c_uint64]
+        L.mg_server_cancel.restype = st
+        L.mg_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+        L.mg_server_wait.restype = st
+        L.mg_server_replay.argtypes = [P, ctypes.POINTER(mg_request), i64, P, ctypes.POINTER(ctypes.c_double)]
+        L.mg_server_replay.restype = st
+        L.mg_server_stats_get.argtypes = [P, ctypes.POINTER(mg_server_stats)]
+        L.mg_server_stats_get.restype = st
+        L.mg_server_free.argtypes = [P]
+        L.mg_server_free.restype = None
         L.mg_sync_status.argtypes = [P, P]
         L.mg_sync_status.restype = st
         L.mg_free.argtypes = [P]
@@ -456,3 +495,145 @@ def mg_sync_status(g: Graph, stream=None):
 
 def mg_free(g: Graph):
     lib().mg_free(g.handle)
+
+
+# --------------------------------------------------------------------------
+# request loop (mg_server_*)
+# --------------------------------------------------------------------------
+_NP_STORAGE = {"f32": "float32", "f16": "float16", "bf16": "uint16"}   # bf16 results as raw bits
+
+
+class Server:
+    """A request loop over resident volumes (mg_server_*).
+
+    Results land in numpy arrays owned by this object until the request is
+    waited for; box results are (S,) uint32 (hist='u32') or float32, TF frames
+    (P, C) in the storage dtype (bf16 as raw uint16 bits)."""
+
+    def __init__(self, slots: int = 4, max_batch: int = 1024, hist: str = "u32", storage: str = "f32",
+                 max_samples: int = 65536, memory_budget: int = 0, plain: bool = False):
+        import numpy as np
+        self._np = np
+        o = mg_server_opts()
+        o.slots, o.max_batch = slots, max_batch
+        o.hist_type = MG_HIST_F32 if hist == "f32" else MG_HIST_U32
+        o.storage = _DTYPES[storage][0]
+        o.max_samples, o.memory_budget, o.plain = max_samples, memory_budget, 1 if plain else 0
+        h = ctypes.c_void_p()
+        _check(lib().mg_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h.value
+        self.hist_dtype = np.float32 if hist == "f32" else np.uint32
+        self.storage_dtype = np.dtype(_NP_STORAGE[storage])
+        self.volumes = []      # (graph, C)
+        self._live = {}        # ticket -> objects the library writes or reads
+
+    def add_volume(self, g: Graph, C: int = 4) -> int:
+        v = ctypes.c_int(-1)
+        with torch.cuda.device(g.device):
+            _check(lib().mg_server_add_volume(self.handle, g.handle, C, ctypes.byref(v)))
+        self.volumes.append((g, C))
+        return v.value
+
+    def start(self):
+        _check(lib().mg_server_start(self.handle))
+
+    def _request(self, kind, volume, box=None, tf=None, samples=None, out=None, arrival=0.0):
+        np = self._np
+        r = mg_request()
+        r.kind, r.volume, r.arrival_s = kind, volume, float(arrival)
+        keep = []
+        g, C = self.volumes[volume] if 0 <= volume < len(self.volumes) else (None, 0)
+        if kind == MG_REQ_BOX:
+            for k in range(6):
+                r.box[k] = int(box[k])
+            if out is None and g is not None:
+                out = np.empty(g.S, self.hist_dtype)
+        else:
+            tf = np.ascontiguousarray(tf, np.float32)
+            keep.append(tf)
+            r.tf = tf.ctypes.data
+            P = 0
+            if samples is not None:
+                samples = np.ascontiguousarray(samples, np.float32)
+                keep.append(samples)
+                r.samples = samples.ctypes.data
+                P = samples.shape[0]
+            r.P = P
+            if out is None:
+                out = np.empty((P, C), self.storage_dtype)
+        if out is not None:
+            r.result = out.ctypes.data
+        keep.append(out)
+        return r, out, keep
+
+    def submit_box(self, volume: int, box, out=None):
+        """Queue a box-histogram request; returns (ticket, result array)."""
+        r, out, keep = self._request(MG_REQ_BOX, volume, box=box, out=out)
+        t = ctypes.c_uint64()
+        _check(lib().mg_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        self._live[t.value] = keep
+        return t.value, out
+
+    def submit_tf(self, volume: int, tf, samples=None, out=None):
+        """Queue a TF frame (propagate tf (S, C), look up samples (P, 4)); returns (ticket, result array)."""
+        r, out, keep = self._request(MG_REQ_TF, volume, tf=tf, samples=samples, out=out)
+        t = ctypes.c_uint64()
+        _check(lib().mg_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        self._live[t.value] = keep
+        return t.value, out
+
+    def wait(self, ticket: int, timeout: float = 0.0) -> float:
+        """Wait for a request; returns its latency in seconds (raises MGError on failure)."""
+        lat = ctypes.c_double()
+        st = lib().mg_server_wait(self.handle, ticket, timeout, ctypes.byref(lat))
+        if st != MG_ERR_TIMEOUT:
+            self._live.pop(ticket, None)
+        _check(st)
+        return lat.value
+
+    def cancel(self, ticket: int):
+        _check(lib().mg_server_cancel(self.handle, ticket))
+
+    def replay(self, requests):
+        """Replay a timed stream.  requests: dicts with kind ('box' | 'tf'),
+        volume, arrival (s) and box, or tf (+ samples).  Returns
+        (results, latencies (n,) seconds, wall seconds)."""
+        np = self._np
+        n = len(requests)
+        arr = (mg_request * max(n, 1))()
+        results, keep = [], []
+        for i, q in enumerate(requests):
+            if q["kind"] == "box":
+                r, out, k = self._request(MG_REQ_BOX, q["volume"], box=q["box"], out=q.get("out"),
+                                          arrival=q["arrival"])
+            else:
+                r, out, k = self._request(MG_REQ_TF, q["volume"], tf=q["tf"], samples=q.get("samples"),
+                                          out=q.get("out"), arrival=q["arrival"])
+            arr[i] = r
+            results.append(out)
+            keep.append(k)
+        lat = np.zeros(max(n, 1), np.float64)
+        wall = ctypes.c_double()
+        _check(lib().mg_server_replay(self.handle, arr, n, lat.ctypes.data, ctypes.byref(wall)))
+        return results, lat[:n], wall.value
+
+    def stats(self) -> dict:
+        s = mg_server_stats()
+        _check(lib().mg_server_stats_get(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in mg_server_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().mg_server_free(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mg_server_create(**kw) -> Server:
+    return Server(**kw)

@@ -13,6 +13,9 @@ segment counts and structure:
          4x along z (Neocortex-like)
   cfg 4  614x961x600 uint16, background 0 plus 15,916 non-overlapping random
          cylinders, radius 2-6, length 50-600 (Polymer-like)
+  cfg 5  serving mix over the volumes of cfgs 1-3: Poisson arrivals (mean
+         20,000 requests/s), 90% box histograms with log-uniform sides, 10%
+         TF frames
 
 Every draw comes from numpy's PCG64 seeded with 2009027020 + config index
 (one independent stream per purpose).  Voronoi assignment is exact integer
@@ -45,6 +48,8 @@ CONFIGS = {
     4: dict(name="cylinders-614x961x600-s15917", dims=(614, 961, 600), S=15917,
             kind="cylinders", queries=10000, box="loguniform", box_max=600,
             radius=(2.0, 6.0), length=(50.0, 600.0), tries=32),
+    5: dict(name="serving-mix-cfg1-3-poisson20k", volumes=(1, 2, 3), rate=20000.0, tf_frac=0.1,
+            requests=40000, frame_samples=4096),
 }
 
 
@@ -268,3 +273,35 @@ def make_samples(cfg_index: int, dims=None, width: int = 1920, height: int = 108
     lod = np.log2(np.maximum(t * pix, 1e-30)) + lod_bias
     out = np.concatenate([pos, lod[..., None]], axis=-1).reshape(-1, 4).astype(np.float32)
     return np.ascontiguousarray(out)
+
+
+# --------------------------------------------------------------------------
+# request streams for the serving loop
+# --------------------------------------------------------------------------
+def make_request_mix(n: int, rate: float, vol_dims, box_max, tf_frac: float = 0.1, stream_offset: int = 0,
+                     cfg_index: int = 5):
+    """A Poisson request stream over several volumes.
+
+    Returns (arrival seconds (n,), kind (n,) 0 = box / 1 = TF frame,
+    volume (n,), boxes (n, 6) int32).  Inter-arrival gaps are exponential with
+    mean 1/rate; each request picks a volume uniformly and is a TF frame with
+    probability tf_frac; box sides are floor(2^U(0, log2(box_max[v] + 1)))
+    clamped to the volume (vol_dims[v] = (nx, ny, nz)), origins uniform so the
+    box lies inside.  Boxes of TF frames are unused (zero)."""
+    rng = rng_for(cfg_index, _STREAM_BOXES + 16 * stream_offset)
+    gaps = rng.exponential(1.0 / rate, size=n)
+    arrival = np.cumsum(gaps) - gaps[0]
+    kind = (rng.random(n) < tf_frac).astype(np.int32)
+    volume = rng.integers(0, len(vol_dims), size=n).astype(np.int32)
+    boxes = np.zeros((n, 6), np.int32)
+    u = rng.random((n, 3))
+    o = rng.random((n, 3))
+    for v, dims in enumerate(vol_dims):
+        m = (volume == v) & (kind == 0)
+        d = np.array(dims, dtype=np.int64)
+        bm = int(box_max[v])
+        side = np.floor(np.exp2(u[m] * math.log2(bm + 1))).astype(np.int64)
+        side = np.clip(side, 1, np.minimum(d, bm)[None, :])
+        origin = np.minimum(np.floor(o[m] * (d[None, :] - side + 1)).astype(np.int64), d[None, :] - side)
+        boxes[m] = np.concatenate([origin, side], axis=1).astype(np.int32)
+    return arrival, kind, volume, boxes

@@ -71,3 +71,52 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(mg, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         mg.lib()
+
+
+def test_server_host_argument_checks(lib):
+    """Request-loop options and handles are checked before any CUDA call."""
+    from paper_2009_02702_gb300 import mg
+    h = ctypes.c_void_p()
+    assert lib.mg_server_create(None, None) == mg.MG_ERR_INVALID_ARG
+    for field, value in (("slots", 65), ("slots", -1), ("max_batch", -3), ("max_batch", (1 << 20) + 1),
+                         ("hist_type", 2), ("storage", 7), ("memory_budget", -1), ("plain", 2),
+                         ("max_samples", -5)):
+        o = mg.mg_server_opts()
+        setattr(o, field, value)
+        assert lib.mg_server_create(ctypes.byref(o), ctypes.byref(h)) == mg.MG_ERR_INVALID_ARG, field
+        assert h.value is None
+    v = ctypes.c_int()
+    assert lib.mg_server_add_volume(None, None, 4, ctypes.byref(v)) == mg.MG_ERR_INVALID_ARG
+    r = mg.mg_request()
+    t = ctypes.c_uint64()
+    assert lib.mg_server_submit(None, ctypes.byref(r), ctypes.byref(t)) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_server_start(None) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_server_cancel(None, 0) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_server_wait(None, 0, 0.0, None) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_server_replay(None, None, 0, None, None) == mg.MG_ERR_INVALID_ARG
+    s = mg.mg_server_stats()
+    assert lib.mg_server_stats_get(None, ctypes.byref(s)) == mg.MG_ERR_INVALID_ARG
+    lib.mg_server_free(None)
+
+
+def test_server_struct_layout_matches_header():
+    """The binding's ctypes structs have the sizes the C compiler gives the header's."""
+    import shutil
+    import subprocess
+    from paper_2009_02702_gb300 import mg
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    work = os.path.join(ROOT, "tests", "_build")
+    os.makedirs(work, exist_ok=True)
+    src = os.path.join(work, "layout.c")
+    exe = os.path.join(work, "layout")
+    with open(src, "w") as f:
+        f.write('#include <stdio.h>\n#include "mg.h"\nint main(void){printf("%zu %zu %zu %zu %zu",'
+                "sizeof(mg_server_opts),sizeof(mg_request),sizeof(mg_server_stats),sizeof(mg_query_opts),"
+                "sizeof(mg_graph_info));return 0;}\n")
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+    sizes = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert sizes == [ctypes.sizeof(mg.mg_server_opts), ctypes.sizeof(mg.mg_request),
+                     ctypes.sizeof(mg.mg_server_stats), ctypes.sizeof(mg.mg_query_opts),
+                     ctypes.sizeof(mg.mg_graph_info)]

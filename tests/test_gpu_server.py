@@ -1,0 +1,240 @@
+"""GPU tests of the request loop (mg_server_*, continuous batching).
+
+Every result served inside a mixed Poisson stream -- box histograms batched
+with other requests, TF frames overlapping them on other streams -- must equal
+the same request run alone through the one-call entry points (bit for bit) and
+the CPU oracle (exact counts; FP32 within the stated tolerance).  Also:
+admission by memory, cancellation, bounded host waits and request checks.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_02702_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL, ATOL_SMALL = 1e-5, 1e-7
+
+# reduced-size volumes with the recipes of configs 1-3
+VOLS = [(1, None, None, 64), (2, (45, 33, 27), 40, 45), (3, (48, 40, 20), 30, 48)]
+
+
+def fp32_close(x, ref):
+    x = np.asarray(x, np.float64)
+    ref = np.asarray(ref, np.float64)
+    tol = np.where(np.abs(ref) < 1e-2, ATOL_SMALL, RTOL * np.abs(ref))
+    return bool(((np.abs(x - ref) <= tol) & ((ref != 0) | (x == 0))).all())
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_2009_02702_gb300 import mg
+    mg.lib()
+    vols, graphs = [], []
+    for cfg, dims, S, bmax in VOLS:
+        vol = synth.make_volume(cfg, dims=dims, S=S)
+        S = S or synth.CONFIGS[cfg]["S"]
+        graphs.append(mg.mg_build(torch.from_numpy(vol).cuda(), S))
+        vols.append(dict(vol=vol, S=S, cfg=cfg, dims=vol.shape[::-1], bmax=bmax))
+    yield mg, vols, graphs
+    for g in graphs:
+        g.close()
+
+
+def make_stream(vols, n, rate, P=300, offset=0):
+    arr, kind, vol, boxes = synth.make_request_mix(n, rate, [v["dims"] for v in vols], [v["bmax"] for v in vols],
+                                                   0.1, stream_offset=offset)
+    reqs = []
+    for i in range(n):
+        v = int(vol[i])
+        if kind[i] == 0:
+            reqs.append(dict(kind="box", volume=v, box=boxes[i], arrival=float(arr[i])))
+        else:
+            tf = synth.make_tf(5, vols[v]["S"], 4, frame=i)
+            samples = synth.make_samples(vols[v]["cfg"], dims=vols[v]["dims"], width=P // 10, height=10, frame=i)
+            reqs.append(dict(kind="tf", volume=v, tf=tf, samples=samples, arrival=float(arr[i])))
+    return reqs
+
+
+def alone_box(mg, g, box, hist):
+    b = torch.from_numpy(np.asarray(box, np.int32).reshape(1, 6)).cuda()
+    return mg.mg_query_boxes(g, b, hist=hist).cpu().numpy()[0]
+
+
+def alone_frame(mg, g, tf, samples, storage):
+    vals = mg.mg_propagate_tf(g, torch.from_numpy(tf).cuda(), storage=storage)
+    out = mg.mg_render_lookup(g, vals, torch.from_numpy(samples).cuda())
+    torch.cuda.synchronize()
+    return out.cpu()
+
+
+def oracle_boxes(vols, reqs, idx):
+    """Brute-force histograms of the listed box requests, per volume."""
+    ref = {}
+    for v in range(len(vols)):
+        ii = [i for i in idx if reqs[i]["volume"] == v]
+        if ii:
+            h = oracle.box_hist(vols[v]["vol"], vols[v]["S"], np.stack([reqs[i]["box"] for i in ii]))
+            ref.update({i: h[k] for k, i in enumerate(ii)})
+    return ref
+
+
+def oracle_frame(vol, S, tf, samples):
+    """fp64 colour of the voxel each sample selects (Sec. 4 lookup, direct sum)."""
+    dims = oracle.level_dims(vol.shape[2], vol.shape[1], vol.shape[0])
+    lev, vox = oracle.sample_voxels(dims, samples)
+    out = np.zeros((samples.shape[0], tf.shape[1]))
+    for l in np.unique(lev):
+        col = oracle.direct_colors(vol, int(l), tf)
+        out[lev == l] = col[vox[lev == l]]
+    return out
+
+
+@pytest.mark.parametrize("hist", ["u32", "f32"])
+def test_mixed_stream_matches_alone_and_oracle(env, hist):
+    mg, vols, graphs = env
+    srv = mg.Server(slots=3, max_batch=64, hist=hist, storage="f32", max_samples=1024)
+    for g in graphs:
+        srv.add_volume(g, 4)
+    srv.start()
+    reqs = make_stream(vols, 400, 20000.0)
+    results, lat, wall = srv.replay(reqs)
+    st = srv.stats()
+    srv.close()
+    n_box = sum(r["kind"] == "box" for r in reqs)
+    assert st["box_requests"] == n_box and st["tf_requests"] == len(reqs) - n_box and st["failed"] == 0
+    assert np.all(lat > 0) and wall > 0
+    box_idx = [i for i, r in enumerate(reqs) if r["kind"] == "box"]
+    ref = oracle_boxes(vols, reqs, box_idx)
+    for i in box_idx:
+        g = graphs[reqs[i]["volume"]]
+        alone = alone_box(mg, g, reqs[i]["box"], hist)
+        if hist == "u32":
+            assert np.array_equal(results[i], ref[i]), i
+            assert np.array_equal(results[i], alone), i
+        else:
+            assert fp32_close(results[i], ref[i]), i
+            assert fp32_close(results[i], alone), i
+    for i, r in enumerate(reqs):
+        if r["kind"] != "tf":
+            continue
+        v = vols[r["volume"]]
+        alone = alone_frame(mg, graphs[r["volume"]], r["tf"], r["samples"], "f32").numpy()
+        assert np.array_equal(results[i], alone), i
+        assert fp32_close(results[i], oracle_frame(v["vol"], v["S"], r["tf"], r["samples"])), i
+
+
+def test_burst_is_batched_and_exact(env):
+    """Requests queued before the worker starts go out as full batches."""
+    mg, vols, graphs = env
+    srv = mg.Server(slots=2, max_batch=32, hist="u32")
+    for g in graphs:
+        srv.add_volume(g, 4)
+    reqs = make_stream(vols, 300, 1e9, offset=1)
+    reqs = [r for r in reqs if r["kind"] == "box"]
+    tickets = [srv.submit_box(r["volume"], r["box"]) for r in reqs]
+    srv.start()
+    for t, _ in tickets:
+        srv.wait(t, timeout=60.0)
+    st = srv.stats()
+    srv.close()
+    assert st["box_requests"] == len(reqs)
+    assert st["max_batch_seen"] == 32
+    assert st["box_launches"] < len(reqs) // 8
+    ref = oracle_boxes(vols, reqs, range(len(reqs)))
+    for i, (_, out) in enumerate(tickets):
+        assert np.array_equal(out, ref[i]), i
+
+
+def test_plain_server_same_results(env):
+    """The unbatched one-launch-per-box form serves the same exact counts."""
+    mg, vols, graphs = env
+    srv = mg.Server(slots=2, max_batch=4, hist="u32", plain=True, max_samples=1024)
+    for g in graphs:
+        srv.add_volume(g, 4)
+    srv.start()
+    reqs = make_stream(vols, 120, 20000.0, offset=2)
+    results, lat, _ = srv.replay(reqs)
+    st = srv.stats()
+    srv.close()
+    box_idx = [i for i, r in enumerate(reqs) if r["kind"] == "box"]
+    assert st["box_launches"] == len(box_idx) and st["max_batch_seen"] == 1
+    ref = oracle_boxes(vols, reqs, box_idx)
+    for i in box_idx:
+        assert np.array_equal(results[i], ref[i]), i
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_low_precision_frames_match_alone(env, storage):
+    mg, vols, graphs = env
+    srv = mg.Server(slots=2, max_batch=16, storage=storage, max_samples=1024)
+    for g in graphs:
+        srv.add_volume(g, 4)
+    srv.start()
+    reqs = [r for r in make_stream(vols, 200, 20000.0, offset=3) if r["kind"] == "tf"][:8]
+    t0 = reqs[0]["arrival"]
+    for r in reqs:
+        r["arrival"] -= t0
+    results, _, _ = srv.replay(reqs)
+    srv.close()
+    for i, r in enumerate(reqs):
+        alone = alone_frame(mg, graphs[r["volume"]], r["tf"], r["samples"], storage)
+        assert np.array_equal(results[i], alone.view(torch.int16).numpy().view(results[i].dtype)), i
+
+
+def test_admission_by_memory_budget(env):
+    mg, vols, graphs = env
+    probe = mg.Server(slots=2, max_batch=16)
+    probe.add_volume(graphs[0], 4)
+    need = probe.stats()["memory_admitted"]
+    probe.close()
+    assert need >= graphs[0].info["device_bytes"]
+    srv = mg.Server(slots=2, max_batch=16, memory_budget=need + need // 2)
+    assert srv.add_volume(graphs[0], 4) == 0
+    with pytest.raises(mg.MGError) as e:
+        srv.add_volume(graphs[0], 4)
+    assert e.value.status == mg.MG_ERR_CAPACITY and "not admitted" in str(e.value)
+    assert srv.stats()["memory_admitted"] == need
+    srv.close()
+
+
+def test_cancel_timeout_and_request_checks(env):
+    mg, vols, graphs = env
+    srv = mg.Server(slots=1, max_batch=8, max_samples=64)
+    v = srv.add_volume(graphs[0], 4)
+    boxes = synth.make_boxes(1, 5)
+    tickets = [srv.submit_box(v, b) for b in boxes]
+    # not started: a bounded wait runs out and leaves the request queued
+    with pytest.raises(mg.MGError) as e:
+        srv.wait(tickets[0][0], timeout=0.05)
+    assert e.value.status == mg.MG_ERR_TIMEOUT
+    srv.cancel(tickets[2][0])
+    with pytest.raises(mg.MGError) as e:
+        srv.cancel(tickets[2][0])
+    assert e.value.status == mg.MG_ERR_INVALID_ARG
+    # host checks at submission
+    bad = [dict(box=(64, 0, 0, 1, 1, 1)), dict(box=(0, 0, 0, 0, 1, 1)), dict(box=(-1, 0, 0, 1, 1, 1))]
+    for b in bad:
+        with pytest.raises(mg.MGError) as e:
+            srv.submit_box(v, b["box"])
+        assert e.value.status == mg.MG_ERR_INVALID_ARG
+    with pytest.raises(mg.MGError):
+        srv.submit_box(7, boxes[0])
+    with pytest.raises(mg.MGError) as e:
+        srv.submit_tf(v, synth.make_tf(1, 64), np.zeros((65, 4), np.float32))
+    assert e.value.status == mg.MG_ERR_INVALID_ARG
+    srv.start()
+    ref = oracle.box_hist(vols[0]["vol"], vols[0]["S"], boxes)
+    for k, (t, out) in enumerate(tickets):
+        if k == 2:
+            with pytest.raises(mg.MGError) as e:
+                srv.wait(t, timeout=30.0)
+            assert e.value.status == mg.MG_ERR_CANCELLED
+        else:
+            srv.wait(t, timeout=30.0)
+            assert np.array_equal(out, ref[k])
+    st = srv.stats()
+    assert st["cancelled"] == 1 and st["box_requests"] == 4
+    srv.close()
