@@ -38,7 +38,7 @@ METRIC = "box-histogram queries/s & TF propagations/s (HBM GB/s vs peak); p99 la
 UNIT = "queries/s"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving mix) measurement")
     ap.add_argument("--serve-requests", type=int, default=0)
     ap.add_argument("--serve-rate", type=float, default=0.0)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload_config(cfg_index, Q, args):
@@ -175,6 +175,36 @@ def measured_traffic(kernel, cfg_i, Q):
 
 
 # --------------------------------------------------------------------------
+# multi-rank plumbing (one replica per GPU, weak scaling, no data-path exchange)
+# --------------------------------------------------------------------------
+def rank_env():
+    """(world, rank, local_rank) from the torchrun environment (1, 0, 0 alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_boxes(cfg_i, Q, rank):
+    """This rank's own batch of boxes: same recipe, an independent stream per rank."""
+    return synth.make_boxes(cfg_i, Q=Q, stream_offset=rank)
+
+
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (the slowest rank times the job)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms_per_step):
+    """Units all ranks processed per second, timed by the slowest rank."""
+    return world * units_per_rank / (ms_per_step / 1e3)
+
+
+# --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
 def run_ours(args):
@@ -182,9 +212,7 @@ def run_ours(args):
     import torch.distributed as dist
     from paper_2009_02702_gb300 import mg
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
@@ -201,7 +229,7 @@ def run_ours(args):
     g = mg.mg_build(vol, S)
     info = g.info
     del vol
-    boxes_h = synth.make_boxes(cfg_i, Q=Q, stream_offset=rank)
+    boxes_h = rank_boxes(cfg_i, Q, rank)
     tf_h = synth.make_tf(cfg_i, S, 4)
     smp_h = synth.make_samples(cfg_i)
     P = smp_h.shape[0]
@@ -274,13 +302,9 @@ def run_ours(args):
     query_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
     look_ms = np.array([e[2].elapsed_time(e[3]) for e in ev])
     main_ms = np.array([t[1] for t in qmain])
-    tot_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(float(step_ms.sum()), world, dev)
     ms_per_step = tot_ms / args.steps
-    value = world * Q / (ms_per_step / 1e3)
+    value = whole_job_rate(world, Q, ms_per_step)
 
     # algorithmic bytes of the query kernel: box in, cube IDs (uint16 at level
     # 0, uint32 above), dense histogram out
@@ -339,12 +363,8 @@ def run_ours(args):
             e2e_step()
             ee[k][1].record(stream)
         torch.cuda.synchronize()
-        e_ms = float(np.sum([a.elapsed_time(b) for a, b in ee]))
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * Q / (e_ms / args.steps / 1e3), "unit": UNIT,
+        e_ms = max_over_ranks(float(np.sum([a.elapsed_time(b) for a, b in ee])), world, dev)
+        e2e = {"value": whole_job_rate(world, Q, e_ms / args.steps), "unit": UNIT,
                "h2d_bytes_per_step": int(boxes_h.nbytes + tf_h.nbytes + smp_h.nbytes),
                "d2h_bytes_per_step": int(Q * S * 4 + P * 16), "ms_per_step": e_ms / args.steps}
 
@@ -604,9 +624,9 @@ def cpu_baseline(cfg_i, boxes, seconds, vol=None):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
-        return
+        return None
     cfg_i = args.config
     cfg = synth.CONFIGS[cfg_i]
     Q = args.queries or cfg["queries"]

@@ -394,6 +394,15 @@ MG_API void mg_server_free(mg_server *sv);
  * Returns MG_OK or the first error recorded by an earlier call's kernels. */
 MG_API mg_status mg_sync_status(mg_graph *g, mg_stream stream);
 
+/* Self-test of failure handling: one GPU thread waits, with the same bounded
+ * wait the single-pass propagation uses between topological levels (Sec. 3.4),
+ * on a device flag that is already set (satisfied = 1: returns MG_OK) or that
+ * nothing ever sets (satisfied = 0: after spin_limit polls of >= 100 ns the
+ * wait gives up and the call returns MG_ERR_TIMEOUT).  The GPU is neither
+ * faulted nor hung and stays usable.  spin_limit: 1..2^22 (the propagation
+ * uses 2^22).  Synchronises `stream`.  The paper has no counterpart. */
+MG_API mg_status mg_selftest_bounded_wait(int satisfied, unsigned spin_limit, mg_stream stream);
+
 /* Release the graph's device memory (stream-ordered on the build stream's
  * allocator semantics; synchronises the device first).  NULL is ignored. */
 MG_API void mg_free(mg_graph *g);

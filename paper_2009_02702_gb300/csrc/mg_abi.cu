@@ -372,6 +372,12 @@ MG_API mg_status mg_sync_status(mg_graph* g, mg_stream stream) {
     return sync_status(g, reinterpret_cast<cudaStream_t>(stream));
 }
 
+MG_API mg_status mg_selftest_bounded_wait(int satisfied, unsigned spin_limit, mg_stream stream) {
+    if (satisfied != 0 && satisfied != 1) return fail(MG_ERR_INVALID_ARG, "satisfied must be 0 or 1");
+    if (spin_limit < 1 || spin_limit > (1u << 22)) return fail(MG_ERR_INVALID_ARG, "spin_limit must be in 1..2^22");
+    return selftest_wait(satisfied == 1, spin_limit, reinterpret_cast<cudaStream_t>(stream));
+}
+
 MG_API void mg_free(mg_graph* g) {
     if (!g) return;
     DeviceGuard dg(g->device);

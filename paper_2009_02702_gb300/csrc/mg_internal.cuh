@@ -186,6 +186,8 @@ mg_status arena_begin(mg_graph* g, cudaStream_t s, Arena** out);
 void arena_drop(mg_graph* g, cudaStream_t s);
 mg_status count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64_t* cubes,
                       cudaStream_t s);
+// the bounded wait of the propagation on a flag that is set (or never set)
+mg_status selftest_wait(bool satisfied, unsigned limit, cudaStream_t s);
 mg_status render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dt, const float* samples,
                         int64_t P, void* out, cudaStream_t s);
 
@@ -227,6 +229,22 @@ __device__ __forceinline__ uint8_t ld_relaxed_u8(const uint8_t* p) {
 }
 __device__ __forceinline__ void set_status(unsigned* st, unsigned bit) {
     if (st) atomicOr(st, bit);
+}
+
+// Poll *p (acquire) until it reaches `need`, sleeping between polls.  After
+// `limit` polls give up: record kStatTimeout in *status and return false, so
+// the caller can leave its kernel instead of hanging the GPU.
+__device__ __forceinline__ bool bounded_wait_geq(const unsigned* p, unsigned need, unsigned limit,
+                                                 unsigned* status) {
+    unsigned it = 0;
+    while (ld_acquire_u32(p) < need) {
+        if (++it > limit) {
+            set_status(status, kStatTimeout);
+            return false;
+        }
+        __nanosleep(100);
+    }
+    return true;
 }
 
 inline unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 30) {

@@ -173,15 +173,7 @@ __global__ void __launch_bounds__(kPropThreads) single_pass_kernel(PropTiles T, 
         const int64_t hi = min(lo + kPropTile, T.first[d] + T.count[d]);
         if (d > 0 && threadIdx.x == 0) {
             const unsigned need = (unsigned)(T.tile0[d] - T.tile0[d - 1]);
-            unsigned it = 0;
-            while (ld_acquire_u32(done + d - 1) < need) {
-                if (++it > kSpinLimit) {
-                    set_status(status, kStatTimeout);
-                    s_abort = 1;
-                    break;
-                }
-                __nanosleep(100);
-            }
+            if (!bounded_wait_geq(done + d - 1, need, kSpinLimit, status)) s_abort = 1;
         }
         __syncthreads();
         if (s_abort) break;
@@ -318,6 +310,29 @@ mg_status ensure_alpha16(mg_graph* g, mg_dtype dt, cudaStream_t s) {
     MG_CUDA(cudaStreamSynchronize(s));
     b.s = nullptr;
     return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded wait: one thread waits, with the propagation's
+// helper, on a word that is either already set or that nothing ever sets.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ unsigned g_selftest_words[2];   // [0] the awaited flag, [1] the status word
+
+__global__ void selftest_wait_kernel(unsigned limit) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) bounded_wait_geq(&g_selftest_words[0], 1u, limit, &g_selftest_words[1]);
+}
+}  // namespace
+
+mg_status selftest_wait(bool satisfied, unsigned limit, cudaStream_t s) {
+    const unsigned init[2] = {satisfied ? 1u : 0u, 0u};
+    MG_CUDA(cudaMemcpyToSymbolAsync(g_selftest_words, init, sizeof(init), 0, cudaMemcpyHostToDevice, s));
+    selftest_wait_kernel<<<1, 32, 0, s>>>(limit);
+    MG_CUDA(cudaGetLastError());
+    unsigned words[2] = {0, 0};
+    MG_CUDA(cudaMemcpyFromSymbolAsync(words, g_selftest_words, sizeof(words), 0, cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    return status_from_bits(words[1]);
 }
 
 mg_status propagate(mg_graph* g, const float* tf, int C, mg_dtype storage, void* vals, cudaStream_t s) {

@@ -18,27 +18,36 @@
 #include <string.h>
 #include <math.h>
 
-void mgs_voronoi(int64_t nx, int64_t ny, int64_t nz, const int64_t *seeds2, const int64_t *weight,
-                 int64_t K, const int64_t *metric, int out_bytes, void *out)
+/* The ex x ey x ez block of the volume starting at voxel (x0, y0, z0),
+ * x-fastest; the whole volume is the block at the origin with its dims. */
+void mgs_voronoi_block(int64_t x0, int64_t y0, int64_t z0, int64_t ex, int64_t ey, int64_t ez,
+                       const int64_t *seeds2, const int64_t *weight, int64_t K, const int64_t *metric,
+                       int out_bytes, void *out)
 {
-    #pragma omp parallel for schedule(static)
-    for (int64_t z = 0; z < nz; z++) {
-        for (int64_t y = 0; y < ny; y++) {
-            for (int64_t x = 0; x < nx; x++) {
-                int64_t px = 2 * x + 1, py = 2 * y + 1, pz = 2 * z + 1;
+    #pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t z = 0; z < ez; z++) {
+        for (int64_t y = 0; y < ey; y++) {
+            for (int64_t x = 0; x < ex; x++) {
+                int64_t px = 2 * (x0 + x) + 1, py = 2 * (y0 + y) + 1, pz = 2 * (z0 + z) + 1;
                 int64_t best = 0, bd = -1, bw = 1;
                 for (int64_t i = 0; i < K; i++) {
-                    int64_t ex = px - seeds2[3 * i], ey = py - seeds2[3 * i + 1], ez = pz - seeds2[3 * i + 2];
-                    int64_t d = metric[0] * ex * ex + metric[1] * ey * ey + metric[2] * ez * ez;
+                    int64_t dx = px - seeds2[3 * i], dy = py - seeds2[3 * i + 1], dz = pz - seeds2[3 * i + 2];
+                    int64_t d = metric[0] * dx * dx + metric[1] * dy * dy + metric[2] * dz * dz;
                     int64_t w = weight[i];
                     if (bd < 0 || d * bw < bd * w) { best = i; bd = d; bw = w; }
                 }
-                int64_t v = (z * ny + y) * nx + x;
+                int64_t v = (z * ey + y) * ex + x;
                 if (out_bytes == 2) ((uint16_t *)out)[v] = (uint16_t)best;
                 else ((uint32_t *)out)[v] = (uint32_t)best;
             }
         }
     }
+}
+
+void mgs_voronoi(int64_t nx, int64_t ny, int64_t nz, const int64_t *seeds2, const int64_t *weight,
+                 int64_t K, const int64_t *metric, int out_bytes, void *out)
+{
+    mgs_voronoi_block(0, 0, 0, nx, ny, nz, seeds2, weight, K, metric, out_bytes, out);
 }
 
 /*
@@ -71,7 +80,8 @@ static void make_pose(const double *u, double r0, double r1, double l0, double l
 }
 
 /* mode 0: count non-background inside voxels; mode 1: paint all inside voxels;
- * mode 2: paint inside background voxels.  Returns count (mode 0) or painted. */
+ * mode 2: paint inside background voxels; mode 3: count all inside voxels.
+ * Returns the count (modes 0, 3) or the number painted. */
 static int64_t raster(const cyl_pose *p, int64_t nx, int64_t ny, int64_t nz, uint16_t *vol,
                       uint16_t id, int mode)
 {
@@ -130,6 +140,7 @@ static int64_t raster(const cyl_pose *p, int64_t nx, int64_t ny, int64_t nz, uin
                 if (rr > p->r2) continue;
                 uint16_t *vp = vol + (z * ny + y) * nx + x;
                 if (mode == 0) { if (*vp) n++; }
+                else if (mode == 3) n++;
                 else if (mode == 1) { *vp = id; n++; }
                 else if (*vp == 0) { *vp = id; n++; }
             }
@@ -143,16 +154,31 @@ int64_t mgs_cylinders(int64_t nx, int64_t ny, int64_t nz, int64_t K, int64_t T, 
 {
     int64_t V = nx * ny * nz;
     memset(vol, 0, (size_t)V * sizeof(uint16_t));
+    /* The tries of one cylinder only read the volume, so a group of them is
+     * tested in parallel; the first accepted try in order wins, exactly as a
+     * serial scan of the tries would choose. */
+    enum { G = 16 };
     for (int64_t k = 1; k <= K; k++) {
         const double *base = rnd + (k - 1) * T * 8;
         cyl_pose p;
         int64_t painted = 0;
         int done = 0;
-        for (int64_t t = 0; t < T && !done; t++) {
-            make_pose(base + t * 8, r0, r1, l0, l1, nx, ny, nz, &p);
-            if (raster(&p, nx, ny, nz, vol, 0, 0) == 0) {
-                painted = raster(&p, nx, ny, nz, vol, (uint16_t)k, 1);
-                if (painted > 0) done = 1;
+        for (int64_t t0 = 0; t0 < T && !done; t0 += G) {
+            int64_t n = T - t0 < G ? T - t0 : G;
+            int64_t blocked[G], inside[G];
+            #pragma omp parallel for schedule(dynamic, 1)
+            for (int64_t j = 0; j < n; j++) {
+                cyl_pose q;
+                make_pose(base + (t0 + j) * 8, r0, r1, l0, l1, nx, ny, nz, &q);
+                blocked[j] = raster(&q, nx, ny, nz, vol, 0, 0);
+                inside[j] = blocked[j] == 0 ? raster(&q, nx, ny, nz, vol, 0, 3) : 0;
+            }
+            for (int64_t j = 0; j < n && !done; j++) {
+                make_pose(base + (t0 + j) * 8, r0, r1, l0, l1, nx, ny, nz, &p);
+                if (blocked[j] == 0 && inside[j] > 0) {
+                    painted = raster(&p, nx, ny, nz, vol, (uint16_t)k, 1);
+                    done = 1;
+                }
             }
         }
         if (!done) painted = raster(&p, nx, ny, nz, vol, (uint16_t)k, 2);

@@ -39,7 +39,7 @@ EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_cop
            "mg_query_set_tuning", "mg_count_cubes", "mg_render_lookup",
            "mg_server_create", "mg_server_add_volume", "mg_server_start", "mg_server_submit", "mg_server_cancel",
            "mg_server_wait", "mg_server_replay", "mg_server_stats_get", "mg_server_free",
-           "mg_sync_status", "mg_free", "mg_last_error", "mg_version")
+           "mg_selftest_bounded_wait", "mg_sync_status", "mg_free", "mg_last_error", "mg_version")
 
 
 class MGError(RuntimeError):
@@ -154,6 +154,8 @@ def lib():
         L.mg_server_stats_get.restype = st
         L.mg_server_free.argtypes = [P]
         L.mg_server_free.restype = None
+        L.mg_selftest_bounded_wait.argtypes = [i32, ctypes.c_uint, P]
+        L.mg_selftest_bounded_wait.restype = st
         L.mg_sync_status.argtypes = [P, P]
         L.mg_sync_status.restype = st
         L.mg_free.argtypes = [P]
@@ -491,6 +493,15 @@ def mg_render_lookup(g: Graph, vals: torch.Tensor, samples: torch.Tensor, out: t
 def mg_sync_status(g: Graph, stream=None):
     """Synchronise and raise MGError if a kernel recorded an error."""
     _check(lib().mg_sync_status(g.handle, _stream(stream)))
+
+
+def mg_selftest_bounded_wait(satisfied: bool, spin_limit: int = 1 << 16, stream=None) -> int:
+    """Status of a bounded device wait on a flag that is set (MG_OK) or never
+    set (MG_ERR_TIMEOUT); raises only for bad arguments or CUDA errors."""
+    st = lib().mg_selftest_bounded_wait(1 if satisfied else 0, spin_limit, _stream(stream))
+    if st not in (MG_OK, MG_ERR_TIMEOUT):
+        _check(st)
+    return st
 
 
 def mg_free(g: Graph):

@@ -74,6 +74,7 @@ def _host_lib():
         lib = ctypes.CDLL(path)
         P, i64 = ctypes.c_void_p, ctypes.c_int64
         lib.mgs_voronoi.argtypes = [i64, i64, i64, P, P, i64, P, ctypes.c_int, P]
+        lib.mgs_voronoi_block.argtypes = [i64, i64, i64, i64, i64, i64, P, P, i64, P, ctypes.c_int, P]
         lib.mgs_cylinders.argtypes = [i64, i64, i64, i64, i64, P, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, P]
         lib.mgs_cylinders.restype = i64
@@ -123,6 +124,21 @@ def voronoi_host(dims, seeds2, W, metric, dtype=np.uint16) -> np.ndarray:
     m = np.ascontiguousarray(np.array(metric, dtype=np.int64))
     _host_lib().mgs_voronoi(nx, ny, nz, seeds2.ctypes.data, W.ctypes.data, seeds2.shape[0],
                             m.ctypes.data, out.itemsize, out.ctypes.data)
+    return out
+
+
+def voronoi_window(cfg_index: int, origin, extent, dims=None, S=None) -> np.ndarray:
+    """The (ez, ey, ex) block at voxel `origin` (x, y, z) of a Voronoi config's
+    volume, generated on the host without the rest of the volume."""
+    cfg = CONFIGS[cfg_index]
+    dims = tuple(dims) if dims is not None else cfg["dims"]
+    S = int(S) if S is not None else cfg["S"]
+    seeds2, W = voronoi_seeds(dims, S, cfg["weighted"], rng_for(cfg_index, _STREAM_VOLUME))
+    ex, ey, ez = (int(e) for e in extent)
+    out = np.zeros((ez, ey, ex), dtype=np.uint16)
+    m = np.ascontiguousarray(np.array(cfg["metric"], dtype=np.int64))
+    _host_lib().mgs_voronoi_block(int(origin[0]), int(origin[1]), int(origin[2]), ex, ey, ez, seeds2.ctypes.data,
+                                  W.ctypes.data, seeds2.shape[0], m.ctypes.data, out.itemsize, out.ctypes.data)
     return out
 
 

@@ -120,3 +120,10 @@ def test_server_struct_layout_matches_header():
     assert sizes == [ctypes.sizeof(mg.mg_server_opts), ctypes.sizeof(mg.mg_request),
                      ctypes.sizeof(mg.mg_server_stats), ctypes.sizeof(mg.mg_query_opts),
                      ctypes.sizeof(mg.mg_graph_info)]
+
+
+def test_selftest_wait_argument_checks(lib):
+    from paper_2009_02702_gb300 import mg
+    assert lib.mg_selftest_bounded_wait(2, 10, None) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_selftest_bounded_wait(0, 0, None) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_selftest_bounded_wait(0, (1 << 22) + 1, None) == mg.MG_ERR_INVALID_ARG
