@@ -92,6 +92,7 @@ typedef struct {
     int64_t pairs;                            /* sum over voxels of (entries - 1) */
     int64_t device_bytes;                     /* bytes the graph holds on the device */
     double build_ms;                          /* wall time of mg_build */
+    int64_t lut_entries;                      /* entries of the mixture lookup table (Sec. 3.6) */
 } mg_graph_info;
 
 /*

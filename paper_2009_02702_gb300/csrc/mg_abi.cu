@@ -155,7 +155,7 @@ mg_status sync_status(mg_graph* g, cudaStream_t s) {
 
 int64_t mg_graph::device_bytes() const {
     return (int64_t)(mip0.bytes + mip.bytes + mip0x[0].bytes + mip0x[1].bytes + mipx[0].bytes + mipx[1].bytes + pq.bytes + ab.bytes + ab32.bytes + alpha.bytes + alpha16.bytes +
-                     alphab16.bytes + status.bytes);
+                     alphab16.bytes + status.bytes + lut_meta.bytes + lut.bytes);
 }
 
 using namespace mg;
@@ -229,6 +229,7 @@ MG_API mg_status mg_graph_info_get(const mg_graph* g, mg_graph_info* info) {
     info->pairs = g->pairs;
     info->device_bytes = g->device_bytes();
     info->build_ms = g->build_ms;
+    info->lut_entries = g->lut_entries;
     return MG_OK;
 }
 

@@ -857,6 +857,7 @@ mg_status build_graph(mg_graph* g, const void* ids, int id_bytes, int64_t nx, in
     MG_TRY(g->alpha.alloc(&al, (size_t)N * sizeof(float), s));
     weights_kernel<<<grid_n(N), 256, 0, s>>>(g->ab.as<ulonglong2>(), N, S, g->ab32.as<uint2>(), g->alpha.as<float>());
     MG_CUDA(cudaGetLastError());
+    MG_TRY(build_lut(g, s));
     unsigned bits = 0;
     MG_TRY(read_scalar(&bits, status, s));
     if (bits) return fail(MG_ERR_CAPACITY, "node table overflow during the build");

@@ -138,6 +138,11 @@ struct mg_graph {
     mg::Buf alpha16;  // lazily: signed __half alpha, swap flag in the sign
     mg::Buf alphab16; // lazily: signed __nv_bfloat16 alpha, swap flag in the sign
     mg::Buf status;   // unsigned int status word
+    // mixture lookup table of the range queries (empty if too large):
+    // lut_meta[n] = (first entry, entries << 8 | lmin), lut = (source, count)
+    mg::Buf lut_meta;
+    mg::Buf lut;
+    int64_t lut_entries = 0;
     // launch shape chosen by mg_query_autotune, per histogram type (0 = none yet)
     int tuned_chunk[2] = {0, 0};
     int tuned_threads[2] = {0, 0};
@@ -175,6 +180,8 @@ mg_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, 
 mg_status build_graph(mg_graph* g, const void* ids, int id_bytes, int64_t nx, int64_t ny, int64_t nz,
                       cudaStream_t s);
 mg_status propagate(mg_graph* g, const float* tf, int C, mg_dtype storage, void* vals, cudaStream_t s);
+// the per-node mixture lookup table of the range queries (after the build)
+mg_status build_lut(mg_graph* g, cudaStream_t s);
 mg_status ensure_alpha16(mg_graph* g, mg_dtype dt, cudaStream_t s);
 mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const mg_query_opts& o,
                       void* out, size_t cap, uint32_t* seg, uint64_t* offsets, size_t* required,

@@ -50,6 +50,9 @@ struct Geom {
     // strides of the second and third axis of each copy (copy 0: x, y, z;
     // copy 1: y, z, x; copy 2: z, x, y)
     uint32_t st1[MG_MAX_LEVELS][3], st2[MG_MAX_LEVELS][3];
+    // bit l of vec_ok[c]: every row of copy c at level l starts on a 16-byte
+    // boundary (row pitch and level offset multiples of 16 bytes)
+    uint32_t vec_ok[3];
 };
 
 struct Ids {
@@ -75,6 +78,15 @@ Geom make_geom(const mg_graph* g) {
         G.st1[l][0] = dx; G.st2[l][0] = dx * dy;
         G.st1[l][1] = dy; G.st2[l][1] = dy * dz;
         G.st1[l][2] = dz; G.st2[l][2] = dz * dx;
+    }
+    for (int c = 0; c < 3; c++) {
+        G.vec_ok[c] = 0;
+        for (int l = 0; l < G.L && l < MG_MAX_LEVELS; l++) {
+            const uint32_t per16 = l == 0 ? 16u / (uint32_t)G.id0_bytes : 4u;   // IDs per 16 bytes
+            const bool ok = G.st1[l][c] % per16 == 0 && G.st2[l][c] % per16 == 0 &&
+                            (l == 0 || G.off[l] % per16 == 0);
+            if (ok) G.vec_ok[c] |= 1u << l;
+        }
     }
     return G;
 }
@@ -323,7 +335,22 @@ struct PushArgs {
     const void* alpha;
     uint32_t S;
     unsigned* status;
+    const uint2* lut_meta;   // mixture lookup table (null: walk the lerp trees)
+    const uint2* lut;
 };
+
+// The table row of node n for a push of weight w: entries (source, count)
+// scaled to 8^lmin, so each source receives (w >> 3 lmin) * count.  len = 0
+// when n has no row or w is not a multiple of 8^lmin (then the tree is walked).
+__device__ __forceinline__ void lut_row(const PushArgs& P, uint32_t n, uint32_t w, uint32_t& off, uint32_t& len,
+                                        uint32_t& k) {
+    const uint2 m = __ldg(P.lut_meta + n);
+    const uint32_t lm = 3u * (m.y & 255u);
+    len = m.y >> 8;
+    off = m.x;
+    k = w >> lm;
+    if (len && (k << lm) != w) len = 0;
+}
 
 // exact integer push of weight W from node n (Sec. 3.6 with the lerp tree of
 // Sec. 3.2): depth-first, one branch kept in registers, the other stacked
@@ -432,11 +459,21 @@ __device__ __forceinline__ void accumulate(const PushArgs& P, const Hist<FP>& H,
     const uint32_t W = (uint32_t)__popc(peers) << (3 * l);
     if (id < P.S) {
         H.add_int(id, W);
-    } else if constexpr (FP) {
-        push_frac<AT>(P, H, id, (float)W);
-    } else {
-        push_int<FP>(P, H, id, W);
+        return;
     }
+    if (std::is_same<AT, float>::value && P.lut_meta) {
+        uint32_t off, len, k;
+        lut_row(P, id, W, off, len, k);
+        if (len) {
+            for (uint32_t e = 0; e < len; e++) {
+                const uint2 ent = __ldg(P.lut + off + e);
+                H.add_int(ent.x, k * ent.y);
+            }
+            return;
+        }
+    }
+    if constexpr (FP) push_frac<AT>(P, H, id, (float)W);
+    else push_int<FP>(P, H, id, W);
 }
 
 template <bool FP>
@@ -506,7 +543,8 @@ struct MainArgs {
     float* accf;
 };
 
-constexpr int kQueue = 64;   // pending internal-node pushes per warp
+constexpr int kQueue = 320;   // pending internal-node pushes per warp (drained at >= 32)
+constexpr size_t kQueueBytes = (size_t)kQueue * 8 + 16;   // nodes, weights, counter
 
 // chunks of the launch: known on the host, or (plans) read on the device,
 // zero when the batch overflows the plan's buffers
@@ -516,195 +554,301 @@ __device__ __forceinline__ unsigned long long main_total(const MainArgs& A) {
     return over_cap(A.lim, A.blk_off, A.chunk_off, Qe) ? 0ull : A.chunk_off[Qe];
 }
 
-// push up to 32 queued (node, weight) entries, one per lane, then move the
-// rest to the front of the queue
+// a warp's queue of internal-node pushes in shared memory
+struct Queue {
+    uint32_t* n;
+    uint32_t* w;
+    uint32_t* count;
+};
+
+__device__ __forceinline__ Queue carve_queue(uint8_t* p) {
+    Queue Qu;
+    Qu.n = reinterpret_cast<uint32_t*>(p);
+    Qu.w = Qu.n + kQueue;
+    Qu.count = Qu.w + kQueue;
+    return Qu;
+}
+
+// push `take` <= 32 queued (node, weight) entries.  With the mixture table
+// the rows of all of them are flattened: entry e goes to lane e % 32, which
+// finds its row by a binary search over the inclusive sums of the row
+// lengths; nodes without a row (and 16-bit weights) walk their lerp trees.
 template <bool FP, typename AT>
-__device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
-                                   uint32_t& qc) {
+__device__ __forceinline__ void push_batch(const PushArgs& P, const Hist<FP>& H, const uint32_t* qn,
+                                           const uint32_t* qw, uint32_t take) {
     const int lane = threadIdx.x & 31;
-    const uint32_t take = min(qc, 32u);
-    if ((uint32_t)lane < take) {
+    if (std::is_same<AT, float>::value && P.lut_meta) {
+        uint32_t off = 0, len = 0, k = 0;
+        if ((uint32_t)lane < take) {
+            const uint32_t n = qn[lane], w = qw[lane];
+            lut_row(P, n, w, off, len, k);
+            if (!len) {
+                if constexpr (FP) push_frac<AT>(P, H, n, (float)w);
+                else push_int<FP>(P, H, n, w);
+            }
+        }
+        __syncwarp();
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t excl = incl - len;
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t e = base + lane;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint32_t v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+                if (v <= e) j += step;
+            }
+            const uint32_t oj = __shfl_sync(0xffffffffu, off, j);
+            const uint32_t kj = __shfl_sync(0xffffffffu, k, j);
+            const uint32_t ej = __shfl_sync(0xffffffffu, excl, j);
+            if (e < total) {
+                const uint2 ent = __ldg(P.lut + oj + (e - ej));
+                H.add_int(ent.x, kj * ent.y);
+            }
+        }
+    } else if ((uint32_t)lane < take) {
         const uint32_t n = qn[lane], w = qw[lane];
         if constexpr (FP) push_frac<AT>(P, H, n, (float)w);
         else push_int<FP>(P, H, n, w);
     }
     __syncwarp();
-    const uint32_t rest = qc - take;
+}
+
+// push queued entries 32 at a time until fewer than 32 (none if `all`) remain,
+// then move the rest to the front
+template <bool FP, typename AT>
+__device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Queue& Qu, bool all) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    const uint32_t qc = *Qu.count;
+    uint32_t done = 0;
+    while (qc - done >= 32 || (all && qc > done)) {
+        const uint32_t take = min(qc - done, 32u);
+        push_batch<FP, AT>(P, H, Qu.n + done, Qu.w + done, take);
+        done += take;
+    }
+    const uint32_t rest = qc - done;
     uint32_t tn = 0, tw = 0;
     if ((uint32_t)lane < rest) {
-        tn = qn[32 + lane];
-        tw = qw[32 + lane];
+        tn = Qu.n[done + lane];
+        tw = Qu.w[done + lane];
     }
     __syncwarp();
     if ((uint32_t)lane < rest) {
-        qn[lane] = tn;
-        qw[lane] = tw;
+        Qu.n[lane] = tn;
+        Qu.w[lane] = tw;
     }
+    if (lane == 0) *Qu.count = rest;
     __syncwarp();
-    qc = rest;
 }
 
-// lanes with `pred` add weight W to node `id`: a source into the shared
-// histogram, an internal node into the warp's push queue (drained at 32)
+// Cubes [w0, w1) of one box by one warp, b the block holding cube w0.
+//
+// The span is a flat stream of units.  A window holds the records of 31
+// consecutive blocks, one per lane; the part of each block inside the span is
+// cut into units -- 16-byte vectors of IDs (8 uint16 or 4 uint32 of one row)
+// where the block's rows are 16-byte aligned (Algorithm 1's runs start on
+// multiples of their own length, so whole rows are) and single cubes for the
+// unaligned head and tail and for every other block -- and a warp scan of
+// the unit counts lets lane k find the block of unit u by a binary search.
+// Each lane takes units u, u + 32, ... with two loads in flight, so no load
+// waits on a block boundary.  Every lane keeps a run (level, node, count) of
+// its own consecutive cubes; a finished run of a source is added to the
+// shared histogram, one of an internal node (levels >= 1) is queued for the
+// warp's pushes.
 template <bool FP, typename AT>
-__device__ __forceinline__ void add_heads(const PushArgs& P, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
-                                          uint32_t& qc, bool pred, uint32_t id, uint32_t W) {
+__device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& H, const Queue& Qu, uint32_t w0,
+                                             uint32_t w1, uint64_t b, uint64_t b1, uint32_t ncube) {
     const int lane = threadIdx.x & 31;
-    const bool internal = pred && id >= P.S;
-    if (pred && !internal) H.add_int(id, W);
-    const unsigned im = __ballot_sync(0xffffffffu, internal);
-    if (im) {
-        if (internal) {
-            const uint32_t pos = qc + __popc(im & ((1u << lane) - 1u));
-            qn[pos] = id;
-            qw[pos] = W;
-        }
-        qc += __popc(im);
-        __syncwarp();
-        if (qc >= 32) drain<FP, AT>(P, H, qn, qw, qc);
-    }
-}
-
-// contribution of one group of (up to) 32 cubes, one per lane; valid lanes
-// are a prefix.  Adjacent lanes with equal (level, node) add once.
-template <bool FP, typename AT>
-__device__ __forceinline__ void add_group(const PushArgs& P, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
-                                          uint32_t& qc, bool valid, uint32_t id, int l, unsigned le) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t pid = __shfl_up_sync(0xffffffffu, id, 1);
-    const int pl = __shfl_up_sync(0xffffffffu, l, 1);
-    const bool head = valid && (lane == 0 || id != pid || l != pl);
-    const unsigned heads = __ballot_sync(0xffffffffu, head);
-    const int nvalid = __popc(__ballot_sync(0xffffffffu, valid));
-    const unsigned after = heads & ~le;
-    const int end = min(after ? __ffs(after) - 1 : 32, nvalid);
-    add_heads<FP, AT>(P, H, qn, qw, qc, head, id, (uint32_t)(end - lane) << (3 * l));
-}
-
-// groups of 32 consecutive cubes of one block, all lanes valid.  Every lane
-// keeps a run (node rid, rcnt cubes) of its own cubes -- lane i sees cubes
-// i, i+32, i+64, ..., which inside a segment carry the same node -- and adds
-// it only when its node changes.  Level-0 IDs are segments (sources, weight
-// 1 each), so that loop is a load, a compare and an increment per cube; at
-// higher levels a finished run may be an internal node, queued warp-wide.
-template <bool FP, typename AT, typename IT, bool L0>
-__device__ __forceinline__ void block_groups(const PushArgs& P, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
-                                             uint32_t& qc, const IT* __restrict__ ids, uint32_t o, uint32_t groups,
-                                             int e0, int e1, uint32_t s1, uint32_t s2, int l) {
-    const uint32_t m0 = (1u << e0) - 1u, m1 = (1u << e1) - 1u;
-    const int sh = e0 + e1, w3 = 3 * l;
+    const uint32_t S = A.P.S;
+    const int lg0 = A.G.id0_bytes == 2 ? 3 : 2;   // log2 level-0 IDs per 16 bytes
     uint32_t rid = kNone, rcnt = 0;
-    for (uint32_t gi = 0; gi < groups; gi += 4, o += 128) {
-        const uint32_t n4 = min(4u, groups - gi);
-        uint32_t v[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const uint32_t oo = o + 32u * u;
-            v[u] = (uint32_t)u < n4 ? (uint32_t)__ldg(ids + (oo & m0) + ((oo >> e0) & m1) * s1 + (oo >> sh) * s2)
-                                    : rid;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            if ((uint32_t)u >= n4) break;
-            const uint32_t x = v[u];
-            const bool change = x != rid;
-            if constexpr (L0) {
-                if (change && rcnt) H.add_int(rid, rcnt);
-            } else {
-                add_heads<FP, AT>(P, H, qn, qw, qc, change && rcnt != 0, rid, rcnt << w3);
-            }
-            rcnt = change ? 1u : rcnt + 1u;
-            rid = x;
-        }
-    }
-    if constexpr (L0) {
-        if (rcnt) H.add_int(rid, rcnt);
-    } else {
-        add_heads<FP, AT>(P, H, qn, qw, qc, rcnt != 0, rid, rcnt << w3);
-    }
-}
-
-// cubes [w0, w1) of box q by one warp; b is the block holding cube w0.
-// Returns the block holding the last cube processed.
-template <bool FP, typename AT>
-__device__ __forceinline__ uint64_t process_span(const MainArgs& A, const Hist<FP>& H, uint32_t* qn, uint32_t* qw,
-                                                 uint32_t& qc, uint32_t w0, uint32_t w1, uint64_t b, uint64_t b1,
-                                                 uint32_t ncube, unsigned le) {
-    const int lane = threadIdx.x & 31;
-    uint32_t cur = w0;   // invariant: cube `cur` lies in block b
-    while (cur < w1) {
-        const Blk B = A.blk[b];
-        const uint32_t bend = b + 1 < b1 ? __ldg(&A.blk[b + 1].start) : ncube;
-        const uint32_t hi = min(bend, w1);
-        if (hi - cur >= 32) {
-            // whole groups of 32 cubes of block b
-            const int l = B.meta & 31, cp = (B.meta >> 5) & 3;
-            const int e0 = (B.meta >> 7) & 31, e1 = (B.meta >> 12) & 31;
-            const uint32_t groups = (hi - cur) >> 5;
-            const uint32_t o = cur - B.start + lane;
-            const uint32_t s1 = A.G.st1[l][cp], s2 = A.G.st2[l][cp];
-            if (l == 0 && A.G.id0_bytes == 2)
-                block_groups<FP, AT, uint16_t, true>(A.P, H, qn, qw, qc,
-                                                     static_cast<const uint16_t*>(A.I.l0[cp]) + B.base, o, groups, e0,
-                                                     e1, s1, s2, 0);
-            else if (l == 0)
-                block_groups<FP, AT, uint32_t, true>(A.P, H, qn, qw, qc,
-                                                     static_cast<const uint32_t*>(A.I.l0[cp]) + B.base, o, groups, e0,
-                                                     e1, s1, s2, 0);
-            else
-                block_groups<FP, AT, uint32_t, false>(A.P, H, qn, qw, qc, A.I.hi[cp] + A.G.off[l] + B.base, o, groups,
-                                                      e0, e1, s1, s2, l);
-            cur += groups << 5;
-            if (cur == bend && b + 1 < b1) b++;
+    int rl = 0;
+    auto finish = [&]() {
+        if (!rcnt) return;
+        const uint32_t W = rcnt << (3 * rl);
+        if (rl == 0 || rid < S) {
+            H.add_int(rid, W);
         } else {
-            // the next (up to) 32 cubes may span several blocks: lane k >= 1
-            // marks where block b+k begins, each lane counts the marks at or
-            // before it
-            const uint32_t cube = cur + lane;
-            const bool valid = cube < w1;
-            uint32_t bit = 0;
-            if (lane > 0 && b + lane < b1) {
-                const uint32_t t = __ldg(&A.blk[b + lane].start) - cur;
-                if (t < 32) bit = 1u << t;
-            }
-            const unsigned M = __reduce_or_sync(0xffffffffu, bit);
-            uint32_t id = 0;
-            int l = 0;
-            if (valid) {
-                const Blk Bl = A.blk[b + __popc(M & le)];
-                id = cube_node(A.G, A.I, Bl, cube - Bl.start, l);
-            }
-            add_group<FP, AT>(A.P, H, qn, qw, qc, valid, id, l, le);
-            b += __popc(M);   // block of cube cur + 31
-            cur = min(cur + 32, w1);
-            if (cur < w1 && b + 1 < b1 && __ldg(&A.blk[b + 1].start) <= cur) b++;
+            const uint32_t pos = atomicAdd(Qu.count, 1u);
+            Qu.n[pos] = rid;
+            Qu.w[pos] = W;
         }
+    };
+    auto feed = [&](uint32_t x, int l) {
+        if (x == rid && l == rl) {
+            rcnt++;
+        } else {
+            finish();
+            rid = x;
+            rl = l;
+            rcnt = 1;
+        }
+    };
+    for (uint64_t bb = b;; bb += 31) {
+        const uint64_t i = bb + lane;
+        uint32_t st = ncube, base = 0, meta = 0;
+        if (i < b1) {
+            const Blk t = A.blk[i];
+            st = t.start;
+            base = t.base;
+            meta = t.meta;
+        }
+        const uint32_t nxt = __shfl_down_sync(0xffffffffu, st, 1);
+        const uint32_t lo_a = max(st, w0), hi_a = min(nxt, w1);
+        const bool use = lane < 31 && lo_a < hi_a;
+        const int l = meta & 31, cp = (meta >> 5) & 3, e0 = (meta >> 7) & 31;
+        const int lg = l == 0 ? lg0 : 2;
+        const uint32_t lo = use ? lo_a - st : 0u, hi = use ? hi_a - st : 0u;
+        const bool vec = use && e0 >= lg && ((A.G.vec_ok[cp] >> l) & 1u) && hi - lo >= (2u << lg);
+        const uint32_t vm = (1u << lg) - 1u;
+        // scalar head [lo, ha), vectors [ha, hb), scalar tail [hb, hi)
+        const uint32_t ha = vec ? (lo + vm) & ~vm : hi;
+        const uint32_t hb = vec ? hi & ~vm : hi;
+        const uint32_t nh = ha - lo, nv = (hb - ha) >> lg;
+        const uint32_t units = use ? (hi - lo) - (hb - ha) + nv : 0u;
+        uint32_t incl = units;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t excl = incl - units;
+        for (uint32_t u0 = 0; u0 < total; u0 += 64) {
+            uint4 v[2];
+            int ul[2], kind[2];   // level; 0 scalar, 1 four uint32, 2 eight uint16
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                const uint32_t u = u0 + 32u * r + lane;
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const uint32_t c = __shfl_sync(0xffffffffu, incl, j + step - 1);
+                    if (c <= u) j += step;
+                }
+                const uint32_t jbase = __shfl_sync(0xffffffffu, base, j);
+                const uint32_t jmeta = __shfl_sync(0xffffffffu, meta, j);
+                const uint32_t jlo = __shfl_sync(0xffffffffu, lo, j);
+                const uint32_t jnh = __shfl_sync(0xffffffffu, nh, j);
+                const uint32_t jnv = __shfl_sync(0xffffffffu, nv, j);
+                const uint32_t jex = __shfl_sync(0xffffffffu, excl, j);
+                kind[r] = -1;
+                v[r] = make_uint4(0u, 0u, 0u, 0u);
+                ul[r] = 0;
+                if (u < total) {
+                    const int jl = jmeta & 31, jc = (jmeta >> 5) & 3;
+                    const int je0 = (jmeta >> 7) & 31, je1 = (jmeta >> 12) & 31;
+                    const int jlg = jl == 0 ? lg0 : 2;
+                    const uint32_t t = u - jex;
+                    uint32_t o;
+                    bool vv = false;
+                    if (t < jnh) {
+                        o = jlo + t;
+                    } else if (t < jnh + jnv) {
+                        o = jlo + jnh + ((t - jnh) << jlg);
+                        vv = true;
+                    } else {
+                        o = jlo + jnh + (jnv << jlg) + (t - jnh - jnv);
+                    }
+                    const uint32_t idx = jbase + (o & ((1u << je0) - 1u)) +
+                                         ((o >> je0) & ((1u << je1) - 1u)) * A.G.st1[jl][jc] +
+                                         (o >> (je0 + je1)) * A.G.st2[jl][jc];
+                    ul[r] = jl;
+                    if (jl == 0) {
+                        if (lg0 == 3) {
+                            const uint16_t* p = static_cast<const uint16_t*>(A.I.l0[jc]) + idx;
+                            if (vv) {
+                                v[r] = __ldg(reinterpret_cast<const uint4*>(p));
+                                kind[r] = 2;
+                            } else {
+                                v[r].x = __ldg(p);
+                                kind[r] = 0;
+                            }
+                        } else {
+                            const uint32_t* p = static_cast<const uint32_t*>(A.I.l0[jc]) + idx;
+                            if (vv) {
+                                v[r] = __ldg(reinterpret_cast<const uint4*>(p));
+                                kind[r] = 1;
+                            } else {
+                                v[r].x = __ldg(p);
+                                kind[r] = 0;
+                            }
+                        }
+                    } else {
+                        const uint32_t* p = A.I.hi[jc] + A.G.off[jl] + idx;
+                        if (vv) {
+                            v[r] = __ldg(reinterpret_cast<const uint4*>(p));
+                            kind[r] = 1;
+                        } else {
+                            v[r].x = __ldg(p);
+                            kind[r] = 0;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                const int l = ul[r];
+                if (kind[r] == 0) {
+                    feed(v[r].x, l);
+                } else if (kind[r] == 1) {
+                    if (rcnt && rl == l && v[r].x == rid && v[r].y == rid && v[r].z == rid && v[r].w == rid) {
+                        rcnt += 4;
+                    } else {
+                        feed(v[r].x, l);
+                        feed(v[r].y, l);
+                        feed(v[r].z, l);
+                        feed(v[r].w, l);
+                    }
+                } else if (kind[r] == 2) {
+                    const uint32_t pr = rid * 0x10001u;
+                    if (rcnt && rl == 0 && ((v[r].x ^ pr) | (v[r].y ^ pr) | (v[r].z ^ pr) | (v[r].w ^ pr)) == 0u) {
+                        rcnt += 8;
+                    } else {
+                        const uint32_t w4[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+#pragma unroll
+                        for (int k = 0; k < 8; k++) feed((w4[k >> 1] >> (16 * (k & 1))) & 0xffffu, 0);
+                    }
+                }
+            }
+            __syncwarp();
+            if (*Qu.count >= 32) drain<FP, AT>(A.P, H, Qu, false);
+        }
+        const uint32_t st31 = __shfl_sync(0xffffffffu, st, 31);
+        if (bb + 31 >= b1 || st31 >= w1) break;
     }
-    return b;
+    finish();
+    __syncwarp();
 }
 
 // Few segments: every warp owns a histogram in shared memory and takes whole
 // chunks from the global ticket, so warps never wait for each other.
 template <bool FP, typename AT>
-__global__ void __launch_bounds__(512) query_warp_kernel(MainArgs A) {
+__global__ void __launch_bounds__(256) query_warp_kernel(MainArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t S = A.P.S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)S * 4 * (FP ? 2 : 1) + 2 * kQueue * 4;
-    uint8_t* mine = smem + warp * per_warp;
+    const size_t hist_bytes = (size_t)S * 4 * (FP ? 2 : 1);
+    uint8_t* mine = smem + warp * (hist_bytes + kQueueBytes);
     Hist<FP> H;
     H.h = reinterpret_cast<uint32_t*>(mine);
     H.hf = FP ? reinterpret_cast<float*>(H.h + S) : nullptr;
     H.touched = nullptr;
     H.ntouched = nullptr;
     H.track = false;
-    uint32_t* qn = reinterpret_cast<uint32_t*>(mine + (size_t)S * 4 * (FP ? 2 : 1));
-    uint32_t* qw = qn + kQueue;
-    const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const Queue Qu = carve_queue(mine + hist_bytes);
     for (uint32_t i = lane; i < S; i += 32) {
         H.h[i] = 0;
         if constexpr (FP) H.hf[i] = 0.f;
     }
+    if (lane == 0) *Qu.count = 0;
     __syncwarp();
     const unsigned long long total = main_total(A);
     for (;;) {
@@ -716,10 +860,8 @@ __global__ void __launch_bounds__(512) query_warp_kernel(MainArgs A) {
         const uint32_t ncube = (uint32_t)A.ncube[q];
         const uint32_t c0 = (uint32_t)(c - A.chunk_off[q]) * A.chunk;
         const uint32_t c1 = min(c0 + A.chunk, ncube);
-        uint32_t qc = 0;
-        process_span<FP, AT>(A, H, qn, qw, qc, c0, c1, __ldg(A.chunk_b + c), A.blk_off[q + 1], ncube, le);
-        if (qc) drain<FP, AT>(A.P, H, qn, qw, qc);
-        __syncwarp();
+        process_span<FP, AT>(A, H, Qu, c0, c1, __ldg(A.chunk_b + c), A.blk_off[q + 1], ncube);
+        drain<FP, AT>(A.P, H, Qu, true);
         for (uint32_t s = lane; s < S; s += 32) {
             const uint32_t v = H.h[s];
             if (v) {
@@ -753,14 +895,13 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
     // per-warp queues follow the touched list
     const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
     uint8_t* qbase = reinterpret_cast<uint8_t*>(H.touched) + ((touched_bytes + 15) & ~(size_t)15);
-    uint32_t* qn = reinterpret_cast<uint32_t*>(qbase) + warp * 2 * kQueue;
-    uint32_t* qw = qn + kQueue;
-    const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);   // lanes <= this one
+    const Queue Qu = carve_queue(qbase + warp * kQueueBytes);
     for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
         H.h[i] = 0;
         if constexpr (FP) H.hf[i] = 0.f;
     }
     if (threadIdx.x == 0) s_ntouched = 0;
+    if (lane == 0) *Qu.count = 0;
     const unsigned long long total = main_total(A);
     for (;;) {
         if (threadIdx.x == 0) {
@@ -779,7 +920,6 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
         const uint64_t b1 = A.blk_off[q + 1];
         const uint32_t sub = max(32u, (((c1 - c0) + 2 * nw - 1) / (2 * nw) + 31) & ~31u);
         uint64_t bhint = __ldg(A.chunk_b + c);   // a warp's sub-spans only move forward
-        uint32_t qc = 0;
         for (;;) {
             uint32_t k = 0;
             if (lane == 0) k = atomicAdd(&s_next, 1u);
@@ -798,9 +938,10 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
                 b = lo;
             }
             b = __shfl_sync(0xffffffffu, b, 0);
-            bhint = process_span<FP, AT>(A, H, qn, qw, qc, w0, w1, b, b1, ncube, le);
+            bhint = b;
+            process_span<FP, AT>(A, H, Qu, w0, w1, b, b1, ncube);
         }
-        if (qc) drain<FP, AT>(A.P, H, qn, qw, qc);
+        drain<FP, AT>(A.P, H, Qu, true);
         __syncthreads();
         flush<FP>(H, S, q, A.acc, A.accf);
         __syncthreads();
@@ -1048,7 +1189,7 @@ mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts&
         return MG_OK;
     }
     // few segments: a private histogram per warp; else one per CTA
-    const size_t per_warp = (size_t)g->S * 4 * (FP ? 2 : 1) + 2 * kQueue * 4;
+    const size_t per_warp = (size_t)g->S * 4 * (FP ? 2 : 1) + kQueueBytes;
     const bool warp_mode = g->S <= kWarpHistMax && threads <= 256 && per_warp * (threads / 32) <= 96 * 1024;
     auto k = warp_mode ? query_warp_kernel<FP, AT> : query_batched_kernel<FP, AT>;
     const size_t sm = warp_mode ? per_warp * (threads / 32) : smem;
@@ -1130,6 +1271,8 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
     A.I = make_ids(g);
     A.P.pq = g->pq.as<uint2>();
     A.P.ab32 = g->ab32.as<uint2>();
+    A.P.lut_meta = g->lut_meta.as<uint2>();
+    A.P.lut = g->lut.as<uint2>();
     A.P.alpha = o.alpha_dtype == MG_F16 ? g->alpha16.p : o.alpha_dtype == MG_BF16 ? g->alphab16.p : g->alpha.p;
     A.P.S = S;
     A.P.status = status;
@@ -1149,7 +1292,7 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
 
     const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
     const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + ((touched_bytes + 15) & ~(size_t)15) +
-                        (size_t)(threads / 32) * 2 * kQueue * 4 + 16;
+                        (size_t)(threads / 32) * kQueueBytes + 16;
     if (smem > 220 * 1024) return fail(MG_ERR_UNSUPPORTED, "too many segments for the shared-memory histogram");
     Buf nblk, ncube, nchunk, blk_off, chunk_off, blk, ticket, chunk_q, chunk_b;
     if (o.schedule == MG_SCHED_BATCHED) {
@@ -1463,6 +1606,8 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     A.I = make_ids(g);
     A.P.pq = g->pq.as<uint2>();
     A.P.ab32 = g->ab32.as<uint2>();
+    A.P.lut_meta = g->lut_meta.as<uint2>();
+    A.P.lut = g->lut.as<uint2>();
     A.P.alpha = std::is_same<AT, __half>::value ? g->alpha16.p : std::is_same<AT, __nv_bfloat16>::value ? g->alphab16.p
                                                                                                           : g->alpha.p;
     A.P.S = S;
@@ -1484,7 +1629,7 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     o.hist_type = FP ? MG_HIST_F32 : MG_HIST_U32;
     const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
     const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + ((touched_bytes + 15) & ~(size_t)15) +
-                        (size_t)(p->threads / 32) * 2 * kQueue * 4 + 16;
+                        (size_t)(p->threads / 32) * kQueueBytes + 16;
     MG_TRY((launch_main<FP, AT>(g, A, o, nullptr, smem, p->threads, s)));
     if (FP) {
         dense_f32_rows_kernel<<<zg, 256, 0, s>>>(acc, accf, p->Qd, S);

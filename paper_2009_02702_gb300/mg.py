@@ -64,7 +64,8 @@ class mg_graph_info(ctypes.Structure):
     _fields_ = [("num_segments", ctypes.c_uint32), ("levels", ctypes.c_int), ("depth", ctypes.c_int),
                 ("num_nodes", ctypes.c_int64), ("dims", (ctypes.c_int64 * 3) * MG_MAX_LEVELS),
                 ("bucket", ctypes.c_int64 * (MG_MAX_DEPTH + 2)), ("max_list", ctypes.c_int64),
-                ("pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double)]
+                ("pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double),
+                ("lut_entries", ctypes.c_int64)]
 
 
 class mg_query_opts(ctypes.Structure):
@@ -278,7 +279,7 @@ def mg_graph_info_get(g: Graph) -> dict:
     return dict(num_segments=info.num_segments, levels=L, depth=D, num_nodes=info.num_nodes,
                 dims=[tuple(info.dims[l][k] for k in range(3)) for l in range(L)],
                 bucket=[info.bucket[d] for d in range(D + 2)], max_list=info.max_list, pairs=info.pairs,
-                device_bytes=info.device_bytes, build_ms=info.build_ms)
+                device_bytes=info.device_bytes, build_ms=info.build_ms, lut_entries=info.lut_entries)
 
 
 def mg_graph_copy_nodes(g: Graph, stream=None):
