@@ -242,9 +242,12 @@ __global__ void plan_count_kernel(Geom G, const int32_t* __restrict__ boxes, int
     }
 }
 
+// Block records of every box, and for every work chunk of `chunk` cubes its
+// box and the block holding its first cube.
 __global__ void plan_write_kernel(Geom G, const int32_t* __restrict__ boxes, int64_t Q,
                                   const uint64_t* __restrict__ blk_off, Blk* __restrict__ blk, Lim lim,
-                                  const uint64_t* __restrict__ chunk_off) {
+                                  const uint64_t* __restrict__ chunk_off, uint32_t chunk,
+                                  uint32_t* __restrict__ chunk_q, uint32_t* __restrict__ chunk_b) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t Qe = live_q(lim, Q);
@@ -256,7 +259,7 @@ __global__ void plan_write_kernel(Geom G, const int32_t* __restrict__ boxes, int
     __shared__ Runs wr[kPlanThreads / 32];
     Runs& R = wr[threadIdx.x >> 5];
     make_runs_warp(b, G, R);
-    const uint64_t base = blk_off[q];
+    const uint64_t base = blk_off[q], cbase = chunk_off[q];
     const int npairs = R.ny * R.nz;
     uint32_t running = 0;
     for (int pbase = 0; pbase < npairs; pbase += 32) {
@@ -277,9 +280,15 @@ __global__ void plan_write_kernel(Geom G, const int32_t* __restrict__ boxes, int
         if (valid) {
             uint32_t start = running + incl - row;
             for (int i = 0; i < R.nx; i++) {
-                blk[base + (uint64_t)pr * R.nx + i] = make_blk(G, start, R.sx[i], R.sy[j], R.sz[k], R.lx[i], R.ly[j],
-                                                               R.lz[k]);
-                start += block_cubes(R.lx[i], R.ly[j], R.lz[k]);
+                const uint64_t bi = base + (uint64_t)pr * R.nx + i;
+                const uint32_t n = block_cubes(R.lx[i], R.ly[j], R.lz[k]);
+                blk[bi] = make_blk(G, start, R.sx[i], R.sy[j], R.sz[k], R.lx[i], R.ly[j], R.lz[k]);
+                // the chunks whose first cube lies in this block
+                for (uint64_t c = ((uint64_t)start + chunk - 1) / chunk; c * chunk < (uint64_t)start + n; c++) {
+                    chunk_q[cbase + c] = (uint32_t)q;
+                    chunk_b[cbase + c] = (uint32_t)bi;
+                }
+                start += n;
             }
         }
         running += tot;
@@ -1109,28 +1118,70 @@ __global__ void csr_write_kernel(const uint32_t* __restrict__ acc, const float* 
 }
 
 // box and first block of every chunk
-__global__ void chunk_map_kernel(const uint64_t* __restrict__ chunk_off, const uint64_t* __restrict__ blk_off,
-                                 const Blk* __restrict__ blk, int64_t Q, uint32_t chunk, uint32_t* __restrict__ chunk_q,
-                                 uint32_t* __restrict__ chunk_b, Lim lim) {
-    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int64_t Qe = live_q(lim, Q);
-    if (q >= Qe || over_cap(lim, blk_off, chunk_off, Qe)) return;
-    const uint64_t b0 = blk_off[q], b1 = blk_off[q + 1];
-    for (uint64_t c = chunk_off[q] + lane; c < chunk_off[q + 1]; c += 32) {
-        chunk_q[c] = (uint32_t)q;
-        const uint32_t first = (uint32_t)(c - chunk_off[q]) * chunk;
-        uint64_t lo = b0, hi = b1;   // blk[lo].start <= first < blk[hi].start
-        while (hi - lo > 1) {
-            const uint64_t mid = (lo + hi) >> 1;
-            if (blk[mid].start <= first) lo = mid;
-            else hi = mid;
+// Exclusive scans of the per-box block and chunk counts for batches of up to
+// kFusedScanMax boxes in one CTA: offsets[q] and the totals at [Q]; for plans
+// the capacity check of the batch (entries past the live batch are zero).
+constexpr int kScanThreads = 1024;
+constexpr int64_t kFusedScanMax = 1 << 18;
+
+__global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(const uint32_t* __restrict__ nblk,
+                                                                 const uint64_t* __restrict__ nchunk, int64_t Q,
+                                                                 uint64_t* __restrict__ blk_off,
+                                                                 uint64_t* __restrict__ chunk_off, Lim lim,
+                                                                 unsigned* __restrict__ status) {
+    __shared__ unsigned long long sb[32], sc[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t per = (Q + kScanThreads - 1) / kScanThreads;
+    const int64_t a = min(Q, (int64_t)t * per), e = min(Q, a + per);
+    unsigned long long tb = 0, tc = 0;
+    for (int64_t i = a; i < e; i++) {
+        tb += nblk[i];
+        tc += nchunk[i];
+    }
+    unsigned long long ib = tb, ic = tc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long yb = __shfl_up_sync(0xffffffffu, ib, o);
+        const unsigned long long yc = __shfl_up_sync(0xffffffffu, ic, o);
+        if (lane >= o) {
+            ib += yb;
+            ic += yc;
         }
-        chunk_b[c] = (uint32_t)lo;
+    }
+    if (lane == 31) {
+        sb[warp] = ib;
+        sc[warp] = ic;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long xb = sb[lane], xc = sc[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long yb = __shfl_up_sync(0xffffffffu, xb, o);
+            const unsigned long long yc = __shfl_up_sync(0xffffffffu, xc, o);
+            if (lane >= o) {
+                xb += yb;
+                xc += yc;
+            }
+        }
+        sb[lane] = xb;
+        sc[lane] = xc;
+    }
+    __syncthreads();
+    unsigned long long ob = (warp ? sb[warp - 1] : 0ull) + ib - tb, oc = (warp ? sc[warp - 1] : 0ull) + ic - tc;
+    for (int64_t i = a; i < e; i++) {
+        blk_off[i] = ob;
+        ob += nblk[i];
+        chunk_off[i] = oc;
+        oc += nchunk[i];
+    }
+    if (t == kScanThreads - 1) {
+        blk_off[Q] = ob;
+        chunk_off[Q] = oc;
+        if (lim.Qd && (ob > lim.cap_blocks || oc > lim.cap_chunks)) set_status(status, kStatCapacity);
     }
 }
 
-// a plan's batch needs more footprint blocks or chunks than it holds
 __global__ void plan_check_kernel(const uint64_t* __restrict__ blk_off, const uint64_t* __restrict__ chunk_off, Lim lim,
                                   unsigned* __restrict__ status) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && over_cap(lim, blk_off, chunk_off, *lim.Qd))
@@ -1306,10 +1357,15 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
                                                                 ncube.as<uint64_t>(), nchunk.as<uint64_t>(),
                                                                 status, Lim{nullptr, 0, 0});
         MG_CUDA(cudaGetLastError());
-        // block offsets are 64-bit sums of the 32-bit per-box counts
-        MG_TRY(scan_exclusive_u64(nchunk.as<uint64_t>(), chunk_off.as<uint64_t>(), Q,
-                                  chunk_off.as<uint64_t>() + Q, al, s));
-        {
+        if (Q <= kFusedScanMax) {
+            plan_scan_kernel<<<1, kScanThreads, 0, s>>>(nblk.as<uint32_t>(), nchunk.as<uint64_t>(), Q,
+                                                        blk_off.as<uint64_t>(), chunk_off.as<uint64_t>(),
+                                                        Lim{nullptr, 0, 0}, status);
+            MG_CUDA(cudaGetLastError());
+        } else {
+            // block offsets are 64-bit sums of the 32-bit per-box counts
+            MG_TRY(scan_exclusive_u64(nchunk.as<uint64_t>(), chunk_off.as<uint64_t>(), Q,
+                                      chunk_off.as<uint64_t>() + Q, al, s));
             Buf nb64;
             MG_TRY(nb64.alloc(&al, (size_t)Q * 8, s));
             widen_kernel<<<grid_for(Q, 256, 152 * 64), 256, 0, s>>>(nblk.as<uint32_t>(), nb64.as<uint64_t>(), Q);
@@ -1334,12 +1390,9 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
         MG_TRY(blk.alloc(&al, (size_t)std::max<uint64_t>(totals[0], 1) * sizeof(Blk), s));
         MG_TRY(chunk_q.alloc(&al, (size_t)std::max<uint64_t>(totals[1], 1) * 4, s));
         MG_TRY(chunk_b.alloc(&al, (size_t)std::max<uint64_t>(totals[1], 1) * 4, s));
-        plan_write_kernel<<<grid_for(Q * 32, kPlanThreads), kPlanThreads, 0, s>>>(G, boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>(),
-                                                                Lim{nullptr, 0, 0}, chunk_off.as<uint64_t>());
-        MG_CUDA(cudaGetLastError());
-        chunk_map_kernel<<<grid_for(Q * 32, 256), 256, 0, s>>>(chunk_off.as<uint64_t>(), blk_off.as<uint64_t>(),
-                                                               blk.as<Blk>(), Q, chunk, chunk_q.as<uint32_t>(),
-                                                               chunk_b.as<uint32_t>(), Lim{nullptr, 0, 0});
+        plan_write_kernel<<<grid_for(Q * 32, kPlanThreads), kPlanThreads, 0, s>>>(
+            G, boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>(), Lim{nullptr, 0, 0}, chunk_off.as<uint64_t>(), chunk,
+            chunk_q.as<uint32_t>(), chunk_b.as<uint32_t>());
         MG_CUDA(cudaGetLastError());
         A.chunk_q = chunk_q.as<uint32_t>();
         A.chunk_b = chunk_b.as<uint32_t>();
@@ -1591,14 +1644,19 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     plan_count_kernel<<<wg, 256, 0, s>>>(G, p->boxes, Q, p->chunk, nblk.as<uint32_t>(), ncube.as<uint64_t>(),
                                          nchunk.as<uint64_t>(), status, lim);
     MG_CUDA(cudaGetLastError());
-    MG_TRY(scan_exclusive_u64(nchunk.as<uint64_t>(), chunk_off.as<uint64_t>(), Q, chunk_off.as<uint64_t>() + Q, al, s));
-    widen_kernel<<<grid_for(Q, 256, 152 * 64), 256, 0, s>>>(nblk.as<uint32_t>(), nb64.as<uint64_t>(), Q);
-    MG_TRY(scan_exclusive_u64(nb64.as<uint64_t>(), blk_off.as<uint64_t>(), Q, blk_off.as<uint64_t>() + Q, al, s));
-    plan_check_kernel<<<1, 32, 0, s>>>(blk_off.as<uint64_t>(), chunk_off.as<uint64_t>(), lim, status);
+    if (Q <= kFusedScanMax) {
+        plan_scan_kernel<<<1, kScanThreads, 0, s>>>(nblk.as<uint32_t>(), nchunk.as<uint64_t>(), Q,
+                                                    blk_off.as<uint64_t>(), chunk_off.as<uint64_t>(), lim, status);
+    } else {
+        MG_TRY(scan_exclusive_u64(nchunk.as<uint64_t>(), chunk_off.as<uint64_t>(), Q, chunk_off.as<uint64_t>() + Q, al,
+                                  s));
+        widen_kernel<<<grid_for(Q, 256, 152 * 64), 256, 0, s>>>(nblk.as<uint32_t>(), nb64.as<uint64_t>(), Q);
+        MG_TRY(scan_exclusive_u64(nb64.as<uint64_t>(), blk_off.as<uint64_t>(), Q, blk_off.as<uint64_t>() + Q, al, s));
+        plan_check_kernel<<<1, 32, 0, s>>>(blk_off.as<uint64_t>(), chunk_off.as<uint64_t>(), lim, status);
+    }
     plan_write_kernel<<<wg, 256, 0, s>>>(G, p->boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>(), lim,
-                                         chunk_off.as<uint64_t>());
-    chunk_map_kernel<<<wg, 256, 0, s>>>(chunk_off.as<uint64_t>(), blk_off.as<uint64_t>(), blk.as<Blk>(), Q, p->chunk,
-                                        chunk_q.as<uint32_t>(), chunk_b.as<uint32_t>(), lim);
+                                         chunk_off.as<uint64_t>(), p->chunk, chunk_q.as<uint32_t>(),
+                                         chunk_b.as<uint32_t>());
     MG_CUDA(cudaGetLastError());
 
     MainArgs A;
