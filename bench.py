@@ -401,7 +401,9 @@ def run_ours(args):
     launches_prop = 1 + sum(1 for d in range(1, info["depth"] + 1) if info["bucket"][d + 1] > info["bucket"][d])
     nscan = 1 if Q <= 2048 else 3   # kernels of one device-wide scan of Q values
     if args.schedule == "batched":
-        launches_query = 1 + 1 + 2 * nscan + 1 + 1 + 1 + 1 + 1   # zero, count, 2 scans, widen, check, write, map, main
+        # batch size, zero rows, count, offsets (one CTA up to 2^18 boxes, else two
+        # device-wide scans, widen and check), write, main
+        launches_query = 1 + 1 + 1 + (1 if Q <= (1 << 18) else 2 * nscan + 2) + 1 + 1
     else:
         launches_query = Q
     line = {

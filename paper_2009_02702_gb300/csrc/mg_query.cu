@@ -1131,56 +1131,59 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(const uint32_t*
                                                                  unsigned* __restrict__ status) {
     __shared__ unsigned long long sb[32], sc[32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t per = (Q + kScanThreads - 1) / kScanThreads;
-    const int64_t a = min(Q, (int64_t)t * per), e = min(Q, a + per);
-    unsigned long long tb = 0, tc = 0;
-    for (int64_t i = a; i < e; i++) {
-        tb += nblk[i];
-        tc += nchunk[i];
-    }
-    unsigned long long ib = tb, ic = tc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long yb = __shfl_up_sync(0xffffffffu, ib, o);
-        const unsigned long long yc = __shfl_up_sync(0xffffffffu, ic, o);
-        if (lane >= o) {
-            ib += yb;
-            ic += yc;
-        }
-    }
-    if (lane == 31) {
-        sb[warp] = ib;
-        sc[warp] = ic;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        unsigned long long xb = sb[lane], xc = sc[lane];
+    unsigned long long carry_b = 0, carry_c = 0;
+    // tiles of kScanThreads consecutive boxes, one per thread (coalesced)
+    for (int64_t t0 = 0; t0 < Q; t0 += kScanThreads) {
+        const int64_t i = t0 + t;
+        const unsigned long long xb = i < Q ? nblk[i] : 0ull, xc = i < Q ? nchunk[i] : 0ull;
+        unsigned long long ib = xb, ic = xc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long yb = __shfl_up_sync(0xffffffffu, xb, o);
-            const unsigned long long yc = __shfl_up_sync(0xffffffffu, xc, o);
+            const unsigned long long yb = __shfl_up_sync(0xffffffffu, ib, o);
+            const unsigned long long yc = __shfl_up_sync(0xffffffffu, ic, o);
             if (lane >= o) {
-                xb += yb;
-                xc += yc;
+                ib += yb;
+                ic += yc;
             }
         }
-        sb[lane] = xb;
-        sc[lane] = xc;
+        if (lane == 31) {
+            sb[warp] = ib;
+            sc[warp] = ic;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long wb = sb[lane], wc = sc[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long yb = __shfl_up_sync(0xffffffffu, wb, o);
+                const unsigned long long yc = __shfl_up_sync(0xffffffffu, wc, o);
+                if (lane >= o) {
+                    wb += yb;
+                    wc += yc;
+                }
+            }
+            sb[lane] = wb;
+            sc[lane] = wc;
+        }
+        __syncthreads();
+        const unsigned long long pb = warp ? sb[warp - 1] : 0ull, pc = warp ? sc[warp - 1] : 0ull;
+        if (i < Q) {
+            blk_off[i] = carry_b + pb + ib - xb;
+            chunk_off[i] = carry_c + pc + ic - xc;
+        }
+        carry_b += sb[31];
+        carry_c += sc[31];
+        __syncthreads();
     }
-    __syncthreads();
-    unsigned long long ob = (warp ? sb[warp - 1] : 0ull) + ib - tb, oc = (warp ? sc[warp - 1] : 0ull) + ic - tc;
-    for (int64_t i = a; i < e; i++) {
-        blk_off[i] = ob;
-        ob += nblk[i];
-        chunk_off[i] = oc;
-        oc += nchunk[i];
-    }
-    if (t == kScanThreads - 1) {
-        blk_off[Q] = ob;
-        chunk_off[Q] = oc;
-        if (lim.Qd && (ob > lim.cap_blocks || oc > lim.cap_chunks)) set_status(status, kStatCapacity);
+    if (t == 0) {
+        blk_off[Q] = carry_b;
+        chunk_off[Q] = carry_c;
+        if (lim.Qd && (carry_b > lim.cap_blocks || carry_c > lim.cap_chunks)) set_status(status, kStatCapacity);
     }
 }
+
+// the live batch size of a plan run, passed by value (no host staging)
+__global__ void set_batch_kernel(int64_t* __restrict__ Qd, int64_t Q) { *Qd = Q; }
 
 __global__ void plan_check_kernel(const uint64_t* __restrict__ blk_off, const uint64_t* __restrict__ chunk_off, Lim lim,
                                   unsigned* __restrict__ status) {
@@ -1812,10 +1815,12 @@ MG_API mg_status mg_query_plan_run(mg_query_plan* p, const int32_t* boxes, int64
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != p->g->device) MG_CUDA(cudaSetDevice(p->g->device));
-    const int64_t q = Q;   // pageable source: copied out before the call returns
     mg_status st = MG_OK;
     cudaError_t e = cudaMemcpyAsync(p->boxes, boxes, (size_t)Q * 24, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->Qd, &q, 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        set_batch_kernel<<<1, 1, 0, s>>>(p->Qd, Q);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaGraphLaunch(p->exec, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, p->result, (size_t)Q * p->g->S * 4, cudaMemcpyDeviceToDevice, s);
