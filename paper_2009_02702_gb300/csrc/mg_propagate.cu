@@ -149,6 +149,39 @@ struct PropTiles {
     int64_t count[MG_MAX_DEPTH + 1];            // nodes of every level
 };
 
+// level of tile t (tile0: first tile of every level)
+__device__ __forceinline__ int tile_level(const PropTiles& T, long long t) {
+    int d = 0;
+    while (t >= T.tile0[d + 1]) d++;
+    return d;
+}
+
+// this thread's edges and weights of tile t: nodes lo + threadIdx.x + k * kPropThreads
+template <typename ST, int NT>
+__device__ __forceinline__ void tile_edges(const PropTiles& T, long long t, long long total,
+                                           const uint2* __restrict__ pq,
+                                           const typename Weight<ST>::T* __restrict__ alpha, uint2 (&e)[NT],
+                                           float (&al)[NT]) {
+#pragma unroll
+    for (int k = 0; k < NT; k++) {
+        e[k] = make_uint2(0u, 0u);
+        al[k] = 0.f;
+    }
+    if (t >= total) return;
+    const int d = tile_level(T, t);
+    if (d == 0) return;
+    const int64_t lo = T.first[d] + (t - T.tile0[d]) * kPropTile;
+    const int64_t hi = min(lo + kPropTile, T.first[d] + T.count[d]);
+#pragma unroll
+    for (int k = 0; k < NT; k++) {
+        const int64_t n = lo + threadIdx.x + (int64_t)k * kPropThreads;
+        if (n < hi) {
+            e[k] = __ldg(pq + n);
+            al[k] = Cvt<typename Weight<ST>::T>::to(alpha[n]);
+        }
+    }
+}
+
 template <typename ST, int C>
 __global__ void __launch_bounds__(kPropThreads) single_pass_kernel(PropTiles T, const uint2* __restrict__ pq,
                                                                    const typename Weight<ST>::T* __restrict__ alpha,
@@ -156,53 +189,98 @@ __global__ void __launch_bounds__(kPropThreads) single_pass_kernel(PropTiles T, 
                                                                    unsigned* __restrict__ done,
                                                                    unsigned long long* __restrict__ ticket,
                                                                    unsigned* __restrict__ status) {
-    __shared__ long long s_tile;
+    constexpr int NT = kPropTile / kPropThreads;      // nodes of a tile per thread
+    constexpr int NPT = C <= 4 ? 4 : C <= 8 ? 2 : 1;  // of them gathered at once
+    __shared__ long long s_next;
     __shared__ int s_abort;
     const long long total = T.tile0[T.levels];
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_tile = (long long)atomicAdd(ticket, 1ull);
-            s_abort = 0;
-        }
-        __syncthreads();
-        const long long t = s_tile;
-        if (t >= total) break;
-        int d = 0;
-        while (t >= T.tile0[d + 1]) d++;
+    // thread 0 holds the ticket after next, taken two tiles ahead so that the
+    // atomic's round trip is never waited on
+    long long ahead = 0;
+    int seen = 0;   // thread 0: every level below this one is known to be complete
+    if (threadIdx.x == 0) {
+        s_next = (long long)atomicAdd(ticket, 1ull);
+        ahead = (long long)atomicAdd(ticket, 1ull);
+    }
+    __syncthreads();
+    long long t = s_next;
+    // Software pipeline over tiles: the next tile's ticket is known and its
+    // (static) edges and weights are loaded while this tile waits and runs.
+    // Tickets are taken in order and a tile only waits for smaller ones, so
+    // the smallest unfinished ticket is always some CTA's current tile.
+    uint2 e[NT];
+    float al[NT];
+    tile_edges<ST, NT>(T, t, total, pq, alpha, e, al);
+    while (t < total) {
+        const int d = tile_level(T, t);
         const int64_t lo = T.first[d] + (t - T.tile0[d]) * kPropTile;
         const int64_t hi = min(lo + kPropTile, T.first[d] + T.count[d]);
-        if (d > 0 && threadIdx.x == 0) {
-            const unsigned need = (unsigned)(T.tile0[d] - T.tile0[d - 1]);
-            if (!bounded_wait_geq(done + d - 1, need, kSpinLimit, status)) s_abort = 1;
+        __syncthreads();   // every thread has read s_next
+        if (threadIdx.x == 0) {
+            s_next = ahead;
+            ahead = (long long)atomicAdd(ticket, 1ull);
+            s_abort = 0;
+            if (d > seen) {   // level d-1 not yet seen complete
+                const unsigned need = (unsigned)(T.tile0[d] - T.tile0[d - 1]);
+                if (bounded_wait_geq(done + d - 1, need, kSpinLimit, status)) seen = d;
+                else s_abort = 1;
+            }
         }
         __syncthreads();
         if (s_abort) break;
-        for (int64_t n = lo + threadIdx.x; n < hi; n += kPropThreads) {
-            float out[C];
-            if (d == 0) {
+        const long long tn = s_next;
+        uint2 en[NT];
+        float aln[NT];
+        tile_edges<ST, NT>(T, tn, total, pq, alpha, en, aln);
+        if (d == 0) {
+            for (int64_t n = lo + threadIdx.x; n < hi; n += kPropThreads) {
+                float out[C];
 #pragma unroll
                 for (int c = 0; c < C; c++) out[c] = tf[n * C + c];
-            } else {
-                const uint2 e = __ldg(pq + n);
-                uint32_t p = e.x, q = e.y;
-                float al = Cvt<typename Weight<ST>::T>::to(alpha[n]);
-                if (al < 0.f) {
-                    al = -al;
-                    p = e.y;
-                    q = e.x;
-                }
-                float vp[C], vq[C];
-                load_row_cg<ST, C>(vals, p, vp);
-                load_row_cg<ST, C>(vals, q, vq);
-#pragma unroll
-                for (int c = 0; c < C; c++) out[c] = fmaf(al, vq[c] - vp[c], vp[c]);
+                store_row<ST, C>(vals, n, out);
             }
-            store_row<ST, C>(vals, n, out);
+        } else {
+            // NPT nodes at a time: both predecessor rows of every node are
+            // loaded before any is stored (nodes of one level never read each other)
+#pragma unroll
+            for (int k0 = 0; k0 < NT; k0 += NPT) {
+                float vp[NPT][C], vq[NPT][C];
+#pragma unroll
+                for (int k = 0; k < NPT; k++) {
+                    const int64_t n = lo + threadIdx.x + (int64_t)(k0 + k) * kPropThreads;
+                    if (n < hi) {
+                        uint32_t p = e[k0 + k].x, q = e[k0 + k].y;
+                        if (al[k0 + k] < 0.f) {   // 16-bit weights: sign = p and q swapped
+                            p = e[k0 + k].y;
+                            q = e[k0 + k].x;
+                        }
+                        load_row_cg<ST, C>(vals, p, vp[k]);
+                        load_row_cg<ST, C>(vals, q, vq[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < NPT; k++) {
+                    const int64_t n = lo + threadIdx.x + (int64_t)(k0 + k) * kPropThreads;
+                    if (n < hi) {
+                        const float a = fabsf(al[k0 + k]);
+                        float out[C];
+#pragma unroll
+                        for (int c = 0; c < C; c++) out[c] = fmaf(a, vq[k][c] - vp[k][c], vp[k][c]);
+                        store_row<ST, C>(vals, n, out);
+                    }
+                }
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(done + d, 1u);
+        }
+        t = tn;
+#pragma unroll
+        for (int k = 0; k < NT; k++) {
+            e[k] = en[k];
+            al[k] = aln[k];
         }
     }
 }
