@@ -58,6 +58,7 @@ def parse(argv=None):
     ap.add_argument("--no-plan", action="store_true", help="time direct calls instead of the captured plan")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain/naive/16-bit extra measurements")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving mix) measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2048x2048x300 and cylinder graph measurements")
     ap.add_argument("--serve-requests", type=int, default=0)
     ap.add_argument("--serve-rate", type=float, default=0.0)
     return ap.parse_args(argv)
@@ -394,6 +395,10 @@ def run_ours(args):
     if not args.no_serve and rank == 0:
         served = serving(mg, g, args, dev)
 
+    large = None
+    if not args.no_large and rank == 0:
+        large = large_workloads(mg, dev, flush, stream, peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg_i, boxes_h, args.cpu_seconds)
@@ -438,6 +443,7 @@ def run_ours(args):
         "query_path": "captured plan (one CUDA graph launch per batch)" if use_plan else "direct calls",
         "forms": forms,
         "serving": served,
+        "large_graphs": large,
         "gpu_launches": args.steps * (launches_prop + launches_query + 1),
         "clocks": clk,
         "wall_s_timed": wall,
@@ -472,10 +478,12 @@ def _time(fn, reps, flush, stream):
     return float(np.median(ts))
 
 
-def storage_errors(mg, g, tf, vol_h, dims, S, nsample=1500, seed=5):
+def storage_errors(mg, g, tf, vol_h, dims, S, nsample=1500, seed=5, block=None, max_level=5):
     """Max / mean |colour - fp64 direct sum| of node values stored in fp32,
-    fp16 and bf16, over sampled interior voxels of levels 1..5 (their mixture
-    is the count of level-0 IDs in the voxel's footprint)."""
+    fp16 and bf16, over sampled interior voxels of levels 1..max_level (their
+    mixture is the count of level-0 IDs in the voxel's footprint).  The
+    voxels come from the host volume, or from block(origin, side) (host
+    generator) when the volume is not held on the host."""
     import torch
     rng = np.random.default_rng(seed)
     tf64 = tf.detach().cpu().numpy().astype(np.float64)
@@ -483,10 +491,13 @@ def storage_errors(mg, g, tf, vol_h, dims, S, nsample=1500, seed=5):
     mips = {}
     errs = {dt: [] for dt in vals}
     for _ in range(nsample):
-        l = int(rng.integers(1, 6))
+        l = int(rng.integers(1, max_level + 1))
         e = 1 << l
         X, Y, Z = [int(rng.integers(0, d // e)) for d in dims]
-        sub = vol_h[Z * e:(Z + 1) * e, Y * e:(Y + 1) * e, X * e:(X + 1) * e].ravel()
+        if block is None:
+            sub = vol_h[Z * e:(Z + 1) * e, Y * e:(Y + 1) * e, X * e:(X + 1) * e].ravel()
+        else:
+            sub = block((X * e, Y * e, Z * e), (e, e, e)).ravel()
         ref = np.bincount(sub, minlength=S).astype(np.float64) @ tf64 / sub.size
         if l not in mips:
             mips[l] = mg.mg_graph_copy_mip(g, l)
@@ -525,6 +536,95 @@ def other_forms(mg, g, boxes, boxes_h, tf, vals, Q, S, dims, cfg_i, flush, strea
     vol_h = synth.make_volume(cfg_i, device="cpu") if max(dims) <= 1024 else None
     if vol_h is not None:
         out["storage_error_vs_fp64"] = storage_errors(mg, g, tf, vol_h, dims, S)
+    return out
+
+
+# --------------------------------------------------------------------------
+# propagation, lookup and 16-bit storage on the larger graphs
+# --------------------------------------------------------------------------
+def large_workloads(mg, dev, flush, stream, peak, nsample=400):
+    """The 2048x2048x300 graph (FP16 weights and colours, 100,000 boxes) and the
+    cylinder graph (BF16 attribute TF, 1920x1080 frame): propagation and lookup
+    rates against the HBM peak for each storage type, errors against fp64 on
+    sampled voxels (host generator / host volume), and for 2048x2048x300 the
+    batched query with fp32 and fp16 weights (error against the brute-force
+    counts of sampled boxes)."""
+    import torch
+    import oracle
+    out = {}
+    for cfg_i in (3, 4):
+        c = synth.CONFIGS[cfg_i]
+        S = c["S"]
+        t0 = time.perf_counter()
+        vol_h = None
+        if c["kind"] == "voronoi":
+            vol = synth.make_volume(cfg_i, device=dev)
+            block = lambda o, sd, ci=cfg_i: synth.voronoi_window(ci, o, sd)
+        else:
+            vol_h = synth.make_volume(cfg_i)
+            vol = torch.from_numpy(vol_h).to(dev)
+            block = None
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        g = mg.mg_build(vol, S)
+        del vol
+        info = g.info
+        tf_h = synth.make_attribute_tf(cfg_i, S) if cfg_i == 4 else synth.make_tf(cfg_i, S, 4)
+        tf = torch.from_numpy(tf_h).to(dev)
+        smp = torch.from_numpy(synth.make_samples(cfg_i)).to(dev)
+        P = smp.shape[0]
+        r = {"workload": c["name"], "nodes": info["num_nodes"], "depth": info["depth"], "levels": info["levels"],
+             "build_ms": info["build_ms"], "device_bytes": info["device_bytes"], "lut_entries": info["lut_entries"],
+             "volume_generation_s": gen_s, "tf": "attribute RGBA (opacity x |axis.view|)" if cfg_i == 4 else "RGBA"}
+        NI = info["num_nodes"] - S
+        for st, dt, esz in (("f32", torch.float32, 4), ("f16", torch.float16, 2), ("bf16", torch.bfloat16, 2)):
+            vals = torch.empty((g.N, 4), dtype=dt, device=dev)
+            look = torch.empty((P, 4), dtype=dt, device=dev)
+            ms_p = _time(lambda: mg.mg_propagate_tf(g, tf, storage=st, out=vals), 10, flush, stream)
+            ms_l = _time(lambda: mg.mg_render_lookup(g, vals, smp, out=look), 10, flush, stream)
+            # algorithmic bytes: edges 8 + weight (4 or 2) + value row out per node; rows in per source
+            pb = NI * (8 + (4 if st == "f32" else 2) + 4 * esz) + S * (16 + 4 * esz)
+            lb = P * (16 + 4 + 8 * esz)
+            r["propagate_" + st] = {"ms": ms_p, "gbs": pb / ms_p / 1e6, "frac": pb / ms_p / 1e6 / peak,
+                                    "bytes": pb}
+            r["lookup_" + st] = {"ms": ms_l, "samples_per_s": P / (ms_l / 1e3), "gbs": lb / ms_l / 1e6,
+                                 "frac": lb / ms_l / 1e6 / peak}
+        dims = c["dims"]
+        r["storage_error_vs_fp64"] = storage_errors(mg, g, tf, vol_h, dims, S, nsample=nsample, seed=11,
+                                                    block=block, max_level=4)
+        if cfg_i == 3:
+            boxes_h = synth.make_boxes(3)
+            boxes = torch.from_numpy(boxes_h).to(dev)
+            Q = boxes_h.shape[0]
+            q = {"boxes": Q}
+            for name, hist, alpha in (("u32", "u32", "f32"), ("f32", "f32", "f32"), ("f32_alpha_f16", "f32", "f16")):
+                mg.mg_query_autotune(g, boxes, hist=hist, alpha=alpha)
+                plan = mg.QueryPlan(g, max_Q=Q, hist=hist, alpha=alpha)
+                res = torch.empty((Q, S), dtype=torch.uint32 if hist == "u32" else torch.float32, device=dev)
+                ms = _time(lambda: plan.run(boxes, out=res), 5, flush, stream)
+                mg.mg_sync_status(g)
+                q[name] = {"ms": ms, "queries_per_s": Q / (ms / 1e3)}
+                if name != "u32":
+                    # relative L1 error of sampled boxes against brute-force counts
+                    rng = np.random.default_rng(12)
+                    d = np.array(dims)
+                    side = np.minimum(boxes_h[:, :3] + boxes_h[:, 3:], d) - boxes_h[:, :3]
+                    vol_q = side.prod(axis=1)
+                    cand = np.flatnonzero(vol_q <= (1 << 18))
+                    errs = []
+                    hres = res.cpu().numpy()
+                    for i in rng.choice(cand, size=min(40, len(cand)), replace=False):
+                        blk = synth.voronoi_window(3, boxes_h[i, :3], side[i])
+                        ref = oracle.box_hist(np.ascontiguousarray(blk), S,
+                                              np.array([[0, 0, 0, *side[i]]], np.int32))[0].astype(np.float64)
+                        errs.append(np.abs(hres[i] - ref).sum() / vol_q[i])
+                    q[name]["rel_l1_error_vs_oracle"] = {"max": float(np.max(errs)), "mean": float(np.mean(errs)),
+                                                         "boxes": len(errs)}
+                plan.close()
+            r["queries"] = q
+        out[c["name"]] = r
+        g.close()
+        del vol_h
     return out
 
 
