@@ -734,7 +734,7 @@ def cpu_baseline(cfg_i, boxes, seconds, vol=None):
     cfg = synth.CONFIGS[cfg_i]
     if vol is None:
         vol = _host_volume(cfg_i)
-    n = min(50, len(boxes))
+    n = min(2000, len(boxes))   # calibration sample (box sizes vary widely)
     t0 = time.perf_counter()
     oracle.box_hist(vol, cfg["S"], boxes[:n])
     dt = time.perf_counter() - t0
