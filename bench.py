@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 from paper_2009_02702_gb300 import synth  # noqa: E402
 
 METRIC = "box-histogram queries/s & TF propagations/s (HBM GB/s vs peak); p99 latency"
+NOMINAL_HBM_GBS = 7900.0   # vendor HBM3e figure; the measured copy peak is the roofline denominator
 UNIT = "queries/s"
 
 
@@ -316,6 +317,13 @@ def run_ours(args):
     main_ms = np.array([t[1] for t in qmain])
     # propagation and lookup each timed alone (L2 flushed) for their rooflines
     prop_alone = _time(lambda: mg.mg_propagate_tf(g, tf, out=vals), 10, flush, stream)
+    tf_pin = torch.from_numpy(tf_h).pin_memory()
+    tf_up = torch.empty_like(tf)
+
+    def prop_upload():
+        tf_up.copy_(tf_pin, non_blocking=True)
+        mg.mg_propagate_tf(g, tf_up, out=vals)
+    prop_with_upload = _time(prop_upload, 10, flush, stream)
     look_alone = _time(lambda: mg.mg_render_lookup(g, vals, smp, out=look), 10, flush, stream)
     tot_ms = max_over_ranks(float(step_ms.sum()), world, dev)
     ms_per_step = tot_ms / args.steps
@@ -401,7 +409,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(cfg_i, boxes_h, args.cpu_seconds)
+        cpu = cpu_baseline(cfg_i, boxes_h, args.cpu_seconds, tf=tf_h)
 
     launches_prop = 1 + sum(1 for d in range(1, info["depth"] + 1) if info["bucket"][d + 1] > info["bucket"][d])
     nscan = 1 if Q <= 2048 else 3   # kernels of one device-wide scan of Q values
@@ -427,8 +435,11 @@ def run_ours(args):
         "stages_ms": {"propagate": float(np.mean(prop_ms)), "query": float(np.mean(query_ms)),
                       "query_plan": float(np.mean([t[0] for t in qmain])), "query_main": float(np.mean(main_ms)),
                       "query_output": float(np.mean([t[2] for t in qmain])), "lookup": float(np.mean(look_ms)),
-                      "propagate_alone": prop_alone, "lookup_alone": look_alone,
+                      "propagate_alone": prop_alone, "propagate_with_tf_upload": prop_with_upload,
+                      "lookup_alone": look_alone,
                       "note": "propagate/lookup run concurrently with the query; *_alone timed by themselves"},
+        "roofline_nominal": {"peak": NOMINAL_HBM_GBS, "unit": "GB/s", "frac": achieved / NOMINAL_HBM_GBS,
+                             "propagate_frac": prop_gbs / NOMINAL_HBM_GBS, "lookup_frac": look_gbs / NOMINAL_HBM_GBS},
         "roofline": {"bound": "hbm", "kernel": ("query_warp_kernel" if S <= 2048 else "query_batched_kernel")
                      if args.schedule == "batched" else "query_plain_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src + " hbm_gbs (copy, burst)",
@@ -726,32 +737,70 @@ def _host_volume(cfg_i):
     return synth.make_volume(cfg_i, device="cpu")
 
 
-def cpu_baseline(cfg_i, boxes, seconds, vol=None):
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(cfg_i, boxes, seconds, vol=None, tf=None):
     """The oracle's brute-force counting timed on the host cores on a bounded
     sample: the step's boxes, then more boxes of the same recipe, up to about
-    `seconds` of work."""
+    `seconds` of work on all cores, a quarter of that on one core; and the
+    oracle's TF propagation as the direct per-voxel sum over sampled levels."""
     import oracle
     cfg = synth.CONFIGS[cfg_i]
     if vol is None:
         vol = _host_volume(cfg_i)
-    n = min(2000, len(boxes))   # calibration sample (box sizes vary widely)
-    t0 = time.perf_counter()
-    oracle.box_hist(vol, cfg["S"], boxes[:n])
-    dt = time.perf_counter() - t0
-    want = int(max(n, n * seconds / max(dt, 1e-6)))
-    sample = boxes
-    k = 1
-    while len(sample) < want:
-        sample = np.concatenate([sample, synth.make_boxes(cfg_i, Q=len(boxes), stream_offset=1000 + k)])
-        k += 1
-    sample = sample[:want]
-    t0 = time.perf_counter()
-    oracle.box_hist(vol, cfg["S"], sample)
-    dt2 = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": len(sample) / dt2, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d boxes (the step's %d, then more of the same recipe), brute-force level-0 counting "
-                      "(OpenMP over boxes), %.1f s" % (len(sample), len(boxes), dt2)}
+    all_threads = oracle.set_threads(0)
+
+    def sample_of(n):
+        smp, k = boxes, 1
+        while len(smp) < n:
+            smp = np.concatenate([smp, synth.make_boxes(cfg_i, Q=len(boxes), stream_offset=1000 + k)])
+            k += 1
+        return smp[:n]
+
+    def timed(secs):
+        n = min(2000, len(boxes))   # calibration sample (box sizes vary widely)
+        t0 = time.perf_counter()
+        oracle.box_hist(vol, cfg["S"], boxes[:n])
+        dt = time.perf_counter() - t0
+        smp = sample_of(int(max(n, n * secs / max(dt, 1e-6))))
+        t0 = time.perf_counter()
+        oracle.box_hist(vol, cfg["S"], smp)
+        return len(smp), time.perf_counter() - t0
+
+    n_all, t_all = timed(seconds)
+    oracle.set_threads(1)
+    n_one, t_one = timed(seconds / 4)
+    oracle.set_threads(all_threads)
+    res = {"value": n_all / t_all, "unit": UNIT, "cores": all_threads, "kind": "oracle",
+           "sample": "%d boxes (the step's %d, then more of the same recipe), brute-force level-0 counting "
+                     "(OpenMP over boxes), %.1f s" % (n_all, len(boxes), t_all),
+           "single_thread": {"value": n_one / t_one, "unit": UNIT, "boxes": n_one, "seconds": t_one},
+           "cpu_model": cpu_model()}
+    if tf is not None:
+        # the paper's 'revisiting every voxel': mixture and fp64 colour of every
+        # voxel of a level, timed on levels 1-3 and scaled to the whole mipmap
+        dims = oracle.level_dims(*cfg["dims"])
+        vox_all = int(np.prod(dims[1:], axis=1).sum())
+        n_vox, t_vox = 0, 0.0
+        for l in (1, 2, 3):
+            t0 = time.perf_counter()
+            oracle.direct_colors(vol, l, tf)
+            t_vox += time.perf_counter() - t0
+            n_vox += int(np.prod(dims[l]))
+        res["propagation"] = {"voxels_per_s": n_vox / t_vox, "sample": "levels 1-3 (%d voxels), %.1f s"
+                              % (n_vox, t_vox), "full_mip_estimate_s": vox_all / (n_vox / t_vox)}
+    return res
 
 
 def run_reference(args):

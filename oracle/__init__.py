@@ -98,6 +98,8 @@ def _load():
         lib.mgo_factor_lists.argtypes = [P, P, P, i64, ctypes.c_uint32, P]
         lib.mgo_factor_lists.restype = P
         lib.mgo_depths.argtypes = [P, P, i64, ctypes.c_uint32, P]
+        lib.mgo_set_threads.argtypes = [i32]
+        lib.mgo_set_threads.restype = i32
         _lib = lib
         return lib
 
@@ -323,3 +325,8 @@ def sample_voxels(dims: np.ndarray, samples: np.ndarray):
     vox = np.zeros(P, np.int64)
     _load().mgo_sample_voxels(_ptr(dims), dims.shape[0], _ptr(samples), P, _ptr(lev), _ptr(vox))
     return lev, vox
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops (0: leave as is); returns the count in use."""
+    return int(_load().mgo_set_threads(int(n)))

@@ -38,6 +38,9 @@
 #include <stdlib.h>
 #include <string.h>
 #include <stdio.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define MGO_MAX_LEVELS 40
 #define MGO_NONE 0xFFFFFFFFu
@@ -820,4 +823,17 @@ void mgo_sample_voxels(const int64_t *dims, int L, const float *samples, int64_t
         level_out[i] = l;
         voxel_out[i] = (v[2] * dl[1] + v[1]) * dl[0] + v[0];
     }
+}
+
+/* Threads of the OpenMP loops (box counting); returns the number now in use.
+ * Used to report the baseline both single-threaded and on all cores. */
+int mgo_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

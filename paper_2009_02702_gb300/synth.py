@@ -49,7 +49,7 @@ CONFIGS = {
             kind="cylinders", queries=10000, box="loguniform", box_max=600,
             radius=(2.0, 6.0), length=(50.0, 600.0), tries=32),
     5: dict(name="serving-mix-cfg1-3-poisson20k", volumes=(1, 2, 3), rate=20000.0, tf_frac=0.1,
-            requests=40000, frame_samples=4096),
+            requests=200000, frame_samples=4096),
 }
 
 
