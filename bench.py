@@ -738,11 +738,18 @@ def _host_volume(cfg_i):
 
 
 def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                k = line.split(":")[0].strip().lower()
-                if k in ("model name", "cpu part", "hardware"):
+                if line.split(":")[0].strip().lower() == "model name":
                     return line.split(":", 1)[1].strip()
     except OSError:
         pass
