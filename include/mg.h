@@ -395,6 +395,26 @@ MG_API void mg_server_free(mg_server *sv);
  * Returns MG_OK or the first error recorded by an earlier call's kernels. */
 MG_API mg_status mg_sync_status(mg_graph *g, mg_stream stream);
 
+/*
+ * Checkpoint / resume: a built graph as one image in host memory (a header
+ * with the sizes, geometry and depth buckets, then the raw device arrays:
+ * mip levels and their axis copies, node table, weights, mixture lookup
+ * table).  The paper stores its graph as a bit-packed stream (Table 1); this
+ * image trades size for a load without any rebuild.
+ * mg_graph_export_size: bytes the image needs.
+ * mg_graph_export: writes the image into `host` (at least that many bytes);
+ *   synchronises `stream`.  MG_ERR_CAPACITY if `bytes` is too small.
+ * mg_graph_import: a new graph (device memory from `allocator`, NULL =
+ *   cudaMallocAsync) on the current device from an image; the header and every
+ *   array size are checked first (MG_ERR_INVALID_ARG for a corrupt or short
+ *   image, MG_ERR_UNSUPPORTED for another version).  Synchronises `stream`;
+ *   the image may be freed on return.  16-bit weights are rebuilt on demand.
+ */
+MG_API mg_status mg_graph_export_size(const mg_graph *g, size_t *bytes);
+MG_API mg_status mg_graph_export(const mg_graph *g, void *host, size_t bytes, mg_stream stream);
+MG_API mg_status mg_graph_import(const void *host, size_t bytes, const mg_allocator *allocator, mg_stream stream,
+                                 mg_graph **out);
+
 /* Self-test of failure handling: one GPU thread waits, with the same bounded
  * wait the single-pass propagation uses between topological levels (Sec. 3.4),
  * on a device flag that is already set (satisfied = 1: returns MG_OK) or that

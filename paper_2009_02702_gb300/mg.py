@@ -39,6 +39,7 @@ EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_cop
            "mg_query_set_tuning", "mg_count_cubes", "mg_render_lookup",
            "mg_server_create", "mg_server_add_volume", "mg_server_start", "mg_server_submit", "mg_server_cancel",
            "mg_server_wait", "mg_server_replay", "mg_server_stats_get", "mg_server_free",
+           "mg_graph_export_size", "mg_graph_export", "mg_graph_import",
            "mg_selftest_bounded_wait", "mg_sync_status", "mg_free", "mg_last_error", "mg_version")
 
 
@@ -155,6 +156,12 @@ def lib():
         L.mg_server_stats_get.restype = st
         L.mg_server_free.argtypes = [P]
         L.mg_server_free.restype = None
+        L.mg_graph_export_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.mg_graph_export_size.restype = st
+        L.mg_graph_export.argtypes = [P, P, ctypes.c_size_t, P]
+        L.mg_graph_export.restype = st
+        L.mg_graph_import.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(mg_allocator), P, ctypes.POINTER(P)]
+        L.mg_graph_import.restype = st
         L.mg_selftest_bounded_wait.argtypes = [i32, ctypes.c_uint, P]
         L.mg_selftest_bounded_wait.restype = st
         L.mg_sync_status.argtypes = [P, P]
@@ -494,6 +501,30 @@ def mg_render_lookup(g: Graph, vals: torch.Tensor, samples: torch.Tensor, out: t
 def mg_sync_status(g: Graph, stream=None):
     """Synchronise and raise MGError if a kernel recorded an error."""
     _check(lib().mg_sync_status(g.handle, _stream(stream)))
+
+
+def mg_graph_export(g: Graph, stream=None):
+    """The graph as a host image (numpy uint8), for mg_graph_import."""
+    import numpy as np
+    n = ctypes.c_size_t()
+    _check(lib().mg_graph_export_size(g.handle, ctypes.byref(n)))
+    img = np.empty(n.value, np.uint8)
+    with torch.cuda.device(g.device):
+        _check(lib().mg_graph_export(g.handle, img.ctypes.data, img.nbytes, _stream(stream)))
+    return img
+
+
+def mg_graph_import(image, device: int = None, stream=None, use_torch_allocator: bool = True) -> Graph:
+    """A graph re-created from an image of mg_graph_export (bytes-like or numpy)."""
+    import numpy as np
+    img = np.ascontiguousarray(np.frombuffer(image, np.uint8) if not isinstance(image, np.ndarray) else image)
+    dev = torch.cuda.current_device() if device is None else device
+    alloc = torch_allocator(dev) if use_torch_allocator else None
+    h = ctypes.c_void_p()
+    with torch.cuda.device(dev):
+        _check(lib().mg_graph_import(img.ctypes.data, img.nbytes, ctypes.byref(alloc) if alloc is not None else None,
+                                     _stream(stream), ctypes.byref(h)))
+    return Graph(h.value, dev, alloc)
 
 
 def mg_selftest_bounded_wait(satisfied: bool, spin_limit: int = 1 << 16, stream=None) -> int:

@@ -127,3 +127,15 @@ def test_selftest_wait_argument_checks(lib):
     assert lib.mg_selftest_bounded_wait(2, 10, None) == mg.MG_ERR_INVALID_ARG
     assert lib.mg_selftest_bounded_wait(0, 0, None) == mg.MG_ERR_INVALID_ARG
     assert lib.mg_selftest_bounded_wait(0, (1 << 22) + 1, None) == mg.MG_ERR_INVALID_ARG
+
+
+def test_graph_io_argument_checks(lib):
+    from paper_2009_02702_gb300 import mg
+    n = ctypes.c_size_t()
+    h = ctypes.c_void_p()
+    assert lib.mg_graph_export_size(None, ctypes.byref(n)) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_graph_export(None, None, 0, None) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_graph_import(None, 0, None, None, ctypes.byref(h)) == mg.MG_ERR_INVALID_ARG
+    junk = (ctypes.c_uint8 * 4096)()
+    assert lib.mg_graph_import(junk, 4096, None, None, ctypes.byref(h)) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_graph_import(junk, 10, None, None, ctypes.byref(h)) == mg.MG_ERR_INVALID_ARG
