@@ -169,6 +169,7 @@ MG_API const char* mg_version(void) { return "mixgraph-gb300 0.1 (sm_103a)"; }
 MG_API mg_status mg_build(const void* ids, int64_t nx, int64_t ny, int64_t nz, uint32_t num_segments,
                           const mg_build_opts* opts, const mg_allocator* allocator, mg_stream stream,
                           mg_graph** out) {
+    MG_RANGE("mg_build");
     t_err.clear();
     if (!out) return fail(MG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -294,6 +295,7 @@ MG_API mg_status mg_graph_copy_mip(const mg_graph* g, int level, uint32_t* dst, 
 
 MG_API mg_status mg_propagate_tf(mg_graph* g, const float* tf, int C, mg_dtype storage, void* vals,
                                  mg_stream stream) {
+    MG_RANGE("mg_propagate_tf");
     if (!g || !tf || !vals) return fail(MG_ERR_INVALID_ARG, "NULL argument");
     if (C < 1 || C > 16) return fail(MG_ERR_INVALID_ARG, "C must be in 1..16");
     if (storage != MG_F32 && storage != MG_F16 && storage != MG_BF16)
@@ -305,6 +307,7 @@ MG_API mg_status mg_propagate_tf(mg_graph* g, const float* tf, int C, mg_dtype s
 MG_API mg_status mg_query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const mg_query_opts* opts,
                                 void* out, size_t out_capacity, uint32_t* seg, uint64_t* offsets,
                                 size_t* out_required, mg_stream stream) {
+    MG_RANGE("mg_query_boxes");
     if (!g) return fail(MG_ERR_INVALID_ARG, "graph is NULL");
     if (Q < 0) return fail(MG_ERR_INVALID_ARG, "Q must be >= 0");
     mg_query_opts o{};
@@ -345,6 +348,7 @@ MG_API mg_status mg_query_timing(const mg_graph* g, float* plan_ms, float* main_
 
 MG_API mg_status mg_count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64_t* cubes,
                                 mg_stream stream) {
+    MG_RANGE("mg_count_cubes");
     if (!g) return fail(MG_ERR_INVALID_ARG, "graph is NULL");
     if (Q < 0) return fail(MG_ERR_INVALID_ARG, "Q must be >= 0");
     if (Q == 0) return MG_OK;
@@ -356,6 +360,7 @@ MG_API mg_status mg_count_cubes(const mg_graph* g, const int32_t* boxes, int64_t
 
 MG_API mg_status mg_render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dtype, const float* samples,
                                   int64_t P, void* out, mg_stream stream) {
+    MG_RANGE("mg_render_lookup");
     if (!g) return fail(MG_ERR_INVALID_ARG, "graph is NULL");
     if (C < 1 || C > 16) return fail(MG_ERR_INVALID_ARG, "C must be in 1..16");
     if (dtype != MG_F32 && dtype != MG_F16 && dtype != MG_BF16)

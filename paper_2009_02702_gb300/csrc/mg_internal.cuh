@@ -13,6 +13,8 @@
 
 #include "mg.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace mg {
 
 // ---------------------------------------------------------------------------
@@ -27,6 +29,17 @@ enum : unsigned {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;   // no predecessor
 constexpr uint32_t kDead = 0xFFFFFFFEu;   // node slot lost a publication race
+
+// ---------------------------------------------------------------------------
+// profiler ranges (NVTX; no cost unless a profiler is attached)
+// ---------------------------------------------------------------------------
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
+#define MG_RANGE(name) ::mg::Range mg_range_scope_(name)
 
 // ---------------------------------------------------------------------------
 // errors

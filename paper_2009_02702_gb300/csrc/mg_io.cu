@@ -59,6 +59,7 @@ MG_API mg_status mg_graph_export_size(const mg_graph* g, size_t* bytes) {
 }
 
 MG_API mg_status mg_graph_export(const mg_graph* g, void* host, size_t bytes, mg_stream stream) {
+    MG_RANGE("mg_graph_export");
     if (!g || !host) return fail(MG_ERR_INVALID_ARG, "NULL argument");
     mg_graph* gm = const_cast<mg_graph*>(g);
     Header h;
@@ -106,6 +107,7 @@ MG_API mg_status mg_graph_export(const mg_graph* g, void* host, size_t bytes, mg
 
 MG_API mg_status mg_graph_import(const void* host, size_t bytes, const mg_allocator* allocator, mg_stream stream,
                                  mg_graph** out) {
+    MG_RANGE("mg_graph_import");
     if (!host || !out) return fail(MG_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (bytes < sizeof(Header)) return fail(MG_ERR_INVALID_ARG, "image shorter than its header");

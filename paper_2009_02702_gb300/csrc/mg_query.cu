@@ -1549,6 +1549,7 @@ size_t per_box_scratch(int64_t Q) {
 
 extern "C" MG_API mg_status mg_query_boxes_noalloc(const mg_graph* g, const int32_t* boxes, int64_t Q, uint32_t* out,
                                                    size_t out_capacity, mg_stream stream) {
+    MG_RANGE("mg_query_boxes_noalloc");
     using namespace mg;
     if (!g) return fail(MG_ERR_INVALID_ARG, "graph is NULL");
     if (Q < 0) return fail(MG_ERR_INVALID_ARG, "Q must be >= 0");
@@ -1717,6 +1718,7 @@ extern "C" {
 
 MG_API mg_status mg_query_plan_create(mg_graph* g, int64_t max_Q, const mg_query_opts* opts, int64_t max_blocks,
                                       int64_t max_chunks, mg_query_plan** out) {
+    MG_RANGE("mg_query_plan_create");
     using namespace mg;
     if (!g || !out) return fail(MG_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
@@ -1808,6 +1810,7 @@ MG_API mg_status mg_query_plan_create(mg_graph* g, int64_t max_Q, const mg_query
 
 MG_API mg_status mg_query_plan_run(mg_query_plan* p, const int32_t* boxes, int64_t Q, void* out, size_t out_capacity,
                                    mg_stream stream) {
+    MG_RANGE("mg_query_plan_run");
     using namespace mg;
     if (!p) return fail(MG_ERR_INVALID_ARG, "plan is NULL");
     if (Q < 0 || Q > p->max_Q) return fail(MG_ERR_INVALID_ARG, "Q must be in 0..max_Q");
@@ -1851,6 +1854,7 @@ MG_API void mg_query_plan_free(mg_query_plan* p) {
 // ---------------------------------------------------------------------------
 extern "C" MG_API mg_status mg_query_autotune(mg_graph* g, const int32_t* boxes, int64_t Q, mg_query_opts* opts,
                                               float* best_ms, mg_stream stream) {
+    MG_RANGE("mg_query_autotune");
     using namespace mg;
     if (!g || !opts) return fail(MG_ERR_INVALID_ARG, "NULL argument");
     if (Q < 1 || !boxes) return fail(MG_ERR_INVALID_ARG, "autotuning needs a non-empty batch");

@@ -208,6 +208,7 @@ mg_status cuda_ok(cudaError_t e, const char* what) { return e == cudaSuccess ? M
 // stage and enqueue one work item on a free slot
 mg_status launch(mg_server* sv, Slot& sl, const std::vector<Req>& w) {
     const Req& head = w[0];
+    MG_RANGE(head.r.kind == MG_REQ_TF ? "mg_server frame" : "mg_server box batch");
     const Volume& vol = sv->vols[head.r.volume];
     VolSlot& vs = sl.vols[head.r.volume];
     mg_graph* g = vol.g;
