@@ -665,7 +665,8 @@ __device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Q
 // where the block's rows are 16-byte aligned (Algorithm 1's runs start on
 // multiples of their own length, so whole rows are) and single cubes for the
 // unaligned head and tail and for every other block -- and a warp scan of
-// the unit counts lets lane k find the block of unit u by a binary search.
+// the unit counts lets lane k find the block of unit u from a ballot of
+// the block ends.
 // Each lane takes units u, u + 32, ... with two loads in flight, so no load
 // waits on a block boundary.  Every lane keeps a run (level, node, count) of
 // its own consecutive cubes; a finished run of a source is added to the
@@ -735,19 +736,20 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
             int ul[2], kind[2];   // level; 0 scalar, 1 four uint32, 2 eight uint16
 #pragma unroll
             for (int r = 0; r < 2; r++) {
-                const uint32_t u = u0 + 32u * r + lane;
-                int j = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint32_t c = __shfl_sync(0xffffffffu, incl, j + step - 1);
-                    if (c <= u) j += step;
-                }
-                const uint32_t jbase = __shfl_sync(0xffffffffu, base, j);
-                const uint32_t jmeta = __shfl_sync(0xffffffffu, meta, j);
-                const uint32_t jlo = __shfl_sync(0xffffffffu, lo, j);
-                const uint32_t jnh = __shfl_sync(0xffffffffu, nh, j);
-                const uint32_t jnv = __shfl_sync(0xffffffffu, nv, j);
-                const uint32_t jex = __shfl_sync(0xffffffffu, excl, j);
+                const uint32_t ub = u0 + 32u * r, u = ub + lane;
+                // block of unit u: blocks ending at or before ub, plus those
+                // ending inside this half at or before u (block ends are
+                // distinct below the total, so one bit each)
+                const unsigned below = __ballot_sync(0xffffffffu, incl <= ub);
+                const uint32_t te = incl - ub;
+                const unsigned ends = __reduce_or_sync(0xffffffffu, incl > ub && te < 32u ? 1u << te : 0u);
+                const int j = __popc(below) + __popc(ends & ((2u << lane) - 1u) & ~1u);
+                const uint32_t jbase = __shfl_sync(0xffffffffu, base, j & 31);
+                const uint32_t jmeta = __shfl_sync(0xffffffffu, meta, j & 31);
+                const uint32_t jlo = __shfl_sync(0xffffffffu, lo, j & 31);
+                const uint32_t jnh = __shfl_sync(0xffffffffu, nh, j & 31);
+                const uint32_t jnv = __shfl_sync(0xffffffffu, nv, j & 31);
+                const uint32_t jex = __shfl_sync(0xffffffffu, excl, j & 31);
                 kind[r] = -1;
                 v[r] = make_uint4(0u, 0u, 0u, 0u);
                 ul[r] = 0;
