@@ -635,6 +635,18 @@ def large_workloads(mg, dev, flush, stream, peak, nsample=400):
         dims = c["dims"]
         r["storage_error_vs_fp64"] = storage_errors(mg, g, tf, vol_h, dims, S, nsample=nsample, seed=11,
                                                     block=block, max_level=4)
+        if cfg_i == 4:
+            # many segments: the CTA-shared histogram kernel, exact u32
+            boxes_h = synth.make_boxes(4)
+            boxes = torch.from_numpy(boxes_h).to(dev)
+            Q = boxes_h.shape[0]
+            tune = mg.mg_query_autotune(g, boxes)
+            plan = mg.QueryPlan(g, max_Q=Q)
+            res = torch.empty((Q, S), dtype=torch.uint32, device=dev)
+            ms = _time(lambda: plan.run(boxes, out=res), 5, flush, stream)
+            mg.mg_sync_status(g)
+            plan.close()
+            r["queries"] = {"boxes": Q, "u32": {"ms": ms, "queries_per_s": Q / (ms / 1e3)}, "autotune": tune}
         if cfg_i == 3:
             boxes_h = synth.make_boxes(3)
             boxes = torch.from_numpy(boxes_h).to(dev)
