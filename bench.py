@@ -443,7 +443,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg_i, boxes_h, args.cpu_seconds, tf=tf_h)
 
-    launches_prop = 1 + sum(1 for d in range(1, info["depth"] + 1) if info["bucket"][d + 1] > info["bucket"][d])
+    # one persistent launch, or (depth beyond the single pass) sources + one launch per level
+    launches_prop = 1 if info["depth"] + 1 <= 64 else 1 + sum(
+        1 for d in range(1, info["depth"] + 1) if info["bucket"][d + 1] > info["bucket"][d])
     nscan = 1 if Q <= 2048 else 3   # kernels of one device-wide scan of Q values
     if args.schedule == "batched":
         # batch size, zero rows, count, offsets (one CTA up to 2^18 boxes, else two
