@@ -252,7 +252,7 @@ MG_API mg_status mg_query_plan_run(mg_query_plan *p, const int32_t *boxes, int64
 MG_API void mg_query_plan_free(mg_query_plan *p);
 
 /* Autotuner of the batched query: times every work-chunk size in
- * {1024, 2048, 4096, 8192} cubes with CTAs of 128 and 256 threads on the
+ * {1024, 2048, 4096, 8192, 16384} cubes with CTAs of 128, 256 and 512 threads on the
  * given batch (dense layout; opts->hist_type and alpha_dtype as the caller
  * will use them), writes the fastest into opts->chunk_cubes/block_threads and
  * keeps it in the graph for later calls and plans that leave them 0.

@@ -296,6 +296,272 @@ __global__ void plan_write_kernel(Geom G, const int32_t* __restrict__ boxes, int
 }
 
 // ---------------------------------------------------------------------------
+// The plan of a query-plan run in one launch: the footprint counts of every
+// box, both exclusive scans in a single pass, the zeroing of the batch's
+// output rows, the block records and the chunk map.  CTAs take tiles of
+// kTileBoxes boxes in ticket order; a tile publishes its own totals, then
+// sums its predecessors' words backwards until it meets one that holds an
+// inclusive prefix, and publishes its own prefix.  Plans only (capacities in
+// `lim`).
+// ---------------------------------------------------------------------------
+constexpr int kTileBoxes = 16;   // one warp per box
+constexpr int kFusedThreads = kTileBoxes * 32;
+constexpr int kFusedItems = 4;                  // blocks per thread and round, interleaved
+constexpr uint64_t kTileAgg = 1ull << 62;       // the word holds the tile's own total
+constexpr uint64_t kTilePre = 2ull << 62;       // the word holds the inclusive prefix
+constexpr uint64_t kTileVal = (1ull << 62) - 1;
+constexpr unsigned kLookbackLimit = 1u << 20;   // polls before the look-back gives up
+
+// zero the tile words of the live batch and both work tickets
+__global__ void plan_reset_kernel(const int64_t* __restrict__ Qd, uint64_t* __restrict__ tiles,
+                                  unsigned long long* __restrict__ tickets) {
+    const int64_t n = 2 * ((*Qd + kTileBoxes - 1) / kTileBoxes);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        tiles[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 2) tickets[threadIdx.x] = 0;
+}
+
+struct FusedOut {
+    uint64_t* ncube;
+    uint64_t* blk_off;
+    uint64_t* chunk_off;
+    Blk* blk;
+    uint32_t* chunk_q;
+    uint32_t* chunk_b;
+    uint64_t* tiles;               // two words per tile: blocks, chunks
+    unsigned long long* ticket;    // tile order
+    uint32_t* acc;                 // rows zeroed for the live batch
+    float* accf;                   // likewise (fp32 histograms), or nullptr
+};
+
+__global__ void __launch_bounds__(kFusedThreads) plan_fused_kernel(Geom G, const int32_t* __restrict__ boxes,
+                                                                   int64_t Q, uint32_t chunk, Lim lim, FusedOut F,
+                                                                   unsigned* __restrict__ status) {
+    __shared__ Runs wr[kTileBoxes];
+    __shared__ uint32_t s_nblk[kTileBoxes];
+    __shared__ uint64_t s_ncube[kTileBoxes];
+    __shared__ uint32_t s_boff[kTileBoxes + 1];   // tile-local block offsets, total last
+    __shared__ uint64_t s_coff[kTileBoxes + 1];   // tile-local chunk offsets, total last
+    __shared__ uint32_t s_cube[kTileBoxes];       // tile-local cube offsets, mod 2^32
+    __shared__ uint32_t s_wsum[kFusedThreads / 32][kFusedItems];
+    __shared__ uint32_t s_rtot[kFusedItems];
+    __shared__ unsigned long long s_tile;
+    __shared__ uint64_t s_pre_b, s_pre_c;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = atomicAdd(F.ticket, 1ull);
+    __syncthreads();
+    const int64_t tile = (int64_t)s_tile;
+    const int64_t Qe = live_q(lim, Q);
+    const int64_t q0 = tile * kTileBoxes;
+    if (q0 >= Qe) return;   // no tile of the live batch waits on this one
+
+    // 1. blocks and cubes of every box, one warp per box
+    const int64_t q = q0 + warp;
+    uint32_t nb = 0;
+    uint64_t cubes = 0;
+    if (q < Qe) {
+        int32_t b[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
+        if (box_ok(b, G)) {
+            Runs& R = wr[warp];
+            make_runs_warp(b, G, R);
+            const int npairs = R.ny * R.nz;
+            for (int pr = lane; pr < npairs; pr += 32) {
+                const int j = pr % R.ny, k = pr / R.ny;
+                for (int i = 0; i < R.nx; i++) cubes += block_cubes(R.lx[i], R.ly[j], R.lz[k]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cubes += __shfl_xor_sync(0xffffffffu, cubes, o);
+            nb = (uint32_t)(R.nx * R.ny * R.nz);
+        } else if (lane == 0) {
+            set_status(status, kStatBadInput);
+        }
+        if (lane == 0) F.ncube[q] = cubes;
+    }
+    if (lane == 0) {
+        s_nblk[warp] = nb;
+        s_ncube[warp] = cubes;
+    }
+    {   // the tile's live output rows are one contiguous span
+        const size_t r0 = (size_t)q0 * G.S, r1 = (size_t)min(q0 + kTileBoxes, Qe) * G.S;
+        for (size_t i = r0 + threadIdx.x; i < r1; i += kFusedThreads) {
+            F.acc[i] = 0u;
+            if (F.accf) F.accf[i] = 0.f;
+        }
+    }
+    __syncthreads();
+
+    // 2. offsets within the tile, then the prefix of all earlier tiles
+    if (warp == 0) {
+        const uint64_t xb = lane < kTileBoxes ? s_nblk[lane] : 0u;
+        const uint64_t xq = lane < kTileBoxes ? s_ncube[lane] : 0u;
+        const uint64_t xc = (xq + chunk - 1) / chunk;
+        uint64_t ib = xb, ic = xc, iq = xq;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t yb = __shfl_up_sync(0xffffffffu, ib, o);
+            const uint64_t yc = __shfl_up_sync(0xffffffffu, ic, o);
+            const uint64_t yq = __shfl_up_sync(0xffffffffu, iq, o);
+            if (lane >= o) {
+                ib += yb;
+                ic += yc;
+                iq += yq;
+            }
+        }
+        if (lane < kTileBoxes) {
+            s_boff[lane] = (uint32_t)(ib - xb);
+            s_coff[lane] = ic - xc;
+            s_cube[lane] = (uint32_t)(iq - xq);
+        }
+        const uint64_t agg_b = __shfl_sync(0xffffffffu, ib, 31), agg_c = __shfl_sync(0xffffffffu, ic, 31);
+        if (lane == 0) {
+            s_boff[kTileBoxes] = (uint32_t)agg_b;
+            s_coff[kTileBoxes] = agg_c;
+        }
+        uint64_t* word = F.tiles + 2 * tile;
+        if (lane == 0) {
+            const uint64_t flag = tile == 0 ? kTilePre : kTileAgg;
+            st_relaxed_u64(word, flag | agg_b);
+            st_relaxed_u64(word + 1, flag | agg_c);
+        }
+        // look back over 32 tiles at a time; a word pair counts once both
+        // words carry the same flag
+        uint64_t eb = 0, ec = 0;
+        int64_t top = tile - 1;
+        unsigned polls = 0;
+        while (top >= 0) {
+            const int64_t t = top - lane;
+            uint64_t wb = kTilePre, wc = kTilePre;   // before the first tile: prefix 0
+            if (t >= 0) {
+                wb = ld_relaxed_u64(F.tiles + 2 * t);
+                wc = ld_relaxed_u64(F.tiles + 2 * t + 1);
+            }
+            const bool ready = (wb >> 62) != 0 && (wb >> 62) == (wc >> 62);
+            const unsigned pre = __ballot_sync(0xffffffffu, ready && (wb >> 62) == 2u);
+            const unsigned late = __ballot_sync(0xffffffffu, !ready);
+            // the lanes up to the nearest tile holding its prefix are needed
+            const unsigned need = pre ? ((pre & (0u - pre)) << 1) - 1u : 0xffffffffu;
+            if (late & need) {
+                if (++polls > kLookbackLimit) {
+                    if (lane == 0) set_status(status, kStatTimeout);
+                    break;
+                }
+                __nanosleep(64);
+                continue;
+            }
+            const bool use = (need >> lane) & 1u;
+            uint64_t vb = use ? wb & kTileVal : 0u, vc = use ? wc & kTileVal : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                vb += __shfl_xor_sync(0xffffffffu, vb, o);
+                vc += __shfl_xor_sync(0xffffffffu, vc, o);
+            }
+            eb += vb;
+            ec += vc;
+            if (pre) break;
+            top -= 32;
+        }
+        if (lane == 0) {
+            if (tile > 0) {
+                st_relaxed_u64(word, kTilePre | (eb + agg_b));
+                st_relaxed_u64(word + 1, kTilePre | (ec + agg_c));
+            }
+            s_pre_b = eb;
+            s_pre_c = ec;
+        }
+    }
+    __syncthreads();
+    const uint64_t pre_b = s_pre_b, pre_c = s_pre_c;
+    const uint64_t tot_b = pre_b + s_boff[kTileBoxes], tot_c = pre_c + s_coff[kTileBoxes];
+    if (q < Qe && lane == 0) {
+        F.blk_off[q] = pre_b + s_boff[warp];
+        F.chunk_off[q] = pre_c + s_coff[warp];
+        if (q == Qe - 1) {
+            F.blk_off[Qe] = tot_b;
+            F.chunk_off[Qe] = tot_c;
+            if (tot_b > lim.cap_blocks || tot_c > lim.cap_chunks) set_status(status, kStatCapacity);
+        }
+    }
+    // past the plan's buffers: the last tile has flagged the batch, nothing is written
+    if (tot_b > lim.cap_blocks || tot_c > lim.cap_chunks) return;
+
+    // 3. block records and the chunk map; item `it` of thread t is the tile's
+    // block r0 + it * kFusedThreads + t
+    const uint32_t nbt = s_boff[kTileBoxes];
+    uint32_t carry = 0;   // cubes of the earlier rounds, mod 2^32
+    for (uint32_t r0 = 0; r0 < nbt; r0 += kFusedThreads * kFusedItems) {
+        uint32_t n[kFusedItems], incl[kFusedItems];
+        int wk[kFusedItems], ik[kFusedItems], jk[kFusedItems], kk[kFusedItems];
+#pragma unroll
+        for (int it = 0; it < kFusedItems; it++) {
+            const uint32_t idx = r0 + it * kFusedThreads + threadIdx.x;
+            n[it] = 0;
+            wk[it] = ik[it] = jk[it] = kk[it] = 0;
+            if (idx < nbt) {
+                int w = 0;   // the last box whose blocks start at or before idx
+#pragma unroll
+                for (int st = kTileBoxes / 2; st > 0; st >>= 1)
+                    if (s_boff[w + st] <= idx) w += st;
+                const Runs& R = wr[w];
+                const uint32_t t = idx - s_boff[w];
+                const uint32_t pr = t / (uint32_t)R.nx;
+                wk[it] = w;
+                ik[it] = (int)(t - pr * (uint32_t)R.nx);
+                jk[it] = (int)(pr % (uint32_t)R.ny);
+                kk[it] = (int)(pr / (uint32_t)R.ny);
+                n[it] = block_cubes(R.lx[ik[it]], R.ly[jk[it]], R.lz[kk[it]]);
+            }
+            uint32_t v = n[it];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            incl[it] = v;
+            if (lane == 31) s_wsum[warp][it] = v;
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int it = 0; it < kFusedItems; it++) {
+                const uint32_t x = lane < kFusedThreads / 32 ? s_wsum[lane][it] : 0u;
+                uint32_t v = x;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += y;
+                }
+                __syncwarp();
+                if (lane < kFusedThreads / 32) s_wsum[lane][it] = v - x;
+                if (lane == 31) s_rtot[it] = v;
+            }
+        }
+        __syncthreads();
+        uint32_t base = carry;
+#pragma unroll
+        for (int it = 0; it < kFusedItems; it++) {
+            const uint32_t idx = r0 + it * kFusedThreads + threadIdx.x;
+            if (idx < nbt) {
+                const int w = wk[it], i = ik[it], j = jk[it], k = kk[it];
+                const Runs& R = wr[w];
+                const uint32_t start = base + s_wsum[warp][it] + incl[it] - n[it] - s_cube[w];
+                const uint64_t bi = pre_b + idx;
+                F.blk[bi] = make_blk(G, start, R.sx[i], R.sy[j], R.sz[k], R.lx[i], R.ly[j], R.lz[k]);
+                const uint64_t cb = pre_c + s_coff[w];
+                for (uint64_t c = ((uint64_t)start + chunk - 1) / chunk; c * chunk < (uint64_t)start + n[it]; c++) {
+                    F.chunk_q[cb + c] = (uint32_t)(q0 + w);
+                    F.chunk_b[cb + c] = (uint32_t)bi;
+                }
+            }
+            base += s_rtot[it];
+        }
+        carry = base;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // shared-memory histogram of one chunk
 // ---------------------------------------------------------------------------
 template <bool FP>
@@ -1190,12 +1456,6 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(const uint32_t*
 // the live batch size of a plan run, passed by value (no host staging)
 __global__ void set_batch_kernel(int64_t* __restrict__ Qd, int64_t Q) { *Qd = Q; }
 
-__global__ void plan_check_kernel(const uint64_t* __restrict__ blk_off, const uint64_t* __restrict__ chunk_off, Lim lim,
-                                  unsigned* __restrict__ status) {
-    if (threadIdx.x == 0 && blockIdx.x == 0 && over_cap(lim, blk_off, chunk_off, *lim.Qd))
-        set_status(status, kStatCapacity);
-}
-
 // zero the first *Qd rows of S counters (plans); n = rows * S bound
 template <typename T>
 __global__ void zero_rows_kernel(T* __restrict__ a, const int64_t* __restrict__ Qd, int64_t S) {
@@ -1624,7 +1884,7 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     const Geom G = make_geom(g);
     unsigned* status = g->status.as<unsigned>();
     const Lim lim{p->Qd, p->cap_blocks, p->cap_chunks};
-    Buf acc_b, nblk, ncube, nchunk, nb64, blk_off, chunk_off, blk, chunk_q, chunk_b, ticket;
+    Buf acc_b, ncube, blk_off, chunk_off, blk, chunk_q, chunk_b, tiles, ticket;
     uint32_t* acc = nullptr;
     float* accf = nullptr;
     if (FP) {
@@ -1634,38 +1894,31 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     } else {
         acc = static_cast<uint32_t*>(p->result);
     }
-    MG_TRY(nblk.alloc(&al, (size_t)Q * 4, s));
+    const int64_t ntiles = (Q + kTileBoxes - 1) / kTileBoxes;
     MG_TRY(ncube.alloc(&al, (size_t)Q * 8, s));
-    MG_TRY(nchunk.alloc(&al, (size_t)Q * 8, s));
-    MG_TRY(nb64.alloc(&al, (size_t)Q * 8, s));
     MG_TRY(blk_off.alloc(&al, (size_t)(Q + 1) * 8, s));
     MG_TRY(chunk_off.alloc(&al, (size_t)(Q + 1) * 8, s));
     MG_TRY(blk.alloc(&al, (size_t)p->cap_blocks * sizeof(Blk), s));
     MG_TRY(chunk_q.alloc(&al, (size_t)p->cap_chunks * 4, s));
     MG_TRY(chunk_b.alloc(&al, (size_t)p->cap_chunks * 4, s));
-    MG_TRY(ticket.alloc(&al, 8, s));
+    MG_TRY(tiles.alloc(&al, (size_t)ntiles * 16, s));
+    MG_TRY(ticket.alloc(&al, 16, s));   // tile order, main-kernel chunks
 
-    MG_CUDA(cudaMemsetAsync(ticket.p, 0, 8, s));
-    const unsigned zg = grid_for(Q * S, 256, 152 * 64);
-    zero_rows_kernel<uint32_t><<<zg, 256, 0, s>>>(acc, p->Qd, S);
-    if (FP) zero_rows_kernel<float><<<zg, 256, 0, s>>>(accf, p->Qd, S);
-    const unsigned wg = grid_for(Q * 32, 256);
-    plan_count_kernel<<<wg, 256, 0, s>>>(G, p->boxes, Q, p->chunk, nblk.as<uint32_t>(), ncube.as<uint64_t>(),
-                                         nchunk.as<uint64_t>(), status, lim);
+    plan_reset_kernel<<<grid_for(2 * ntiles, 256, 152 * 4), 256, 0, s>>>(p->Qd, tiles.as<uint64_t>(),
+                                                                         ticket.as<unsigned long long>());
     MG_CUDA(cudaGetLastError());
-    if (Q <= kFusedScanMax) {
-        plan_scan_kernel<<<1, kScanThreads, 0, s>>>(nblk.as<uint32_t>(), nchunk.as<uint64_t>(), Q,
-                                                    blk_off.as<uint64_t>(), chunk_off.as<uint64_t>(), lim, status);
-    } else {
-        MG_TRY(scan_exclusive_u64(nchunk.as<uint64_t>(), chunk_off.as<uint64_t>(), Q, chunk_off.as<uint64_t>() + Q, al,
-                                  s));
-        widen_kernel<<<grid_for(Q, 256, 152 * 64), 256, 0, s>>>(nblk.as<uint32_t>(), nb64.as<uint64_t>(), Q);
-        MG_TRY(scan_exclusive_u64(nb64.as<uint64_t>(), blk_off.as<uint64_t>(), Q, blk_off.as<uint64_t>() + Q, al, s));
-        plan_check_kernel<<<1, 32, 0, s>>>(blk_off.as<uint64_t>(), chunk_off.as<uint64_t>(), lim, status);
-    }
-    plan_write_kernel<<<wg, 256, 0, s>>>(G, p->boxes, Q, blk_off.as<uint64_t>(), blk.as<Blk>(), lim,
-                                         chunk_off.as<uint64_t>(), p->chunk, chunk_q.as<uint32_t>(),
-                                         chunk_b.as<uint32_t>());
+    FusedOut F;
+    F.ncube = ncube.as<uint64_t>();
+    F.blk_off = blk_off.as<uint64_t>();
+    F.chunk_off = chunk_off.as<uint64_t>();
+    F.blk = blk.as<Blk>();
+    F.chunk_q = chunk_q.as<uint32_t>();
+    F.chunk_b = chunk_b.as<uint32_t>();
+    F.tiles = tiles.as<uint64_t>();
+    F.ticket = ticket.as<unsigned long long>();
+    F.acc = acc;
+    F.accf = accf;
+    plan_fused_kernel<<<(unsigned)ntiles, kFusedThreads, 0, s>>>(G, p->boxes, Q, p->chunk, lim, F, status);
     MG_CUDA(cudaGetLastError());
 
     MainArgs A;
@@ -1689,7 +1942,7 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     A.lim = lim;
     A.Q = Q;
     A.chunk = p->chunk;
-    A.ticket = ticket.as<unsigned long long>();
+    A.ticket = ticket.as<unsigned long long>() + 1;
     A.acc = acc;
     A.accf = accf;
     mg_query_opts o{};
@@ -1699,7 +1952,7 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
                         (size_t)(p->threads / 32) * kQueueBytes + 16;
     MG_TRY((launch_main<FP, AT>(g, A, o, nullptr, smem, p->threads, s)));
     if (FP) {
-        dense_f32_rows_kernel<<<zg, 256, 0, s>>>(acc, accf, p->Qd, S);
+        dense_f32_rows_kernel<<<grid_for(Q * S, 256, 152 * 64), 256, 0, s>>>(acc, accf, p->Qd, S);
         MG_CUDA(cudaGetLastError());
     }
     return MG_OK;
@@ -1758,10 +2011,12 @@ MG_API mg_status mg_query_plan_create(mg_graph* g, int64_t max_Q, const mg_query
     if (st == MG_OK) {
         const size_t S = g->S, Q = (size_t)max_Q;
         auto r = [](size_t n) { return (n + 255) & ~(size_t)255; };
-        const size_t parts = 4 * (r(8 * ((Q + 2047) / 2048)) + r(8 * ((Q + 2047) / 2048 / 2048 + 1)) + 2 * r(8));
-        const size_t bytes = r(Q * 24) + r(8) + r(Q * S * 4) * (p->fp ? 2 : 1) + r(4 * Q) + 3 * r(8 * Q) +
-                             2 * r(8 * (Q + 1)) + r(p->cap_blocks * sizeof(Blk)) + 2 * r(p->cap_chunks * 4) + r(8) +
-                             parts + 65536;
+        // boxes, batch size, results (+ u32 scratch), cube counts, both offset
+        // arrays, blocks, chunk map, tile words, tickets
+        const size_t tiles = (Q + kTileBoxes - 1) / kTileBoxes;
+        const size_t bytes = r(Q * 24) + r(8) + r(Q * S * 4) * (p->fp ? 2 : 1) + r(8 * Q) + 2 * r(8 * (Q + 1)) +
+                             r(p->cap_blocks * sizeof(Blk)) + 2 * r(p->cap_chunks * 4) + r(16 * tiles) + r(16) +
+                             65536;
         st = p->pool.alloc(&g->al, bytes, nullptr);
         if (st == MG_OK) {
             cudaError_t e = cudaStreamSynchronize(nullptr);
@@ -1874,10 +2129,13 @@ extern "C" MG_API mg_status mg_query_autotune(mg_graph* g, const int32_t* boxes,
     st = outb.alloc(&g->al, (size_t)Q * g->S * 4, s);
     if (st == MG_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = fail(MG_ERR_CUDA, "cudaEventCreate");
-    const int chunks[] = {1024, 2048, 4096, 8192};
-    const int threads[] = {128, 256};
-    for (int ci = 0; st == MG_OK && ci < 4; ci++) {
-        for (int ti = 0; st == MG_OK && ti < 2; ti++) {
+    // 512 threads matter when one histogram per CTA fills shared memory
+    // (many segments): two CTAs per SM then hold 32 warps instead of 8
+    const int chunks[] = {1024, 2048, 4096, 8192, 16384};
+    const int threads[] = {128, 256, 512};
+    const int nc = (int)(sizeof(chunks) / sizeof(chunks[0])), nt = (int)(sizeof(threads) / sizeof(threads[0]));
+    for (int ci = 0; st == MG_OK && ci < nc; ci++) {
+        for (int ti = 0; st == MG_OK && ti < nt; ti++) {
             mg_query_opts o = *opts;
             o.layout = MG_LAYOUT_DENSE;
             o.schedule = MG_SCHED_BATCHED;
