@@ -303,12 +303,22 @@ def run_ours(args):
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     mg.mg_sync_status(g)
-    # stage split of the query (plan, histogram kernel, output) from CUDA events
-    # the library records on this stream, same launch shape, L2 flushed first
-    for k in range(args.steps):
-        flush.zero_()
-        mg.mg_query_boxes(g, boxes, out=hist, timing=True, **qkw)
-        qmain.append(mg.mg_query_timing(g))
+    # stage split of the query from CUDA events the library records: a plan
+    # with timing events in its graph (plan stage, main kernel), else the
+    # direct call's (plan, main kernel, output); same launch shape, L2 flushed
+    if use_plan:
+        plan_t = mg.QueryPlan(g, max_Q=Q, chunk_cubes=args.chunk, block_threads=args.threads, timing=True)
+        for k in range(args.steps):
+            flush.zero_()
+            plan_t.run(boxes, out=hist, stream=stream)
+            pm, mm = plan_t.timing()
+            qmain.append((pm, mm, None))
+        plan_t.close()
+    else:
+        for k in range(args.steps):
+            flush.zero_()
+            mg.mg_query_boxes(g, boxes, out=hist, timing=True, **qkw)
+            qmain.append(mg.mg_query_timing(g))
     torch.cuda.synchronize()
     step_ms = np.array([e[0].elapsed_time(e[4]) for e in ev])
     prop_ms = np.array([e[0].elapsed_time(e[1]) for e in ev])
@@ -468,10 +478,16 @@ def run_ours(args):
                        "lookup_p50": float(np.percentile(look_ms, 50))},
         "stages_ms": {"propagate": float(np.mean(prop_ms)), "query": float(np.mean(query_ms)),
                       "query_plan": float(np.mean([t[0] for t in qmain])), "query_main": float(np.mean(main_ms)),
-                      "query_output": float(np.mean([t[2] for t in qmain])), "lookup": float(np.mean(look_ms)),
+                      "query_rest": float(np.mean(query_ms) - np.mean([t[0] for t in qmain]) - np.mean(main_ms)),
+                      "lookup": float(np.mean(look_ms)),
                       "propagate_alone": prop_alone, "propagate_with_tf_upload": prop_with_upload,
                       "lookup_alone": look_alone,
-                      "note": "propagate/lookup run concurrently with the query; *_alone timed by themselves"},
+                      "note": "propagate/lookup run concurrently with the query; *_alone timed by themselves; "
+                              "query_plan = tile reset + fused plan kernel, query_main = histogram kernel (events "
+                              "in a timed copy of the plan's graph), query_rest = the rest of a batch (box copy, "
+                              "batch size, result copy, launch gaps)" if use_plan else
+                              "propagate/lookup run concurrently with the query; *_alone timed by themselves; "
+                              "query_rest includes the output stage"},
         "roofline_nominal": {"peak": NOMINAL_HBM_GBS, "unit": "GB/s", "frac": achieved / NOMINAL_HBM_GBS,
                              "propagate_frac": prop_gbs / NOMINAL_HBM_GBS, "lookup_frac": look_gbs / NOMINAL_HBM_GBS},
         "roofline": {"bound": "hbm", "kernel": ("query_warp_kernel" if S <= 2048 else "query_batched_kernel")

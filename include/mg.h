@@ -239,6 +239,9 @@ MG_API mg_status mg_query_timing(const mg_graph *g, float *plan_ms, float *main_
  * max_blocks, max_chunks: footprint blocks and work chunks one run may need
  *   (0 = 1024 and 256 per box).  A run whose boxes need more writes zero
  *   histograms and sets MG_ERR_CAPACITY in the status word (mg_sync_status).
+ * opts->timing set: the graph also records CUDA events around its plan stage
+ *   (tile reset and the fused plan kernel) and its main kernel; read the
+ *   durations of the last run with mg_query_plan_timing.
  * The plan holds its memory (from the graph's allocator) until
  * mg_query_plan_free; runs of one plan share it, so runs of one plan on
  * different streams must not overlap.
@@ -249,6 +252,10 @@ MG_API mg_status mg_query_plan_create(mg_graph *g, int64_t max_Q, const mg_query
 /* boxes: Q x 6 int32 (device), 0 <= Q <= max_Q; out: Q x S (uint32 or fp32). */
 MG_API mg_status mg_query_plan_run(mg_query_plan *p, const int32_t *boxes, int64_t Q, void *out, size_t out_capacity,
                                    mg_stream stream);
+/* Durations in milliseconds of the last run's plan stage and main kernel, for a
+ * plan created with opts->timing; waits for that run's main kernel.
+ * MG_ERR_INVALID_ARG: NULL argument, a plan made without timing, or no run yet. */
+MG_API mg_status mg_query_plan_timing(const mg_query_plan *p, float *plan_ms, float *main_ms);
 MG_API void mg_query_plan_free(mg_query_plan *p);
 
 /* Autotuner of the batched query: times every work-chunk size in

@@ -250,6 +250,14 @@ __device__ __forceinline__ uint8_t ld_relaxed_u8(const uint8_t* p) {
     asm volatile("ld.relaxed.gpu.global.u8 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
     return (uint8_t)v;
 }
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start before the previous kernel on its stream has
+// finished; grid_dependency_wait() blocks until that kernel has completed and
+// its writes are visible (a no-op for an ordinary launch).  The previous kernel
+// lets it start early with grid_dependents_launch().
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 __device__ __forceinline__ void set_status(unsigned* st, unsigned bit) {
     if (st) atomicOr(st, bit);
 }

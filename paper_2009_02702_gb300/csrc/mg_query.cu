@@ -179,6 +179,39 @@ __device__ __forceinline__ uint32_t block_cubes(int lx, int ly, int lz) {
     return 1u << (lx + ly + lz - 3 * l);
 }
 
+// Footprint cubes of a box in closed form.  On each axis let F(m) be the sum
+// over its runs of level a >= m of 2^(a-m), and P(m) = Fx(m) Fy(m) Fz(m).  A
+// block of run levels (a, b, c) with minimum m0 adds 2^(a+b+c-3m) to P(m) for
+// every m <= m0, so the blocks' cubes, sum 2^(a+b+c-3 m0), equal
+// P(0) - 7 * sum over m >= 1 of P(m).  Algorithm 1's steps on one axis rise
+// to a peak and fall again, so no level occurs more than twice and two bit
+// masks hold an axis's levels: F(m) = (once >> m) + (twice >> m).
+__device__ __forceinline__ void level_masks(const uint8_t* l, int n, uint64_t& once, uint64_t& twice) {
+    once = twice = 0;
+    for (int i = 0; i < n; i++) {
+        const uint64_t bit = 1ull << l[i];
+        if (once & bit) twice |= bit;
+        else once |= bit;
+    }
+}
+
+__device__ __forceinline__ uint64_t cubes_from_masks(uint64_t x1, uint64_t x2, uint64_t y1, uint64_t y2, uint64_t z1,
+                                                     uint64_t z2) {
+    const uint64_t p0 = (x1 + x2) * (y1 + y2) * (z1 + z2);
+    uint64_t rest = 0;
+    for (int m = 1; m < 64 && (x1 >> m) && (y1 >> m) && (z1 >> m); m++)
+        rest += ((x1 >> m) + (x2 >> m)) * ((y1 >> m) + (y2 >> m)) * ((z1 >> m) + (z2 >> m));
+    return p0 - 7 * rest;
+}
+
+__device__ __forceinline__ uint64_t footprint_cubes(const Runs& R) {
+    uint64_t x1, x2, y1, y2, z1, z2;
+    level_masks(R.lx, R.nx, x1, x2);
+    level_masks(R.ly, R.ny, y1, y2);
+    level_masks(R.lz, R.nz, z1, z2);
+    return cubes_from_masks(x1, x2, y1, y2, z1, z2);
+}
+
 // Batch size and capacities read on the device, for query plans replayed as
 // CUDA graphs: the launches cover Q boxes, *Qd of them are live, and the
 // footprint must fit the plan's buffers.  Qd == nullptr: all Q are live and
@@ -227,15 +260,8 @@ __global__ void plan_count_kernel(Geom G, const int32_t* __restrict__ boxes, int
     __shared__ Runs wr[kPlanThreads / 32];
     Runs& R = wr[threadIdx.x >> 5];
     make_runs_warp(b, G, R);
-    uint64_t cubes = 0;
-    const int npairs = R.ny * R.nz;
-    for (int pr = lane; pr < npairs; pr += 32) {
-        const int j = pr % R.ny, k = pr / R.ny;
-        for (int i = 0; i < R.nx; i++) cubes += block_cubes(R.lx[i], R.ly[j], R.lz[k]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cubes += __shfl_xor_sync(0xffffffffu, cubes, o);
     if (lane == 0) {
+        const uint64_t cubes = footprint_cubes(R);
         if (nblk) nblk[q] = (uint32_t)(R.nx * R.ny * R.nz);
         ncube[q] = cubes;
         if (nchunk) nchunk[q] = (cubes + chunk - 1) / chunk;
@@ -298,24 +324,35 @@ __global__ void plan_write_kernel(Geom G, const int32_t* __restrict__ boxes, int
 // ---------------------------------------------------------------------------
 // The plan of a query-plan run in one launch: the footprint counts of every
 // box, both exclusive scans in a single pass, the zeroing of the batch's
-// output rows, the block records and the chunk map.  CTAs take tiles of
-// kTileBoxes boxes in ticket order; a tile publishes its own totals, then
-// sums its predecessors' words backwards until it meets one that holds an
-// inclusive prefix, and publishes its own prefix.  Plans only (capacities in
-// `lim`).
+// output rows, the block records and the chunk map.  CTAs take tiles of `tb`
+// boxes in ticket order (tb chosen on the host so that the tiles of a full
+// batch fill the GPU once); a tile publishes its own totals, then sums its
+// predecessors' words backwards until it meets one that holds an inclusive
+// prefix, and publishes its own prefix.  Plans only (capacities in `lim`).
 // ---------------------------------------------------------------------------
-constexpr int kTileBoxes = 16;   // one warp per box
-constexpr int kFusedThreads = kTileBoxes * 32;
-constexpr int kFusedItems = 4;                  // blocks per thread and round, interleaved
-constexpr uint64_t kTileAgg = 1ull << 62;       // the word holds the tile's own total
-constexpr uint64_t kTilePre = 2ull << 62;       // the word holds the inclusive prefix
+constexpr int kTileMax = 64;                     // boxes per tile at most
+constexpr int kFusedThreads = 512;
+constexpr int kFusedWarps = kFusedThreads / 32;
+constexpr int kBoxLanes = 16;                    // lanes per box in the count phase
+constexpr int kBoxGroups = kFusedThreads / kBoxLanes;
+constexpr int kScanPerLane = kTileMax / 32;      // boxes per lane in the tile scan
+constexpr int kFusedItems = 4;                   // blocks per thread and round, interleaved
+constexpr int kLookWindows = 4;                  // look-back windows of 32 tiles loaded per poll
+constexpr uint64_t kTileAgg = 1ull << 62;        // the word holds the tile's own total
+constexpr uint64_t kTilePre = 2ull << 62;        // the word holds the inclusive prefix
 constexpr uint64_t kTileVal = (1ull << 62) - 1;
-constexpr unsigned kLookbackLimit = 1u << 20;   // polls before the look-back gives up
+constexpr unsigned kLookbackLimit = 1u << 20;    // polls before the look-back gives up
+
+// boxes per tile for a batch of Q: about one tile per resident CTA
+int tile_boxes(int64_t Q, int sms) {
+    const int64_t slots = (int64_t)sms * 2;
+    return (int)std::min<int64_t>(kTileMax, std::max<int64_t>(1, (Q + slots - 1) / slots));
+}
 
 // zero the tile words of the live batch and both work tickets
-__global__ void plan_reset_kernel(const int64_t* __restrict__ Qd, uint64_t* __restrict__ tiles,
+__global__ void plan_reset_kernel(const int64_t* __restrict__ Qd, int tb, uint64_t* __restrict__ tiles,
                                   unsigned long long* __restrict__ tickets) {
-    const int64_t n = 2 * ((*Qd + kTileBoxes - 1) / kTileBoxes);
+    const int64_t n = 2 * ((*Qd + tb - 1) / tb);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         tiles[i] = 0;
     if (blockIdx.x == 0 && threadIdx.x < 2) tickets[threadIdx.x] = 0;
@@ -330,73 +367,140 @@ struct FusedOut {
     uint32_t* chunk_b;
     uint64_t* tiles;               // two words per tile: blocks, chunks
     unsigned long long* ticket;    // tile order
-    uint32_t* acc;                 // rows zeroed for the live batch
+    uint32_t* acc;                 // rows zeroed for the live batch (16-byte aligned)
     float* accf;                   // likewise (fp32 histograms), or nullptr
 };
 
-__global__ void __launch_bounds__(kFusedThreads) plan_fused_kernel(Geom G, const int32_t* __restrict__ boxes,
-                                                                   int64_t Q, uint32_t chunk, Lim lim, FusedOut F,
-                                                                   unsigned* __restrict__ status) {
-    __shared__ Runs wr[kTileBoxes];
-    __shared__ uint32_t s_nblk[kTileBoxes];
-    __shared__ uint64_t s_ncube[kTileBoxes];
-    __shared__ uint32_t s_boff[kTileBoxes + 1];   // tile-local block offsets, total last
-    __shared__ uint64_t s_coff[kTileBoxes + 1];   // tile-local chunk offsets, total last
-    __shared__ uint32_t s_cube[kTileBoxes];       // tile-local cube offsets, mod 2^32
-    __shared__ uint32_t s_wsum[kFusedThreads / 32][kFusedItems];
+// Algorithm 1's steps on one axis (as footprint_1d) together with the axis's
+// level masks (levels seen once, levels seen twice)
+__device__ __forceinline__ int axis_runs(int64_t i, int64_t di, int64_t dim, uint8_t* r, int32_t* start,
+                                         uint64_t& once, uint64_t& twice) {
+    int n = 0;
+    once = twice = 0;
+    di = min(i + di, dim) - i;
+    while (di > 0 && n < kMaxRuns) {
+        const int a = 63 - __clzll(di);
+        const int b = i == 0 ? 63 : __ffsll(i) - 1;
+        const int l = min(a, b);
+        const uint64_t bit = 1ull << l;
+        if (once & bit) twice |= bit;
+        else once |= bit;
+        r[n] = (uint8_t)l;
+        start[n] = (int32_t)i;
+        n++;
+        di -= (int64_t)1 << l;
+        i += (int64_t)1 << l;
+    }
+    return n;
+}
+
+// zero a[r0, r1) with 16-byte stores between the unaligned ends
+template <typename T>
+__device__ __forceinline__ void zero_span(T* a, size_t r0, size_t r1) {
+    const size_t a0 = min((r0 + 3) & ~(size_t)3, r1), a1 = max(r1 & ~(size_t)3, a0);
+    for (size_t i = r0 + threadIdx.x; i < a0; i += kFusedThreads) a[i] = T(0);
+    for (size_t i = a1 + threadIdx.x; i < r1; i += kFusedThreads) a[i] = T(0);
+    uint4* v = reinterpret_cast<uint4*>(a + a0);
+    for (size_t i = threadIdx.x; i < (a1 - a0) / 4; i += kFusedThreads) v[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 2) plan_fused_kernel(Geom G, const int32_t* __restrict__ boxes,
+                                                                      int64_t Q, int tb, uint32_t chunk,
+                                                                      int chunk_shift, Lim lim, FusedOut F,
+                                                                      unsigned* __restrict__ status) {
+    __shared__ Runs wr[kTileMax];
+    __shared__ uint32_t s_nblk[kTileMax];
+    __shared__ uint64_t s_ncube[kTileMax];
+    __shared__ uint64_t s_mx[kTileMax], s_my[kTileMax];   // ceil(2^32 / nx), ceil(2^32 / ny)
+    __shared__ uint32_t s_boff[kTileMax + 1];   // tile-local block offsets, total last
+    __shared__ uint64_t s_coff[kTileMax + 1];   // tile-local chunk offsets, total last
+    __shared__ uint32_t s_cube[kTileMax];       // tile-local cube offsets, mod 2^32
+    __shared__ uint32_t s_wsum[kFusedWarps][kFusedItems];
     __shared__ uint32_t s_rtot[kFusedItems];
     __shared__ unsigned long long s_tile;
     __shared__ uint64_t s_pre_b, s_pre_c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_tile = atomicAdd(F.ticket, 1ull);
+    // the main kernel may be scheduled once every tile has started; it waits
+    // for this grid's completion before it reads anything written here
+    grid_dependents_launch();
     __syncthreads();
     const int64_t tile = (int64_t)s_tile;
     const int64_t Qe = live_q(lim, Q);
-    const int64_t q0 = tile * kTileBoxes;
+    const int64_t q0 = tile * tb;
     if (q0 >= Qe) return;   // no tile of the live batch waits on this one
 
-    // 1. blocks and cubes of every box, one warp per box
-    const int64_t q = q0 + warp;
-    uint32_t nb = 0;
-    uint64_t cubes = 0;
-    if (q < Qe) {
-        int32_t b[6];
+    // 1. blocks and cubes of every box: kBoxLanes lanes per box, lanes 0-2 of
+    // a group building one axis's runs each
+    const int grp = threadIdx.x / kBoxLanes, bl = threadIdx.x % kBoxLanes;
+    for (int w0 = 0; w0 < tb; w0 += kBoxGroups) {
+        const int w = w0 + grp;
+        const int64_t q = q0 + w;
+        const bool live = w < tb && q < Qe;
+        bool ok = false;
+        uint64_t once = 0, twice = 0;
+        if (live) {
+            int32_t b[6];
 #pragma unroll
-        for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
-        if (box_ok(b, G)) {
-            Runs& R = wr[warp];
-            make_runs_warp(b, G, R);
-            const int npairs = R.ny * R.nz;
-            for (int pr = lane; pr < npairs; pr += 32) {
-                const int j = pr % R.ny, k = pr / R.ny;
-                for (int i = 0; i < R.nx; i++) cubes += block_cubes(R.lx[i], R.ly[j], R.lz[k]);
+            for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
+            ok = box_ok(b, G);
+            if (!ok && bl == 0) set_status(status, kStatBadInput);
+            if (ok && bl < 3) {
+                Runs& R = wr[w];
+                const int64_t i0 = bl == 0 ? b[0] : bl == 1 ? b[1] : b[2];
+                const int64_t di = bl == 0 ? b[3] : bl == 1 ? b[4] : b[5];
+                const int64_t dim = bl == 0 ? G.dims[0][0] : bl == 1 ? G.dims[0][1] : G.dims[0][2];
+                uint8_t* lv = bl == 0 ? R.lx : bl == 1 ? R.ly : R.lz;
+                int32_t* sv = bl == 0 ? R.sx : bl == 1 ? R.sy : R.sz;
+                const int n = axis_runs(i0, di, dim, lv, sv, once, twice);
+                if (bl == 0) R.nx = n;
+                else if (bl == 1) R.ny = n;
+                else R.nz = n;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cubes += __shfl_xor_sync(0xffffffffu, cubes, o);
-            nb = (uint32_t)(R.nx * R.ny * R.nz);
-        } else if (lane == 0) {
-            set_status(status, kStatBadInput);
         }
-        if (lane == 0) F.ncube[q] = cubes;
-    }
-    if (lane == 0) {
-        s_nblk[warp] = nb;
-        s_ncube[warp] = cubes;
+        // lanes 1 and 2 of a group hand their masks to lane 0
+        const uint64_t y1 = __shfl_down_sync(0xffffffffu, once, 1, kBoxLanes);
+        const uint64_t y2 = __shfl_down_sync(0xffffffffu, twice, 1, kBoxLanes);
+        const uint64_t z1 = __shfl_down_sync(0xffffffffu, once, 2, kBoxLanes);
+        const uint64_t z2 = __shfl_down_sync(0xffffffffu, twice, 2, kBoxLanes);
+        __syncwarp();
+        if (bl == 0 && w < tb) {
+            uint64_t cubes = 0;
+            uint32_t nb = 0;
+            if (ok) {
+                const Runs& R = wr[w];
+                cubes = cubes_from_masks(once, twice, y1, y2, z1, z2);
+                nb = (uint32_t)(R.nx * R.ny * R.nz);
+                s_mx[w] = ((1ull << 32) + R.nx - 1) / (uint64_t)R.nx;
+                s_my[w] = ((1ull << 32) + R.ny - 1) / (uint64_t)R.ny;
+            }
+            if (live) F.ncube[q] = cubes;
+            s_nblk[w] = nb;
+            s_ncube[w] = cubes;
+        }
     }
     {   // the tile's live output rows are one contiguous span
-        const size_t r0 = (size_t)q0 * G.S, r1 = (size_t)min(q0 + kTileBoxes, Qe) * G.S;
-        for (size_t i = r0 + threadIdx.x; i < r1; i += kFusedThreads) {
-            F.acc[i] = 0u;
-            if (F.accf) F.accf[i] = 0.f;
-        }
+        const size_t r0 = (size_t)q0 * G.S, r1 = (size_t)min(q0 + tb, Qe) * G.S;
+        zero_span(F.acc, r0, r1);
+        if (F.accf) zero_span(F.accf, r0, r1);
     }
     __syncthreads();
 
-    // 2. offsets within the tile, then the prefix of all earlier tiles
+    // 2. offsets within the tile (kScanPerLane consecutive boxes per lane),
+    // then the prefix of all earlier tiles
     if (warp == 0) {
-        const uint64_t xb = lane < kTileBoxes ? s_nblk[lane] : 0u;
-        const uint64_t xq = lane < kTileBoxes ? s_ncube[lane] : 0u;
-        const uint64_t xc = (xq + chunk - 1) / chunk;
+        uint64_t nbk[kScanPerLane], nck[kScanPerLane], nqk[kScanPerLane];
+        uint64_t xb = 0, xc = 0, xq = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPerLane; k++) {
+            const int w = lane * kScanPerLane + k;
+            nbk[k] = w < tb ? s_nblk[w] : 0u;
+            nqk[k] = w < tb ? s_ncube[w] : 0u;
+            nck[k] = chunk_shift >= 0 ? (nqk[k] + chunk - 1) >> chunk_shift : (nqk[k] + chunk - 1) / chunk;
+            xb += nbk[k];
+            xc += nck[k];
+            xq += nqk[k];
+        }
         uint64_t ib = xb, ic = xc, iq = xq;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -409,15 +513,20 @@ __global__ void __launch_bounds__(kFusedThreads) plan_fused_kernel(Geom G, const
                 iq += yq;
             }
         }
-        if (lane < kTileBoxes) {
-            s_boff[lane] = (uint32_t)(ib - xb);
-            s_coff[lane] = ic - xc;
-            s_cube[lane] = (uint32_t)(iq - xq);
+        uint64_t ob = ib - xb, oc = ic - xc, oq = iq - xq;
+#pragma unroll
+        for (int k = 0; k < kScanPerLane; k++) {
+            s_boff[lane * kScanPerLane + k] = (uint32_t)ob;
+            s_coff[lane * kScanPerLane + k] = oc;
+            s_cube[lane * kScanPerLane + k] = (uint32_t)oq;
+            ob += nbk[k];
+            oc += nck[k];
+            oq += nqk[k];
         }
         const uint64_t agg_b = __shfl_sync(0xffffffffu, ib, 31), agg_c = __shfl_sync(0xffffffffu, ic, 31);
         if (lane == 0) {
-            s_boff[kTileBoxes] = (uint32_t)agg_b;
-            s_coff[kTileBoxes] = agg_c;
+            s_boff[kTileMax] = (uint32_t)agg_b;
+            s_coff[kTileMax] = agg_c;
         }
         uint64_t* word = F.tiles + 2 * tile;
         if (lane == 0) {
@@ -425,42 +534,55 @@ __global__ void __launch_bounds__(kFusedThreads) plan_fused_kernel(Geom G, const
             st_relaxed_u64(word, flag | agg_b);
             st_relaxed_u64(word + 1, flag | agg_c);
         }
-        // look back over 32 tiles at a time; a word pair counts once both
-        // words carry the same flag
+        // look back kLookWindows windows of 32 tiles per poll; a word pair
+        // counts once both words carry the same flag
         uint64_t eb = 0, ec = 0;
         int64_t top = tile - 1;
         unsigned polls = 0;
-        while (top >= 0) {
-            const int64_t t = top - lane;
-            uint64_t wb = kTilePre, wc = kTilePre;   // before the first tile: prefix 0
-            if (t >= 0) {
-                wb = ld_relaxed_u64(F.tiles + 2 * t);
-                wc = ld_relaxed_u64(F.tiles + 2 * t + 1);
+        bool done = top < 0;
+        while (!done) {
+            uint64_t wb[kLookWindows], wc[kLookWindows];
+#pragma unroll
+            for (int k = 0; k < kLookWindows; k++) {
+                const int64_t t = top - lane - 32 * k;
+                wb[k] = wc[k] = kTilePre;   // before the first tile: prefix 0
+                if (t >= 0) {
+                    wb[k] = ld_relaxed_u64(F.tiles + 2 * t);
+                    wc[k] = ld_relaxed_u64(F.tiles + 2 * t + 1);
+                }
             }
-            const bool ready = (wb >> 62) != 0 && (wb >> 62) == (wc >> 62);
-            const unsigned pre = __ballot_sync(0xffffffffu, ready && (wb >> 62) == 2u);
-            const unsigned late = __ballot_sync(0xffffffffu, !ready);
-            // the lanes up to the nearest tile holding its prefix are needed
-            const unsigned need = pre ? ((pre & (0u - pre)) << 1) - 1u : 0xffffffffu;
-            if (late & need) {
+            bool late_seen = false;
+#pragma unroll
+            for (int k = 0; k < kLookWindows; k++) {
+                if (done || late_seen) continue;
+                const bool ready = (wb[k] >> 62) != 0 && (wb[k] >> 62) == (wc[k] >> 62);
+                const unsigned pre = __ballot_sync(0xffffffffu, ready && (wb[k] >> 62) == 2u);
+                const unsigned late = __ballot_sync(0xffffffffu, !ready);
+                // the lanes up to the nearest tile holding its prefix are needed
+                const unsigned need = pre ? ((pre & (0u - pre)) << 1) - 1u : 0xffffffffu;
+                if (late & need) {
+                    late_seen = true;
+                    continue;
+                }
+                const bool use = (need >> lane) & 1u;
+                uint64_t vb = use ? wb[k] & kTileVal : 0u, vc = use ? wc[k] & kTileVal : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    vb += __shfl_xor_sync(0xffffffffu, vb, o);
+                    vc += __shfl_xor_sync(0xffffffffu, vc, o);
+                }
+                eb += vb;
+                ec += vc;
+                if (pre) done = true;
+                else top -= 32;
+            }
+            if (late_seen && !done) {
                 if (++polls > kLookbackLimit) {
                     if (lane == 0) set_status(status, kStatTimeout);
                     break;
                 }
                 __nanosleep(64);
-                continue;
             }
-            const bool use = (need >> lane) & 1u;
-            uint64_t vb = use ? wb & kTileVal : 0u, vc = use ? wc & kTileVal : 0u;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                vb += __shfl_xor_sync(0xffffffffu, vb, o);
-                vc += __shfl_xor_sync(0xffffffffu, vc, o);
-            }
-            eb += vb;
-            ec += vc;
-            if (pre) break;
-            top -= 32;
         }
         if (lane == 0) {
             if (tile > 0) {
@@ -473,10 +595,12 @@ __global__ void __launch_bounds__(kFusedThreads) plan_fused_kernel(Geom G, const
     }
     __syncthreads();
     const uint64_t pre_b = s_pre_b, pre_c = s_pre_c;
-    const uint64_t tot_b = pre_b + s_boff[kTileBoxes], tot_c = pre_c + s_coff[kTileBoxes];
-    if (q < Qe && lane == 0) {
-        F.blk_off[q] = pre_b + s_boff[warp];
-        F.chunk_off[q] = pre_c + s_coff[warp];
+    const uint64_t tot_b = pre_b + s_boff[kTileMax], tot_c = pre_c + s_coff[kTileMax];
+    for (int w = threadIdx.x; w < tb; w += kFusedThreads) {
+        const int64_t q = q0 + w;
+        if (q >= Qe) break;
+        F.blk_off[q] = pre_b + s_boff[w];
+        F.chunk_off[q] = pre_c + s_coff[w];
         if (q == Qe - 1) {
             F.blk_off[Qe] = tot_b;
             F.chunk_off[Qe] = tot_c;
@@ -487,8 +611,10 @@ __global__ void __launch_bounds__(kFusedThreads) plan_fused_kernel(Geom G, const
     if (tot_b > lim.cap_blocks || tot_c > lim.cap_chunks) return;
 
     // 3. block records and the chunk map; item `it` of thread t is the tile's
-    // block r0 + it * kFusedThreads + t
-    const uint32_t nbt = s_boff[kTileBoxes];
+    // block r0 + it * kFusedThreads + t.  A box's block t is row pr = t / nx,
+    // column i = t - pr nx; the quotients by nx, ny < 2^16 of numerators
+    // < 2^16 are exact as (n * ceil(2^32 / d)) >> 32.
+    const uint32_t nbt = s_boff[kTileMax];
     uint32_t carry = 0;   // cubes of the earlier rounds, mod 2^32
     for (uint32_t r0 = 0; r0 < nbt; r0 += kFusedThreads * kFusedItems) {
         uint32_t n[kFusedItems], incl[kFusedItems];
@@ -501,15 +627,16 @@ __global__ void __launch_bounds__(kFusedThreads) plan_fused_kernel(Geom G, const
             if (idx < nbt) {
                 int w = 0;   // the last box whose blocks start at or before idx
 #pragma unroll
-                for (int st = kTileBoxes / 2; st > 0; st >>= 1)
+                for (int st = kTileMax / 2; st > 0; st >>= 1)
                     if (s_boff[w + st] <= idx) w += st;
                 const Runs& R = wr[w];
                 const uint32_t t = idx - s_boff[w];
-                const uint32_t pr = t / (uint32_t)R.nx;
+                const uint32_t pr = (uint32_t)(((uint64_t)t * s_mx[w]) >> 32);
+                const uint32_t k = (uint32_t)(((uint64_t)pr * s_my[w]) >> 32);
                 wk[it] = w;
                 ik[it] = (int)(t - pr * (uint32_t)R.nx);
-                jk[it] = (int)(pr % (uint32_t)R.ny);
-                kk[it] = (int)(pr / (uint32_t)R.ny);
+                jk[it] = (int)(pr - k * (uint32_t)R.ny);
+                kk[it] = (int)k;
                 n[it] = block_cubes(R.lx[ik[it]], R.ly[jk[it]], R.lz[kk[it]]);
             }
             uint32_t v = n[it];
@@ -525,7 +652,7 @@ __global__ void __launch_bounds__(kFusedThreads) plan_fused_kernel(Geom G, const
         if (warp == 0) {
 #pragma unroll
             for (int it = 0; it < kFusedItems; it++) {
-                const uint32_t x = lane < kFusedThreads / 32 ? s_wsum[lane][it] : 0u;
+                const uint32_t x = lane < kFusedWarps ? s_wsum[lane][it] : 0u;
                 uint32_t v = x;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -533,7 +660,7 @@ __global__ void __launch_bounds__(kFusedThreads) plan_fused_kernel(Geom G, const
                     if (lane >= o) v += y;
                 }
                 __syncwarp();
-                if (lane < kFusedThreads / 32) s_wsum[lane][it] = v - x;
+                if (lane < kFusedWarps) s_wsum[lane][it] = v - x;
                 if (lane == 31) s_rtot[it] = v;
             }
         }
@@ -549,7 +676,9 @@ __global__ void __launch_bounds__(kFusedThreads) plan_fused_kernel(Geom G, const
                 const uint64_t bi = pre_b + idx;
                 F.blk[bi] = make_blk(G, start, R.sx[i], R.sy[j], R.sz[k], R.lx[i], R.ly[j], R.lz[k]);
                 const uint64_t cb = pre_c + s_coff[w];
-                for (uint64_t c = ((uint64_t)start + chunk - 1) / chunk; c * chunk < (uint64_t)start + n[it]; c++) {
+                const uint64_t first = (uint64_t)start + chunk - 1;
+                for (uint64_t c = chunk_shift >= 0 ? first >> chunk_shift : first / chunk;
+                     c * chunk < (uint64_t)start + n[it]; c++) {
                     F.chunk_q[cb + c] = (uint32_t)(q0 + w);
                     F.chunk_b[cb + c] = (uint32_t)bi;
                 }
@@ -1130,6 +1259,7 @@ __global__ void __launch_bounds__(256, 5) query_warp_kernel(MainArgs A) {
     }
     if (lane == 0) *Qu.count = 0;
     __syncwarp();
+    grid_dependency_wait();
     const unsigned long long total = main_total(A);
     for (;;) {
         unsigned long long c = 0;
@@ -1182,6 +1312,7 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
     }
     if (threadIdx.x == 0) s_ntouched = 0;
     if (lane == 0) *Qu.count = 0;
+    grid_dependency_wait();
     const unsigned long long total = main_total(A);
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1484,9 +1615,11 @@ mg_status prepare_kernel(K kernel, size_t smem) {
     return MG_OK;
 }
 
+// pdl: launch the batched kernel with programmatic stream serialisation (its
+// CTAs start while the plan kernel finishes and wait for it on the device)
 template <bool FP, typename AT>
 mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts& o, const int32_t* boxes,
-                      size_t smem, int threads, cudaStream_t s) {
+                      size_t smem, int threads, cudaStream_t s, bool pdl = false) {
     if (o.schedule == MG_SCHED_NAIVE) {
         auto k = query_naive_kernel<FP>;
         const size_t sm = (size_t)g->S * 4;
@@ -1517,8 +1650,22 @@ mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts&
     MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, sm));
     if (per_sm < 1) return fail(MG_ERR_UNSUPPORTED, "query kernel does not fit on an SM");
     const int grid = per_sm * sm_count(g->device);
-    k<<<grid, threads, sm, s>>>(A);
-    MG_CUDA(cudaGetLastError());
+    if (!pdl) {
+        k<<<grid, threads, sm, s>>>(A);
+        MG_CUDA(cudaGetLastError());
+        return MG_OK;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    MG_CUDA(cudaLaunchKernelEx(&cfg, k, A));
     return MG_OK;
 }
 
@@ -1866,7 +2013,11 @@ struct mg_query_plan {
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    bool timed = false, ran = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // graph start, plan done, main done
     ~mg_query_plan() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -1894,7 +2045,9 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     } else {
         acc = static_cast<uint32_t*>(p->result);
     }
-    const int64_t ntiles = (Q + kTileBoxes - 1) / kTileBoxes;
+    const int tb = tile_boxes(Q, sm_count(g->device));
+    const int64_t ntiles = (Q + tb - 1) / tb;
+    const int chunk_shift = (p->chunk & (p->chunk - 1)) == 0 ? __builtin_ctz(p->chunk) : -1;
     MG_TRY(ncube.alloc(&al, (size_t)Q * 8, s));
     MG_TRY(blk_off.alloc(&al, (size_t)(Q + 1) * 8, s));
     MG_TRY(chunk_off.alloc(&al, (size_t)(Q + 1) * 8, s));
@@ -1904,7 +2057,8 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     MG_TRY(tiles.alloc(&al, (size_t)ntiles * 16, s));
     MG_TRY(ticket.alloc(&al, 16, s));   // tile order, main-kernel chunks
 
-    plan_reset_kernel<<<grid_for(2 * ntiles, 256, 152 * 4), 256, 0, s>>>(p->Qd, tiles.as<uint64_t>(),
+    if (p->timed) MG_CUDA(cudaEventRecordWithFlags(p->ev[0], s, cudaEventRecordExternal));
+    plan_reset_kernel<<<grid_for(2 * ntiles, 256, 152 * 4), 256, 0, s>>>(p->Qd, tb, tiles.as<uint64_t>(),
                                                                          ticket.as<unsigned long long>());
     MG_CUDA(cudaGetLastError());
     FusedOut F;
@@ -1918,8 +2072,10 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     F.ticket = ticket.as<unsigned long long>();
     F.acc = acc;
     F.accf = accf;
-    plan_fused_kernel<<<(unsigned)ntiles, kFusedThreads, 0, s>>>(G, p->boxes, Q, p->chunk, lim, F, status);
+    plan_fused_kernel<<<(unsigned)ntiles, kFusedThreads, 0, s>>>(G, p->boxes, Q, tb, p->chunk, chunk_shift, lim, F,
+                                                                 status);
     MG_CUDA(cudaGetLastError());
+    if (p->timed) MG_CUDA(cudaEventRecordWithFlags(p->ev[1], s, cudaEventRecordExternal));
 
     MainArgs A;
     A.G = G;
@@ -1950,7 +2106,8 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
     const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + ((touched_bytes + 15) & ~(size_t)15) +
                         (size_t)(p->threads / 32) * kQueueBytes + 16;
-    MG_TRY((launch_main<FP, AT>(g, A, o, nullptr, smem, p->threads, s)));
+    MG_TRY((launch_main<FP, AT>(g, A, o, nullptr, smem, p->threads, s, !p->timed)));
+    if (p->timed) MG_CUDA(cudaEventRecordWithFlags(p->ev[2], s, cudaEventRecordExternal));
     if (FP) {
         dense_f32_rows_kernel<<<grid_for(Q * S, 256, 152 * 64), 256, 0, s>>>(acc, accf, p->Qd, S);
         MG_CUDA(cudaGetLastError());
@@ -2013,7 +2170,7 @@ MG_API mg_status mg_query_plan_create(mg_graph* g, int64_t max_Q, const mg_query
         auto r = [](size_t n) { return (n + 255) & ~(size_t)255; };
         // boxes, batch size, results (+ u32 scratch), cube counts, both offset
         // arrays, blocks, chunk map, tile words, tickets
-        const size_t tiles = (Q + kTileBoxes - 1) / kTileBoxes;
+        const size_t tiles = Q;   // at most one tile word pair per box
         const size_t bytes = r(Q * 24) + r(8) + r(Q * S * 4) * (p->fp ? 2 : 1) + r(8 * Q) + 2 * r(8 * (Q + 1)) +
                              r(p->cap_blocks * sizeof(Blk)) + 2 * r(p->cap_chunks * 4) + r(16 * tiles) + r(16) +
                              65536;
@@ -2034,6 +2191,13 @@ MG_API mg_status mg_query_plan_create(mg_graph* g, int64_t max_Q, const mg_query
     if (st == MG_OK) {
         cudaError_t e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    if (st == MG_OK && o.timing) {
+        p->timed = true;
+        for (cudaEvent_t& ev : p->ev) {
+            const cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess && st == MG_OK) st = cuda_fail(e, "cudaEventCreate");
+        }
     }
     if (st == MG_OK) {
         // scratch comes from the plan's pool, so nothing is allocated while capturing
@@ -2085,11 +2249,28 @@ MG_API mg_status mg_query_plan_run(mg_query_plan* p, const int32_t* boxes, int64
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(p->exec, s);
+    if (e == cudaSuccess) p->ran = true;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, p->result, (size_t)Q * p->g->S * 4, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) st = cuda_fail(e, "mg_query_plan_run");
     if (prev >= 0 && prev != p->g->device) cudaSetDevice(prev);
     return st;
+}
+
+MG_API mg_status mg_query_plan_timing(const mg_query_plan* p, float* plan_ms, float* main_ms) {
+    using namespace mg;
+    if (!p || !plan_ms || !main_ms) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    if (!p->timed) return fail(MG_ERR_INVALID_ARG, "plan created without opts->timing");
+    if (!p->ran) return fail(MG_ERR_INVALID_ARG, "plan has not run");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != p->g->device) MG_CUDA(cudaSetDevice(p->g->device));
+    cudaError_t e = cudaEventSynchronize(p->ev[2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(plan_ms, p->ev[0], p->ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(main_ms, p->ev[1], p->ev[2]);
+    if (prev >= 0 && prev != p->g->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "mg_query_plan_timing");
+    return MG_OK;
 }
 
 MG_API void mg_query_plan_free(mg_query_plan* p) {

@@ -22,8 +22,13 @@ __device__ __forceinline__ int64_t floor_coord(float x, int32_t d0) {
     return (int64_t)xc;                         // truncation is the floor for xc >= 0
 }
 
+// 128-thread CTAs of at most 32 registers a thread: one fits beside a
+// persistent query kernel that leaves 4,096 registers of an SM free, so a
+// lookup issued on another stream runs concurrently with it
+constexpr int kLookupThreads = 128;
+
 template <typename RowT>
-__global__ void lookup_kernel(Geom G, const void* __restrict__ mip0, const uint32_t* __restrict__ mip,
+__global__ void __launch_bounds__(kLookupThreads, 16) lookup_kernel(Geom G, const void* __restrict__ mip0, const uint32_t* __restrict__ mip,
                               const float4* __restrict__ samples, int64_t P, const RowT* __restrict__ vals,
                               int words, RowT* __restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -68,20 +73,20 @@ mg_status render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dt,
         G.off[l] = g->geom.off[l];
     }
     const size_t row = (size_t)C * (dt == MG_F32 ? 4 : 2);
-    const unsigned grid = grid_for(P, 256);
+    const unsigned grid = grid_for(P, kLookupThreads);
     const float4* sm = reinterpret_cast<const float4*>(samples);
     const uint32_t* mip = g->mip.as<uint32_t>();
     if (row % 16 == 0 && aligned(vals, 16) && aligned(out, 16))
-        lookup_kernel<uint4><<<grid, 256, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint4*)vals, (int)(row / 16),
+        lookup_kernel<uint4><<<grid, kLookupThreads, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint4*)vals, (int)(row / 16),
                                                   (uint4*)out);
     else if (row % 8 == 0 && aligned(vals, 8) && aligned(out, 8))
-        lookup_kernel<uint2><<<grid, 256, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint2*)vals, (int)(row / 8),
+        lookup_kernel<uint2><<<grid, kLookupThreads, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint2*)vals, (int)(row / 8),
                                                   (uint2*)out);
     else if (row % 4 == 0 && aligned(vals, 4) && aligned(out, 4))
-        lookup_kernel<uint32_t><<<grid, 256, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint32_t*)vals,
+        lookup_kernel<uint32_t><<<grid, kLookupThreads, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint32_t*)vals,
                                                      (int)(row / 4), (uint32_t*)out);
     else
-        lookup_kernel<uint16_t><<<grid, 256, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint16_t*)vals,
+        lookup_kernel<uint16_t><<<grid, kLookupThreads, 0, s>>>(G, g->mip0.p, mip, sm, P, (const uint16_t*)vals,
                                                      (int)(row / 2), (uint16_t*)out);
     MG_CUDA(cudaGetLastError());
     return MG_OK;

@@ -35,7 +35,8 @@ _TORCH_TO_MG = {torch.float32: MG_F32, torch.float16: MG_F16, torch.bfloat16: MG
 # names of every symbol include/mg.h declares (checked by the CPU tests)
 EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_copy_mip", "mg_propagate_tf",
            "mg_query_boxes", "mg_query_boxes_noalloc", "mg_query_timing",
-           "mg_query_plan_create", "mg_query_plan_run", "mg_query_plan_free", "mg_query_autotune",
+           "mg_query_plan_create", "mg_query_plan_run", "mg_query_plan_timing", "mg_query_plan_free",
+           "mg_query_autotune",
            "mg_query_set_tuning", "mg_count_cubes", "mg_render_lookup",
            "mg_server_create", "mg_server_add_volume", "mg_server_start", "mg_server_submit", "mg_server_cancel",
            "mg_server_wait", "mg_server_replay", "mg_server_stats_get", "mg_server_free",
@@ -126,6 +127,8 @@ def lib():
         L.mg_query_plan_create.restype = st
         L.mg_query_plan_run.argtypes = [P, P, i64, P, ctypes.c_size_t, P]
         L.mg_query_plan_run.restype = st
+        L.mg_query_plan_timing.argtypes = [P, P, P]
+        L.mg_query_plan_timing.restype = st
         L.mg_query_plan_free.argtypes = [P]
         L.mg_query_plan_free.restype = None
         L.mg_query_autotune.argtypes = [P, P, i64, ctypes.POINTER(mg_query_opts), ctypes.POINTER(ctypes.c_float), P]
@@ -386,12 +389,13 @@ class QueryPlan:
     """A captured batched query (mg_query_plan_*): one graph launch per batch."""
 
     def __init__(self, g: Graph, max_Q: int, hist: str = "u32", alpha: str = "f32", chunk_cubes: int = 0,
-                 block_threads: int = 0, max_blocks: int = 0, max_chunks: int = 0):
+                 block_threads: int = 0, max_blocks: int = 0, max_chunks: int = 0, timing: bool = False):
         o = mg_query_opts()
         o.hist_type = MG_HIST_F32 if hist == "f32" else MG_HIST_U32
         o.alpha_dtype = _DTYPES[alpha][0]
         o.chunk_cubes = chunk_cubes
         o.block_threads = block_threads
+        o.timing = 1 if timing else 0
         h = ctypes.c_void_p()
         with torch.cuda.device(g.device):
             _check(lib().mg_query_plan_create(g.handle, max_Q, ctypes.byref(o), max_blocks, max_chunks,
@@ -410,6 +414,12 @@ class QueryPlan:
         _check(lib().mg_query_plan_run(self.handle, boxes.data_ptr(), Q, out.data_ptr(), out.numel(),
                                        _stream(stream)))
         return out
+
+    def timing(self):
+        """(plan_ms, main_ms) of the last run (plans created with timing=True)."""
+        t = [ctypes.c_float(), ctypes.c_float()]
+        _check(lib().mg_query_plan_timing(self.handle, *[ctypes.byref(x) for x in t]))
+        return tuple(x.value for x in t)
 
     def close(self):
         if self.handle:

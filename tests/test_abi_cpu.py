@@ -61,6 +61,8 @@ def test_host_argument_checks(lib):
     assert lib.mg_render_lookup(None, None, 4, 0, None, 0, None, None) == mg.MG_ERR_INVALID_ARG
     assert lib.mg_count_cubes(None, None, 0, None, None) == mg.MG_ERR_INVALID_ARG
     assert lib.mg_sync_status(None, None) == mg.MG_ERR_INVALID_ARG
+    f = ctypes.c_float()
+    assert lib.mg_query_plan_timing(None, ctypes.byref(f), ctypes.byref(f)) == mg.MG_ERR_INVALID_ARG
     lib.mg_free(None)
     assert mg.mg_version().startswith("mixgraph-gb300")
 

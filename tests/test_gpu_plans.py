@@ -36,6 +36,48 @@ def test_plan_u32_matches_oracle_for_varying_batches(mg, cfg1):
     plan.close()
 
 
+def test_plan_many_tiles_partial_tiles_and_timing(mg, cfg1):
+    # hundreds of 16-box tiles chained by the plan's single-pass scan, a
+    # partial last tile, and a malformed box in the middle of the batch
+    vol, g = cfg1
+    plan = mg.QueryPlan(g, max_Q=6000, timing=True)
+    for k, Q in enumerate([6000, 4999, 17]):
+        boxes = synth.make_boxes(1, Q=Q, stream_offset=10 + k)
+        h = plan.run(torch.from_numpy(boxes).cuda()).cpu().numpy()
+        mg.mg_sync_status(g)
+        assert np.array_equal(h, oracle.box_hist(vol, 64, boxes)), Q
+        plan_ms, main_ms = plan.timing()
+        assert plan_ms > 0 and main_ms > 0
+    boxes = synth.make_boxes(1, Q=3000, stream_offset=20)
+    bad = boxes.copy()
+    bad[1234, 3] = 0   # empty extent
+    h = plan.run(torch.from_numpy(bad).cuda()).cpu().numpy()
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_sync_status(g)
+    assert e.value.status == mg.MG_ERR_INVALID_ARG   # the device saw a malformed box
+    ref = oracle.box_hist(vol, 64, boxes)
+    keep = np.arange(3000) != 1234
+    assert np.array_equal(h[keep], ref[keep]) and (h[1234] == 0).all()
+    plan.close()
+    untimed = mg.QueryPlan(g, max_Q=10)
+    untimed.run(torch.from_numpy(synth.make_boxes(1, Q=10)).cuda())
+    with pytest.raises(mg.MGError) as e:
+        untimed.timing()
+    assert e.value.status == mg.MG_ERR_INVALID_ARG
+    untimed.close()
+
+
+def test_plan_long_lookback_chain(mg, cfg1):
+    # 6,250 tiles chained by the look-back of the single-pass scan
+    vol, g = cfg1
+    boxes = synth.make_boxes(1, Q=100000, stream_offset=30)
+    plan = mg.QueryPlan(g, max_Q=100000)
+    h = plan.run(torch.from_numpy(boxes).cuda()).cpu().numpy()
+    mg.mg_sync_status(g)
+    assert np.array_equal(h, oracle.box_hist(vol, 64, boxes))
+    plan.close()
+
+
 def test_plan_fp32_and_bf16(mg, cfg1):
     vol, g = cfg1
     boxes = synth.make_boxes(1, Q=300)
