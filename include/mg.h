@@ -232,7 +232,8 @@ MG_API mg_status mg_query_timing(const mg_graph *g, float *plan_ms, float *main_
 /*
  * Query plans: the batched pipeline of mg_query_boxes for up to max_Q boxes,
  * captured once as a CUDA graph with every buffer preallocated, so that a run
- * is three copies and one graph launch, with no host synchronisation.
+ * is one small kernel (the batch size and the caller's buffers) and one graph
+ * launch, with no copies and no host synchronisation.
  * opts: dense layout and batched schedule only; hist_type, alpha_dtype and the
  *   launch shape (0 = the graph's tuned shape, else the defaults) as for
  *   mg_query_boxes.
@@ -249,7 +250,9 @@ MG_API mg_status mg_query_timing(const mg_graph *g, float *plan_ms, float *main_
 typedef struct mg_query_plan mg_query_plan;
 MG_API mg_status mg_query_plan_create(mg_graph *g, int64_t max_Q, const mg_query_opts *opts, int64_t max_blocks,
                                       int64_t max_chunks, mg_query_plan **out);
-/* boxes: Q x 6 int32 (device), 0 <= Q <= max_Q; out: Q x S (uint32 or fp32). */
+/* boxes: Q x 6 int32 (device), 0 <= Q <= max_Q; out: Q x S (uint32 or fp32),
+ * both 4-byte aligned.  The graph reads `boxes` and writes `out` in the order
+ * of `stream`: they must stay valid until the run has completed on it. */
 MG_API mg_status mg_query_plan_run(mg_query_plan *p, const int32_t *boxes, int64_t Q, void *out, size_t out_capacity,
                                    mg_stream stream);
 /* Durations in milliseconds of the last run's plan stage and main kernel, for a

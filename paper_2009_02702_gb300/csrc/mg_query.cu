@@ -367,8 +367,9 @@ struct FusedOut {
     uint32_t* chunk_b;
     uint64_t* tiles;               // two words per tile: blocks, chunks
     unsigned long long* ticket;    // tile order
-    uint32_t* acc;                 // rows zeroed for the live batch (16-byte aligned)
+    uint32_t* acc;                 // rows zeroed for the live batch
     float* accf;                   // likewise (fp32 histograms), or nullptr
+    void* const* io;               // io[0]: the boxes; io[1]: the output (acc for u32, accf for fp32)
 };
 
 // Algorithm 1's steps on one axis (as footprint_1d) together with the axis's
@@ -394,10 +395,13 @@ __device__ __forceinline__ int axis_runs(int64_t i, int64_t di, int64_t dim, uin
     return n;
 }
 
-// zero a[r0, r1) with 16-byte stores between the unaligned ends
+// zero a[r0, r1) of 4-byte elements (a 4-byte aligned) with 16-byte stores
+// between the unaligned ends
 template <typename T>
 __device__ __forceinline__ void zero_span(T* a, size_t r0, size_t r1) {
-    const size_t a0 = min((r0 + 3) & ~(size_t)3, r1), a1 = max(r1 & ~(size_t)3, a0);
+    static_assert(sizeof(T) == 4, "4-byte elements");
+    const size_t lead = ((16u - (reinterpret_cast<uintptr_t>(a + r0) & 15u)) & 15u) / 4u;
+    const size_t a0 = min(r0 + lead, r1), a1 = a0 + ((r1 - a0) & ~(size_t)3);
     for (size_t i = r0 + threadIdx.x; i < a0; i += kFusedThreads) a[i] = T(0);
     for (size_t i = a1 + threadIdx.x; i < r1; i += kFusedThreads) a[i] = T(0);
     uint4* v = reinterpret_cast<uint4*>(a + a0);
@@ -429,6 +433,13 @@ __global__ void __launch_bounds__(kFusedThreads, 2) plan_fused_kernel(Geom G, co
     const int64_t Qe = live_q(lim, Q);
     const int64_t q0 = tile * tb;
     if (q0 >= Qe) return;   // no tile of the live batch waits on this one
+    uint32_t* acc = F.acc;
+    float* accf = F.accf;
+    if (F.io) {
+        boxes = static_cast<const int32_t*>(F.io[0]);
+        if (accf) accf = static_cast<float*>(F.io[1]);
+        else acc = static_cast<uint32_t*>(F.io[1]);
+    }
 
     // 1. blocks and cubes of every box: kBoxLanes lanes per box, lanes 0-2 of
     // a group building one axis's runs each
@@ -481,8 +492,8 @@ __global__ void __launch_bounds__(kFusedThreads, 2) plan_fused_kernel(Geom G, co
     }
     {   // the tile's live output rows are one contiguous span
         const size_t r0 = (size_t)q0 * G.S, r1 = (size_t)min(q0 + tb, Qe) * G.S;
-        zero_span(F.acc, r0, r1);
-        if (F.accf) zero_span(F.accf, r0, r1);
+        zero_span(acc, r0, r1);
+        if (accf) zero_span(accf, r0, r1);
     }
     __syncthreads();
 
@@ -945,7 +956,20 @@ struct MainArgs {
     unsigned long long* ticket;
     uint32_t* acc;
     float* accf;
+    void* const* io;             // plans: io[1] is the output (acc for u32, accf for fp32)
 };
+
+// the output a main kernel accumulates into: fixed, or (plans) the caller's
+// buffer named in the plan's io slots
+template <bool FP>
+__device__ __forceinline__ void main_out(const MainArgs& A, uint32_t*& acc, float*& accf) {
+    acc = A.acc;
+    accf = A.accf;
+    if (A.io) {
+        if constexpr (FP) accf = static_cast<float*>(A.io[1]);
+        else acc = static_cast<uint32_t*>(A.io[1]);
+    }
+}
 
 constexpr int kQueue = 320;   // pending internal-node pushes per warp (drained at >= 32)
 constexpr size_t kQueueBytes = (size_t)kQueue * 8 + 16;   // nodes, weights, counter
@@ -1260,6 +1284,9 @@ __global__ void __launch_bounds__(256, 5) query_warp_kernel(MainArgs A) {
     if (lane == 0) *Qu.count = 0;
     __syncwarp();
     grid_dependency_wait();
+    uint32_t* acc;
+    float* accf;
+    main_out<FP>(A, acc, accf);
     const unsigned long long total = main_total(A);
     for (;;) {
         unsigned long long c = 0;
@@ -1276,13 +1303,13 @@ __global__ void __launch_bounds__(256, 5) query_warp_kernel(MainArgs A) {
             const uint32_t v = H.h[s];
             if (v) {
                 H.h[s] = 0;
-                atomicAdd(A.acc + (size_t)q * S + s, v);
+                atomicAdd(acc + (size_t)q * S + s, v);
             }
             if constexpr (FP) {
                 const float f = H.hf[s];
                 if (f != 0.f) {
                     H.hf[s] = 0.f;
-                    atomicAdd(A.accf + (size_t)q * S + s, f);
+                    atomicAdd(accf + (size_t)q * S + s, f);
                 }
             }
         }
@@ -1313,6 +1340,9 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
     if (threadIdx.x == 0) s_ntouched = 0;
     if (lane == 0) *Qu.count = 0;
     grid_dependency_wait();
+    uint32_t* acc;
+    float* accf;
+    main_out<FP>(A, acc, accf);
     const unsigned long long total = main_total(A);
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1354,7 +1384,7 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
         }
         drain<FP, AT>(A.P, H, Qu, true);
         __syncthreads();
-        flush<FP>(H, S, q, A.acc, A.accf);
+        flush<FP>(H, S, q, acc, accf);
         __syncthreads();
         if (threadIdx.x == 0) s_ntouched = 0;
     }
@@ -1458,8 +1488,9 @@ __global__ void __launch_bounds__(256) query_naive_kernel(Geom G, const void* __
 // ---------------------------------------------------------------------------
 // finalisation
 // ---------------------------------------------------------------------------
-__global__ void dense_f32_rows_kernel(const uint32_t* __restrict__ acc, float* __restrict__ out,
+__global__ void dense_f32_rows_kernel(const uint32_t* __restrict__ acc, void* const* __restrict__ io,
                                       const int64_t* __restrict__ Qd, int64_t S) {
+    float* out = static_cast<float*>(io[1]);
     const int64_t n = *Qd * S;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (float)acc[i] + out[i];
@@ -1585,7 +1616,13 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(const uint32_t*
 }
 
 // the live batch size of a plan run, passed by value (no host staging)
-__global__ void set_batch_kernel(int64_t* __restrict__ Qd, int64_t Q) { *Qd = Q; }
+// and the caller's boxes and output named in the plan's io slots
+__global__ void set_batch_kernel(int64_t* __restrict__ Qd, int64_t Q, void** __restrict__ io, const void* boxes,
+                                 void* out) {
+    *Qd = Q;
+    io[0] = const_cast<void*>(boxes);
+    io[1] = out;
+}
 
 // zero the first *Qd rows of S counters (plans); n = rows * S bound
 template <typename T>
@@ -1755,6 +1792,7 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
     A.total_chunks = 0;
     A.lim = Lim{nullptr, 0, 0};
     A.ticket = nullptr;
+    A.io = nullptr;
 
     const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
     const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + ((touched_bytes + 15) & ~(size_t)15) +
@@ -2010,6 +2048,7 @@ struct mg_query_plan {
     int32_t* boxes = nullptr;
     int64_t* Qd = nullptr;
     void* result = nullptr;   // max_Q x S, uint32 or fp32
+    void** io = nullptr;      // device slots: the run's boxes and output (default: boxes, result)
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -2072,6 +2111,7 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     F.ticket = ticket.as<unsigned long long>();
     F.acc = acc;
     F.accf = accf;
+    F.io = p->io;
     plan_fused_kernel<<<(unsigned)ntiles, kFusedThreads, 0, s>>>(G, p->boxes, Q, tb, p->chunk, chunk_shift, lim, F,
                                                                  status);
     MG_CUDA(cudaGetLastError());
@@ -2101,6 +2141,7 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     A.ticket = ticket.as<unsigned long long>() + 1;
     A.acc = acc;
     A.accf = accf;
+    A.io = p->io;
     mg_query_opts o{};
     o.hist_type = FP ? MG_HIST_F32 : MG_HIST_U32;
     const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
@@ -2109,7 +2150,7 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     MG_TRY((launch_main<FP, AT>(g, A, o, nullptr, smem, p->threads, s, !p->timed)));
     if (p->timed) MG_CUDA(cudaEventRecordWithFlags(p->ev[2], s, cudaEventRecordExternal));
     if (FP) {
-        dense_f32_rows_kernel<<<grid_for(Q * S, 256, 152 * 64), 256, 0, s>>>(acc, accf, p->Qd, S);
+        dense_f32_rows_kernel<<<grid_for(Q * S, 256, 152 * 64), 256, 0, s>>>(acc, p->io, p->Qd, S);
         MG_CUDA(cudaGetLastError());
     }
     return MG_OK;
@@ -2171,7 +2212,7 @@ MG_API mg_status mg_query_plan_create(mg_graph* g, int64_t max_Q, const mg_query
         // boxes, batch size, results (+ u32 scratch), cube counts, both offset
         // arrays, blocks, chunk map, tile words, tickets
         const size_t tiles = Q;   // at most one tile word pair per box
-        const size_t bytes = r(Q * 24) + r(8) + r(Q * S * 4) * (p->fp ? 2 : 1) + r(8 * Q) + 2 * r(8 * (Q + 1)) +
+        const size_t bytes = r(Q * 24) + r(8) + r(16) + r(Q * S * 4) * (p->fp ? 2 : 1) + r(8 * Q) + 2 * r(8 * (Q + 1)) +
                              r(p->cap_blocks * sizeof(Blk)) + 2 * r(p->cap_chunks * 4) + r(16 * tiles) + r(16) +
                              65536;
         st = p->pool.alloc(&g->al, bytes, nullptr);
@@ -2185,6 +2226,10 @@ MG_API mg_status mg_query_plan_create(mg_graph* g, int64_t max_Q, const mg_query
             p->boxes = static_cast<int32_t*>(pool_alloc(&p->bump, Q * 24, nullptr));
             p->Qd = static_cast<int64_t*>(pool_alloc(&p->bump, 8, nullptr));
             p->result = pool_alloc(&p->bump, Q * S * 4, nullptr);
+            p->io = static_cast<void**>(pool_alloc(&p->bump, 16, nullptr));
+            void* io0[2] = {p->boxes, p->result};
+            const cudaError_t e = cudaMemcpy(p->io, io0, sizeof(io0), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = cuda_fail(e, "plan io slots");
         }
     }
     if (st == MG_OK && p->fp && o.alpha_dtype != MG_F32) st = ensure_alpha16(g, (mg_dtype)o.alpha_dtype, nullptr);
@@ -2238,20 +2283,18 @@ MG_API mg_status mg_query_plan_run(mg_query_plan* p, const int32_t* boxes, int64
     if (Q == 0) return MG_OK;
     if (!boxes || !out) return fail(MG_ERR_INVALID_ARG, "NULL argument");
     if ((uint64_t)out_capacity < (uint64_t)Q * p->g->S) return fail(MG_ERR_INVALID_ARG, "out_capacity must be >= Q*S");
+    if (reinterpret_cast<uintptr_t>(boxes) % 4 || reinterpret_cast<uintptr_t>(out) % 4)
+        return fail(MG_ERR_INVALID_ARG, "boxes and out must be 4-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != p->g->device) MG_CUDA(cudaSetDevice(p->g->device));
     mg_status st = MG_OK;
-    cudaError_t e = cudaMemcpyAsync(p->boxes, boxes, (size_t)Q * 24, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) {
-        set_batch_kernel<<<1, 1, 0, s>>>(p->Qd, Q);
-        e = cudaGetLastError();
-    }
+    // the graph reads the boxes from and accumulates into the caller's buffers
+    set_batch_kernel<<<1, 1, 0, s>>>(p->Qd, Q, p->io, boxes, out);
+    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaGraphLaunch(p->exec, s);
     if (e == cudaSuccess) p->ran = true;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(out, p->result, (size_t)Q * p->g->S * 4, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) st = cuda_fail(e, "mg_query_plan_run");
     if (prev >= 0 && prev != p->g->device) cudaSetDevice(prev);
     return st;

@@ -67,6 +67,29 @@ def test_plan_many_tiles_partial_tiles_and_timing(mg, cfg1):
     untimed.close()
 
 
+@pytest.mark.parametrize("hist", ["u32", "f32"])
+def test_plan_runs_on_unaligned_caller_buffers(mg, cfg1, hist):
+    # the plan reads the boxes from and accumulates into the caller's buffers;
+    # views one element past a 16-byte boundary exercise the zeroing's ends
+    vol, g = cfg1
+    Q = 700
+    boxes = synth.make_boxes(1, Q=Q, stream_offset=40)
+    dt = torch.uint32 if hist == "u32" else torch.float32
+    plan = mg.QueryPlan(g, max_Q=Q, hist=hist)
+    bflat = torch.empty(Q * 6 + 1, dtype=torch.int32, device="cuda")
+    bview = bflat[1:].view(Q, 6)
+    bview.copy_(torch.from_numpy(boxes))
+    oflat = torch.full((Q * 64 + 3,), 7, dtype=dt, device="cuda")
+    oview = oflat[1:1 + Q * 64].view(Q, 64)
+    plan.run(bview, out=oview)
+    mg.mg_sync_status(g)
+    ref = oracle.box_hist(vol, 64, boxes)
+    assert np.array_equal(oview.cpu().numpy().astype(np.int64), ref.astype(np.int64))
+    # nothing outside the output rows is touched
+    assert oflat[0].item() == 7 and (oflat[1 + Q * 64:] == 7).all().item()
+    plan.close()
+
+
 def test_plan_long_lookback_chain(mg, cfg1):
     # 6,250 tiles chained by the look-back of the single-pass scan
     vol, g = cfg1
