@@ -189,6 +189,28 @@ def test_count_cubes(mg):
     assert np.array_equal(c, ref)
 
 
+def test_count_cubes_odd_dims_large_boxes(mg):
+    # odd extents at every level and boxes up to the whole volume: many runs
+    # per axis, both rising and falling, and clipping at the far faces
+    rng = np.random.default_rng(77)
+    dims = (300, 257, 129)
+    vol = rng.integers(0, 8, size=dims[::-1], dtype=np.uint16)
+    g = mg.mg_build(torch.from_numpy(vol).to(dev()), 8)
+    o = np.stack([rng.integers(0, d, 3000) for d in dims], 1)
+    e = np.exp2(rng.uniform(0, 9.5, (3000, 3))).astype(np.int64)
+    boxes = np.concatenate([o, e], 1).astype(np.int32)
+    boxes[:5] = [[0, 0, 0, 300, 257, 129], [1, 1, 1, 299, 256, 128], [299, 256, 128, 1, 1, 1],
+                 [3, 5, 7, 1000, 1000, 1000], [255, 127, 63, 2, 2, 2]]
+    c = mg.mg_count_cubes(g, torch.from_numpy(boxes).to(dev())).cpu().numpy()
+    ref = np.array([oracle.fa_count(b, *dims) for b in boxes], np.uint64)
+    assert np.array_equal(c, ref)
+    plan = mg.QueryPlan(g, max_Q=3000)
+    h = plan.run(torch.from_numpy(boxes).to(dev())).cpu().numpy()
+    mg.mg_sync_status(g)
+    assert np.array_equal(h, oracle.box_hist(vol, 8, boxes))
+    plan.close()
+
+
 def test_query_edge_cases(mg):
     vol = synth.make_volume(1, dims=(19, 13, 11), S=12)
     g = mg.mg_build(torch.from_numpy(vol).to(dev()), 12)
