@@ -457,10 +457,13 @@ def run_ours(args):
     launches_prop = 1 if info["depth"] + 1 <= 64 else 1 + sum(
         1 for d in range(1, info["depth"] + 1) if info["bucket"][d + 1] > info["bucket"][d])
     nscan = 1 if Q <= 2048 else 3   # kernels of one device-wide scan of Q values
-    if args.schedule == "batched":
-        # batch size, zero rows, count, offsets (one CTA up to 2^18 boxes, else two
-        # device-wide scans, widen and check), write, main
-        launches_query = 1 + 1 + 1 + (1 if Q <= (1 << 18) else 2 * nscan + 2) + 1 + 1
+    if args.schedule == "batched" and use_plan:
+        # batch size and io slots, tile reset, fused plan kernel, main kernel
+        launches_query = 4
+    elif args.schedule == "batched":
+        # count, offsets (one CTA up to 2^18 boxes, else two device-wide scans
+        # and a widen), write, main
+        launches_query = 1 + (1 if Q <= (1 << 18) else 2 * nscan + 1) + 1 + 1
     else:
         launches_query = Q
     line = {
