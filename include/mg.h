@@ -67,8 +67,9 @@ typedef enum { MG_F32 = 0, MG_F16 = 1, MG_BF16 = 2 } mg_dtype;
 typedef struct mg_graph mg_graph;   /* opaque, library-owned */
 
 /* Device memory for the graph and for per-call scratch.  alloc returns a
- * device pointer usable in stream order on `stream` (NULL = out of memory);
- * free releases it in stream order.  Pass NULL to mg_build to use
+ * device pointer usable in stream order on `stream` (NULL = out of memory),
+ * 256-byte aligned as cudaMalloc's (else the call fails with
+ * MG_ERR_INVALID_ARG); free releases it in stream order.  Pass NULL to mg_build to use
  * cudaMallocAsync / cudaFreeAsync. */
 typedef struct {
     void *ctx;

@@ -78,6 +78,10 @@ mg_status Buf::alloc(const Alloc* a, size_t n, cudaStream_t st) {
         bytes = 0;
         return fail(MG_ERR_OOM, "device allocation of " + std::to_string(n) + " bytes failed");
     }
+    if (reinterpret_cast<uintptr_t>(p) % 256) {   // the kernels' vector loads rely on it
+        release();
+        return fail(MG_ERR_INVALID_ARG, "the allocator returned a pointer that is not 256-byte aligned");
+    }
     return MG_OK;
 }
 

@@ -50,9 +50,9 @@ struct Geom {
     // strides of the second and third axis of each copy (copy 0: x, y, z;
     // copy 1: y, z, x; copy 2: z, x, y)
     uint32_t st1[MG_MAX_LEVELS][3], st2[MG_MAX_LEVELS][3];
-    // bit l of vec_ok[c]: every row of copy c at level l starts on a 16-byte
-    // boundary (row pitch and level offset multiples of 16 bytes)
-    uint32_t vec_ok[3];
+    // bit l of vec_ok[c] / vec32_ok[c]: every row of copy c at level l starts
+    // on a 16-byte / 32-byte boundary (row pitch and level offset multiples)
+    uint32_t vec_ok[3], vec32_ok[3];
 };
 
 struct Ids {
@@ -80,12 +80,16 @@ Geom make_geom(const mg_graph* g) {
         G.st1[l][2] = dz; G.st2[l][2] = dz * dx;
     }
     for (int c = 0; c < 3; c++) {
-        G.vec_ok[c] = 0;
+        G.vec_ok[c] = G.vec32_ok[c] = 0;
         for (int l = 0; l < G.L && l < MG_MAX_LEVELS; l++) {
             const uint32_t per16 = l == 0 ? 16u / (uint32_t)G.id0_bytes : 4u;   // IDs per 16 bytes
             const bool ok = G.st1[l][c] % per16 == 0 && G.st2[l][c] % per16 == 0 &&
                             (l == 0 || G.off[l] % per16 == 0);
+            const uint32_t per32 = 2 * per16;
+            const bool ok32 = G.st1[l][c] % per32 == 0 && G.st2[l][c] % per32 == 0 &&
+                              (l == 0 || G.off[l] % per32 == 0);
             if (ok) G.vec_ok[c] |= 1u << l;
+            if (ok32) G.vec32_ok[c] |= 1u << l;
         }
     }
     return G;
@@ -1080,14 +1084,15 @@ __device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Q
 //
 // The span is a flat stream of units.  A window holds the records of 31
 // consecutive blocks, one per lane; the part of each block inside the span is
-// cut into units -- 16-byte vectors of IDs (8 uint16 or 4 uint32 of one row)
-// where the block's rows are 16-byte aligned (Algorithm 1's runs start on
-// multiples of their own length, so whole rows are) and single cubes for the
+// cut into units -- 32-byte vectors of IDs (16 uint16 or 8 uint32 of one row)
+// where the block's rows are 32-byte aligned and at least that long, else
+// 16-byte vectors where they are 16-byte aligned (Algorithm 1's runs start on
+// multiples of their own length, so whole rows are), and single cubes for the
 // unaligned head and tail and for every other block -- and a warp scan of
 // the unit counts lets lane k find the block of unit u from a ballot of
 // the block ends.
-// Each lane takes units u, u + 32, ... with two loads in flight, so no load
-// waits on a block boundary.  Every lane keeps a run (level, node, count) of
+// Each lane takes units u, u + 32, ... (a 32-byte unit is two 16-byte loads),
+// so no load waits on a block boundary.  Every lane keeps a run (level, node, count) of
 // its own consecutive cubes; a finished run of a source is added to the
 // shared histogram, one of an internal node (levels >= 1) is queued for the
 // warp's pushes.
@@ -1133,8 +1138,11 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
         const uint32_t lo_a = max(st, w0), hi_a = min(nxt, w1);
         const bool use = lane < 31 && lo_a < hi_a;
         const int l = meta & 31, cp = (meta >> 5) & 3, e0 = (meta >> 7) & 31;
-        const int lg = l == 0 ? lg0 : 2;
+        // 32-byte units where the block's rows allow them, else 16-byte ones
+        const int lg16 = l == 0 ? lg0 : 2;
         const uint32_t lo = use ? lo_a - st : 0u, hi = use ? hi_a - st : 0u;
+        const bool wide = use && e0 > lg16 && ((A.G.vec32_ok[cp] >> l) & 1u) && hi - lo >= (4u << lg16);
+        const int lg = lg16 + (wide ? 1 : 0);
         const bool vec = use && e0 >= lg && ((A.G.vec_ok[cp] >> l) & 1u) && hi - lo >= (2u << lg);
         const uint32_t vm = (1u << lg) - 1u;
         // scalar head [lo, ha), vectors [ha, hb), scalar tail [hb, hi)
@@ -1142,6 +1150,7 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
         const uint32_t hb = vec ? hi & ~vm : hi;
         const uint32_t nh = ha - lo, nv = (hb - ha) >> lg;
         const uint32_t units = use ? (hi - lo) - (hb - ha) + nv : 0u;
+        const uint32_t wmeta = meta | (wide ? 1u << 22 : 0u);
         uint32_t incl = units;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1150,101 +1159,93 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
         }
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t excl = incl - units;
-        for (uint32_t u0 = 0; u0 < total; u0 += 64) {
-            uint4 v[2];
-            int ul[2], kind[2];   // level; 0 scalar, 1 four uint32, 2 eight uint16
-#pragma unroll
-            for (int r = 0; r < 2; r++) {
-                const uint32_t ub = u0 + 32u * r, u = ub + lane;
-                // block of unit u: blocks ending at or before ub, plus those
-                // ending inside this half at or before u (block ends are
-                // distinct below the total, so one bit each)
-                const unsigned below = __ballot_sync(0xffffffffu, incl <= ub);
-                const uint32_t te = incl - ub;
-                const unsigned ends = __reduce_or_sync(0xffffffffu, incl > ub && te < 32u ? 1u << te : 0u);
-                const int j = __popc(below) + __popc(ends & ((2u << lane) - 1u) & ~1u);
-                const uint32_t jbase = __shfl_sync(0xffffffffu, base, j & 31);
-                const uint32_t jmeta = __shfl_sync(0xffffffffu, meta, j & 31);
-                const uint32_t jlo = __shfl_sync(0xffffffffu, lo, j & 31);
-                const uint32_t jnh = __shfl_sync(0xffffffffu, nh, j & 31);
-                const uint32_t jnv = __shfl_sync(0xffffffffu, nv, j & 31);
-                const uint32_t jex = __shfl_sync(0xffffffffu, excl, j & 31);
-                kind[r] = -1;
-                v[r] = make_uint4(0u, 0u, 0u, 0u);
-                ul[r] = 0;
-                if (u < total) {
-                    const int jl = jmeta & 31, jc = (jmeta >> 5) & 3;
-                    const int je0 = (jmeta >> 7) & 31, je1 = (jmeta >> 12) & 31;
-                    const int jlg = jl == 0 ? lg0 : 2;
-                    const uint32_t t = u - jex;
-                    uint32_t o;
-                    bool vv = false;
-                    if (t < jnh) {
-                        o = jlo + t;
-                    } else if (t < jnh + jnv) {
-                        o = jlo + jnh + ((t - jnh) << jlg);
-                        vv = true;
-                    } else {
-                        o = jlo + jnh + (jnv << jlg) + (t - jnh - jnv);
-                    }
-                    const uint32_t idx = jbase + (o & ((1u << je0) - 1u)) +
-                                         ((o >> je0) & ((1u << je1) - 1u)) * A.G.st1[jl][jc] +
-                                         (o >> (je0 + je1)) * A.G.st2[jl][jc];
-                    ul[r] = jl;
-                    if (jl == 0) {
-                        if (lg0 == 3) {
-                            const uint16_t* p = static_cast<const uint16_t*>(A.I.l0[jc]) + idx;
-                            if (vv) {
-                                v[r] = __ldg(reinterpret_cast<const uint4*>(p));
-                                kind[r] = 2;
-                            } else {
-                                v[r].x = __ldg(p);
-                                kind[r] = 0;
-                            }
-                        } else {
-                            const uint32_t* p = static_cast<const uint32_t*>(A.I.l0[jc]) + idx;
-                            if (vv) {
-                                v[r] = __ldg(reinterpret_cast<const uint4*>(p));
-                                kind[r] = 1;
-                            } else {
-                                v[r].x = __ldg(p);
-                                kind[r] = 0;
-                            }
-                        }
-                    } else {
-                        const uint32_t* p = A.I.hi[jc] + A.G.off[jl] + idx;
-                        if (vv) {
-                            v[r] = __ldg(reinterpret_cast<const uint4*>(p));
-                            kind[r] = 1;
-                        } else {
-                            v[r].x = __ldg(p);
-                            kind[r] = 0;
-                        }
-                    }
+        for (uint32_t u0 = 0; u0 < total; u0 += 32) {
+            const uint32_t u = u0 + lane;
+            // block of unit u: blocks ending at or before u0, plus those ending
+            // inside this group at or before u (block ends are distinct below
+            // the total, so one bit each)
+            const unsigned below = __ballot_sync(0xffffffffu, incl <= u0);
+            const uint32_t te = incl - u0;
+            const unsigned ends = __reduce_or_sync(0xffffffffu, incl > u0 && te < 32u ? 1u << te : 0u);
+            const int j = __popc(below) + __popc(ends & ((2u << lane) - 1u) & ~1u);
+            const uint32_t jbase = __shfl_sync(0xffffffffu, base, j & 31);
+            const uint32_t jmeta = __shfl_sync(0xffffffffu, wmeta, j & 31);
+            const uint32_t jlo = __shfl_sync(0xffffffffu, lo, j & 31);
+            const uint32_t jnh = __shfl_sync(0xffffffffu, nh, j & 31);
+            const uint32_t jnv = __shfl_sync(0xffffffffu, nv, j & 31);
+            const uint32_t jex = __shfl_sync(0xffffffffu, excl, j & 31);
+            // kind: 0 scalar; 1 / 3: four / eight uint32; 2 / 4: eight / sixteen uint16
+            int kind = -1, ul = 0;
+            uint4 va = make_uint4(0u, 0u, 0u, 0u), vb = va;
+            if (u < total) {
+                const int jl = jmeta & 31, jc = (jmeta >> 5) & 3;
+                const int je0 = (jmeta >> 7) & 31, je1 = (jmeta >> 12) & 31;
+                const bool jw = (jmeta >> 22) & 1u;
+                const int jlg = (jl == 0 ? lg0 : 2) + (jw ? 1 : 0);
+                const uint32_t t = u - jex;
+                uint32_t o;
+                bool vv = false;
+                if (t < jnh) {
+                    o = jlo + t;
+                } else if (t < jnh + jnv) {
+                    o = jlo + jnh + ((t - jnh) << jlg);
+                    vv = true;
+                } else {
+                    o = jlo + jnh + (jnv << jlg) + (t - jnh - jnv);
+                }
+                const uint32_t idx = jbase + (o & ((1u << je0) - 1u)) +
+                                     ((o >> je0) & ((1u << je1) - 1u)) * A.G.st1[jl][jc] +
+                                     (o >> (je0 + je1)) * A.G.st2[jl][jc];
+                ul = jl;
+                const bool u16 = jl == 0 && lg0 == 3;
+                const void* row = jl == 0 ? A.I.l0[jc] : static_cast<const void*>(A.I.hi[jc] + A.G.off[jl]);
+                if (vv) {
+                    const uint4* p = reinterpret_cast<const uint4*>(u16 ? static_cast<const void*>(
+                                                                              static_cast<const uint16_t*>(row) + idx)
+                                                                        : static_cast<const void*>(
+                                                                              static_cast<const uint32_t*>(row) + idx));
+                    va = __ldg(p);
+                    if (jw) vb = __ldg(p + 1);
+                    kind = (u16 ? 2 : 1) + (jw ? 2 : 0);
+                } else {
+                    va.x = u16 ? (uint32_t)__ldg(static_cast<const uint16_t*>(row) + idx)
+                               : __ldg(static_cast<const uint32_t*>(row) + idx);
+                    kind = 0;
                 }
             }
-#pragma unroll
-            for (int r = 0; r < 2; r++) {
-                const int l = ul[r];
-                if (kind[r] == 0) {
-                    feed(v[r].x, l);
-                } else if (kind[r] == 1) {
-                    if (rcnt && rl == l && v[r].x == rid && v[r].y == rid && v[r].z == rid && v[r].w == rid) {
-                        rcnt += 4;
-                    } else {
-                        feed(v[r].x, l);
-                        feed(v[r].y, l);
-                        feed(v[r].z, l);
-                        feed(v[r].w, l);
+            if (kind == 0) {
+                feed(va.x, ul);
+            } else if (kind == 1 || kind == 3) {
+                const bool same = rcnt && rl == ul && va.x == rid && va.y == rid && va.z == rid && va.w == rid &&
+                                  (kind == 1 || (vb.x == rid && vb.y == rid && vb.z == rid && vb.w == rid));
+                if (same) {
+                    rcnt += kind == 1 ? 4 : 8;
+                } else {
+                    feed(va.x, ul);
+                    feed(va.y, ul);
+                    feed(va.z, ul);
+                    feed(va.w, ul);
+                    if (kind == 3) {
+                        feed(vb.x, ul);
+                        feed(vb.y, ul);
+                        feed(vb.z, ul);
+                        feed(vb.w, ul);
                     }
-                } else if (kind[r] == 2) {
-                    const uint32_t pr = rid * 0x10001u;
-                    if (rcnt && rl == 0 && ((v[r].x ^ pr) | (v[r].y ^ pr) | (v[r].z ^ pr) | (v[r].w ^ pr)) == 0u) {
-                        rcnt += 8;
-                    } else {
-                        const uint32_t w4[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+                }
+            } else if (kind == 2 || kind == 4) {
+                const uint32_t pr = rid * 0x10001u;
+                uint32_t diff = (va.x ^ pr) | (va.y ^ pr) | (va.z ^ pr) | (va.w ^ pr);
+                if (kind == 4) diff |= (vb.x ^ pr) | (vb.y ^ pr) | (vb.z ^ pr) | (vb.w ^ pr);
+                if (rcnt && rl == 0 && diff == 0u) {
+                    rcnt += kind == 2 ? 8 : 16;
+                } else {
+                    const uint32_t w4[4] = {va.x, va.y, va.z, va.w};
 #pragma unroll
-                        for (int k = 0; k < 8; k++) feed((w4[k >> 1] >> (16 * (k & 1))) & 0xffffu, 0);
+                    for (int k = 0; k < 8; k++) feed((w4[k >> 1] >> (16 * (k & 1))) & 0xffffu, 0);
+                    if (kind == 4) {
+                        const uint32_t x4[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+                        for (int k = 0; k < 8; k++) feed((x4[k >> 1] >> (16 * (k & 1))) & 0xffffu, 0);
                     }
                 }
             }

@@ -83,3 +83,33 @@ def test_allocator_returning_null_gives_oom(mg):
         assert not live, (budget, len(live))   # everything handed out was given back
     assert outcomes[0] == mg.MG_ERR_OOM and outcomes[-1] == mg.MG_OK
     assert _graph_works(mg)
+
+
+def test_misaligned_allocator_is_refused(mg):
+    # an allocator whose pointers are not 256-byte aligned is refused before
+    # any kernel reads through them; everything handed out is given back
+    vol = synth.make_volume(1, dims=(24, 20, 18), S=12)
+    ids = torch.from_numpy(vol).cuda()
+    lib = mg.lib()
+    live = {}
+
+    def alloc(ctx, nbytes, stream):
+        p = torch.cuda.caching_allocator_alloc(int(nbytes) + 256, 0, int(stream or 0))
+        live[p + 16] = p
+        return p + 16
+
+    def free(ctx, ptr, nbytes, stream):
+        p = live.pop(int(ptr), None)
+        if p is not None:
+            torch.cuda.caching_allocator_delete(p)
+
+    a = mg.mg_allocator(None, mg.ALLOC_FN(alloc), mg.FREE_FN(free))
+    h = ctypes.c_void_p()
+    nz, ny, nx = ids.shape
+    st = lib.mg_build(ids.data_ptr(), nx, ny, nz, 12, ctypes.byref(mg.mg_build_opts(2)), ctypes.byref(a),
+                      torch.cuda.current_stream().cuda_stream, ctypes.byref(h))
+    torch.cuda.synchronize()
+    assert st == mg.MG_ERR_INVALID_ARG and h.value is None
+    assert "256-byte" in mg.mg_last_error()
+    assert not live
+    assert _graph_works(mg)
