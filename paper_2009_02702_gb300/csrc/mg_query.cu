@@ -337,10 +337,10 @@ __global__ void plan_write_kernel(Geom G, const int32_t* __restrict__ boxes, int
 constexpr int kTileMax = 64;                     // boxes per tile at most
 constexpr int kFusedThreads = 512;
 constexpr int kFusedWarps = kFusedThreads / 32;
-constexpr int kBoxLanes = 16;                    // lanes per box in the count phase
+constexpr int kBoxLanes = 8;                     // lanes per box in the count phase (three build runs)
 constexpr int kBoxGroups = kFusedThreads / kBoxLanes;
 constexpr int kScanPerLane = kTileMax / 32;      // boxes per lane in the tile scan
-constexpr int kFusedItems = 4;                   // blocks per thread and round, interleaved
+constexpr int kFusedItems = 6;                   // blocks per thread and round, interleaved
 constexpr int kLookWindows = 4;                  // look-back windows of 32 tiles loaded per poll
 constexpr uint64_t kTileAgg = 1ull << 62;        // the word holds the tile's own total
 constexpr uint64_t kTilePre = 2ull << 62;        // the word holds the inclusive prefix
