@@ -1159,99 +1159,118 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
         }
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t excl = incl - units;
-        for (uint32_t u0 = 0; u0 < total; u0 += 32) {
-            const uint32_t u = u0 + lane;
-            // block of unit u: blocks ending at or before u0, plus those ending
-            // inside this group at or before u (block ends are distinct below
-            // the total, so one bit each)
-            const unsigned below = __ballot_sync(0xffffffffu, incl <= u0);
-            const uint32_t te = incl - u0;
-            const unsigned ends = __reduce_or_sync(0xffffffffu, incl > u0 && te < 32u ? 1u << te : 0u);
-            const int j = __popc(below) + __popc(ends & ((2u << lane) - 1u) & ~1u);
-            const uint32_t jbase = __shfl_sync(0xffffffffu, base, j & 31);
-            const uint32_t jmeta = __shfl_sync(0xffffffffu, wmeta, j & 31);
-            const uint32_t jlo = __shfl_sync(0xffffffffu, lo, j & 31);
-            const uint32_t jnh = __shfl_sync(0xffffffffu, nh, j & 31);
-            const uint32_t jnv = __shfl_sync(0xffffffffu, nv, j & 31);
-            const uint32_t jex = __shfl_sync(0xffffffffu, excl, j & 31);
-            // kind: 0 scalar; 1 / 3: four / eight uint32; 2 / 4: eight / sixteen uint16
-            int kind = -1, ul = 0;
-            uint4 va = make_uint4(0u, 0u, 0u, 0u), vb = va;
-            if (u < total) {
-                const int jl = jmeta & 31, jc = (jmeta >> 5) & 3;
-                const int je0 = (jmeta >> 7) & 31, je1 = (jmeta >> 12) & 31;
-                const bool jw = (jmeta >> 22) & 1u;
-                const int jlg = (jl == 0 ? lg0 : 2) + (jw ? 1 : 0);
-                const uint32_t t = u - jex;
-                uint32_t o;
-                bool vv = false;
-                if (t < jnh) {
-                    o = jlo + t;
-                } else if (t < jnh + jnv) {
-                    o = jlo + jnh + ((t - jnh) << jlg);
-                    vv = true;
-                } else {
-                    o = jlo + jnh + (jnv << jlg) + (t - jnh - jnv);
-                }
-                const uint32_t idx = jbase + (o & ((1u << je0) - 1u)) +
-                                     ((o >> je0) & ((1u << je1) - 1u)) * A.G.st1[jl][jc] +
-                                     (o >> (je0 + je1)) * A.G.st2[jl][jc];
-                ul = jl;
-                const bool u16 = jl == 0 && lg0 == 3;
-                const void* row = jl == 0 ? A.I.l0[jc] : static_cast<const void*>(A.I.hi[jc] + A.G.off[jl]);
-                if (vv) {
-                    const uint4* p = reinterpret_cast<const uint4*>(u16 ? static_cast<const void*>(
-                                                                              static_cast<const uint16_t*>(row) + idx)
-                                                                        : static_cast<const void*>(
-                                                                              static_cast<const uint32_t*>(row) + idx));
-                    va = __ldg(p);
-                    if (jw) vb = __ldg(p + 1);
-                    kind = (u16 ? 2 : 1) + (jw ? 2 : 0);
-                } else {
-                    va.x = u16 ? (uint32_t)__ldg(static_cast<const uint16_t*>(row) + idx)
-                               : __ldg(static_cast<const uint32_t*>(row) + idx);
-                    kind = 0;
-                }
-            }
-            if (kind == 0) {
-                feed(va.x, ul);
-            } else if (kind == 1 || kind == 3) {
-                const bool same = rcnt && rl == ul && va.x == rid && va.y == rid && va.z == rid && va.w == rid &&
-                                  (kind == 1 || (vb.x == rid && vb.y == rid && vb.z == rid && vb.w == rid));
-                if (same) {
-                    rcnt += kind == 1 ? 4 : 8;
-                } else {
-                    feed(va.x, ul);
-                    feed(va.y, ul);
-                    feed(va.z, ul);
-                    feed(va.w, ul);
-                    if (kind == 3) {
-                        feed(vb.x, ul);
-                        feed(vb.y, ul);
-                        feed(vb.z, ul);
-                        feed(vb.w, ul);
+        // R units per lane per step: one (16- or 32-byte) where the window
+        // has 32-byte units, else two, so scalar-heavy windows keep two loads
+        // in flight per lane
+        auto run_units = [&](auto rc) {
+            constexpr int R = decltype(rc)::value;
+            for (uint32_t u0 = 0; u0 < total; u0 += 32u * R) {
+                uint4 va[R], vb[R];
+                int kind[R], ul[R];   // kind: 0 scalar; 1 / 3: 4 / 8 uint32; 2 / 4: 8 / 16 uint16
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const uint32_t ub = u0 + 32u * r, u = ub + lane;
+                    // block of unit u: blocks ending at or before ub, plus those
+                    // ending inside this group at or before u (block ends are
+                    // distinct below the total, so one bit each)
+                    const unsigned below = __ballot_sync(0xffffffffu, incl <= ub);
+                    const uint32_t te = incl - ub;
+                    const unsigned ends = __reduce_or_sync(0xffffffffu, incl > ub && te < 32u ? 1u << te : 0u);
+                    const int j = __popc(below) + __popc(ends & ((2u << lane) - 1u) & ~1u);
+                    const uint32_t jbase = __shfl_sync(0xffffffffu, base, j & 31);
+                    const uint32_t jmeta = __shfl_sync(0xffffffffu, wmeta, j & 31);
+                    const uint32_t jlo = __shfl_sync(0xffffffffu, lo, j & 31);
+                    const uint32_t jnh = __shfl_sync(0xffffffffu, nh, j & 31);
+                    const uint32_t jnv = __shfl_sync(0xffffffffu, nv, j & 31);
+                    const uint32_t jex = __shfl_sync(0xffffffffu, excl, j & 31);
+                    kind[r] = -1;
+                    ul[r] = 0;
+                    va[r] = make_uint4(0u, 0u, 0u, 0u);
+                    vb[r] = va[r];
+                    if (u < total) {
+                        const int jl = jmeta & 31, jc = (jmeta >> 5) & 3;
+                        const int je0 = (jmeta >> 7) & 31, je1 = (jmeta >> 12) & 31;
+                        const bool jw = R == 1 && ((jmeta >> 22) & 1u);
+                        const int jlg = (jl == 0 ? lg0 : 2) + (jw ? 1 : 0);
+                        const uint32_t t = u - jex;
+                        uint32_t o;
+                        bool vv = false;
+                        if (t < jnh) {
+                            o = jlo + t;
+                        } else if (t < jnh + jnv) {
+                            o = jlo + jnh + ((t - jnh) << jlg);
+                            vv = true;
+                        } else {
+                            o = jlo + jnh + (jnv << jlg) + (t - jnh - jnv);
+                        }
+                        const uint32_t idx = jbase + (o & ((1u << je0) - 1u)) +
+                                             ((o >> je0) & ((1u << je1) - 1u)) * A.G.st1[jl][jc] +
+                                             (o >> (je0 + je1)) * A.G.st2[jl][jc];
+                        ul[r] = jl;
+                        const bool u16 = jl == 0 && lg0 == 3;
+                        const void* row =
+                            jl == 0 ? A.I.l0[jc] : static_cast<const void*>(A.I.hi[jc] + A.G.off[jl]);
+                        if (vv) {
+                            const uint4* p = reinterpret_cast<const uint4*>(
+                                u16 ? static_cast<const void*>(static_cast<const uint16_t*>(row) + idx)
+                                    : static_cast<const void*>(static_cast<const uint32_t*>(row) + idx));
+                            va[r] = __ldg(p);
+                            if (jw) vb[r] = __ldg(p + 1);
+                            kind[r] = (u16 ? 2 : 1) + (jw ? 2 : 0);
+                        } else {
+                            va[r].x = u16 ? (uint32_t)__ldg(static_cast<const uint16_t*>(row) + idx)
+                                          : __ldg(static_cast<const uint32_t*>(row) + idx);
+                            kind[r] = 0;
+                        }
                     }
                 }
-            } else if (kind == 2 || kind == 4) {
-                const uint32_t pr = rid * 0x10001u;
-                uint32_t diff = (va.x ^ pr) | (va.y ^ pr) | (va.z ^ pr) | (va.w ^ pr);
-                if (kind == 4) diff |= (vb.x ^ pr) | (vb.y ^ pr) | (vb.z ^ pr) | (vb.w ^ pr);
-                if (rcnt && rl == 0 && diff == 0u) {
-                    rcnt += kind == 2 ? 8 : 16;
-                } else {
-                    const uint32_t w4[4] = {va.x, va.y, va.z, va.w};
 #pragma unroll
-                    for (int k = 0; k < 8; k++) feed((w4[k >> 1] >> (16 * (k & 1))) & 0xffffu, 0);
-                    if (kind == 4) {
-                        const uint32_t x4[4] = {vb.x, vb.y, vb.z, vb.w};
+                for (int r = 0; r < R; r++) {
+                    const int k = kind[r], l = ul[r];
+                    const uint4 x = va[r], y = vb[r];
+                    if (k == 0) {
+                        feed(x.x, l);
+                    } else if (k == 1 || k == 3) {
+                        const bool same = rcnt && rl == l && x.x == rid && x.y == rid && x.z == rid && x.w == rid &&
+                                          (k == 1 || (y.x == rid && y.y == rid && y.z == rid && y.w == rid));
+                        if (same) {
+                            rcnt += k == 1 ? 4 : 8;
+                        } else {
+                            feed(x.x, l);
+                            feed(x.y, l);
+                            feed(x.z, l);
+                            feed(x.w, l);
+                            if (k == 3) {
+                                feed(y.x, l);
+                                feed(y.y, l);
+                                feed(y.z, l);
+                                feed(y.w, l);
+                            }
+                        }
+                    } else if (k == 2 || k == 4) {
+                        const uint32_t pr = rid * 0x10001u;
+                        uint32_t diff = (x.x ^ pr) | (x.y ^ pr) | (x.z ^ pr) | (x.w ^ pr);
+                        if (k == 4) diff |= (y.x ^ pr) | (y.y ^ pr) | (y.z ^ pr) | (y.w ^ pr);
+                        if (rcnt && rl == 0 && diff == 0u) {
+                            rcnt += k == 2 ? 8 : 16;
+                        } else {
+                            const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-                        for (int k = 0; k < 8; k++) feed((x4[k >> 1] >> (16 * (k & 1))) & 0xffffu, 0);
+                            for (int q = 0; q < 8; q++) feed((w4[q >> 1] >> (16 * (q & 1))) & 0xffffu, 0);
+                            if (k == 4) {
+                                const uint32_t x4[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                                for (int q = 0; q < 8; q++) feed((x4[q >> 1] >> (16 * (q & 1))) & 0xffffu, 0);
+                            }
+                        }
                     }
                 }
+                __syncwarp();
+                if (*Qu.count >= 32) drain<FP, AT>(A.P, H, Qu, false);
             }
-            __syncwarp();
-            if (*Qu.count >= 32) drain<FP, AT>(A.P, H, Qu, false);
-        }
+        };
+        if (__any_sync(0xffffffffu, wide)) run_units(std::integral_constant<int, 1>{});
+        else run_units(std::integral_constant<int, 2>{});
         const uint32_t st31 = __shfl_sync(0xffffffffu, st, 31);
         if (bb + 31 >= b1 || st31 >= w1) break;
     }
