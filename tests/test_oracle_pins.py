@@ -336,6 +336,28 @@ def test_fa_cubes_tile_the_clipped_box():
         assert (mark == want).all(), box
 
 
+def test_fa_cube_count_closed_form():
+    # Algorithm 1's block of run levels (a, b, c) holds 2^(a+b+c-3m) cubes at
+    # level m = min(a, b, c).  With F(m) = sum over an axis's steps of level
+    # >= m of 2^(level-m) and P(m) = Fx Fy Fz, every block adds 2^(a+b+c-3m')
+    # to P(m') for each m' <= m, so the total is P(0) - 7 * sum_{m>=1} P(m):
+    # a count that never lists the blocks.
+    rng = np.random.default_rng(23)
+    for _ in range(400):
+        dims = [int(rng.choice([7, 64, 300, 384, 961, 2048])) for _ in range(3)]
+        o = [int(rng.integers(0, n)) for n in dims]
+        s = [int(2 ** rng.uniform(0, 11.5)) for _ in range(3)]
+        steps = [oracle.footprint_1d(o[k], s[k], dims[k]) for k in range(3)]
+
+        def F(levels, m):
+            return sum(1 << (lv - m) for lv in levels if lv >= m)
+
+        P = [F(steps[0], m) * F(steps[1], m) * F(steps[2], m) for m in range(40)]
+        closed = P[0] - 7 * sum(P[1:])
+        assert oracle.fa_count(o + s, *dims) == closed, (dims, o, s)
+        assert P[0] == np.prod([min(o[k] + s[k], dims[k]) - o[k] for k in range(3)])
+
+
 def test_fa_query_equals_brute_force():
     vol = synth.make_volume(1)
     g = oracle.Graph(vol, 64)
