@@ -90,6 +90,18 @@ def test_plan_runs_on_unaligned_caller_buffers(mg, cfg1, hist):
     plan.close()
 
 
+@pytest.mark.parametrize("chunk", [1000, 3, 65536])
+def test_plan_non_power_of_two_and_extreme_chunks(mg, cfg1, chunk):
+    # chunk maps by division (non powers of two) and by shift, tiny and huge chunks
+    vol, g = cfg1
+    boxes = synth.make_boxes(1, Q=500, stream_offset=50)
+    plan = mg.QueryPlan(g, max_Q=500, chunk_cubes=chunk, max_chunks=500 * 4096)
+    h = plan.run(torch.from_numpy(boxes).cuda()).cpu().numpy()
+    mg.mg_sync_status(g)
+    assert np.array_equal(h, oracle.box_hist(vol, 64, boxes))
+    plan.close()
+
+
 def test_plan_long_lookback_chain(mg, cfg1):
     # 6,250 tiles chained by the look-back of the single-pass scan
     vol, g = cfg1
