@@ -312,6 +312,15 @@ def mg_graph_copy_mip(g: Graph, level: int, stream=None):
     return out
 
 
+def _check_out(out, shape, dtype, device, name="out"):
+    """A caller's output tensor is written through its data pointer: it must be
+    contiguous, with the shape, dtype and device of the result."""
+    if (not isinstance(out, torch.Tensor) or out.dtype != dtype or tuple(out.shape) != tuple(shape)
+            or out.device != device or not out.is_contiguous()):
+        raise ValueError("%s must be a contiguous %s tensor of shape %s on %s" % (name, dtype, tuple(shape), device))
+    return out
+
+
 def mg_propagate_tf(g: Graph, tf: torch.Tensor, storage: str = "f32", out: torch.Tensor = None,
                     stream=None) -> torch.Tensor:
     """Node values (N, C) in `storage` dtype from an (S, C) fp32 CUDA transfer function."""
@@ -322,6 +331,7 @@ def mg_propagate_tf(g: Graph, tf: torch.Tensor, storage: str = "f32", out: torch
     C = tf.shape[1]
     if out is None:
         out = torch.empty((g.N, C), dtype=dt, device=tf.device)
+    _check_out(out, (g.N, C), dt, tf.device)
     _check(lib().mg_propagate_tf(g.handle, tf.data_ptr(), C, code, out.data_ptr(), _stream(stream)))
     return out
 
@@ -352,6 +362,7 @@ def mg_query_boxes(g: Graph, boxes: torch.Tensor, hist: str = "u32", layout: str
     if layout != "csr":
         if out is None:
             out = torch.empty((Q, g.S), dtype=vdt, device=dev)
+        _check_out(out, (Q, g.S), vdt, dev)
         _check(lib().mg_query_boxes(g.handle, boxes.data_ptr(), Q, ctypes.byref(o), out.data_ptr(),
                                     out.numel(), None, None, ctypes.byref(req), _stream(stream)))
         return out
@@ -411,6 +422,7 @@ class QueryPlan:
         Q = boxes.shape[0]
         if out is None:
             out = torch.empty((Q, self.graph.S), dtype=self.dtype, device=boxes.device)
+        _check_out(out, (Q, self.graph.S), self.dtype, boxes.device)
         _check(lib().mg_query_plan_run(self.handle, boxes.data_ptr(), Q, out.data_ptr(), out.numel(),
                                        _stream(stream)))
         return out
@@ -503,6 +515,7 @@ def mg_render_lookup(g: Graph, vals: torch.Tensor, samples: torch.Tensor, out: t
     C = vals.shape[1]
     if out is None:
         out = torch.empty((samples.shape[0], C), dtype=vals.dtype, device=vals.device)
+    _check_out(out, (samples.shape[0], C), vals.dtype, vals.device)
     _check(lib().mg_render_lookup(g.handle, vals.data_ptr(), C, _TORCH_TO_MG[vals.dtype], samples.data_ptr(),
                                   samples.shape[0], out.data_ptr(), _stream(stream)))
     return out

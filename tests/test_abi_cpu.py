@@ -141,3 +141,20 @@ def test_graph_io_argument_checks(lib):
     junk = (ctypes.c_uint8 * 4096)()
     assert lib.mg_graph_import(junk, 4096, None, None, ctypes.byref(h)) == mg.MG_ERR_INVALID_ARG
     assert lib.mg_graph_import(junk, 10, None, None, ctypes.byref(h)) == mg.MG_ERR_INVALID_ARG
+
+
+def test_output_tensor_checks():
+    # caller outputs are written through their data pointers: contiguous, and
+    # the result's shape, dtype and device, else ValueError before any call
+    torch = pytest.importorskip("torch")
+    from paper_2009_02702_gb300 import mg
+    cpu = torch.device("cpu")
+    ok = torch.empty((5, 7), dtype=torch.uint32)
+    assert mg._check_out(ok, (5, 7), torch.uint32, cpu) is ok
+    bad = [torch.empty((5, 7), dtype=torch.float32), torch.empty((7, 5), dtype=torch.uint32),
+           torch.empty((5, 14), dtype=torch.uint32)[:, ::2], torch.empty(35, dtype=torch.uint32), None]
+    for b in bad:
+        with pytest.raises(ValueError):
+            mg._check_out(b, (5, 7), torch.uint32, cpu)
+    with pytest.raises(ValueError):
+        mg._check_out(ok, (5, 7), torch.uint32, torch.device("cuda", 0))
