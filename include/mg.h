@@ -210,8 +210,8 @@ MG_API mg_status mg_query_boxes(const mg_graph *g, const int32_t *boxes, int64_t
  * loads libmg holds it until the process exits), so the call allocates
  * nothing.  A batch must fit it: up to about 500,000 boxes, and footprint
  * blocks and chunks of at most 32 MiB (12 bytes per block, 8 per chunk);
- * larger batches return MG_ERR_CAPACITY before any histogram is written, with
- * the limit in mg_last_error() -- split them.
+ * larger batches return MG_ERR_CAPACITY with `out` left unchanged and the
+ * limit in mg_last_error() -- split them.
  * The first call on a device looks up the array's device address (so make
  * it before any stream capture).  All calls share the one array and leave
  * their scratch in it: calls that overlap on the GPU (other streams, other
@@ -295,7 +295,7 @@ MG_API mg_status mg_render_lookup(const mg_graph *g, const void *vals, int C, mg
 /*
  * Request loop (serving).  A server keeps the graphs of several volumes
  * resident on one GPU and runs box-histogram requests (Sec. 3.6) and
- * TF-update frames (propagation, Sec. 3.5, then ray-sample lookups, Sec. 4)
+ * TF-update frames (propagation, Sec. 3.4, then ray-sample lookups, Sec. 4)
  * as they arrive.  A worker thread owns `slots` CUDA streams.  Whenever a
  * slot is free it takes the oldest queued request; a box request takes with
  * it every queued box of the same volume that still fits the slot's batch

@@ -1785,9 +1785,7 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
             MG_TRY(accf_b.alloc(&al, cells * 4, s));
             accf = accf_b.as<float>();
         }
-        MG_CUDA(cudaMemsetAsync(accf, 0, cells * 4, s));
     }
-    MG_CUDA(cudaMemsetAsync(acc, 0, cells * 4, s));
 
     MainArgs A;
     A.G = G;
@@ -1877,6 +1875,10 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
         A.chunk_off = chunk_off.as<uint64_t>();
         A.ticket = ticket.as<unsigned long long>();
     }
+    // the accumulators are cleared only once the footprint is known to fit, so
+    // a refused call leaves the caller's output as it was
+    if (FP) MG_CUDA(cudaMemsetAsync(accf, 0, cells * 4, s));
+    MG_CUDA(cudaMemsetAsync(acc, 0, cells * 4, s));
     if (timed) MG_CUDA(cudaEventRecord(gm->qev[1], s));
     if (FP) {
         if (o.alpha_dtype == MG_F16) MG_TRY((launch_main<true, __half>(g, A, o, boxes, smem, threads, s)));

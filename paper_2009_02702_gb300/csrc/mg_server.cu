@@ -1,5 +1,5 @@
 // mg_server.cu -- request loop with continuous batching, the host runtime
-// around the query (Sec. 3.6), propagation (Sec. 3.5) and lookup (Sec. 4)
+// around the query (Sec. 3.6), propagation (Sec. 3.4) and lookup (Sec. 4)
 // kernels.
 //
 // Resident volumes are admitted against a memory budget; each gets, per slot

@@ -391,6 +391,7 @@ def mg_query_boxes_noalloc(g: Graph, boxes: torch.Tensor, out: torch.Tensor = No
     Q = boxes.shape[0]
     if out is None:
         out = torch.empty((Q, g.S), dtype=torch.uint32, device=boxes.device)
+    _check_out(out, (Q, g.S), torch.uint32, boxes.device)
     _check(lib().mg_query_boxes_noalloc(g.handle, boxes.data_ptr(), Q, out.data_ptr(), out.numel(),
                                         _stream(stream)))
     return out

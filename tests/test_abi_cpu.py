@@ -158,3 +158,26 @@ def test_output_tensor_checks():
             mg._check_out(b, (5, 7), torch.uint32, cpu)
     with pytest.raises(ValueError):
         mg._check_out(ok, (5, 7), torch.uint32, torch.device("cuda", 0))
+
+
+def test_noalloc_binding_checks_the_output(monkeypatch):
+    # the fixed-scratch query writes Q*S uint32 through out's data pointer: an
+    # output of another dtype, shape or layout is refused before the library
+    # is called (here a stand-in that fails the test if it is reached)
+    torch = pytest.importorskip("torch")
+    from types import SimpleNamespace
+    from paper_2009_02702_gb300 import mg
+
+    def unreachable():
+        raise AssertionError("the library was called with a bad output")
+    monkeypatch.setattr(mg, "lib", unreachable)
+    boxes = SimpleNamespace(is_cuda=True, dtype=torch.int32, shape=(5, 6), device=torch.device("cpu"),
+                            dim=lambda: 2)
+    boxes.contiguous = lambda: boxes
+    g = SimpleNamespace(S=7, handle=None)
+    bad = [torch.empty((5, 7), dtype=torch.uint8), torch.empty((5, 7), dtype=torch.int16),
+           torch.empty((5, 7), dtype=torch.float32), torch.empty((7, 5), dtype=torch.uint32),
+           torch.empty((5, 14), dtype=torch.uint32)[:, ::2], torch.empty(35, dtype=torch.uint32)]
+    for b in bad:
+        with pytest.raises(ValueError):
+            mg.mg_query_boxes_noalloc(g, boxes, out=b)
