@@ -48,31 +48,34 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=3)
+    ap.add_argument("--secondary", type=int, default=2, help="second workload measured the same way (0: none)")
+    ap.add_argument("--storage", default="", choices=["", "f32", "f16", "bf16"],
+                    help="node value storage of the step's propagation (default: f16 for config 3, else f32)")
+    ap.add_argument("--cpu-boxes", type=int, default=1000, help="boxes of the CPU oracle's timed sample")
     ap.add_argument("--queries", type=int, default=0)
     ap.add_argument("--schedule", default="batched", choices=["batched", "plain"])
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-plan", action="store_true", help="time direct calls instead of the captured plan")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain/naive/16-bit extra measurements")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving mix) measurement")
-    ap.add_argument("--no-large", action="store_true", help="skip the 2048x2048x300 and cylinder graph measurements")
+    ap.add_argument("--no-large", action="store_true", help="skip the cylinder graph measurements")
     ap.add_argument("--serve-requests", type=int, default=0)
     ap.add_argument("--serve-rate", type=float, default=0.0)
     return ap.parse_args(argv)
 
 
-def workload_config(cfg_index, Q, args):
+def workload_config(cfg_index, Q, args, storage="f32"):
     cfg = synth.CONFIGS[cfg_index]
     nx, ny, nz = cfg["dims"]
     return {"workload": "%s (synthetic, seeded; stands in for the paper's volume)" % cfg["name"],
             "volume": "%dx%dx%d uint16" % (nx, ny, nz), "segments": cfg["S"],
             "queries_per_step": Q, "box_sides": "%s 1..%d" % (cfg["box"], cfg["box_max"]),
             "hist": "exact u32, dense Q x S", "schedule": args.schedule,
-            "tf": "RGBA fp32", "samples_per_step": 1920 * 1080,
+            "tf": "RGBA fp32 in, node values stored as %s" % storage, "samples_per_step": 1920 * 1080,
             "l2": "flushed between steps (write of a 512 MiB buffer)"}
 
 
@@ -164,19 +167,25 @@ def cube_levels(boxes, dims):
 
 
 def measured_traffic(kernel, cfg_i, Q):
-    """DRAM bytes per launch from the committed ncu record, only while the
-    kernel's source is the one the counters were taken on (else None)."""
+    """DRAM bytes per launch from the committed ncu records (profiles/
+    traffic.json: one record per kernel and workload), only while the kernel's
+    source is the one the counters were taken on (else None)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f)[kernel]
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+            recs = json.load(f)["records"]
     except (OSError, KeyError, ValueError):
         return None
-    if sha != rec["sha256_16"] or cfg_i != 2 or Q != synth.CONFIGS[2]["queries"]:
-        return None
-    return rec["dram_bytes_per_launch"]
+    for rec in recs:
+        if rec.get("kernel") != kernel or rec.get("config") != cfg_i or rec.get("queries") != Q:
+            continue
+        try:
+            with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+                sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        except (OSError, KeyError):
+            return None
+        return rec["dram_bytes_per_launch"] if sha == rec["sha256_16"] else None
+    return None
 
 
 # --------------------------------------------------------------------------
@@ -212,69 +221,99 @@ def whole_job_rate(world, units_per_rank, ms_per_step):
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
-def run_ours(args):
+def load_peak():
+    """(HBM GB/s, source) from the driver-written measurement, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def query_kernel_name(S, threads, hist="u32"):
+    """The histogram kernel the library launches for S segments and a CTA size
+    (a private histogram per warp when it fits, else one per CTA)."""
+    per_warp = S * 4 * (2 if hist == "f32" else 1) + 320 * 8 + 16
+    warp_mode = S <= 2048 and threads <= 256 and per_warp * (threads // 32) <= 96 * 1024
+    return "query_warp_kernel" if warp_mode else "query_batched_kernel"
+
+
+def query_bytes(boxes_h, dims, S):
+    """Algorithmic bytes of one query launch: the box, every footprint cube's
+    node ID (uint16 at level 0, uint32 above) and the dense u32 row out."""
+    lv = cube_levels(boxes_h, dims)
+    id0 = 2 if S <= 65536 else 4
+    Q = len(boxes_h)
+    return 24 * Q + id0 * int(lv[0]) + 4 * int(lv[1:].sum()) + 4 * Q * S, int(lv.sum()), lv
+
+
+def build_graph(mg, cfg_i, dev):
+    """The config's volume (GPU generator for Voronoi volumes, host for the
+    cylinders) and its graph; returns (graph, seconds of volume generation)."""
     import torch
-    import torch.distributed as dist
-    from paper_2009_02702_gb300 import mg
-
-    world, rank, local = rank_env()
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    cfg_i = args.config
-    cfg = synth.CONFIGS[cfg_i]
-    S = cfg["S"]
-    Q = args.queries or cfg["queries"]
-    dims = cfg["dims"]
-
-    vol = synth.make_volume(cfg_i, device=dev)
+    c = synth.CONFIGS[cfg_i]
+    t0 = time.perf_counter()
+    if c["kind"] == "voronoi":
+        vol = synth.make_volume(cfg_i, device=dev)
+    else:
+        vol = torch.from_numpy(synth.make_volume(cfg_i)).to(dev)
     torch.cuda.synchronize()
-    g = mg.mg_build(vol, S)
-    info = g.info
+    gen_s = time.perf_counter() - t0
+    g = mg.mg_build(vol, c["S"])
     del vol
-    boxes_h = rank_boxes(cfg_i, Q, rank)
+    return g, gen_s
+
+
+STORAGE = {"f32": ("torch.float32", 4), "f16": ("torch.float16", 2), "bf16": ("torch.bfloat16", 2)}
+
+
+def measure_step(mg, g, cfg_i, boxes_h, storage, args, dev, flush, stream, world, peak, peak_src,
+                 clocks_index=None, e2e=True):
+    """Time whole steps of one workload: the box queries on the main stream
+    and, concurrently on a side stream, the TF propagation followed by the
+    lookup of one 1920x1080 frame.  Returns the workload's measurements."""
+    import torch
+    from paper_2009_02702_gb300 import mg as _mg
+    cfg = synth.CONFIGS[cfg_i]
+    S, dims = cfg["S"], cfg["dims"]
+    Q = len(boxes_h)
+    info = g.info
+    dt = _mg._DTYPES[storage][1]
+    esz = STORAGE[storage][1]
     tf_h = synth.make_tf(cfg_i, S, 4)
     smp_h = synth.make_samples(cfg_i)
     P = smp_h.shape[0]
     boxes = torch.from_numpy(boxes_h).to(dev)
     tf = torch.from_numpy(tf_h).to(dev)
     smp = torch.from_numpy(smp_h).to(dev)
-    vals = torch.empty((g.N, 4), dtype=torch.float32, device=dev)
+    vals = torch.empty((g.N, 4), dtype=dt, device=dev)
     hist = torch.empty((Q, S), dtype=torch.uint32, device=dev)
-    look = torch.empty((P, 4), dtype=torch.float32, device=dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    look = torch.empty((P, 4), dtype=dt, device=dev)
     tune = None
     if args.schedule == "batched" and not args.chunk and not args.threads:
         tune = mg.mg_query_autotune(g, boxes, cache=os.environ.get("MG_AUTOTUNE_CACHE"),
                                     key="%s-Q%d" % (cfg["name"], Q))
+    threads = args.threads or (tune or {}).get("block_threads") or 256
     qkw = dict(schedule=args.schedule, chunk_cubes=args.chunk, block_threads=args.threads)
     use_plan = args.schedule == "batched" and not args.no_plan
     plan = mg.QueryPlan(g, max_Q=Q, chunk_cubes=args.chunk, block_threads=args.threads) if use_plan else None
 
-    def query(bx, timing=False):
-        if plan is not None:
-            plan.run(bx, out=hist, stream=stream)
+    def query(bx, out, st, pl):
+        if pl is not None:
+            pl.run(bx, out=out, stream=st)
         else:
-            mg.mg_query_boxes(g, bx, out=hist, timing=timing, stream=stream, **qkw)
+            mg.mg_query_boxes(g, bx, out=out, stream=st, **qkw)
 
-    # One step: the box queries on the main stream and, concurrently on a side
-    # stream (they share no data), the TF propagation followed by the lookup.
     side = torch.cuda.Stream(dev)
 
-    def step(e, bx=None, tfx=None, smpx=None):
-        bx = boxes if bx is None else bx
-        tfx = tf if tfx is None else tfx
-        smpx = smp if smpx is None else smpx
+    def step(e):
         e[0].record(stream)
         side.wait_event(e[0])
-        mg.mg_propagate_tf(g, tfx, out=vals, stream=side)
+        mg.mg_propagate_tf(g, tf, storage=storage, out=vals, stream=side)
         e[1].record(side)
-        mg.mg_render_lookup(g, vals, smpx, out=look, stream=side)
+        mg.mg_render_lookup(g, vals, smp, out=look, stream=side)
         e[2].record(side)
-        query(bx)
+        query(boxes, hist, stream, plan)
         e[3].record(stream)
         stream.wait_event(e[2])
         e[4].record(stream)
@@ -286,11 +325,12 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
-    qmain = []
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
+    clocks = ClockSampler(clocks_index) if clocks_index is not None else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
@@ -301,11 +341,12 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     mg.mg_sync_status(g)
     # stage split of the query from CUDA events the library records: a plan
     # with timing events in its graph (plan stage, main kernel), else the
     # direct call's (plan, main kernel, output); same launch shape, L2 flushed
+    qmain = []
     if use_plan:
         plan_t = mg.QueryPlan(g, max_Q=Q, chunk_cubes=args.chunk, block_threads=args.threads, timing=True)
         for k in range(args.steps):
@@ -326,153 +367,38 @@ def run_ours(args):
     query_ms = np.array([e[0].elapsed_time(e[3]) for e in ev])
     main_ms = np.array([t[1] for t in qmain])
     # propagation and lookup each timed alone (L2 flushed) for their rooflines
-    prop_alone = _time(lambda: mg.mg_propagate_tf(g, tf, out=vals), 10, flush, stream)
+    prop_alone = _time(lambda: mg.mg_propagate_tf(g, tf, storage=storage, out=vals), 10, flush, stream)
     tf_pin = torch.from_numpy(tf_h).pin_memory()
     tf_up = torch.empty_like(tf)
 
     def prop_upload():
         tf_up.copy_(tf_pin, non_blocking=True)
-        mg.mg_propagate_tf(g, tf_up, out=vals)
+        mg.mg_propagate_tf(g, tf_up, storage=storage, out=vals)
     prop_with_upload = _time(prop_upload, 10, flush, stream)
     look_alone = _time(lambda: mg.mg_render_lookup(g, vals, smp, out=look), 10, flush, stream)
     tot_ms = max_over_ranks(float(step_ms.sum()), world, dev)
     ms_per_step = tot_ms / args.steps
     value = whole_job_rate(world, Q, ms_per_step)
 
-    # algorithmic bytes of the query kernel: box in, cube IDs (uint16 at level
-    # 0, uint32 above), dense histogram out
-    lv = cube_levels(boxes_h, dims)
-    cubes = int(lv.sum())
-    id0 = 2 if S <= 65536 else 4
-    q_bytes = 24 * Q + id0 * int(lv[0]) + 4 * int(lv[1:].sum()) + 4 * Q * S
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-        peak = float(peaks["hbm_gbs"])
-        peak_src = "measured"
-    except Exception:
-        peak, peak_src = 6800.0, "fallback"
+    q_bytes, cubes, _ = query_bytes(boxes_h, dims, S)
+    kernel = query_kernel_name(S, threads) if args.schedule == "batched" else "query_plain_kernel"
     achieved = q_bytes / (float(np.mean(main_ms)) / 1e3) / 1e9
-    traffic = measured_traffic("query_warp_kernel", cfg_i, Q)
+    traffic = measured_traffic(kernel, cfg_i, Q)
     n_int = info["num_nodes"] - S
-    prop_bytes = 28 * n_int + 16 * S
+    # edges 8 + weight (4 or 2) + value row out per internal node; TF row in and value row out per source
+    prop_bytes = n_int * (8 + (4 if storage == "f32" else 2) + 4 * esz) + S * (16 + 4 * esz)
     prop_gbs = prop_bytes / (prop_alone / 1e3) / 1e9
-    look_bytes = 52 * P
+    look_bytes = P * (16 + 4 + 8 * esz)
     look_gbs = look_bytes / (look_alone / 1e3) / 1e9
 
-    # end to end through the public API with host buffers
-    e2e = None
-    if not args.no_e2e:
-        boxes_p = torch.from_numpy(boxes_h).pin_memory()
-        tf_p = torch.from_numpy(tf_h).pin_memory()
-        smp_p = torch.from_numpy(smp_h).pin_memory()
-
-        class Lane:
-            """One of three pipelines taking steps in turn: boxes -> queries ->
-            histograms on its query stream, TF and samples -> propagation ->
-            lookup -> colours on its frame stream, each with its own buffers
-            (and query plan, whose buffers a run owns until it ends)."""
-
-            def __init__(self):
-                self.qs, self.fs = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-                self.boxes = torch.empty_like(boxes)
-                self.tf, self.smp = torch.empty_like(tf), torch.empty_like(smp)
-                self.vals, self.look = torch.empty_like(vals), torch.empty_like(look)
-                self.hist = torch.empty_like(hist)
-                self.hist_p = torch.empty((Q, S), dtype=torch.uint32).pin_memory()
-                self.look_p = torch.empty((P, 4), dtype=torch.float32).pin_memory()
-                self.plan = mg.QueryPlan(g, max_Q=Q, chunk_cubes=args.chunk,
-                                         block_threads=args.threads) if use_plan else None
-
-            def step(self):
-                with torch.cuda.stream(self.fs):
-                    self.tf.copy_(tf_p, non_blocking=True)
-                    self.smp.copy_(smp_p, non_blocking=True)
-                mg.mg_propagate_tf(g, self.tf, out=self.vals, stream=self.fs)
-                mg.mg_render_lookup(g, self.vals, self.smp, out=self.look, stream=self.fs)
-                with torch.cuda.stream(self.fs):
-                    self.look_p.copy_(self.look, non_blocking=True)
-                with torch.cuda.stream(self.qs):
-                    self.boxes.copy_(boxes_p, non_blocking=True)
-                if self.plan is not None:
-                    self.plan.run(self.boxes, out=self.hist, stream=self.qs)
-                else:
-                    mg.mg_query_boxes(g, self.boxes, out=self.hist, stream=self.qs, **qkw)
-                with torch.cuda.stream(self.qs):
-                    self.hist_p.copy_(self.hist, non_blocking=True)
-
-            def streams(self):
-                return (self.qs, self.fs)
-
-        lanes = [Lane() for _ in range(3)]
-        for k in range(6):
-            lanes[k % 3].step()
-        torch.cuda.synchronize()
-        # one window over all steps: step k runs on lane k mod 3, so a step's
-        # copies overlap the other lanes' kernels; each lane's streams keep its
-        # buffers from being reused before its copies are done
-        e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e_start.record(stream)
-        for ln in lanes:
-            for st_ in ln.streams():
-                st_.wait_event(e_start)
-        for k in range(args.steps):
-            lanes[k % 3].step()
-        for ln in lanes:
-            for st_ in ln.streams():
-                ev_ = torch.cuda.Event()
-                ev_.record(st_)
-                stream.wait_event(ev_)
-        e_end.record(stream)
-        torch.cuda.synchronize()
-        for ln in lanes:
-            if ln.plan is not None:
-                ln.plan.close()
-        e_ms = max_over_ranks(float(e_start.elapsed_time(e_end)), world, dev)
-        e2e = {"value": whole_job_rate(world, Q, e_ms / args.steps), "unit": UNIT,
-               "h2d_bytes_per_step": int(boxes_h.nbytes + tf_h.nbytes + smp_h.nbytes),
-               "d2h_bytes_per_step": int(Q * S * 4 + P * 16), "ms_per_step": e_ms / args.steps,
-               "timing": "one window over all steps on three lanes taking steps in turn (query and frame streams each), "
-                         "joined at its end: a step's copies overlap the other lane's kernels",
-               "l2": "not flushed: every step reads ~0.6 GB of distinct IDs of a 0.79 GB graph (L2 is 129 MB)"}
-
-    forms = None
-    if not args.no_forms:
-        forms = other_forms(mg, g, boxes, boxes_h, tf, vals, Q, S, dims, cfg_i, flush, stream)
-
-    served = None
-    if not args.no_serve and rank == 0:
-        served = serving(mg, g, args, dev)
-
-    large = None
-    if not args.no_large and rank == 0:
-        large = large_workloads(mg, dev, flush, stream, peak)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(cfg_i, boxes_h, args.cpu_seconds, tf=tf_h)
-
-    # one persistent launch, or (depth beyond the single pass) sources + one launch per level
-    launches_prop = 1 if info["depth"] + 1 <= 64 else 1 + sum(
-        1 for d in range(1, info["depth"] + 1) if info["bucket"][d + 1] > info["bucket"][d])
-    nscan = 1 if Q <= 2048 else 3   # kernels of one device-wide scan of Q values
-    if args.schedule == "batched" and use_plan:
-        # batch size and io slots, tile reset, fused plan kernel, main kernel
-        launches_query = 4
-    elif args.schedule == "batched":
-        # count, offsets (one CTA up to 2^18 boxes, else two device-wide scans
-        # and a widen), write, main
-        launches_query = 1 + (1 if Q <= (1 << 18) else 2 * nscan + 1) + 1 + 1
-    else:
-        launches_query = Q
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32 counts / f32 colours", "data": "synthetic",
-        "config": workload_config(cfg_i, Q, args),
-        "tf_propagations_per_s": 1e3 / prop_alone,
-        "samples_per_s": P / (look_alone / 1e3),
+    e2e_rec = None
+    if e2e:
+        e2e_rec = end_to_end(mg, g, boxes_h, tf_h, smp_h, storage, Q, S, P, esz, args, dev, stream, flush, world,
+                             use_plan, qkw)
+    res = {
+        "workload": cfg["name"], "value": value, "ms_per_step": ms_per_step, "queries_per_step": Q,
+        "storage": storage,
+        "tf_propagations_per_s": 1e3 / prop_alone, "samples_per_s": P / (look_alone / 1e3),
         "latency_ms": {"step_p50": float(np.percentile(step_ms, 50)), "step_p99": float(np.percentile(step_ms, 99)),
                        "query_batch_p50": float(np.percentile(query_ms, 50)),
                        "query_batch_p99": float(np.percentile(query_ms, 99)),
@@ -487,38 +413,232 @@ def run_ours(args):
                       "lookup_alone": look_alone,
                       "note": "propagate/lookup run concurrently with the query; *_alone timed by themselves; "
                               "query_plan = tile reset + fused plan kernel, query_main = histogram kernel (events "
-                              "in a timed copy of the plan's graph), query_rest = the rest of a batch (box copy, "
-                              "batch size, result copy, launch gaps)" if use_plan else
+                              "in a timed copy of the plan's graph), query_rest = the rest of a batch (batch size "
+                              "and io slots, launch gaps)" if use_plan else
                               "propagate/lookup run concurrently with the query; *_alone timed by themselves; "
                               "query_rest includes the output stage"},
         "roofline_nominal": {"peak": NOMINAL_HBM_GBS, "unit": "GB/s", "frac": achieved / NOMINAL_HBM_GBS,
                              "propagate_frac": prop_gbs / NOMINAL_HBM_GBS, "lookup_frac": look_gbs / NOMINAL_HBM_GBS},
-        "roofline": {"bound": "hbm", "kernel": ("query_warp_kernel" if S <= 2048 else "query_batched_kernel")
-                     if args.schedule == "batched" else "query_plain_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src + " hbm_gbs (copy, burst)",
-                     "traffic": traffic, "algorithmic_bytes_per_launch": q_bytes, "cubes_per_launch": cubes},
-        "other_kernels": {"propagate_gbs": prop_gbs, "propagate_frac": prop_gbs / peak,
-                          "propagate_bytes": prop_bytes, "lookup_gbs": look_gbs, "lookup_frac": look_gbs / peak},
+                     "traffic": traffic, "algorithmic_bytes_per_launch": q_bytes, "cubes_per_launch": cubes,
+                     "kernel_ms": float(np.mean(main_ms))},
+        "other_kernels": {"propagate_gbs": prop_gbs, "propagate_frac": prop_gbs / peak, "propagate_bytes": prop_bytes,
+                          "propagate_storage": storage,
+                          "lookup_gbs": look_gbs, "lookup_frac": look_gbs / peak, "lookup_bytes": look_bytes},
         "graph": {"nodes": info["num_nodes"], "depth": info["depth"], "levels": info["levels"],
                   "build_ms": info["build_ms"], "device_bytes": info["device_bytes"],
-                  "max_list": info["max_list"], "pairs": info["pairs"]},
-        "e2e": e2e,
+                  "max_list": info["max_list"], "pairs": info["pairs"], "lut_entries": info["lut_entries"]},
+        "e2e": e2e_rec,
         "autotune": tune,
         "query_path": "captured plan (one CUDA graph launch per batch)" if use_plan else "direct calls",
-        "forms": forms,
-        "serving": served,
-        "large_graphs": large,
-        "gpu_launches": args.steps * (launches_prop + launches_query + 1),
         "clocks": clk,
         "wall_s_timed": wall,
     }
+    # one persistent propagation launch (depth within the single pass), the lookup, and the query:
+    # batch size and io slots, tile reset, fused plan kernel, main kernel (plans)
+    launches_prop = 1 if info["depth"] + 1 <= 64 else 1 + sum(
+        1 for d in range(1, info["depth"] + 1) if info["bucket"][d + 1] > info["bucket"][d])
+    if args.schedule == "batched" and use_plan:
+        launches_query = 4
+    elif args.schedule == "batched":
+        nscan = 1 if Q <= 2048 else 3
+        launches_query = 1 + (1 if Q <= (1 << 18) else 2 * nscan + 1) + 1 + 1
+    else:
+        launches_query = Q
+    res["gpu_launches"] = args.steps * (launches_prop + launches_query + 1)
+    if plan is not None:
+        plan.close()
+    return res
+
+
+def end_to_end(mg, g, boxes_h, tf_h, smp_h, storage, Q, S, P, esz, args, dev, stream, flush, world, use_plan,
+               qkw):
+    """The step through the public API with host buffers: every step copies its
+    boxes, TF and samples in from pinned memory and its histograms and colours
+    out.  Pipelined: three lanes take steps in turn, so a step's copies overlap
+    the other lanes' kernels.  Serial: one lane, each step on its own with the
+    L2 flushed before it (the footing of `value`)."""
+    import torch
+    from paper_2009_02702_gb300 import mg as _mg
+    dt = _mg._DTYPES[storage][1]
+    boxes_p = torch.from_numpy(boxes_h).pin_memory()
+    tf_p = torch.from_numpy(tf_h).pin_memory()
+    smp_p = torch.from_numpy(smp_h).pin_memory()
+
+    class Lane:
+        """Boxes -> queries -> histograms on its query stream, TF and samples ->
+        propagation -> lookup -> colours on its frame stream, each with its own
+        buffers (and query plan, whose buffers a run owns until it ends)."""
+
+        def __init__(self):
+            self.qs, self.fs = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+            self.boxes = torch.empty((Q, 6), dtype=torch.int32, device=dev)
+            self.tf = torch.empty((S, 4), dtype=torch.float32, device=dev)
+            self.smp = torch.empty((P, 4), dtype=torch.float32, device=dev)
+            self.vals = torch.empty((g.N, 4), dtype=dt, device=dev)
+            self.look = torch.empty((P, 4), dtype=dt, device=dev)
+            self.hist = torch.empty((Q, S), dtype=torch.uint32, device=dev)
+            self.hist_p = torch.empty((Q, S), dtype=torch.uint32).pin_memory()
+            self.look_p = torch.empty((P, 4), dtype=dt).pin_memory()
+            self.plan = mg.QueryPlan(g, max_Q=Q, chunk_cubes=args.chunk,
+                                     block_threads=args.threads) if use_plan else None
+
+        def step(self):
+            with torch.cuda.stream(self.fs):
+                self.tf.copy_(tf_p, non_blocking=True)
+                self.smp.copy_(smp_p, non_blocking=True)
+            mg.mg_propagate_tf(g, self.tf, storage=storage, out=self.vals, stream=self.fs)
+            mg.mg_render_lookup(g, self.vals, self.smp, out=self.look, stream=self.fs)
+            with torch.cuda.stream(self.fs):
+                self.look_p.copy_(self.look, non_blocking=True)
+            with torch.cuda.stream(self.qs):
+                self.boxes.copy_(boxes_p, non_blocking=True)
+            if self.plan is not None:
+                self.plan.run(self.boxes, out=self.hist, stream=self.qs)
+            else:
+                mg.mg_query_boxes(g, self.boxes, out=self.hist, stream=self.qs, **qkw)
+            with torch.cuda.stream(self.qs):
+                self.hist_p.copy_(self.hist, non_blocking=True)
+
+        def streams(self):
+            return (self.qs, self.fs)
+
+        def close(self):
+            if self.plan is not None:
+                self.plan.close()
+
+    def window(lanes, steps, flushed):
+        e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_start.record(stream)
+        for ln in lanes:
+            for st_ in ln.streams():
+                st_.wait_event(e_start)
+        ms = 0.0
+        for k in range(steps):
+            ln = lanes[k % len(lanes)]
+            if flushed:
+                # each step alone: flush the L2, then time from its first copy to its last
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for st_ in ln.streams():
+                    st_.wait_event(a)
+            ln.step()
+            if flushed:
+                for st_ in ln.streams():
+                    ev_ = torch.cuda.Event()
+                    ev_.record(st_)
+                    stream.wait_event(ev_)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms += a.elapsed_time(b)
+        for ln in lanes:
+            for st_ in ln.streams():
+                ev_ = torch.cuda.Event()
+                ev_.record(st_)
+                stream.wait_event(ev_)
+        e_end.record(stream)
+        torch.cuda.synchronize()
+        return ms if flushed else float(e_start.elapsed_time(e_end))
+
+    lanes = [Lane() for _ in range(3)]
+    for k in range(6):
+        lanes[k % 3].step()
+    torch.cuda.synchronize()
+    e_ms = max_over_ranks(window(lanes, args.steps, False), world, dev)
+    s_ms = max_over_ranks(window(lanes[:1], args.steps, True), world, dev)
+    for ln in lanes:
+        ln.close()
+    return {"value": whole_job_rate(world, Q, e_ms / args.steps), "unit": UNIT,
+            "h2d_bytes_per_step": int(boxes_h.nbytes + tf_h.nbytes + smp_h.nbytes),
+            "d2h_bytes_per_step": int(Q * S * 4 + P * 4 * esz), "ms_per_step": e_ms / args.steps,
+            "timing": "one window over all steps on three lanes taking steps in turn (query and frame streams "
+                      "each), joined at its end: a step's copies overlap the other lanes' kernels",
+            "l2": "not flushed in the pipelined window (a step reads far more distinct IDs than the 129 MB L2)",
+            "serial_flushed": {"value": whole_job_rate(world, Q, s_ms / args.steps), "unit": UNIT,
+                               "ms_per_step": s_ms / args.steps,
+                               "timing": "one lane, each step alone: L2 flushed, copies in, kernels, copies out"}}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2009_02702_gb300 import mg
+
+    world, rank, local = rank_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peak, peak_src = load_peak()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    cfg_i = args.config
+    cfg = synth.CONFIGS[cfg_i]
+    S = cfg["S"]
+    Q = args.queries or cfg["queries"]
+    dims = cfg["dims"]
+    storage = args.storage or ("f16" if cfg_i == 3 else "f32")
+
+    g, gen_s = build_graph(mg, cfg_i, dev)
+    boxes_h = rank_boxes(cfg_i, Q, rank)
+    head = measure_step(mg, g, cfg_i, boxes_h, storage, args, dev, flush, stream, world, peak, peak_src,
+                        clocks_index=local, e2e=not args.no_e2e)
+    head["graph"]["volume_generation_s"] = gen_s
+    boxes = torch.from_numpy(boxes_h).to(dev)
+
+    forms = None
+    if not args.no_forms:
+        forms = other_forms(mg, g, boxes, boxes_h, Q, S, dims, cfg_i, flush, stream, peak)
+        forms["storage_types"] = storage_forms(mg, g, cfg_i, flush, stream, peak)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg_i, boxes_h, args.cpu_boxes)
+
+    secondary = None
+    graphs = {cfg_i: g}
+    if args.secondary and rank == 0 and args.secondary != cfg_i:
+        c2 = args.secondary
+        g2, gen2 = build_graph(mg, c2, dev)
+        graphs[c2] = g2
+        b2 = synth.make_boxes(c2)
+        secondary = measure_step(mg, g2, c2, b2, "f32", args, dev, flush, stream, 1, peak, peak_src,
+                                 e2e=not args.no_e2e)
+        secondary["graph"]["volume_generation_s"] = gen2
+        if not args.no_cpu_baseline:
+            secondary["cpu_baseline"] = cpu_baseline(c2, b2, args.cpu_boxes, tf=synth.make_tf(c2, synth.CONFIGS[c2]["S"], 4))
+
+    served = None
+    if not args.no_serve and rank == 0:
+        served = serving(mg, graphs, args, dev)
+
+    large = None
+    if not args.no_large and rank == 0:
+        large = cylinder_workload(mg, dev, flush, stream, peak)
+
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 counts / %s colours (f32 math)" % storage, "data": "synthetic",
+        "config": workload_config(cfg_i, Q, args, storage),
+    }
+    for k in ("tf_propagations_per_s", "samples_per_s", "latency_ms", "stages_ms", "roofline_nominal", "roofline",
+              "other_kernels", "graph", "e2e", "autotune", "query_path", "gpu_launches", "clocks", "wall_s_timed"):
+        line[k] = head[k]
+    line["forms"] = forms
+    line["secondary"] = secondary
+    line["serving"] = served
+    line["cylinders"] = large
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line))
-    if plan is not None:
-        plan.close()
-    g.close()
+    for c, gg in graphs.items():
+        gg.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -571,15 +691,46 @@ def storage_errors(mg, g, tf, vol_h, dims, S, nsample=1500, seed=5, block=None, 
     return {dt: {"max_abs": float(np.max(v)), "mean_abs": float(np.mean(v))} for dt, v in errs.items()}
 
 
-def other_forms(mg, g, boxes, boxes_h, tf, vals, Q, S, dims, cfg_i, flush, stream):
+def error_sample(boxes_h, dims, n, seed):
+    """n boxes of the batch spread over its size range: equal numbers from each
+    decile of clipped volume (seeded)."""
+    d = np.array(dims, np.int64)
+    side = np.minimum(boxes_h[:, :3].astype(np.int64) + boxes_h[:, 3:], d) - boxes_h[:, :3]
+    vol = side.prod(axis=1)
+    order = np.argsort(vol, kind="stable")
+    rng = np.random.default_rng(seed)
+    parts = np.array_split(order, 10)
+    pick = np.concatenate([rng.choice(p, size=min(len(p), n // 10), replace=False) for p in parts])
+    return np.sort(pick), vol
+
+
+def other_forms(mg, g, boxes, boxes_h, Q, S, dims, cfg_i, flush, stream, peak, n_err=500):
+    """The batch in the other forms: direct calls (u32, f32, f32 with 16-bit
+    weights) with their error against the oracle's brute-force counts on
+    n_err boxes across the size range, the plain one-launch-per-box form and
+    the naive level-0 count."""
     import torch
+    import oracle
     out = {}
     hist = torch.empty((Q, S), dtype=torch.uint32, device=boxes.device)
     histf = torch.empty((Q, S), dtype=torch.float32, device=boxes.device)
     ms = _time(lambda: mg.mg_query_boxes(g, boxes, out=hist), 5, flush, stream)
     out["batched_direct_u32"] = {"queries_per_s": Q / (ms / 1e3), "ms": ms}
-    ms = _time(lambda: mg.mg_query_boxes(g, boxes, out=histf, hist="f32"), 5, flush, stream)
-    out["batched_direct_f32"] = {"queries_per_s": Q / (ms / 1e3), "ms": ms}
+    pick, vol = error_sample(boxes_h, dims, n_err, 21)
+    vol_h = synth.make_volume(cfg_i)
+    ref = oracle.box_hist(vol_h, S, boxes_h[pick]).astype(np.float64)
+    del vol_h
+    hu = hist.cpu().numpy()[pick]
+    out["batched_direct_u32"]["exact_vs_oracle"] = {"boxes": int(len(pick)), "equal": bool(np.array_equal(hu, ref))}
+    for name, alpha in (("batched_direct_f32", "f32"), ("batched_direct_f32_alpha_f16", "f16"),
+                        ("batched_direct_f32_alpha_bf16", "bf16")):
+        ms = _time(lambda: mg.mg_query_boxes(g, boxes, out=histf, hist="f32", alpha=alpha), 5, flush, stream)
+        h = histf.cpu().numpy()[pick].astype(np.float64)
+        rel = np.abs(h - ref).sum(axis=1) / vol[pick]
+        out[name] = {"queries_per_s": Q / (ms / 1e3), "ms": ms,
+                     "rel_l1_error_vs_oracle": {"max": float(rel.max()), "mean": float(rel.mean()),
+                                                "boxes": int(len(pick)),
+                                                "box_voxels": [int(vol[pick].min()), int(vol[pick].max())]}}
     n = min(Q, 1000)
     sub = boxes[:n].contiguous()
     hs = torch.empty((n, S), dtype=torch.float32, device=boxes.device)
@@ -587,121 +738,86 @@ def other_forms(mg, g, boxes, boxes_h, tf, vals, Q, S, dims, cfg_i, flush, strea
     out["plain_one_launch_per_box_f32"] = {"queries_per_s": n / (ms / 1e3), "ms": ms, "boxes": n}
     hn = torch.empty((n, S), dtype=torch.uint32, device=boxes.device)
     ms = _time(lambda: mg.mg_query_boxes(g, sub, out=hn, schedule="naive"), 3, flush, stream)
-    out["naive_gpu_level0_u32"] = {"queries_per_s": n / (ms / 1e3), "ms": ms, "boxes": n}
-    for alpha in ("f16", "bf16"):
-        ms = _time(lambda: mg.mg_query_boxes(g, boxes, out=histf, hist="f32", alpha=alpha), 5, flush, stream)
-        out["batched_direct_f32_alpha_%s" % alpha] = {"queries_per_s": Q / (ms / 1e3), "ms": ms}
-    # 16-bit storage of the propagated values (A9)
-    for dt in ("f16", "bf16"):
-        v16 = torch.empty((g.N, vals.shape[1]), dtype=torch.float16 if dt == "f16" else torch.bfloat16,
-                          device=vals.device)
-        ms = _time(lambda: mg.mg_propagate_tf(g, tf, storage=dt, out=v16), 10, flush, stream)
-        out["propagate_%s_ms" % dt] = ms
-    vol_h = synth.make_volume(cfg_i, device="cpu") if max(dims) <= 1024 else None
-    if vol_h is not None:
-        out["storage_error_vs_fp64"] = storage_errors(mg, g, tf, vol_h, dims, S)
+    nv = int(vol[:n].sum())
+    out["naive_gpu_level0_u32"] = {"queries_per_s": n / (ms / 1e3), "ms": ms, "boxes": n,
+                                   "gbs": 2 * nv / (ms / 1e3) / 1e9, "frac": 2 * nv / (ms / 1e3) / 1e9 / peak}
     return out
 
 
-# --------------------------------------------------------------------------
-# propagation, lookup and 16-bit storage on the larger graphs
-# --------------------------------------------------------------------------
-def large_workloads(mg, dev, flush, stream, peak, nsample=400):
-    """The 2048x2048x300 graph (FP16 weights and colours, 100,000 boxes) and the
-    cylinder graph (BF16 attribute TF, 1920x1080 frame): propagation and lookup
-    rates against the HBM peak for each storage type, errors against fp64 on
-    sampled voxels (host generator / host volume), and for 2048x2048x300 the
-    batched query with fp32 and fp16 weights (error against the brute-force
-    counts of sampled boxes)."""
+def storage_forms(mg, g, cfg_i, flush, stream, peak, nsample=400):
+    """Propagation and lookup for each node-value storage type against the HBM
+    peak, with the error of each against fp64 on sampled voxels (host volume)."""
     import torch
-    import oracle
-    out = {}
-    for cfg_i in (3, 4):
-        c = synth.CONFIGS[cfg_i]
-        S = c["S"]
-        t0 = time.perf_counter()
-        vol_h = None
-        if c["kind"] == "voronoi":
-            vol = synth.make_volume(cfg_i, device=dev)
-            block = lambda o, sd, ci=cfg_i: synth.voronoi_window(ci, o, sd)
-        else:
-            vol_h = synth.make_volume(cfg_i)
-            vol = torch.from_numpy(vol_h).to(dev)
-            block = None
-        torch.cuda.synchronize()
-        gen_s = time.perf_counter() - t0
-        g = mg.mg_build(vol, S)
-        del vol
-        info = g.info
-        tf_h = synth.make_attribute_tf(cfg_i, S) if cfg_i == 4 else synth.make_tf(cfg_i, S, 4)
-        tf = torch.from_numpy(tf_h).to(dev)
-        smp = torch.from_numpy(synth.make_samples(cfg_i)).to(dev)
-        P = smp.shape[0]
-        r = {"workload": c["name"], "nodes": info["num_nodes"], "depth": info["depth"], "levels": info["levels"],
-             "build_ms": info["build_ms"], "device_bytes": info["device_bytes"], "lut_entries": info["lut_entries"],
-             "volume_generation_s": gen_s, "tf": "attribute RGBA (opacity x |axis.view|)" if cfg_i == 4 else "RGBA"}
-        NI = info["num_nodes"] - S
-        for st, dt, esz in (("f32", torch.float32, 4), ("f16", torch.float16, 2), ("bf16", torch.bfloat16, 2)):
-            vals = torch.empty((g.N, 4), dtype=dt, device=dev)
-            look = torch.empty((P, 4), dtype=dt, device=dev)
-            ms_p = _time(lambda: mg.mg_propagate_tf(g, tf, storage=st, out=vals), 10, flush, stream)
-            ms_l = _time(lambda: mg.mg_render_lookup(g, vals, smp, out=look), 10, flush, stream)
-            # algorithmic bytes: edges 8 + weight (4 or 2) + value row out per node; rows in per source
-            pb = NI * (8 + (4 if st == "f32" else 2) + 4 * esz) + S * (16 + 4 * esz)
-            lb = P * (16 + 4 + 8 * esz)
-            r["propagate_" + st] = {"ms": ms_p, "gbs": pb / ms_p / 1e6, "frac": pb / ms_p / 1e6 / peak,
-                                    "bytes": pb}
-            r["lookup_" + st] = {"ms": ms_l, "samples_per_s": P / (ms_l / 1e3), "gbs": lb / ms_l / 1e6,
-                                 "frac": lb / ms_l / 1e6 / peak}
-        dims = c["dims"]
-        r["storage_error_vs_fp64"] = storage_errors(mg, g, tf, vol_h, dims, S, nsample=nsample, seed=11,
-                                                    block=block, max_level=4)
-        if cfg_i == 4:
-            # many segments: the CTA-shared histogram kernel, exact u32
-            boxes_h = synth.make_boxes(4)
-            boxes = torch.from_numpy(boxes_h).to(dev)
-            Q = boxes_h.shape[0]
-            tune = mg.mg_query_autotune(g, boxes)
-            plan = mg.QueryPlan(g, max_Q=Q)
-            res = torch.empty((Q, S), dtype=torch.uint32, device=dev)
-            ms = _time(lambda: plan.run(boxes, out=res), 5, flush, stream)
-            mg.mg_sync_status(g)
-            plan.close()
-            r["queries"] = {"boxes": Q, "u32": {"ms": ms, "queries_per_s": Q / (ms / 1e3)}, "autotune": tune}
-        if cfg_i == 3:
-            boxes_h = synth.make_boxes(3)
-            boxes = torch.from_numpy(boxes_h).to(dev)
-            Q = boxes_h.shape[0]
-            q = {"boxes": Q}
-            for name, hist, alpha in (("u32", "u32", "f32"), ("f32", "f32", "f32"), ("f32_alpha_f16", "f32", "f16")):
-                mg.mg_query_autotune(g, boxes, hist=hist, alpha=alpha)
-                plan = mg.QueryPlan(g, max_Q=Q, hist=hist, alpha=alpha)
-                res = torch.empty((Q, S), dtype=torch.uint32 if hist == "u32" else torch.float32, device=dev)
-                ms = _time(lambda: plan.run(boxes, out=res), 5, flush, stream)
-                mg.mg_sync_status(g)
-                q[name] = {"ms": ms, "queries_per_s": Q / (ms / 1e3)}
-                if name != "u32":
-                    # relative L1 error of sampled boxes against brute-force counts
-                    rng = np.random.default_rng(12)
-                    d = np.array(dims)
-                    side = np.minimum(boxes_h[:, :3] + boxes_h[:, 3:], d) - boxes_h[:, :3]
-                    vol_q = side.prod(axis=1)
-                    cand = np.flatnonzero(vol_q <= (1 << 18))
-                    errs = []
-                    hres = res.cpu().numpy()
-                    for i in rng.choice(cand, size=min(40, len(cand)), replace=False):
-                        blk = synth.voronoi_window(3, boxes_h[i, :3], side[i])
-                        ref = oracle.box_hist(np.ascontiguousarray(blk), S,
-                                              np.array([[0, 0, 0, *side[i]]], np.int32))[0].astype(np.float64)
-                        errs.append(np.abs(hres[i] - ref).sum() / vol_q[i])
-                    q[name]["rel_l1_error_vs_oracle"] = {"max": float(np.max(errs)), "mean": float(np.mean(errs)),
-                                                         "boxes": len(errs)}
-                plan.close()
-            r["queries"] = q
-        out[c["name"]] = r
-        g.close()
-        del vol_h
-    return out
+    c = synth.CONFIGS[cfg_i]
+    S = c["S"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    info = g.info
+    tf_h = synth.make_attribute_tf(cfg_i, S) if cfg_i == 4 else synth.make_tf(cfg_i, S, 4)
+    tf = torch.from_numpy(tf_h).to(dev)
+    smp = torch.from_numpy(synth.make_samples(cfg_i)).to(dev)
+    P = smp.shape[0]
+    NI = info["num_nodes"] - S
+    r = {}
+    for st, dt, esz in (("f32", torch.float32, 4), ("f16", torch.float16, 2), ("bf16", torch.bfloat16, 2)):
+        vals = torch.empty((g.N, 4), dtype=dt, device=dev)
+        look = torch.empty((P, 4), dtype=dt, device=dev)
+        ms_p = _time(lambda: mg.mg_propagate_tf(g, tf, storage=st, out=vals), 10, flush, stream)
+        ms_l = _time(lambda: mg.mg_render_lookup(g, vals, smp, out=look), 10, flush, stream)
+        pb = NI * (8 + (4 if st == "f32" else 2) + 4 * esz) + S * (16 + 4 * esz)
+        lb = P * (16 + 4 + 8 * esz)
+        r["propagate_" + st] = {"ms": ms_p, "gbs": pb / ms_p / 1e6, "frac": pb / ms_p / 1e6 / peak, "bytes": pb}
+        r["lookup_" + st] = {"ms": ms_l, "samples_per_s": P / (ms_l / 1e3), "gbs": lb / ms_l / 1e6,
+                             "frac": lb / ms_l / 1e6 / peak}
+    vol_h = synth.make_volume(cfg_i)
+    r["storage_error_vs_fp64"] = storage_errors(mg, g, tf, vol_h, c["dims"], S, nsample=nsample, seed=11,
+                                                max_level=4)
+    return r
+
+
+# --------------------------------------------------------------------------
+# the cylinder graph: many segments, attribute TF, bf16 frames
+# --------------------------------------------------------------------------
+def cylinder_workload(mg, dev, flush, stream, peak):
+    """The cylinder graph (15,917 segments, 8.9 M nodes): propagation and
+    lookup per storage type against the HBM peak, errors against fp64 on
+    sampled voxels, and a 10,000-box batch through the CTA-shared histogram
+    kernel, with its own roofline."""
+    import torch
+    cfg_i = 4
+    c = synth.CONFIGS[cfg_i]
+    S = c["S"]
+    g, gen_s = build_graph(mg, cfg_i, dev)
+    info = g.info
+    r = {"workload": c["name"], "nodes": info["num_nodes"], "depth": info["depth"], "levels": info["levels"],
+         "build_ms": info["build_ms"], "device_bytes": info["device_bytes"], "lut_entries": info["lut_entries"],
+         "volume_generation_s": gen_s, "tf": "attribute RGBA (opacity x |axis.view|)"}
+    r.update(storage_forms(mg, g, cfg_i, flush, stream, peak))
+    boxes_h = synth.make_boxes(cfg_i)
+    boxes = torch.from_numpy(boxes_h).to(dev)
+    Q = boxes_h.shape[0]
+    tune = mg.mg_query_autotune(g, boxes)
+    plan = mg.QueryPlan(g, max_Q=Q)
+    res = torch.empty((Q, S), dtype=torch.uint32, device=dev)
+    ms = _time(lambda: plan.run(boxes, out=res), 5, flush, stream)
+    mg.mg_sync_status(g)
+    plan.close()
+    plan_t = mg.QueryPlan(g, max_Q=Q, timing=True)
+    mains = []
+    for _ in range(5):
+        flush.zero_()
+        plan_t.run(boxes, out=res, stream=stream)
+        mains.append(plan_t.timing()[1])
+    plan_t.close()
+    qb, cubes, _ = query_bytes(boxes_h, c["dims"], S)
+    main_ms = float(np.median(mains))
+    kernel = query_kernel_name(S, tune.get("block_threads") or 256)
+    r["queries"] = {"boxes": Q, "u32": {"ms": ms, "queries_per_s": Q / (ms / 1e3)}, "autotune": tune,
+                    "roofline": {"bound": "hbm", "kernel": kernel, "kernel_ms": main_ms,
+                                 "achieved": qb / main_ms / 1e6, "peak": peak, "unit": "GB/s",
+                                 "frac": qb / main_ms / 1e6 / peak, "algorithmic_bytes_per_launch": qb,
+                                 "cubes_per_launch": cubes, "traffic": measured_traffic(kernel, cfg_i, Q)}}
+    g.close()
+    return r
 
 
 # --------------------------------------------------------------------------
@@ -711,7 +827,7 @@ def _pct(x, q):
     return float(np.percentile(x, q)) * 1e3 if len(x) else None
 
 
-def serving(mg, g2, args, dev):
+def serving(mg, have, args, dev):
     """Replay the Poisson mix through the continuously batched server and
     through the plain one-launch-per-box server (both fp32 histograms, so at
     equal accuracy), at the offered rate and as one saturating burst."""
@@ -723,8 +839,8 @@ def serving(mg, g2, args, dev):
     graphs, meta = [], []
     for ci in c5["volumes"]:
         cfg = synth.CONFIGS[ci]
-        if ci == 2:
-            g = g2
+        if ci in have:
+            g = have[ci]
         else:
             vol = synth.make_volume(ci, device=dev)
             torch.cuda.synchronize()
@@ -790,7 +906,7 @@ def serving(mg, g2, args, dev):
     out["batched_over_plain_queries_per_s"] = {m: out["batched"][m]["queries_per_s"] / out["plain"][m]["queries_per_s"]
                                                for m in ("offered", "burst")}
     for g in graphs:
-        if g is not g2:
+        if all(g is not h for h in have.values()):
             g.close()
     return out
 
@@ -822,46 +938,34 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
-def cpu_baseline(cfg_i, boxes, seconds, vol=None, tf=None):
-    """The oracle's brute-force counting timed on the host cores on a bounded
-    sample: the step's boxes, then more boxes of the same recipe, up to about
-    `seconds` of work on all cores, a quarter of that on one core; and the
-    oracle's TF propagation as the direct per-voxel sum over sampled levels."""
+def cpu_baseline(cfg_i, boxes, n_boxes, vol=None, tf=None):
+    """The oracle's brute-force counting timed on the host cores on a seeded
+    sample of the step's boxes (n_boxes of them on all cores, a tenth on one
+    core); with tf, also the oracle's TF propagation as the direct per-voxel
+    sum over levels 1-3 (the paper's 'revisiting every voxel')."""
     import oracle
     cfg = synth.CONFIGS[cfg_i]
     if vol is None:
         vol = _host_volume(cfg_i)
     all_threads = oracle.set_threads(0)
-
-    def sample_of(n):
-        smp, k = boxes, 1
-        while len(smp) < n:
-            smp = np.concatenate([smp, synth.make_boxes(cfg_i, Q=len(boxes), stream_offset=1000 + k)])
-            k += 1
-        return smp[:n]
-
-    def timed(secs):
-        n = min(2000, len(boxes))   # calibration sample (box sizes vary widely)
-        t0 = time.perf_counter()
-        oracle.box_hist(vol, cfg["S"], boxes[:n])
-        dt = time.perf_counter() - t0
-        smp = sample_of(int(max(n, n * secs / max(dt, 1e-6))))
-        t0 = time.perf_counter()
-        oracle.box_hist(vol, cfg["S"], smp)
-        return len(smp), time.perf_counter() - t0
-
-    n_all, t_all = timed(seconds)
+    rng = np.random.default_rng(1000 + cfg_i)
+    n = min(n_boxes, len(boxes))
+    smp = boxes[np.sort(rng.choice(len(boxes), size=n, replace=False))]
+    t0 = time.perf_counter()
+    oracle.box_hist(vol, cfg["S"], smp)
+    t_all = time.perf_counter() - t0
     oracle.set_threads(1)
-    n_one, t_one = timed(seconds / 4)
+    n1 = max(1, n // 10)
+    t0 = time.perf_counter()
+    oracle.box_hist(vol, cfg["S"], smp[:n1])
+    t_one = time.perf_counter() - t0
     oracle.set_threads(all_threads)
-    res = {"value": n_all / t_all, "unit": UNIT, "cores": all_threads, "kind": "oracle",
-           "sample": "%d boxes (the step's %d, then more of the same recipe), brute-force level-0 counting "
-                     "(OpenMP over boxes), %.1f s" % (n_all, len(boxes), t_all),
-           "single_thread": {"value": n_one / t_one, "unit": UNIT, "boxes": n_one, "seconds": t_one},
+    res = {"value": n / t_all, "unit": UNIT, "cores": all_threads, "kind": "oracle",
+           "sample": "seeded %d-box subset of the step's %d boxes, brute-force level-0 counting "
+                     "(OpenMP over boxes), %.1f s" % (n, len(boxes), t_all),
+           "single_thread": {"value": n1 / t_one, "unit": UNIT, "boxes": n1, "seconds": t_one},
            "cpu_model": cpu_model()}
     if tf is not None:
-        # the paper's 'revisiting every voxel': mixture and fp64 colour of every
-        # voxel of a level, timed on levels 1-3 and scaled to the whole mipmap
         dims = oracle.level_dims(*cfg["dims"])
         vox_all = int(np.prod(dims[1:], axis=1).sum())
         n_vox, t_vox = 0, 0.0
@@ -885,11 +989,11 @@ def run_reference(args):
     import oracle
     vol = _host_volume(cfg_i)
     boxes = synth.make_boxes(cfg_i, Q=Q)
-    # size one step to ~6 s of host work
+    # size one step to ~4 s of host work (calibrated on 200 boxes: sizes vary widely)
     t0 = time.perf_counter()
-    oracle.box_hist(vol, cfg["S"], boxes[:40])
+    oracle.box_hist(vol, cfg["S"], boxes[:200])
     dt = time.perf_counter() - t0
-    n = int(min(Q, max(40, 40 * 6.0 / max(dt, 1e-6))))
+    n = int(min(Q, max(200, 200 * 4.0 / max(dt, 1e-6))))
     times = []
     for k in range(max(args.warmup, 3) + args.steps):
         sl = boxes[(k * n) % Q:][:n]
@@ -901,12 +1005,12 @@ def run_reference(args):
             times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     value = n / (ms / 1e3)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.set_threads(0)
     sample = "%d of the %d boxes per step, brute-force level-0 counting (OpenMP over boxes)" % (n, Q)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32 counts", "data": "synthetic", "impl": "reference",
-            "config": workload_config(cfg_i, Q, args),
+            "config": workload_config(cfg_i, Q, args, args.storage or ("f16" if cfg_i == 3 else "f32")),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

@@ -19,10 +19,10 @@
 #include <math.h>
 
 /* The ex x ey x ez block of the volume starting at voxel (x0, y0, z0),
- * x-fastest; the whole volume is the block at the origin with its dims. */
-void mgs_voronoi_block(int64_t x0, int64_t y0, int64_t z0, int64_t ex, int64_t ey, int64_t ez,
-                       const int64_t *seeds2, const int64_t *weight, int64_t K, const int64_t *metric,
-                       int out_bytes, void *out)
+ * x-fastest, every voxel tested against every seed (the rule as stated). */
+void mgs_voronoi_block_brute(int64_t x0, int64_t y0, int64_t z0, int64_t ex, int64_t ey, int64_t ez,
+                             const int64_t *seeds2, const int64_t *weight, int64_t K, const int64_t *metric,
+                             int out_bytes, void *out)
 {
     #pragma omp parallel for collapse(2) schedule(static)
     for (int64_t z = 0; z < ez; z++) {
@@ -41,6 +41,79 @@ void mgs_voronoi_block(int64_t x0, int64_t y0, int64_t z0, int64_t ex, int64_t e
                 else ((uint32_t *)out)[v] = (uint32_t)best;
             }
         }
+    }
+}
+
+/* Squared metric distance from seed coordinate s to the nearest (mode 0) or
+ * farthest (mode 1) of the doubled centres lo..hi along one axis. */
+static int64_t axis_bound(int64_t s, int64_t lo, int64_t hi, int mode)
+{
+    int64_t a = s - lo < 0 ? lo - s : s - lo, b = s - hi < 0 ? hi - s : s - hi;
+    if (mode == 1) return a > b ? a * a : b * b;
+    if (s >= lo && s <= hi) return 0;
+    return a < b ? a * a : b * b;
+}
+
+#define MGS_TILE 16
+
+/* The same block, tile by tile: for a tile of voxels, seed i's ratio d_i/W_i
+ * at any voxel lies in [lo_i/W_i, hi_i/W_i] (nearest / farthest centre of the
+ * tile).  With j the seed of the smallest hi_j/W_j, every voxel's best ratio is
+ * at most hi_j/W_j, so a seed with lo_i/W_i > hi_j/W_j is strictly worse than
+ * the best everywhere in the tile: it can neither win nor tie.  The remaining
+ * seeds, in index order, go through the rule as stated, which therefore picks
+ * the same seed as the brute force for every voxel. */
+void mgs_voronoi_block(int64_t x0, int64_t y0, int64_t z0, int64_t ex, int64_t ey, int64_t ez,
+                       const int64_t *seeds2, const int64_t *weight, int64_t K, const int64_t *metric,
+                       int out_bytes, void *out)
+{
+    int64_t tx = (ex + MGS_TILE - 1) / MGS_TILE, ty = (ey + MGS_TILE - 1) / MGS_TILE;
+    int64_t tz = (ez + MGS_TILE - 1) / MGS_TILE;
+    int64_t ntiles = tx * ty * tz;
+    #pragma omp parallel
+    {
+        int64_t *cand = (int64_t *)malloc((size_t)(K > 0 ? K : 1) * sizeof(int64_t));
+        int64_t *lob = (int64_t *)malloc((size_t)(K > 0 ? K : 1) * sizeof(int64_t));
+        #pragma omp for schedule(dynamic, 4)
+        for (int64_t t = 0; t < ntiles; t++) {
+            int64_t bx = (t % tx) * MGS_TILE, by = ((t / tx) % ty) * MGS_TILE, bz = (t / (tx * ty)) * MGS_TILE;
+            int64_t wx = ex - bx < MGS_TILE ? ex - bx : MGS_TILE;
+            int64_t wy = ey - by < MGS_TILE ? ey - by : MGS_TILE;
+            int64_t wz = ez - bz < MGS_TILE ? ez - bz : MGS_TILE;
+            int64_t lo[3] = {2 * (x0 + bx) + 1, 2 * (y0 + by) + 1, 2 * (z0 + bz) + 1};
+            int64_t hi[3] = {lo[0] + 2 * (wx - 1), lo[1] + 2 * (wy - 1), lo[2] + 2 * (wz - 1)};
+            int64_t j = -1, hj = 0, wj = 1;
+            for (int64_t i = 0; i < K; i++) {
+                int64_t h = 0, l = 0;
+                for (int k = 0; k < 3; k++) {
+                    h += metric[k] * axis_bound(seeds2[3 * i + k], lo[k], hi[k], 1);
+                    l += metric[k] * axis_bound(seeds2[3 * i + k], lo[k], hi[k], 0);
+                }
+                lob[i] = l;
+                if (j < 0 || h * wj < hj * weight[i]) { j = i; hj = h; wj = weight[i]; }
+            }
+            int64_t nc = 0;
+            for (int64_t i = 0; i < K; i++)
+                if (!(lob[i] * wj > hj * weight[i])) cand[nc++] = i;
+            for (int64_t z = bz; z < bz + wz; z++)
+            for (int64_t y = by; y < by + wy; y++)
+            for (int64_t x = bx; x < bx + wx; x++) {
+                int64_t px = 2 * (x0 + x) + 1, py = 2 * (y0 + y) + 1, pz = 2 * (z0 + z) + 1;
+                int64_t best = 0, bd = -1, bw = 1;
+                for (int64_t c = 0; c < nc; c++) {
+                    int64_t i = cand[c];
+                    int64_t dx = px - seeds2[3 * i], dy = py - seeds2[3 * i + 1], dz = pz - seeds2[3 * i + 2];
+                    int64_t d = metric[0] * dx * dx + metric[1] * dy * dy + metric[2] * dz * dz;
+                    int64_t w = weight[i];
+                    if (bd < 0 || d * bw < bd * w) { best = i; bd = d; bw = w; }
+                }
+                int64_t v = (z * ey + y) * ex + x;
+                if (out_bytes == 2) ((uint16_t *)out)[v] = (uint16_t)best;
+                else ((uint32_t *)out)[v] = (uint32_t)best;
+            }
+        }
+        free(cand);
+        free(lob);
     }
 }
 

@@ -75,6 +75,7 @@ def _host_lib():
         P, i64 = ctypes.c_void_p, ctypes.c_int64
         lib.mgs_voronoi.argtypes = [i64, i64, i64, P, P, i64, P, ctypes.c_int, P]
         lib.mgs_voronoi_block.argtypes = [i64, i64, i64, i64, i64, i64, P, P, i64, P, ctypes.c_int, P]
+        lib.mgs_voronoi_block_brute.argtypes = lib.mgs_voronoi_block.argtypes
         lib.mgs_cylinders.argtypes = [i64, i64, i64, i64, i64, P, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, P]
         lib.mgs_cylinders.restype = i64

@@ -27,18 +27,30 @@ def test_cube_census_matches_the_oracle_footprint():
 
 def test_traffic_record_applies_only_to_its_source_and_workload():
     with open(os.path.join(bench.ROOT, "profiles", "traffic.json")) as f:
-        rec = json.load(f)["query_warp_kernel"]
-    Q = synth.CONFIGS[2]["queries"]
-    t = bench.measured_traffic("query_warp_kernel", 2, Q)
-    assert t is None or t == rec["dram_bytes_per_launch"]
-    assert bench.measured_traffic("query_warp_kernel", 3, Q) is None
-    assert bench.measured_traffic("query_warp_kernel", 2, Q + 1) is None
-    assert bench.measured_traffic("no_such_kernel", 2, Q) is None
+        recs = json.load(f)["records"]
+    assert recs
+    for rec in recs:
+        k, c, Q = rec["kernel"], rec["config"], rec["queries"]
+        t = bench.measured_traffic(k, c, Q)
+        assert t is None or t == rec["dram_bytes_per_launch"]
+        assert bench.measured_traffic(k, c, Q + 1) is None
+        assert bench.measured_traffic(k, 99, Q) is None
+        assert bench.measured_traffic("no_such_kernel", c, Q) is None
+
+
+def test_error_sample_spans_the_size_range():
+    boxes = synth.make_boxes(3)
+    pick, vol = bench.error_sample(boxes, synth.CONFIGS[3]["dims"], 500, 21)
+    assert len(pick) == 500 and len(np.unique(pick)) == 500
+    # every decile of box volume contributes, so the largest boxes are in it
+    assert vol[pick].max() >= np.percentile(vol, 90) and vol[pick].min() <= np.percentile(vol, 10)
 
 
 def test_command_line_defaults_fit_the_contract():
     a = bench.parse([])
     assert a.gpus == 1 and a.steps >= 1 and a.warmup >= 3
+    # the headline is the largest single-GPU workload: 2048x2048x300, 100,000 boxes
+    assert a.config == 3 and synth.CONFIGS[a.config]["queries"] == 100000 and a.secondary == 2
     r = bench.parse(["--impl", "reference", "--steps", "2", "--warmup", "3"])
     assert r.impl == "reference" and r.steps == 2
     assert bench.whole_job_rate(1, 10000, 0.5) == 10000 / 0.5e-3

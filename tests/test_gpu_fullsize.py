@@ -8,7 +8,9 @@ outputs the oracle computes one by one -- box histograms by brute-force
 counting over the box's voxels, and voxel / ray-sample colours as the direct
 fp64 sum over the voxel's footprint (Sec. 3.4).  The oracle's voxels come
 from the host generators (a window of the volume, or the whole volume), never
-from the GPU.
+from the GPU.  Besides the sampled boxes, the ten largest boxes of every batch
+and whole-volume boxes appended to it are compared element by element with
+the oracle's brute-force counts over the host volume.
 """
 import numpy as np
 import pytest
@@ -85,13 +87,29 @@ def run_plan(mg, g, boxes_d, hist, key, alpha="f32"):
     return res
 
 
-def check_counts(h, boxes, dims, win, S, n, max_voxels, seed):
+def largest_boxes(boxes, dims, k, extra=0):
+    """The k boxes of the batch with the largest clipped volume, plus the last
+    `extra` rows (boxes appended to the batch)."""
+    _, side = clipped(boxes, dims)
+    body = len(boxes) - extra
+    big = np.argsort(side[:body].prod(axis=1), kind="stable")[::-1][:k]
+    return np.concatenate([big, np.arange(body, len(boxes))])
+
+
+def check_counts(h, boxes, dims, win, S, n, max_voxels, seed, vol_h=None, extra=0):
     _, side = clipped(boxes, dims)
     sums = h.astype(np.uint64).sum(axis=1)
     assert np.array_equal(sums, side.prod(axis=1).astype(np.uint64))
     for i in sample_boxes(boxes, dims, n, max_voxels, seed):
         ref = win.hist(boxes[i, :3], side[i], S)
         assert np.array_equal(h[i], ref), i
+    if vol_h is not None:
+        # the largest footprints (highest mip levels, longest run lists) and
+        # the appended whole-volume boxes, element by element
+        idx = largest_boxes(boxes, dims, 10, extra)
+        ref = oracle.box_hist(vol_h, S, boxes[idx])
+        for k, i in enumerate(idx):
+            assert np.array_equal(h[i], ref[k]), (int(i), boxes[i].tolist())
 
 
 def voxel_colour_checks(mg, g, vals, win, tf, dims, S, levels, per_level, seed, check):
@@ -154,26 +172,45 @@ def cfg2(mg):
     g.close()
 
 
-def test_cfg2_full_batch_u32_exact(mg, cfg2):
+@pytest.fixture(scope="module")
+def vol2():
+    return synth.make_volume(2)
+
+
+def with_whole_volume(boxes, dims):
+    """The batch with two boxes appended: the whole volume, and the volume
+    less one voxel on every face (odd origins: runs rise and fall on every
+    axis)."""
+    nx, ny, nz = dims
+    extra = np.array([[0, 0, 0, nx, ny, nz], [1, 1, 1, nx - 2, ny - 2, nz - 2]], np.int32)
+    return np.ascontiguousarray(np.concatenate([boxes, extra])), len(extra)
+
+
+def test_cfg2_full_batch_u32_exact(mg, cfg2, vol2):
     g, c = cfg2
-    boxes = synth.make_boxes(2)
+    boxes, extra = with_whole_volume(synth.make_boxes(2), c["dims"])
     h = run_plan(mg, g, torch.from_numpy(boxes).cuda(), "u32", c["name"])
-    check_counts(h, boxes, c["dims"], Windows(2), c["S"], 40, 1 << 21, 1)
+    check_counts(h, boxes, c["dims"], Windows(2, vol2), c["S"], 40, 1 << 21, 1, vol_h=vol2, extra=extra)
 
 
-def test_cfg2_full_batch_f32_within_tolerance(mg, cfg2):
+def test_cfg2_full_batch_f32_within_tolerance(mg, cfg2, vol2):
     g, c = cfg2
-    boxes = synth.make_boxes(2)
+    boxes, extra = with_whole_volume(synth.make_boxes(2), c["dims"])
     h = run_plan(mg, g, torch.from_numpy(boxes).cuda(), "f32", c["name"])
     _, side = clipped(boxes, c["dims"])
     assert np.allclose(h.astype(np.float64).sum(axis=1), side.prod(axis=1), rtol=1e-5)
-    win = Windows(2)
+    win = Windows(2, vol2)
     for i in sample_boxes(boxes, c["dims"], 24, 1 << 21, 2):
         ok, err = fp32_close(h[i], win.hist(boxes[i, :3], side[i], c["S"]))
         assert ok, (i, err)
+    idx = largest_boxes(boxes, c["dims"], 10, extra)
+    ref = oracle.box_hist(vol2, c["S"], boxes[idx])
+    for k, i in enumerate(idx):
+        ok, err = fp32_close(h[i], ref[k])
+        assert ok, (int(i), err)
 
 
-def test_cfg2_propagate_and_frame(mg, cfg2):
+def test_cfg2_propagate_and_frame(mg, cfg2, vol2):
     g, c = cfg2
     tf = synth.make_tf(2, c["S"], 4)
     vals_d = mg.mg_propagate_tf(g, torch.from_numpy(tf).cuda())
@@ -181,7 +218,7 @@ def test_cfg2_propagate_and_frame(mg, cfg2):
     look = mg.mg_render_lookup(g, vals_d, torch.from_numpy(samples).cuda()).cpu().numpy()
     mg.mg_sync_status(g)
     vals = vals_d.cpu().numpy()
-    win = Windows(2)
+    win = Windows(2, vol2)
     voxel_colour_checks(mg, g, vals, win, tf, c["dims"], c["S"], (0, 1, 3, 5, 7), 12, 3, fp32_check)
     sample_colour_checks(mg, g, look, samples, c["dims"], win, tf, c["S"], 120, 4, fp32_check)
 
@@ -197,14 +234,19 @@ def cfg3(mg):
     g.close()
 
 
-def test_cfg3_full_batch_u32_exact(mg, cfg3):
+@pytest.fixture(scope="module")
+def vol3():
+    return synth.make_volume(3)
+
+
+def test_cfg3_full_batch_u32_exact(mg, cfg3, vol3):
     g, c = cfg3
-    boxes = synth.make_boxes(3)
+    boxes, extra = with_whole_volume(synth.make_boxes(3), c["dims"])
     h = run_plan(mg, g, torch.from_numpy(boxes).cuda(), "u32", c["name"])
-    check_counts(h, boxes, c["dims"], Windows(3), c["S"], 24, 1 << 20, 5)
+    check_counts(h, boxes, c["dims"], Windows(3, vol3), c["S"], 24, 1 << 20, 5, vol_h=vol3, extra=extra)
 
 
-def test_cfg3_fp16_weights_error_bound(mg, cfg3):
+def test_cfg3_fp16_weights_error_bound(mg, cfg3, vol3):
     g, c = cfg3
     boxes = synth.make_boxes(3, Q=20000)
     h = run_plan(mg, g, torch.from_numpy(boxes).cuda(), "f32", c["name"] + "-20k", alpha="f16")
@@ -212,21 +254,22 @@ def test_cfg3_fp16_weights_error_bound(mg, cfg3):
     vol_q = side.prod(axis=1).astype(np.float64)
     assert np.allclose(h.astype(np.float64).sum(axis=1), vol_q, rtol=1e-5)
     D = g.info["depth"]
-    win = Windows(3)
-    for i in sample_boxes(boxes, c["dims"], 16, 1 << 20, 6):
+    win = Windows(3, vol3)
+    idx = np.concatenate([sample_boxes(boxes, c["dims"], 16, 1 << 20, 6), largest_boxes(boxes, c["dims"], 4)])
+    for i in idx:
         ref = win.hist(boxes[i, :3], side[i], c["S"]).astype(np.float64)
         # every pushed unit of weight crosses at most D rounded weights
         assert np.abs(h[i] - ref).sum() <= 1.5 * D * 2.0 ** -11 * vol_q[i] + 1e-3, i
 
 
-def test_cfg3_propagate_f16_storage(mg, cfg3):
+def test_cfg3_propagate_f16_storage(mg, cfg3, vol3):
     g, c = cfg3
     tf = synth.make_tf(3, c["S"], 4)
     v32 = mg.mg_propagate_tf(g, torch.from_numpy(tf).cuda()).cpu().numpy()
     v16 = mg.mg_propagate_tf(g, torch.from_numpy(tf).cuda(), storage="f16").float().cpu().numpy()
     mg.mg_sync_status(g)
     D = g.info["depth"]
-    win = Windows(3)
+    win = Windows(3, vol3)
 
     def f16_check(x, ref, where):
         assert np.abs(np.asarray(x, np.float64) - ref).max() <= (2 * D + 1) * 2.0 ** -11, where
@@ -249,9 +292,9 @@ def cfg4(mg):
 
 def test_cfg4_full_batch_u32_exact(mg, cfg4):
     g, c, vol_h = cfg4
-    boxes = synth.make_boxes(4)
+    boxes, extra = with_whole_volume(synth.make_boxes(4), c["dims"])
     h = run_plan(mg, g, torch.from_numpy(boxes).cuda(), "u32", c["name"])
-    check_counts(h, boxes, c["dims"], Windows(4, vol_h), c["S"], 40, 1 << 23, 8)
+    check_counts(h, boxes, c["dims"], Windows(4, vol_h), c["S"], 40, 1 << 23, 8, vol_h=vol_h, extra=extra)
 
 
 def test_cfg4_bf16_attribute_frame(mg, cfg4):

@@ -4,6 +4,7 @@ checks the Mixture Graph's arithmetic."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_2009_02702_gb300 import synth
 
@@ -80,3 +81,45 @@ def test_request_mix_is_poisson_with_the_stated_mix():
         b = boxes[m]
         assert (b[:, 3:] >= 1).all() and (b[:, :3] + b[:, 3:] <= np.array(d)).all()
     assert (boxes[kind == 1] == 0).all()
+
+
+def _voronoi_pair(dims, K, weighted, metric, seed, origin=(0, 0, 0), extent=None):
+    rng = np.random.default_rng(seed)
+    seeds2, W = synth.voronoi_seeds(dims, K, weighted, rng)
+    ext = extent or dims
+    outs = []
+    for fn in ("mgs_voronoi_block", "mgs_voronoi_block_brute"):
+        out = np.zeros(ext[::-1], np.uint16)
+        m = np.array(metric, np.int64)
+        getattr(synth._host_lib(), fn)(*origin, *ext, seeds2.ctypes.data, W.ctypes.data, K, m.ctypes.data, 2,
+                                       out.ctypes.data)
+        outs.append(out)
+    return outs
+
+
+@pytest.mark.parametrize("dims,K,weighted,metric", [
+    ((53, 41, 37), 40, False, (1, 1, 1)),
+    ((70, 33, 29), 25, True, (1, 1, 1)),
+    ((64, 64, 20), 30, False, (16, 16, 1)),
+    ((17, 90, 16), 300, True, (1, 4, 9)),
+    ((40, 40, 40), 1, False, (1, 1, 1)),
+])
+def test_tiled_voronoi_equals_brute_force(dims, K, weighted, metric):
+    """Pruning seeds per tile changes no voxel, ties included (lowest index)."""
+    fast, brute = _voronoi_pair(dims, K, weighted, metric, seed=K)
+    assert np.array_equal(fast, brute)
+    # an offset window, with tiles cut at its far faces
+    fast, brute = _voronoi_pair(dims, K, weighted, metric, seed=K, origin=(5, 3, 2), extent=(37, 19, 23))
+    assert np.array_equal(fast, brute)
+
+
+def test_tiled_voronoi_ties_go_to_the_lowest_index():
+    # duplicated seeds tie everywhere: the lower index must win each voxel
+    dims = (24, 24, 24)
+    seeds2 = np.array([[10, 10, 10], [30, 30, 30], [10, 10, 10], [30, 30, 30]], np.int64)
+    W = np.ones(4, np.int64)
+    m = np.ones(3, np.int64)
+    out = np.zeros(dims[::-1], np.uint16)
+    synth._host_lib().mgs_voronoi_block(0, 0, 0, *dims, seeds2.ctypes.data, W.ctypes.data, 4, m.ctypes.data, 2,
+                                        out.ctypes.data)
+    assert set(np.unique(out).tolist()) == {0, 1}
