@@ -53,6 +53,8 @@ def parse(argv=None):
     ap.add_argument("--storage", default="", choices=["", "f32", "f16", "bf16"],
                     help="node value storage of the step's propagation (default: f16 for config 3, else f32)")
     ap.add_argument("--cpu-boxes", type=int, default=1000, help="boxes of the CPU oracle's timed sample")
+    ap.add_argument("--dims", default="", help="nx,ny,nz: the config's recipe on a volume of these dims "
+                                               "(profiling cases; not a bench workload)")
     ap.add_argument("--queries", type=int, default=0)
     ap.add_argument("--schedule", default="batched", choices=["batched", "plain"])
     ap.add_argument("--chunk", type=int, default=0)
@@ -247,16 +249,17 @@ def query_bytes(boxes_h, dims, S):
     return 24 * Q + id0 * int(lv[0]) + 4 * int(lv[1:].sum()) + 4 * Q * S, int(lv.sum()), lv
 
 
-def build_graph(mg, cfg_i, dev):
+def build_graph(mg, cfg_i, dev, dims=None):
     """The config's volume (GPU generator for Voronoi volumes, host for the
-    cylinders) and its graph; returns (graph, seconds of volume generation)."""
+    cylinders), optionally at other dims, and its graph; returns (graph,
+    seconds of volume generation)."""
     import torch
     c = synth.CONFIGS[cfg_i]
     t0 = time.perf_counter()
     if c["kind"] == "voronoi":
-        vol = synth.make_volume(cfg_i, device=dev)
+        vol = synth.make_volume(cfg_i, device=dev, dims=dims)
     else:
-        vol = torch.from_numpy(synth.make_volume(cfg_i)).to(dev)
+        vol = torch.from_numpy(synth.make_volume(cfg_i, dims=dims)).to(dev)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     g = mg.mg_build(vol, c["S"])
@@ -275,13 +278,14 @@ def measure_step(mg, g, cfg_i, boxes_h, storage, args, dev, flush, stream, world
     import torch
     from paper_2009_02702_gb300 import mg as _mg
     cfg = synth.CONFIGS[cfg_i]
-    S, dims = cfg["S"], cfg["dims"]
+    S = cfg["S"]
+    dims = tuple(g.info["dims"][0])
     Q = len(boxes_h)
     info = g.info
     dt = _mg._DTYPES[storage][1]
     esz = STORAGE[storage][1]
     tf_h = synth.make_tf(cfg_i, S, 4)
-    smp_h = synth.make_samples(cfg_i)
+    smp_h = synth.make_samples(cfg_i, dims=dims)
     P = smp_h.shape[0]
     boxes = torch.from_numpy(boxes_h).to(dev)
     tf = torch.from_numpy(tf_h).to(dev)
@@ -581,9 +585,11 @@ def run_ours(args):
     Q = args.queries or cfg["queries"]
     dims = cfg["dims"]
     storage = args.storage or ("f16" if cfg_i == 3 else "f32")
+    if args.dims:
+        dims = tuple(int(v) for v in args.dims.split(","))
 
-    g, gen_s = build_graph(mg, cfg_i, dev)
-    boxes_h = rank_boxes(cfg_i, Q, rank)
+    g, gen_s = build_graph(mg, cfg_i, dev, dims=dims if args.dims else None)
+    boxes_h = synth.make_boxes(cfg_i, Q=Q, dims=dims, stream_offset=rank) if args.dims else rank_boxes(cfg_i, Q, rank)
     head = measure_step(mg, g, cfg_i, boxes_h, storage, args, dev, flush, stream, world, peak, peak_src,
                         clocks_index=local, e2e=not args.no_e2e)
     head["graph"]["volume_generation_s"] = gen_s
@@ -626,6 +632,8 @@ def run_ours(args):
         "dtype": "u32 counts / %s colours (f32 math)" % storage, "data": "synthetic",
         "config": workload_config(cfg_i, Q, args, storage),
     }
+    if args.dims:
+        line["config"]["volume"] = "%dx%dx%d uint16 (the recipe at other dims: a profiling case)" % dims
     for k in ("tf_propagations_per_s", "samples_per_s", "latency_ms", "stages_ms", "roofline_nominal", "roofline",
               "other_kernels", "graph", "e2e", "autotune", "query_path", "gpu_launches", "clocks", "wall_s_timed"):
         line[k] = head[k]

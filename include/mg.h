@@ -150,6 +150,22 @@ MG_API mg_status mg_graph_copy_mip(const mg_graph *g, int level, uint32_t *dst, 
 MG_API mg_status mg_propagate_tf(mg_graph *g, const float *tf, int C, mg_dtype storage, void *vals,
                                  mg_stream stream);
 
+/*
+ * mg_propagate_tf_multi -- k transfer functions propagated in one pass over the
+ * graph (Sec. 3.4), e.g. k pending TF updates of one volume: the k*C values of
+ * a node are one row, so each level's wait and each predecessor gather serve
+ * all k.  Channel c of TF j is channel j*C + c of the row; every channel is
+ * the lerp of mg_propagate_tf, so row slice j equals mg_propagate_tf(TF j).
+ * tfs: k x S x C fp32 (TF j at tfs + j*S*C, each row-major S x C).
+ * k in 1..32, C in 1..16, and k*C one of 1-8, 12, 16, 20, 24, 28, 32
+ *   (else MG_ERR_UNSUPPORTED).
+ * storage: as for mg_propagate_tf.
+ * vals: N x (k*C) in `storage`, caller-owned, fully overwritten; 16-byte
+ *   aligned when a row is a multiple of 16 bytes (8-byte when of 8).
+ */
+MG_API mg_status mg_propagate_tf_multi(mg_graph *g, const float *tfs, int k, int C, mg_dtype storage, void *vals,
+                                       mg_stream stream);
+
 /* Query output forms. */
 typedef enum { MG_HIST_U32 = 0, MG_HIST_F32 = 1 } mg_hist_type;
 typedef enum { MG_LAYOUT_DENSE = 0, MG_LAYOUT_CSR = 1 } mg_layout;
@@ -291,6 +307,19 @@ MG_API mg_status mg_count_cubes(const mg_graph *g, const int32_t *boxes, int64_t
  */
 MG_API mg_status mg_render_lookup(const mg_graph *g, const void *vals, int C, mg_dtype dtype,
                                   const float *samples, int64_t P, void *out, mg_stream stream);
+
+/*
+ * mg_render_lookup_multi -- ray-sample lookups of k frames in one launch, each
+ * frame against its own slice of a k-TF palette (vals from
+ * mg_propagate_tf_multi): samples [offsets[j], offsets[j+1]) belong to frame
+ * j, and sample i of frame j gets channels [j*C, (j+1)*C) of the row of the
+ * node under it, chosen exactly as by mg_render_lookup (Sec. 4).
+ * offsets: k + 1 int64 in HOST memory, offsets[0] = 0, non-decreasing.
+ * samples: offsets[k] x 4 fp32.  vals: N x (k*C) in dtype.
+ * out: offsets[k] x C in dtype.
+ */
+MG_API mg_status mg_render_lookup_multi(const mg_graph *g, const void *vals, int k, int C, mg_dtype dtype,
+                                        const float *samples, const int64_t *offsets, void *out, mg_stream stream);
 
 /*
  * Request loop (serving).  A server keeps the graphs of several volumes

@@ -308,6 +308,18 @@ MG_API mg_status mg_propagate_tf(mg_graph* g, const float* tf, int C, mg_dtype s
     return propagate(g, tf, C, storage, vals, reinterpret_cast<cudaStream_t>(stream));
 }
 
+MG_API mg_status mg_propagate_tf_multi(mg_graph* g, const float* tfs, int k, int C, mg_dtype storage, void* vals,
+                                       mg_stream stream) {
+    MG_RANGE("mg_propagate_tf_multi");
+    if (!g || !tfs || !vals) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    if (k < 1 || k > 32) return fail(MG_ERR_INVALID_ARG, "k must be in 1..32");
+    if (C < 1 || C > 16) return fail(MG_ERR_INVALID_ARG, "C must be in 1..16");
+    if (storage != MG_F32 && storage != MG_F16 && storage != MG_BF16)
+        return fail(MG_ERR_INVALID_ARG, "storage must be MG_F32, MG_F16 or MG_BF16");
+    DeviceGuard dg(g->device);
+    return propagate_multi(g, tfs, k, C, storage, vals, reinterpret_cast<cudaStream_t>(stream));
+}
+
 MG_API mg_status mg_query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const mg_query_opts* opts,
                                 void* out, size_t out_capacity, uint32_t* seg, uint64_t* offsets,
                                 size_t* out_required, mg_stream stream) {
@@ -374,6 +386,23 @@ MG_API mg_status mg_render_lookup(const mg_graph* g, const void* vals, int C, mg
     if (!vals || !samples || !out) return fail(MG_ERR_INVALID_ARG, "NULL argument");
     DeviceGuard dg(g->device);
     return render_lookup(g, vals, C, dtype, samples, P, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+MG_API mg_status mg_render_lookup_multi(const mg_graph* g, const void* vals, int k, int C, mg_dtype dtype,
+                                        const float* samples, const int64_t* offsets, void* out, mg_stream stream) {
+    MG_RANGE("mg_render_lookup_multi");
+    if (!g || !offsets) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    if (k < 1 || k > 32) return fail(MG_ERR_INVALID_ARG, "k must be in 1..32");
+    if (C < 1 || C > 16) return fail(MG_ERR_INVALID_ARG, "C must be in 1..16");
+    if (dtype != MG_F32 && dtype != MG_F16 && dtype != MG_BF16)
+        return fail(MG_ERR_INVALID_ARG, "dtype must be MG_F32, MG_F16 or MG_BF16");
+    if (offsets[0] != 0) return fail(MG_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int j = 0; j < k; j++)
+        if (offsets[j + 1] < offsets[j]) return fail(MG_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    if (offsets[k] == 0) return MG_OK;
+    if (!vals || !samples || !out) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(g->device);
+    return render_lookup_multi(g, vals, k, C, dtype, samples, offsets, out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 MG_API mg_status mg_sync_status(mg_graph* g, mg_stream stream) {

@@ -193,6 +193,7 @@ mg_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, 
 mg_status build_graph(mg_graph* g, const void* ids, int id_bytes, int64_t nx, int64_t ny, int64_t nz,
                       cudaStream_t s);
 mg_status propagate(mg_graph* g, const float* tf, int C, mg_dtype storage, void* vals, cudaStream_t s);
+mg_status propagate_multi(mg_graph* g, const float* tf, int k, int C, mg_dtype storage, void* vals, cudaStream_t s);
 // the per-node mixture lookup table of the range queries (after the build)
 mg_status build_lut(mg_graph* g, cudaStream_t s);
 mg_status ensure_alpha16(mg_graph* g, mg_dtype dt, cudaStream_t s);
@@ -210,6 +211,8 @@ mg_status count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64
 mg_status selftest_wait(bool satisfied, unsigned limit, cudaStream_t s);
 mg_status render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dt, const float* samples,
                         int64_t P, void* out, cudaStream_t s);
+mg_status render_lookup_multi(const mg_graph* g, const void* vals, int k, int C, mg_dtype dt, const float* samples,
+                              const int64_t* offsets, void* out, cudaStream_t s);
 
 // A query plan's own buffers, executable graph and footprint capacities, for
 // the request loop, which stages boxes straight into them: a run is the boxes

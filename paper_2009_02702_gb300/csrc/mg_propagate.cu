@@ -34,75 +34,95 @@ template <> struct Cvt<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 from(float x) { return __float2bfloat16_rn(x); }
 };
 
-// load / store one row of C values (vectorised when the row is 8 or 16 bytes)
-template <typename ST, int C>
-__device__ __forceinline__ void load_row(const ST* __restrict__ base, int64_t row, float (&v)[C]) {
-    const ST* r = base + row * C;
-    if constexpr (sizeof(ST) * C == 16) {
-        const uint4 u = __ldg(reinterpret_cast<const uint4*>(r));
-        const ST* e = reinterpret_cast<const ST*>(&u);
-#pragma unroll
-        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(e[c]);
-    } else if constexpr (sizeof(ST) * C == 8) {
-        const uint2 u = __ldg(reinterpret_cast<const uint2*>(r));
-        const ST* e = reinterpret_cast<const ST*>(&u);
-#pragma unroll
-        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(e[c]);
-    } else {
-#pragma unroll
-        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(r[c]);
-    }
+// load / store one row of C values: as 16-byte vectors when the row is a
+// multiple of 16 bytes, 8-byte ones when it is a multiple of 8, else element
+// by element.  kL2 loads go through L2 only (rows written earlier in the same
+// launch are never read through the read-only cache).
+template <bool kL2, typename V>
+__device__ __forceinline__ V ld_vec(const V* p) {
+    if constexpr (kL2) return __ldcg(p);
+    else return __ldg(p);
 }
 
-template <typename ST, int C>
-__device__ __forceinline__ void store_row(ST* __restrict__ base, int64_t row, const float (&v)[C]) {
-    ST* r = base + row * C;
-    if constexpr (sizeof(ST) * C == 16 || sizeof(ST) * C == 8) {
-        ST e[C];
-#pragma unroll
-        for (int c = 0; c < C; c++) e[c] = Cvt<ST>::from(v[c]);
-        if constexpr (sizeof(ST) * C == 16)
-            *reinterpret_cast<uint4*>(r) = *reinterpret_cast<const uint4*>(e);
-        else
-            *reinterpret_cast<uint2*>(r) = *reinterpret_cast<const uint2*>(e);
-    } else {
-#pragma unroll
-        for (int c = 0; c < C; c++) r[c] = Cvt<ST>::from(v[c]);
-    }
-}
-
-// the same row load through L2 only, for rows written earlier in this launch
-template <typename ST, int C>
-__device__ __forceinline__ void load_row_cg(const ST* __restrict__ base, int64_t row, float (&v)[C]) {
+template <typename ST, int C, bool kL2>
+__device__ __forceinline__ void load_row_t(const ST* __restrict__ base, int64_t row, float (&v)[C]) {
     const ST* r = base + row * C;
-    if constexpr (sizeof(ST) * C == 16) {
-        const uint4 u = __ldcg(reinterpret_cast<const uint4*>(r));
-        const ST* e = reinterpret_cast<const ST*>(&u);
+    constexpr int B = (int)sizeof(ST) * C;
+    if constexpr (B % 16 == 0) {
+        constexpr int E = 16 / (int)sizeof(ST);
 #pragma unroll
-        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(e[c]);
-    } else if constexpr (sizeof(ST) * C == 8) {
-        const uint2 u = __ldcg(reinterpret_cast<const uint2*>(r));
-        const ST* e = reinterpret_cast<const ST*>(&u);
+        for (int w = 0; w < B / 16; w++) {
+            const uint4 u = ld_vec<kL2>(reinterpret_cast<const uint4*>(r) + w);
+            const ST* e = reinterpret_cast<const ST*>(&u);
 #pragma unroll
-        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(e[c]);
+            for (int c = 0; c < E; c++) v[w * E + c] = Cvt<ST>::to(e[c]);
+        }
+    } else if constexpr (B % 8 == 0) {
+        constexpr int E = 8 / (int)sizeof(ST);
+#pragma unroll
+        for (int w = 0; w < B / 8; w++) {
+            const uint2 u = ld_vec<kL2>(reinterpret_cast<const uint2*>(r) + w);
+            const ST* e = reinterpret_cast<const ST*>(&u);
+#pragma unroll
+            for (int c = 0; c < E; c++) v[w * E + c] = Cvt<ST>::to(e[c]);
+        }
     } else if constexpr (sizeof(ST) == 4) {
 #pragma unroll
-        for (int c = 0; c < C; c++) v[c] = Cvt<ST>::to(__ldcg(reinterpret_cast<const float*>(r) + c));
+        for (int c = 0; c < C; c++) v[c] = ld_vec<kL2>(reinterpret_cast<const float*>(r) + c);
     } else {
 #pragma unroll
         for (int c = 0; c < C; c++) {
-            const unsigned short u = __ldcg(reinterpret_cast<const unsigned short*>(r) + c);
+            const unsigned short u = ld_vec<kL2>(reinterpret_cast<const unsigned short*>(r) + c);
             v[c] = Cvt<ST>::to(*reinterpret_cast<const ST*>(&u));
         }
     }
 }
 
 template <typename ST, int C>
-__global__ void sources_kernel(const float* __restrict__ tf, uint32_t S, ST* __restrict__ vals) {
+__device__ __forceinline__ void load_row(const ST* __restrict__ base, int64_t row, float (&v)[C]) {
+    load_row_t<ST, C, false>(base, row, v);
+}
+
+template <typename ST, int C>
+__device__ __forceinline__ void load_row_cg(const ST* __restrict__ base, int64_t row, float (&v)[C]) {
+    load_row_t<ST, C, true>(base, row, v);
+}
+
+template <typename ST, int C>
+__device__ __forceinline__ void store_row(ST* __restrict__ base, int64_t row, const float (&v)[C]) {
+    ST* r = base + row * C;
+    constexpr int B = (int)sizeof(ST) * C;
+    if constexpr (B % 16 == 0 || B % 8 == 0) {
+        constexpr int VB = B % 16 == 0 ? 16 : 8;
+        constexpr int E = VB / (int)sizeof(ST);
+#pragma unroll
+        for (int w = 0; w < B / VB; w++) {
+            ST e[E];
+#pragma unroll
+            for (int c = 0; c < E; c++) e[c] = Cvt<ST>::from(v[w * E + c]);
+            if constexpr (VB == 16)
+                reinterpret_cast<uint4*>(r)[w] = *reinterpret_cast<const uint4*>(e);
+            else
+                reinterpret_cast<uint2*>(r)[w] = *reinterpret_cast<const uint2*>(e);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < C; c++) r[c] = Cvt<ST>::from(v[c]);
+    }
+}
+
+// channel c of source n: k transfer functions of cin channels each, TF j at
+// tf + j * S * cin (k = 1: the row-major S x C table)
+__device__ __forceinline__ float tf_value(const float* __restrict__ tf, int64_t n, int c, int cin, int64_t tf_stride) {
+    return tf[(int64_t)(c / cin) * tf_stride + n * cin + (c % cin)];
+}
+
+template <typename ST, int C>
+__global__ void sources_kernel(const float* __restrict__ tf, uint32_t S, int cin, ST* __restrict__ vals) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
         float v[C];
 #pragma unroll
-        for (int c = 0; c < C; c++) v[c] = tf[s * C + c];
+        for (int c = 0; c < C; c++) v[c] = tf_value(tf, s, c, cin, (int64_t)S * cin);
         store_row<ST, C>(vals, s, v);
     }
 }
@@ -185,8 +205,8 @@ __device__ __forceinline__ void tile_edges(const PropTiles& T, long long t, long
 template <typename ST, int C>
 __global__ void __launch_bounds__(kPropThreads) single_pass_kernel(PropTiles T, const uint2* __restrict__ pq,
                                                                    const typename Weight<ST>::T* __restrict__ alpha,
-                                                                   const float* __restrict__ tf, ST* __restrict__ vals,
-                                                                   unsigned* __restrict__ done,
+                                                                   const float* __restrict__ tf, int cin,
+                                                                   ST* __restrict__ vals, unsigned* __restrict__ done,
                                                                    unsigned long long* __restrict__ ticket,
                                                                    unsigned* __restrict__ status) {
     constexpr int NT = kPropTile / kPropThreads;      // nodes of a tile per thread
@@ -236,7 +256,7 @@ __global__ void __launch_bounds__(kPropThreads) single_pass_kernel(PropTiles T, 
             for (int64_t n = lo + threadIdx.x; n < hi; n += kPropThreads) {
                 float out[C];
 #pragma unroll
-                for (int c = 0; c < C; c++) out[c] = tf[n * C + c];
+                for (int c = 0; c < C; c++) out[c] = tf_value(tf, n, c, cin, T.count[0] * cin);
                 store_row<ST, C>(vals, n, out);
             }
         } else {
@@ -309,7 +329,7 @@ int sm_count_prop(int dev) {
 }
 
 template <typename ST, int C>
-mg_status run_single_pass(mg_graph* g, const float* tf, const void* alpha, ST* vals, cudaStream_t s) {
+mg_status run_single_pass(mg_graph* g, const float* tf, int cin, const void* alpha, ST* vals, cudaStream_t s) {
     PropTiles T;
     T.levels = g->D + 1;
     int64_t tiles = 0;
@@ -334,15 +354,16 @@ mg_status run_single_pass(mg_graph* g, const float* tf, const void* alpha, ST* v
     MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kPropThreads, 0));
     const int64_t grid = std::min<int64_t>(tiles, (int64_t)std::max(per_sm, 1) * sm_count_prop(g->device));
     k<<<(unsigned)std::max<int64_t>(grid, 1), kPropThreads, 0, s>>>(T, g->pq.as<uint2>(), static_cast<const W*>(alpha),
-                                                                    tf, vals, done, ticket, g->status.as<unsigned>());
+                                                                    tf, cin, vals, done, ticket,
+                                                                    g->status.as<unsigned>());
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
 
 template <typename ST, int C>
-mg_status run(mg_graph* g, const float* tf, const void* alpha, ST* vals, cudaStream_t s) {
-    if (g->D + 1 <= MG_MAX_DEPTH) return run_single_pass<ST, C>(g, tf, alpha, vals, s);
-    sources_kernel<ST, C><<<grid_for(g->S, 256, 152 * 16), 256, 0, s>>>(tf, g->S, vals);
+mg_status run(mg_graph* g, const float* tf, int cin, const void* alpha, ST* vals, cudaStream_t s) {
+    if (g->D + 1 <= MG_MAX_DEPTH) return run_single_pass<ST, C>(g, tf, cin, alpha, vals, s);
+    sources_kernel<ST, C><<<grid_for(g->S, 256, 152 * 16), 256, 0, s>>>(tf, g->S, cin, vals);
     MG_CUDA(cudaGetLastError());
     using W = typename Weight<ST>::T;
     for (int d = 1; d <= g->D; d++) {
@@ -356,22 +377,26 @@ mg_status run(mg_graph* g, const float* tf, const void* alpha, ST* vals, cudaStr
 }
 
 template <typename ST>
-mg_status dispatch_c(mg_graph* g, const float* tf, int C, const void* alpha, void* vals, cudaStream_t s) {
+mg_status dispatch_c(mg_graph* g, const float* tf, int C, int cin, const void* alpha, void* vals, cudaStream_t s) {
     ST* v = static_cast<ST*>(vals);
     switch (C) {
-        case 1: return run<ST, 1>(g, tf, alpha, v, s);
-        case 2: return run<ST, 2>(g, tf, alpha, v, s);
-        case 3: return run<ST, 3>(g, tf, alpha, v, s);
-        case 4: return run<ST, 4>(g, tf, alpha, v, s);
-        case 5: return run<ST, 5>(g, tf, alpha, v, s);
-        case 6: return run<ST, 6>(g, tf, alpha, v, s);
-        case 7: return run<ST, 7>(g, tf, alpha, v, s);
-        case 8: return run<ST, 8>(g, tf, alpha, v, s);
-        case 12: return run<ST, 12>(g, tf, alpha, v, s);
-        case 16: return run<ST, 16>(g, tf, alpha, v, s);
+        case 1: return run<ST, 1>(g, tf, cin, alpha, v, s);
+        case 2: return run<ST, 2>(g, tf, cin, alpha, v, s);
+        case 3: return run<ST, 3>(g, tf, cin, alpha, v, s);
+        case 4: return run<ST, 4>(g, tf, cin, alpha, v, s);
+        case 5: return run<ST, 5>(g, tf, cin, alpha, v, s);
+        case 6: return run<ST, 6>(g, tf, cin, alpha, v, s);
+        case 7: return run<ST, 7>(g, tf, cin, alpha, v, s);
+        case 8: return run<ST, 8>(g, tf, cin, alpha, v, s);
+        case 12: return run<ST, 12>(g, tf, cin, alpha, v, s);
+        case 16: return run<ST, 16>(g, tf, cin, alpha, v, s);
+        case 20: return run<ST, 20>(g, tf, cin, alpha, v, s);
+        case 24: return run<ST, 24>(g, tf, cin, alpha, v, s);
+        case 28: return run<ST, 28>(g, tf, cin, alpha, v, s);
+        case 32: return run<ST, 32>(g, tf, cin, alpha, v, s);
         default: break;
     }
-    return fail(MG_ERR_UNSUPPORTED, "channel count C must be 1-8, 12 or 16");
+    return fail(MG_ERR_UNSUPPORTED, "channels per node (k * C) must be 1-8, 12, 16, 20, 24, 28 or 32");
 }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -413,15 +438,20 @@ mg_status selftest_wait(bool satisfied, unsigned limit, cudaStream_t s) {
     return status_from_bits(words[1]);
 }
 
-mg_status propagate(mg_graph* g, const float* tf, int C, mg_dtype storage, void* vals, cudaStream_t s) {
+mg_status propagate_multi(mg_graph* g, const float* tf, int k, int C, mg_dtype storage, void* vals, cudaStream_t s) {
+    const int CT = k * C;
     const size_t esz = storage == MG_F32 ? 4 : 2;
-    const size_t row = esz * (size_t)C;
-    if ((row == 16 || row == 8) && !aligned(vals, row))
-        return fail(MG_ERR_INVALID_ARG, "vals must be aligned to its row size");
-    if (storage == MG_F32) return dispatch_c<float>(g, tf, C, g->alpha.p, vals, s);
+    const size_t row = esz * (size_t)CT;
+    if (row % 16 == 0 ? !aligned(vals, 16) : row % 8 == 0 ? !aligned(vals, 8) : false)
+        return fail(MG_ERR_INVALID_ARG, "vals must be aligned to 16 bytes (rows of a multiple of 16 bytes) or 8");
+    if (storage == MG_F32) return dispatch_c<float>(g, tf, CT, C, g->alpha.p, vals, s);
     MG_TRY(ensure_alpha16(g, storage, s));
-    if (storage == MG_F16) return dispatch_c<__half>(g, tf, C, g->alpha16.p, vals, s);
-    return dispatch_c<__nv_bfloat16>(g, tf, C, g->alphab16.p, vals, s);
+    if (storage == MG_F16) return dispatch_c<__half>(g, tf, CT, C, g->alpha16.p, vals, s);
+    return dispatch_c<__nv_bfloat16>(g, tf, CT, C, g->alphab16.p, vals, s);
+}
+
+mg_status propagate(mg_graph* g, const float* tf, int C, mg_dtype storage, void* vals, cudaStream_t s) {
+    return propagate_multi(g, tf, 1, C, storage, vals, s);
 }
 
 }  // namespace mg

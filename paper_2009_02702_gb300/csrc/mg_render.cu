@@ -58,20 +58,103 @@ __global__ void __launch_bounds__(kLookupThreads, 16) lookup_kernel(Geom G, cons
     for (int w = 0; w < words; w++) dst[w] = __ldg(src + w);
 }
 
+// k frames in one launch: samples [off[j], off[j+1]) belong to frame j and
+// read the j-th slice of `words` words of every value row (rows of k slices,
+// the layout of a k-TF propagation)
+constexpr int kMaxFrames = 32;
+struct FrameOffsets {
+    int64_t off[kMaxFrames + 1];
+};
+
+template <typename RowT>
+__global__ void __launch_bounds__(kLookupThreads, 16) lookup_multi_kernel(Geom G, const void* __restrict__ mip0,
+                                                                          const uint32_t* __restrict__ mip,
+                                                                          const float4* __restrict__ samples,
+                                                                          FrameOffsets F, int k,
+                                                                          const RowT* __restrict__ vals, int words,
+                                                                          RowT* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= F.off[k]) return;
+    int j = 0;
+    while (j + 1 < k && F.off[j + 1] <= i) j++;
+    const float4 smp = __ldg(samples + i);
+    const float t = smp.w + 0.5f;
+    int l;
+    if (!(t >= 0.f)) l = 0;
+    else if (t >= (float)(G.L - 1)) l = G.L - 1;
+    else l = (int)t;
+    int64_t v[3];
+    const float c[3] = {smp.x, smp.y, smp.z};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int64_t x = floor_coord(c[a], G.dims[0][a]) >> l;
+        v[a] = min(x, (int64_t)G.dims[l][a] - 1);
+    }
+    const int64_t idx = (v[2] * G.dims[l][1] + v[1]) * G.dims[l][0] + v[0];
+    uint32_t node;
+    if (l == 0)
+        node = G.id0_bytes == 2 ? (uint32_t)__ldg(static_cast<const uint16_t*>(mip0) + idx)
+                                : __ldg(static_cast<const uint32_t*>(mip0) + idx);
+    else
+        node = __ldg(mip + G.off[l] + idx);
+    const RowT* src = vals + ((int64_t)node * k + j) * words;
+    RowT* dst = out + i * words;
+    for (int w = 0; w < words; w++) dst[w] = __ldg(src + w);
+}
+
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-}  // namespace
-
-mg_status render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dt, const float* samples, int64_t P,
-                        void* out, cudaStream_t s) {
-    if (!aligned(samples, 16)) return fail(MG_ERR_INVALID_ARG, "samples must be 16-byte aligned");
+Geom render_geom(const mg_graph* g) {
     Geom G;
     G.L = g->L;
     G.id0_bytes = g->id0_bytes;
     for (int l = 0; l < MG_MAX_LEVELS; l++) {
-        for (int k = 0; k < 3; k++) G.dims[l][k] = g->geom.dims[l][k];
+        for (int a = 0; a < 3; a++) G.dims[l][a] = g->geom.dims[l][a];
         G.off[l] = g->geom.off[l];
     }
+    return G;
+}
+
+}  // namespace
+
+mg_status render_lookup_multi(const mg_graph* g, const void* vals, int k, int C, mg_dtype dt, const float* samples,
+                              const int64_t* offsets, void* out, cudaStream_t s) {
+    if (k < 1 || k > kMaxFrames) return fail(MG_ERR_INVALID_ARG, "k must be 1..32 frames");
+    if (!aligned(samples, 16)) return fail(MG_ERR_INVALID_ARG, "samples must be 16-byte aligned");
+    FrameOffsets F;
+    for (int j = 0; j <= kMaxFrames; j++) F.off[j] = offsets[j <= k ? j : k];
+    if (F.off[0] != 0) return fail(MG_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int j = 0; j < k; j++)
+        if (F.off[j + 1] < F.off[j]) return fail(MG_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    const int64_t P = F.off[k];
+    if (P == 0) return MG_OK;
+    const Geom G = render_geom(g);
+    const size_t row = (size_t)C * (dt == MG_F32 ? 4 : 2);
+    const unsigned grid = grid_for(P, kLookupThreads);
+    const float4* sm = reinterpret_cast<const float4*>(samples);
+    const uint32_t* mip = g->mip.as<uint32_t>();
+    if (row % 16 == 0 && aligned(vals, 16) && aligned(out, 16))
+        lookup_multi_kernel<uint4><<<grid, kLookupThreads, 0, s>>>(G, g->mip0.p, mip, sm, F, k, (const uint4*)vals,
+                                                                  (int)(row / 16), (uint4*)out);
+    else if (row % 8 == 0 && aligned(vals, 8) && aligned(out, 8))
+        lookup_multi_kernel<uint2><<<grid, kLookupThreads, 0, s>>>(G, g->mip0.p, mip, sm, F, k, (const uint2*)vals,
+                                                                  (int)(row / 8), (uint2*)out);
+    else if (row % 4 == 0 && aligned(vals, 4) && aligned(out, 4))
+        lookup_multi_kernel<uint32_t><<<grid, kLookupThreads, 0, s>>>(G, g->mip0.p, mip, sm, F, k,
+                                                                     (const uint32_t*)vals, (int)(row / 4),
+                                                                     (uint32_t*)out);
+    else
+        lookup_multi_kernel<uint16_t><<<grid, kLookupThreads, 0, s>>>(G, g->mip0.p, mip, sm, F, k,
+                                                                     (const uint16_t*)vals, (int)(row / 2),
+                                                                     (uint16_t*)out);
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dt, const float* samples, int64_t P,
+                        void* out, cudaStream_t s) {
+    if (!aligned(samples, 16)) return fail(MG_ERR_INVALID_ARG, "samples must be 16-byte aligned");
+    const Geom G = render_geom(g);
     const size_t row = (size_t)C * (dt == MG_F32 ? 4 : 2);
     const unsigned grid = grid_for(P, kLookupThreads);
     const float4* sm = reinterpret_cast<const float4*>(samples);

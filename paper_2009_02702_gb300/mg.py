@@ -37,7 +37,8 @@ EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_cop
            "mg_query_boxes", "mg_query_boxes_noalloc", "mg_query_timing",
            "mg_query_plan_create", "mg_query_plan_run", "mg_query_plan_timing", "mg_query_plan_free",
            "mg_query_autotune",
-           "mg_query_set_tuning", "mg_count_cubes", "mg_render_lookup",
+           "mg_query_set_tuning", "mg_count_cubes", "mg_render_lookup", "mg_propagate_tf_multi",
+           "mg_render_lookup_multi",
            "mg_server_create", "mg_server_add_volume", "mg_server_start", "mg_server_submit", "mg_server_cancel",
            "mg_server_wait", "mg_server_replay", "mg_server_stats_get", "mg_server_free",
            "mg_graph_export_size", "mg_graph_export", "mg_graph_import",
@@ -118,6 +119,10 @@ def lib():
         L.mg_graph_copy_mip.restype = st
         L.mg_propagate_tf.argtypes = [P, P, i32, i32, P, P]
         L.mg_propagate_tf.restype = st
+        L.mg_propagate_tf_multi.argtypes = [P, P, i32, i32, i32, P, P]
+        L.mg_propagate_tf_multi.restype = st
+        L.mg_render_lookup_multi.argtypes = [P, P, i32, i32, i32, P, P, P, P]
+        L.mg_render_lookup_multi.restype = st
         L.mg_query_boxes.argtypes = [P, P, i64, ctypes.POINTER(mg_query_opts), P, ctypes.c_size_t, P, P,
                                      ctypes.POINTER(ctypes.c_size_t), P]
         L.mg_query_boxes.restype = st
@@ -333,6 +338,44 @@ def mg_propagate_tf(g: Graph, tf: torch.Tensor, storage: str = "f32", out: torch
         out = torch.empty((g.N, C), dtype=dt, device=tf.device)
     _check_out(out, (g.N, C), dt, tf.device)
     _check(lib().mg_propagate_tf(g.handle, tf.data_ptr(), C, code, out.data_ptr(), _stream(stream)))
+    return out
+
+
+def mg_propagate_tf_multi(g: Graph, tfs: torch.Tensor, storage: str = "f32", out: torch.Tensor = None,
+                          stream=None) -> torch.Tensor:
+    """Node values (N, k*C) of k transfer functions (k, S, C) fp32 in one pass;
+    columns [j*C, (j+1)*C) hold TF j's values."""
+    if not tfs.is_cuda or tfs.dtype != torch.float32 or tfs.dim() != 3 or tfs.shape[1] != g.S:
+        raise ValueError("tfs must be a CUDA float32 tensor of shape (k, S, C)")
+    tfs = tfs.contiguous()
+    code, dt = _DTYPES[storage]
+    k, C = tfs.shape[0], tfs.shape[2]
+    if out is None:
+        out = torch.empty((g.N, k * C), dtype=dt, device=tfs.device)
+    _check_out(out, (g.N, k * C), dt, tfs.device)
+    _check(lib().mg_propagate_tf_multi(g.handle, tfs.data_ptr(), k, C, code, out.data_ptr(), _stream(stream)))
+    return out
+
+
+def mg_render_lookup_multi(g: Graph, vals: torch.Tensor, k: int, samples: torch.Tensor, offsets,
+                           out: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """Lookups of k frames: samples (P, 4), offsets (k+1,) host ints; frame j's
+    samples read columns [j*C, (j+1)*C) of vals (N, k*C).  Returns (P, C)."""
+    import numpy as np
+    if samples.dtype != torch.float32 or samples.dim() != 2 or samples.shape[1] != 4:
+        raise ValueError("samples must be float32 of shape (P, 4)")
+    if vals.dim() != 2 or vals.shape[1] % k:
+        raise ValueError("vals must have k*C columns")
+    samples = samples.contiguous()
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    if off.shape != (k + 1,) or off[-1] != samples.shape[0]:
+        raise ValueError("offsets must have k+1 entries ending at the number of samples")
+    C = vals.shape[1] // k
+    if out is None:
+        out = torch.empty((samples.shape[0], C), dtype=vals.dtype, device=vals.device)
+    _check_out(out, (samples.shape[0], C), vals.dtype, vals.device)
+    _check(lib().mg_render_lookup_multi(g.handle, vals.data_ptr(), k, C, _TORCH_TO_MG[vals.dtype], samples.data_ptr(),
+                                        off.ctypes.data, out.data_ptr(), _stream(stream)))
     return out
 
 

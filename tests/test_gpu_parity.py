@@ -268,3 +268,49 @@ def test_generators_agree(cfg, dims, S):
     host = synth.make_volume(cfg, dims=dims, S=S)
     gpu = synth.make_volume(cfg, device="cuda", dims=dims, S=S).cpu().numpy()
     assert np.array_equal(host, gpu)
+
+
+@pytest.mark.parametrize("k,C,storage", [(3, 4, "f32"), (8, 4, "f32"), (5, 4, "f16"), (2, 16, "bf16"), (7, 3, "f32")])
+def test_propagate_multi_tf(mg, k, C, storage):
+    """k TFs in one pass: slice j of every row equals the single-TF propagation
+    of TF j bit for bit, and (fp32) the oracle's fp64 lerps within tolerance."""
+    vol = synth.make_volume(1, dims=(37, 29, 23), S=24)
+    g, og = build_pair(mg, vol, 24)
+    tfs = np.stack([synth.make_tf(1, 24, C, frame=j) for j in range(k)])
+    if k * C not in (1, 2, 3, 4, 5, 6, 7, 8, 12, 16, 20, 24, 28, 32):
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_propagate_tf_multi(g, torch.from_numpy(tfs).to(dev()), storage=storage)
+        assert e.value.status == mg.MG_ERR_UNSUPPORTED
+        return
+    vals = mg.mg_propagate_tf_multi(g, torch.from_numpy(tfs).to(dev()), storage=storage)
+    mg.mg_sync_status(g)
+    for j in range(k):
+        one = mg.mg_propagate_tf(g, torch.from_numpy(tfs[j]).to(dev()), storage=storage)
+        assert torch.equal(vals[:, j * C:(j + 1) * C].cpu(), one.cpu()), j
+        if storage == "f32":
+            ref = oracle.propagate(og.p, og.q, og.a, og.b, 24, tfs[j].astype(np.float64))
+            ok, err = fp32_close(vals[:, j * C:(j + 1) * C].cpu().numpy(), ref)
+            assert ok, (j, err)
+
+
+def test_render_lookup_multi(mg):
+    dims = (37, 29, 23)
+    vol = synth.make_volume(1, dims=dims, S=24)
+    g = mg.mg_build(torch.from_numpy(vol).to(dev()), 24)
+    k, C = 4, 4
+    tfs = np.stack([synth.make_tf(1, 24, C, frame=j) for j in range(k)])
+    for storage in ("f32", "f16"):
+        vals = mg.mg_propagate_tf_multi(g, torch.from_numpy(tfs).to(dev()), storage=storage)
+        frames = [synth.make_samples(1, dims=dims, width=w, height=h, frame=j)
+                  for j, (w, h) in enumerate([(40, 30), (1, 1), (2, 1), (64, 17)])]
+        frames[2] = frames[2][:0]   # a frame without samples
+        off = np.cumsum([0] + [len(f) for f in frames])
+        smp = torch.from_numpy(np.concatenate(frames)).to(dev())
+        out = mg.mg_render_lookup_multi(g, vals, k, smp, off).cpu()
+        for j in range(k):
+            if off[j + 1] == off[j]:
+                continue
+            one = mg.mg_render_lookup(g, vals[:, j * C:(j + 1) * C].contiguous(),
+                                      torch.from_numpy(frames[j]).to(dev())).cpu()
+            assert torch.equal(out[off[j]:off[j + 1]], one), (storage, j)
+    g.close()
