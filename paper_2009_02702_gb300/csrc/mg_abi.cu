@@ -158,7 +158,8 @@ mg_status sync_status(mg_graph* g, cudaStream_t s) {
 }  // namespace mg
 
 int64_t mg_graph::device_bytes() const {
-    return (int64_t)(mip0.bytes + mip.bytes + mip0x[0].bytes + mip0x[1].bytes + mipx[0].bytes + mipx[1].bytes + pq.bytes + ab.bytes + ab32.bytes + alpha.bytes + alpha16.bytes +
+    return (int64_t)(mip0.bytes + mip.bytes + mip0x[0].bytes + mip0x[1].bytes + mip0x[2].bytes + mipx[0].bytes +
+                     mipx[1].bytes + mipx[2].bytes + pq.bytes + ab.bytes + ab32.bytes + alpha.bytes + alpha16.bytes +
                      alphab16.bytes + status.bytes + lut_meta.bytes + lut.bytes);
 }
 
@@ -213,8 +214,8 @@ MG_API mg_status mg_build(const void* ids, int64_t nx, int64_t ny, int64_t nz, u
     g->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 
     // graph buffers are released on the legacy stream after a device sync
-    for (Buf* b : {&g->mip0, &g->mip, &g->mip0x[0], &g->mip0x[1], &g->mipx[0], &g->mipx[1], &g->pq, &g->ab,
-                   &g->ab32, &g->alpha, &g->status})
+    for (Buf* b : {&g->mip0, &g->mip, &g->mip0x[0], &g->mip0x[1], &g->mip0x[2], &g->mipx[0], &g->mipx[1],
+                   &g->mipx[2], &g->pq, &g->ab, &g->ab32, &g->alpha, &g->status})
         b->s = nullptr;
     *out = g;
     return MG_OK;

@@ -496,17 +496,27 @@ __global__ void weights_kernel(const ulonglong2* __restrict__ ab, int64_t N, uin
 }
 
 // ---------------------------------------------------------------------------
-// axis-major copies: copy 1 orders (y, z, x), copy 2 orders (z, x, y)
+// axis-major copies: copy 0 orders (x, y, z), copy 1 (y, z, x), copy 2
+// (z, x, y); rows of `pitch` IDs, the ones past the row's end set to 0
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void transpose_copy_kernel(const T* __restrict__ src, T* __restrict__ dst, Dims3 d, int copy) {
-    const int64_t n = nvox(d);
-    const int32_t d0 = copy == 1 ? d.y : d.z, d1 = copy == 1 ? d.z : d.x;
+__global__ void transpose_copy_kernel(const T* __restrict__ src, T* __restrict__ dst, Dims3 d, int copy,
+                                      int64_t pitch) {
+    const int32_t d0 = copy == 0 ? d.x : copy == 1 ? d.y : d.z;
+    const int32_t d1 = copy == 0 ? d.y : copy == 1 ? d.z : d.x;
+    const int32_t d2 = copy == 0 ? d.z : copy == 1 ? d.x : d.y;
+    const int64_t n = pitch * d1 * d2;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t f = i % d0, r = i / d0;
+        const int64_t f = i % pitch, r = i / pitch;
+        if (f >= d0) {
+            dst[i] = T(0);
+            continue;
+        }
         const int64_t sc = r % d1, t = r / d1;
         int64_t x, y, z;
-        if (copy == 1) {
+        if (copy == 0) {
+            x = f; y = sc; z = t;
+        } else if (copy == 1) {
             y = f; z = sc; x = t;
         } else {
             z = f; x = sc; y = t;
@@ -833,26 +843,7 @@ mg_status build_graph(mg_graph* g, const void* ids, int id_bytes, int64_t nx, in
         remap_kernel<<<grid_n(total_hi), 256, 0, s>>>(g->mip.as<uint32_t>(), total_hi, canon.as<uint32_t>(), status);
         MG_CUDA(cudaGetLastError());
     }
-    // axis-major copies for the query path
-    for (int c = 0; c < 2; c++) {
-        const Dims3 d0 = dims_of(0);
-        MG_TRY(g->mip0x[c].alloc(&al, (size_t)V0 * g->id0_bytes, s));
-        if (g->id0_bytes == 2)
-            transpose_copy_kernel<uint16_t><<<grid_n(V0), 256, 0, s>>>(g->mip0.as<uint16_t>(), g->mip0x[c].as<uint16_t>(),
-                                                                       d0, c + 1);
-        else
-            transpose_copy_kernel<uint32_t><<<grid_n(V0), 256, 0, s>>>(g->mip0.as<uint32_t>(), g->mip0x[c].as<uint32_t>(),
-                                                                       d0, c + 1);
-        MG_CUDA(cudaGetLastError());
-        if (total_hi > 0) {
-            MG_TRY(g->mipx[c].alloc(&al, (size_t)total_hi * 4, s));
-            for (int l = 1; l < L; l++) {
-                transpose_copy_kernel<uint32_t><<<grid_n(nvox(dims_of(l))), 256, 0, s>>>(
-                    g->mip.as<uint32_t>() + G.off[l], g->mipx[c].as<uint32_t>() + G.off[l], dims_of(l), c + 1);
-                MG_CUDA(cudaGetLastError());
-            }
-        }
-    }
+    MG_TRY(build_query_copies(g, s));
     MG_TRY(g->ab32.alloc(&al, (size_t)N * sizeof(uint2), s));
     MG_TRY(g->alpha.alloc(&al, (size_t)N * sizeof(float), s));
     weights_kernel<<<grid_n(N), 256, 0, s>>>(g->ab.as<ulonglong2>(), N, S, g->ab32.as<uint2>(), g->alpha.as<float>());
@@ -862,6 +853,64 @@ mg_status build_graph(mg_graph* g, const void* ids, int id_bytes, int64_t nx, in
     MG_TRY(read_scalar(&bits, status, s));
     if (bits) return fail(MG_ERR_CAPACITY, "node table overflow during the build");
     MG_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
+    return MG_OK;
+}
+
+// The padded axis-major copies of the box queries (copy c of level l: rows
+// of the copy's fastest axis, qpitch[l][c] IDs apart, a multiple of 32 bytes
+// unless that would take a copy past 2^32 IDs).
+mg_status build_query_copies(mg_graph* g, cudaStream_t s) {
+    const int L = g->L;
+    auto dims_of = [&](int l) {
+        Dims3 d;
+        d.x = g->geom.dims[l][0];
+        d.y = g->geom.dims[l][1];
+        d.z = g->geom.dims[l][2];
+        return d;
+    };
+    auto grid_n = [](int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 64); };
+    int64_t hi_total[3] = {0, 0, 0};
+    for (int c = 0; c < 3; c++) {
+        for (int l = 0; l < L; l++) {
+            const Dims3 d = dims_of(l);
+            const int64_t d0 = c == 0 ? d.x : c == 1 ? d.y : d.z;
+            const int64_t rows = nvox(d) / d0;
+            const int64_t per32 = l == 0 ? 32 / g->id0_bytes : 8;
+            int64_t pitch = (d0 + per32 - 1) / per32 * per32;
+            if (pitch * rows >= (1ll << 32)) pitch = d0;
+            g->qpitch[l][c] = (int32_t)pitch;
+            if (l >= 1) {
+                g->qoff[l][c] = hi_total[c];
+                hi_total[c] += pitch * rows;
+            }
+        }
+    }
+    for (int c = 0; c < 3; c++) {
+        const Dims3 d0 = dims_of(0);
+        const int64_t pitch0 = g->qpitch[0][c];
+        if (c > 0 || pitch0 != d0.x) {
+            const int64_t n = pitch0 * (nvox(d0) / (c == 0 ? d0.x : c == 1 ? d0.y : d0.z));
+            MG_TRY(g->mip0x[c].alloc(&g->al, (size_t)n * g->id0_bytes, s));
+            if (g->id0_bytes == 2)
+                transpose_copy_kernel<uint16_t><<<grid_n(n), 256, 0, s>>>(g->mip0.as<uint16_t>(),
+                                                                          g->mip0x[c].as<uint16_t>(), d0, c, pitch0);
+            else
+                transpose_copy_kernel<uint32_t><<<grid_n(n), 256, 0, s>>>(g->mip0.as<uint32_t>(),
+                                                                          g->mip0x[c].as<uint32_t>(), d0, c, pitch0);
+            MG_CUDA(cudaGetLastError());
+        }
+        if (hi_total[c] > 0) {
+            MG_TRY(g->mipx[c].alloc(&g->al, (size_t)hi_total[c] * 4, s));
+            for (int l = 1; l < L; l++) {
+                const Dims3 d = dims_of(l);
+                const int64_t pitch = g->qpitch[l][c];
+                const int64_t n = pitch * (nvox(d) / (c == 0 ? d.x : c == 1 ? d.y : d.z));
+                transpose_copy_kernel<uint32_t><<<grid_n(n), 256, 0, s>>>(
+                    g->mip.as<uint32_t>() + g->geom.off[l], g->mipx[c].as<uint32_t>() + g->qoff[l][c], d, c, pitch);
+                MG_CUDA(cudaGetLastError());
+            }
+        }
+    }
     return MG_OK;
 }
 

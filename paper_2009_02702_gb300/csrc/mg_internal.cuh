@@ -137,12 +137,17 @@ struct mg_graph {
     mg::Buf mip0;
     // levels 1..L-1 concatenated, uint32 node IDs
     mg::Buf mip;
-    // axis-major copies of the same IDs for box queries: copy 1 is y-fastest
-    // (order y, z, x), copy 2 is z-fastest (order z, x, y); copy 0 is the
-    // x-fastest array above.  A footprint block reads the copy whose fastest
-    // axis is its longest side.
-    mg::Buf mip0x[2];
-    mg::Buf mipx[2];
+    // axis-major copies of the same IDs for box queries: copy 0 is x-fastest
+    // (order x, y, z), copy 1 y-fastest (order y, z, x), copy 2 z-fastest
+    // (order z, x, y).  A footprint block reads the copy whose fastest axis is
+    // its longest side.  Rows of copy c at level l are qpitch[l][c] IDs apart,
+    // the row length rounded up to 32 bytes, so every row starts on a 32-byte
+    // boundary; levels >= 1 are concatenated at qoff[l][c].  Copy 0 of level 0
+    // is mip0 itself when its rows need no padding (mip0x[0] empty then).
+    mg::Buf mip0x[3];
+    mg::Buf mipx[3];
+    int32_t qpitch[MG_MAX_LEVELS][3] = {};
+    int64_t qoff[MG_MAX_LEVELS][3] = {};
     // node table, canonical order, N entries
     mg::Buf pq;       // uint2 (p, q); (kNone, kNone) for sources
     mg::Buf ab;       // ulonglong2 (a, b) exact coprime weights
@@ -196,6 +201,8 @@ mg_status propagate(mg_graph* g, const float* tf, int C, mg_dtype storage, void*
 mg_status propagate_multi(mg_graph* g, const float* tf, int k, int C, mg_dtype storage, void* vals, cudaStream_t s);
 // the per-node mixture lookup table of the range queries (after the build)
 mg_status build_lut(mg_graph* g, cudaStream_t s);
+// the padded axis-major copies of the box queries, from mip0 and mip
+mg_status build_query_copies(mg_graph* g, cudaStream_t s);
 mg_status ensure_alpha16(mg_graph* g, mg_dtype dt, cudaStream_t s);
 mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const mg_query_opts& o,
                       void* out, size_t cap, uint32_t* seg, uint64_t* offsets, size_t* required,

@@ -6,7 +6,8 @@
 // Image: a fixed header (magic, version, sizes, geometry, depth buckets, the
 // byte size of every array), then the arrays in header order, each starting
 // on a 256-byte boundary.  Import validates the header and every size before
-// allocating anything.
+// allocating anything.  The padded axis-major copies of the box queries are
+// not stored: import rebuilds them from the mip levels.
 #include "mg_internal.cuh"
 
 #include <cstring>
@@ -15,8 +16,8 @@ namespace mg {
 namespace {
 
 constexpr char kMagic[8] = {'M', 'G', 'R', 'A', 'P', 'H', '0', '1'};
-constexpr uint32_t kVersion = 1;
-constexpr int kArrays = 12;   // mip0, mip, mip0x[2], mipx[2], pq, ab, ab32, alpha, lut_meta, lut
+constexpr uint32_t kVersion = 2;
+constexpr int kArrays = 8;   // mip0, mip, pq, ab, ab32, alpha, lut_meta, lut
 
 struct Header {
     char magic[8];
@@ -32,8 +33,7 @@ struct Header {
 size_t round_up(size_t n) { return (n + 255) & ~(size_t)255; }
 
 Buf* arrays(mg_graph* g, int k) {
-    Buf* a[kArrays] = {&g->mip0, &g->mip, &g->mip0x[0], &g->mip0x[1], &g->mipx[0], &g->mipx[1],
-                       &g->pq,   &g->ab,  &g->ab32,     &g->alpha,    &g->lut_meta, &g->lut};
+    Buf* a[kArrays] = {&g->mip0, &g->mip, &g->pq, &g->ab, &g->ab32, &g->alpha, &g->lut_meta, &g->lut};
     return a[k];
 }
 
@@ -132,15 +132,13 @@ MG_API mg_status mg_graph_import(const void* host, size_t bytes, const mg_alloca
     }
     if (ok) {
         const uint64_t want[kArrays] = {(uint64_t)V0 * h.id0_bytes, (uint64_t)hi * 4,
-                                        (uint64_t)V0 * h.id0_bytes, (uint64_t)V0 * h.id0_bytes,
-                                        (uint64_t)hi * 4, (uint64_t)hi * 4,
                                         (uint64_t)h.N * 8, (uint64_t)h.N * 16, (uint64_t)h.N * 8, (uint64_t)h.N * 4,
-                                        h.bytes[10] ? (uint64_t)h.N * 8 : 0ull, h.bytes[11]};
+                                        h.bytes[6] ? (uint64_t)h.N * 8 : 0ull, h.bytes[7]};
         for (int k = 0; k < kArrays; k++)
             if (h.bytes[k] != want[k]) ok = false;
         // the table: a row directory of N entries, or none; entries at least lut_entries
-        if (h.bytes[11] < (uint64_t)h.lut_entries * 8) ok = false;
-        if (!h.bytes[10] && (h.bytes[11] || h.lut_entries)) ok = false;
+        if (h.bytes[7] < (uint64_t)h.lut_entries * 8) ok = false;
+        if (!h.bytes[6] && (h.bytes[7] || h.lut_entries)) ok = false;
         if (h.bucket[0] != 0 || h.bucket[1] != (int64_t)h.S || h.bucket[h.D + 1] != h.N) ok = false;
         for (int d = 0; d <= h.D; d++)
             if (h.bucket[d + 1] < h.bucket[d]) ok = false;
@@ -181,8 +179,10 @@ MG_API mg_status mg_graph_import(const void* host, size_t bytes, const mg_alloca
     }
     MG_TRY(g->status.alloc(&g->al, sizeof(unsigned), s));
     MG_CUDA(cudaMemsetAsync(g->status.p, 0, sizeof(unsigned), s));
+    MG_TRY(build_query_copies(g.get(), s));
     MG_CUDA(cudaStreamSynchronize(s));   // the host image may be freed on return
     for (int k = 0; k < kArrays; k++) arrays(g.get(), k)->s = nullptr;
+    for (int c = 0; c < 3; c++) g->mip0x[c].s = g->mipx[c].s = nullptr;
     g->status.s = nullptr;
     *out = g.release();
     return MG_OK;

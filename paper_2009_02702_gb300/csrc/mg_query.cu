@@ -46,9 +46,10 @@ struct Geom {
     int id0_bytes;
     uint32_t S;
     int32_t dims[MG_MAX_LEVELS][3];
-    int64_t off[MG_MAX_LEVELS];
+    // offset of level l >= 1 in copy c's concatenated levels
+    int64_t off[MG_MAX_LEVELS][3];
     // strides of the second and third axis of each copy (copy 0: x, y, z;
-    // copy 1: y, z, x; copy 2: z, x, y)
+    // copy 1: y, z, x; copy 2: z, x, y): the row pitch and pitch x middle dim
     uint32_t st1[MG_MAX_LEVELS][3], st2[MG_MAX_LEVELS][3];
     // bit l of vec_ok[c] / vec32_ok[c]: every row of copy c at level l starts
     // on a 16-byte / 32-byte boundary (row pitch and level offset multiples)
@@ -73,21 +74,24 @@ Geom make_geom(const mg_graph* g) {
     G.S = g->S;
     for (int l = 0; l < MG_MAX_LEVELS; l++) {
         for (int k = 0; k < 3; k++) G.dims[l][k] = g->geom.dims[l][k];
-        G.off[l] = g->geom.off[l];
         const uint32_t dx = (uint32_t)G.dims[l][0], dy = (uint32_t)G.dims[l][1], dz = (uint32_t)G.dims[l][2];
-        G.st1[l][0] = dx; G.st2[l][0] = dx * dy;
-        G.st1[l][1] = dy; G.st2[l][1] = dy * dz;
-        G.st1[l][2] = dz; G.st2[l][2] = dz * dx;
+        const uint32_t mid[3] = {dy, dz, dx};
+        for (int c = 0; c < 3; c++) {
+            G.off[l][c] = g->qoff[l][c];
+            const uint32_t pitch = l < g->L ? (uint32_t)g->qpitch[l][c] : 1u;
+            G.st1[l][c] = pitch;
+            G.st2[l][c] = pitch * mid[c];
+        }
     }
     for (int c = 0; c < 3; c++) {
         G.vec_ok[c] = G.vec32_ok[c] = 0;
         for (int l = 0; l < G.L && l < MG_MAX_LEVELS; l++) {
             const uint32_t per16 = l == 0 ? 16u / (uint32_t)G.id0_bytes : 4u;   // IDs per 16 bytes
             const bool ok = G.st1[l][c] % per16 == 0 && G.st2[l][c] % per16 == 0 &&
-                            (l == 0 || G.off[l] % per16 == 0);
+                            (l == 0 || G.off[l][c] % per16 == 0);
             const uint32_t per32 = 2 * per16;
             const bool ok32 = G.st1[l][c] % per32 == 0 && G.st2[l][c] % per32 == 0 &&
-                              (l == 0 || G.off[l] % per32 == 0);
+                              (l == 0 || G.off[l][c] % per32 == 0);
             if (ok) G.vec_ok[c] |= 1u << l;
             if (ok32) G.vec32_ok[c] |= 1u << l;
         }
@@ -97,12 +101,10 @@ Geom make_geom(const mg_graph* g) {
 
 Ids make_ids(const mg_graph* g) {
     Ids I;
-    I.l0[0] = g->mip0.p;
-    I.l0[1] = g->mip0x[0].p;
-    I.l0[2] = g->mip0x[1].p;
-    I.hi[0] = g->mip.as<uint32_t>();
-    I.hi[1] = g->mipx[0].as<uint32_t>();
-    I.hi[2] = g->mipx[1].as<uint32_t>();
+    for (int c = 0; c < 3; c++) {
+        I.l0[c] = g->mip0x[c].p ? g->mip0x[c].p : g->mip0.p;   // copy 0 may be mip0 itself
+        I.hi[c] = g->mipx[c].as<uint32_t>();
+    }
     return I;
 }
 
@@ -112,18 +114,17 @@ __device__ __forceinline__ Blk make_blk(const Geom& G, uint32_t start, int32_t x
     const int l = min(lx, min(ly, lz));
     const int ex = lx - l, ey = ly - l, ez = lz - l;
     const uint32_t X = (uint32_t)x0 >> l, Y = (uint32_t)y0 >> l, Z = (uint32_t)z0 >> l;
-    const uint32_t dx = (uint32_t)G.dims[l][0], dy = (uint32_t)G.dims[l][1], dz = (uint32_t)G.dims[l][2];
     int c, e0, e1, e2;
     uint32_t base;
     if (ex >= ey && ex >= ez) {
         c = 0; e0 = ex; e1 = ey; e2 = ez;
-        base = (Z * dy + Y) * dx + X;
+        base = Z * G.st2[l][0] + Y * G.st1[l][0] + X;
     } else if (ey >= ez) {
         c = 1; e0 = ey; e1 = ez; e2 = ex;
-        base = (X * dz + Z) * dy + Y;
+        base = X * G.st2[l][1] + Z * G.st1[l][1] + Y;
     } else {
         c = 2; e0 = ez; e1 = ex; e2 = ey;
-        base = (Y * dx + X) * dz + Z;
+        base = Y * G.st2[l][2] + X * G.st1[l][2] + Z;
     }
     Blk B;
     B.start = start;
@@ -851,11 +852,30 @@ __device__ void push_frac(const PushArgs& P, const Hist<true>& H, uint32_t n, fl
     }
 }
 
+// the push of one (node, weight) by one lane: its mixture-table row, else its
+// lerp tree
+template <bool FP, typename AT>
+__device__ __noinline__ void push_one(const PushArgs& P, const Hist<FP>& H, uint32_t n, uint32_t w) {
+    if (std::is_same<AT, float>::value && P.lut_meta) {
+        uint32_t off, len, k;
+        lut_row(P, n, w, off, len, k);
+        if (len) {
+            for (uint32_t e = 0; e < len; e++) {
+                const uint2 ent = __ldg(P.lut + off + e);
+                H.add_int(ent.x, k * ent.y);
+            }
+            return;
+        }
+    }
+    if constexpr (FP) push_frac<AT>(P, H, n, (float)w);
+    else push_int<FP>(P, H, n, w);
+}
+
 __device__ __forceinline__ uint32_t read_id(const Geom& G, const Ids& I, int l, int c, uint32_t idx) {
     if (l == 0)
         return G.id0_bytes == 2 ? (uint32_t)__ldg(static_cast<const uint16_t*>(I.l0[c]) + idx)
                                 : __ldg(static_cast<const uint32_t*>(I.l0[c]) + idx);
-    return __ldg(I.hi[c] + G.off[l] + idx);
+    return __ldg(I.hi[c] + G.off[l][c] + idx);
 }
 
 // node ID of cube o of block B
@@ -880,19 +900,7 @@ __device__ __forceinline__ void accumulate(const PushArgs& P, const Hist<FP>& H,
         H.add_int(id, W);
         return;
     }
-    if (std::is_same<AT, float>::value && P.lut_meta) {
-        uint32_t off, len, k;
-        lut_row(P, id, W, off, len, k);
-        if (len) {
-            for (uint32_t e = 0; e < len; e++) {
-                const uint2 ent = __ldg(P.lut + off + e);
-                H.add_int(ent.x, k * ent.y);
-            }
-            return;
-        }
-    }
-    if constexpr (FP) push_frac<AT>(P, H, id, (float)W);
-    else push_int<FP>(P, H, id, W);
+    push_one<FP, AT>(P, H, id, W);
 }
 
 template <bool FP>
@@ -975,8 +983,16 @@ __device__ __forceinline__ void main_out(const MainArgs& A, uint32_t*& acc, floa
     }
 }
 
-constexpr int kQueue = 320;   // pending internal-node pushes per warp (drained at >= 32)
-constexpr size_t kQueueBytes = (size_t)kQueue * 8 + 16;   // nodes, weights, counter
+// A warp's pending internal-node pushes: an open-addressing table in shared
+// memory keyed by node ID, so runs of one node in a chunk are summed and the
+// node is expanded (mixture table row or lerp tree) once, when the table has
+// kTableFill distinct nodes between two unit steps or when the chunk ends.
+// Weights are box volumes' parts, so the sums stay below 2^32.
+constexpr int kTable = 256;                  // slots per warp (a power of two)
+constexpr uint32_t kTableFill = 96;          // distinct nodes that trigger an expansion
+constexpr int kProbes = 16;                  // probes before a push bypasses the table
+constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;  // never a node ID (N < 2^32)
+constexpr size_t kQueueBytes = (size_t)kTable * 8 + 16;   // keys, weights, counter
 
 // chunks of the launch: known on the host, or (plans) read on the device,
 // zero when the batch overflows the plan's buffers
@@ -986,33 +1002,58 @@ __device__ __forceinline__ unsigned long long main_total(const MainArgs& A) {
     return over_cap(A.lim, A.blk_off, A.chunk_off, Qe) ? 0ull : A.chunk_off[Qe];
 }
 
-// a warp's queue of internal-node pushes in shared memory
 struct Queue {
-    uint32_t* n;
-    uint32_t* w;
-    uint32_t* count;
+    uint32_t* n;       // node of every slot (kEmptyKey: free)
+    uint32_t* w;       // summed weight of every slot
+    uint32_t* count;   // occupied slots
 };
 
 __device__ __forceinline__ Queue carve_queue(uint8_t* p) {
     Queue Qu;
     Qu.n = reinterpret_cast<uint32_t*>(p);
-    Qu.w = Qu.n + kQueue;
-    Qu.count = Qu.w + kQueue;
+    Qu.w = Qu.n + kTable;
+    Qu.count = Qu.w + kTable;
     return Qu;
 }
 
-// push `take` <= 32 queued (node, weight) entries.  With the mixture table
-// the rows of all of them are flattened: entry e goes to lane e % 32, which
-// finds its row by a binary search over the inclusive sums of the row
-// lengths; nodes without a row (and 16-bit weights) walk their lerp trees.
+// every slot free (one warp)
+__device__ __forceinline__ void clear_queue(const Queue& Qu) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < kTable; i += 32) {
+        Qu.n[i] = kEmptyKey;
+        Qu.w[i] = 0u;
+    }
+    if (lane == 0) *Qu.count = 0u;
+    __syncwarp();
+}
+
+// add weight w to node n's slot (one lane); false when every probed slot
+// holds another node
+__device__ __forceinline__ bool table_add(const Queue& Qu, uint32_t n, uint32_t w) {
+    uint32_t h = (n * 0x9E3779B1u) >> 24;   // top 8 bits: kTable = 256
+    for (int i = 0; i < kProbes; i++) {
+        const uint32_t old = atomicCAS(Qu.n + h, kEmptyKey, n);
+        if (old == kEmptyKey || old == n) {
+            if (old == kEmptyKey) atomicAdd(Qu.count, 1u);
+            atomicAdd(Qu.w + h, w);
+            return true;
+        }
+        h = (h + 1) & (kTable - 1);
+    }
+    return false;
+}
+
+// push one (node, weight) per lane where `valid`.  With the mixture table the
+// rows of all of them are flattened: entry e goes to lane e % 32, which finds
+// its row by a binary search over the inclusive sums of the row lengths;
+// nodes without a row (and 16-bit weights) walk their lerp trees.
 template <bool FP, typename AT>
-__device__ __forceinline__ void push_batch(const PushArgs& P, const Hist<FP>& H, const uint32_t* qn,
-                                           const uint32_t* qw, uint32_t take) {
+__device__ __forceinline__ void push_lanes(const PushArgs& P, const Hist<FP>& H, bool valid, uint32_t n,
+                                           uint32_t w) {
     const int lane = threadIdx.x & 31;
     if (std::is_same<AT, float>::value && P.lut_meta) {
         uint32_t off = 0, len = 0, k = 0;
-        if ((uint32_t)lane < take) {
-            const uint32_t n = qn[lane], w = qw[lane];
+        if (valid) {
             lut_row(P, n, w, off, len, k);
             if (!len) {
                 if constexpr (FP) push_frac<AT>(P, H, n, (float)w);
@@ -1044,39 +1085,32 @@ __device__ __forceinline__ void push_batch(const PushArgs& P, const Hist<FP>& H,
                 H.add_int(ent.x, kj * ent.y);
             }
         }
-    } else if ((uint32_t)lane < take) {
-        const uint32_t n = qn[lane], w = qw[lane];
+    } else if (valid) {
         if constexpr (FP) push_frac<AT>(P, H, n, (float)w);
         else push_int<FP>(P, H, n, w);
     }
     __syncwarp();
 }
 
-// push queued entries 32 at a time until fewer than 32 (none if `all`) remain,
-// then move the rest to the front
+// expand every node of the warp's table (32 slots at a time) and free the slots
 template <bool FP, typename AT>
-__device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Queue& Qu, bool all) {
+__device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Queue& Qu) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
-    const uint32_t qc = *Qu.count;
-    uint32_t done = 0;
-    while (qc - done >= 32 || (all && qc > done)) {
-        const uint32_t take = min(qc - done, 32u);
-        push_batch<FP, AT>(P, H, Qu.n + done, Qu.w + done, take);
-        done += take;
-    }
-    const uint32_t rest = qc - done;
-    uint32_t tn = 0, tw = 0;
-    if ((uint32_t)lane < rest) {
-        tn = Qu.n[done + lane];
-        tw = Qu.w[done + lane];
+    if (*Qu.count == 0u) return;
+    for (int b = 0; b < kTable; b += 32) {
+        const uint32_t n = Qu.n[b + lane];
+        const bool v = n != kEmptyKey;
+        uint32_t w = 0u;
+        if (v) {
+            w = Qu.w[b + lane];
+            Qu.n[b + lane] = kEmptyKey;
+            Qu.w[b + lane] = 0u;
+        }
+        if (__any_sync(0xffffffffu, v)) push_lanes<FP, AT>(P, H, v, n, w);
     }
     __syncwarp();
-    if ((uint32_t)lane < rest) {
-        Qu.n[lane] = tn;
-        Qu.w[lane] = tw;
-    }
-    if (lane == 0) *Qu.count = rest;
+    if (lane == 0) *Qu.count = 0u;
     __syncwarp();
 }
 
@@ -1109,10 +1143,8 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
         const uint32_t W = rcnt << (3 * rl);
         if (rl == 0 || rid < S) {
             H.add_int(rid, W);
-        } else {
-            const uint32_t pos = atomicAdd(Qu.count, 1u);
-            Qu.n[pos] = rid;
-            Qu.w[pos] = W;
+        } else if (!table_add(Qu, rid, W)) {
+            push_one<FP, AT>(A.P, H, rid, W);
         }
     };
     auto feed = [&](uint32_t x, int l) {
@@ -1209,7 +1241,7 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
                         ul[r] = jl;
                         const bool u16 = jl == 0 && lg0 == 3;
                         const void* row =
-                            jl == 0 ? A.I.l0[jc] : static_cast<const void*>(A.I.hi[jc] + A.G.off[jl]);
+                            jl == 0 ? A.I.l0[jc] : static_cast<const void*>(A.I.hi[jc] + A.G.off[jl][jc]);
                         if (vv) {
                             const uint4* p = reinterpret_cast<const uint4*>(
                                 u16 ? static_cast<const void*>(static_cast<const uint16_t*>(row) + idx)
@@ -1231,10 +1263,20 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
                     if (k == 0) {
                         feed(x.x, l);
                     } else if (k == 1 || k == 3) {
-                        const bool same = rcnt && rl == l && x.x == rid && x.y == rid && x.z == rid && x.w == rid &&
-                                          (k == 1 || (y.x == rid && y.y == rid && y.z == rid && y.w == rid));
-                        if (same) {
-                            rcnt += k == 1 ? 4 : 8;
+                        // a vector of one node: extend the lane's run or start a new one
+                        const uint32_t f = x.x;
+                        const bool uni = x.y == f && x.z == f && x.w == f &&
+                                         (k == 1 || (y.x == f && y.y == f && y.z == f && y.w == f));
+                        if (uni) {
+                            const uint32_t nn = k == 1 ? 4u : 8u;
+                            if (rcnt && rl == l && rid == f) {
+                                rcnt += nn;
+                            } else {
+                                finish();
+                                rid = f;
+                                rl = l;
+                                rcnt = nn;
+                            }
                         } else {
                             feed(x.x, l);
                             feed(x.y, l);
@@ -1248,11 +1290,20 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
                             }
                         }
                     } else if (k == 2 || k == 4) {
-                        const uint32_t pr = rid * 0x10001u;
+                        const uint32_t f = x.x & 0xffffu;   // the vector's first ID
+                        const uint32_t pr = f * 0x10001u;
                         uint32_t diff = (x.x ^ pr) | (x.y ^ pr) | (x.z ^ pr) | (x.w ^ pr);
                         if (k == 4) diff |= (y.x ^ pr) | (y.y ^ pr) | (y.z ^ pr) | (y.w ^ pr);
-                        if (rcnt && rl == 0 && diff == 0u) {
-                            rcnt += k == 2 ? 8 : 16;
+                        if (diff == 0u) {
+                            const uint32_t nn = k == 2 ? 8u : 16u;
+                            if (rcnt && rl == 0 && rid == f) {
+                                rcnt += nn;
+                            } else {
+                                finish();
+                                rid = f;
+                                rl = 0;
+                                rcnt = nn;
+                            }
                         } else {
                             const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
@@ -1266,7 +1317,7 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
                     }
                 }
                 __syncwarp();
-                if (*Qu.count >= 32) drain<FP, AT>(A.P, H, Qu, false);
+                if (*Qu.count >= kTableFill) drain<FP, AT>(A.P, H, Qu);
             }
         };
         if (__any_sync(0xffffffffu, wide)) run_units(std::integral_constant<int, 1>{});
@@ -1301,8 +1352,7 @@ __global__ void __launch_bounds__(256, 5) query_warp_kernel(MainArgs A) {
         H.h[i] = 0;
         if constexpr (FP) H.hf[i] = 0.f;
     }
-    if (lane == 0) *Qu.count = 0;
-    __syncwarp();
+    clear_queue(Qu);
     grid_dependency_wait();
     uint32_t* acc;
     float* accf;
@@ -1318,7 +1368,7 @@ __global__ void __launch_bounds__(256, 5) query_warp_kernel(MainArgs A) {
         const uint32_t c0 = (uint32_t)(c - A.chunk_off[q]) * A.chunk;
         const uint32_t c1 = min(c0 + A.chunk, ncube);
         process_span<FP, AT>(A, H, Qu, c0, c1, __ldg(A.chunk_b + c), A.blk_off[q + 1], ncube);
-        drain<FP, AT>(A.P, H, Qu, true);
+        drain<FP, AT>(A.P, H, Qu);
         for (uint32_t s = lane; s < S; s += 32) {
             const uint32_t v = H.h[s];
             if (v) {
@@ -1358,7 +1408,7 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
         if constexpr (FP) H.hf[i] = 0.f;
     }
     if (threadIdx.x == 0) s_ntouched = 0;
-    if (lane == 0) *Qu.count = 0;
+    clear_queue(Qu);
     grid_dependency_wait();
     uint32_t* acc;
     float* accf;
@@ -1402,7 +1452,7 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
             bhint = b;
             process_span<FP, AT>(A, H, Qu, w0, w1, b, b1, ncube);
         }
-        drain<FP, AT>(A.P, H, Qu, true);
+        drain<FP, AT>(A.P, H, Qu);
         __syncthreads();
         flush<FP>(H, S, q, acc, accf);
         __syncthreads();
@@ -1410,9 +1460,14 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
     }
 }
 
-// baseline: one CTA per box, one launch per box, blocks walked in order
+// Baseline (MG_SCHED_PLAIN): one launch per box, unbatched.  The launch has
+// as many CTAs as the box's footprint needs (about 4,096 cubes each, at most
+// a few per SM); CTA b walks the blocks in order and counts cubes
+// [b * per_cta, (b + 1) * per_cta) of the box into its shared histogram, then
+// adds it to the box's row.
 template <bool FP, typename AT>
-__global__ void __launch_bounds__(256) query_plain_kernel(MainArgs A, const int32_t* __restrict__ boxes, int64_t q) {
+__global__ void __launch_bounds__(256) query_plain_kernel(MainArgs A, const int32_t* __restrict__ boxes, int64_t q,
+                                                          uint32_t per_cta) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t s_ntouched;
     __shared__ Runs R;
@@ -1426,7 +1481,7 @@ __global__ void __launch_bounds__(256) query_plain_kernel(MainArgs A, const int3
 #pragma unroll
     for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
     if (!box_ok(b, A.G)) {
-        if (threadIdx.x == 0) set_status(A.P.status, kStatBadInput);
+        if (threadIdx.x == 0 && blockIdx.x == 0) set_status(A.P.status, kStatBadInput);
         return;
     }
     if (threadIdx.x == 0) {
@@ -1434,74 +1489,143 @@ __global__ void __launch_bounds__(256) query_plain_kernel(MainArgs A, const int3
         make_runs(b, A.G, R);
     }
     __syncthreads();
-    for (int k = 0; k < R.nz; k++)
-        for (int j = 0; j < R.ny; j++)
-            for (int i = 0; i < R.nx; i++) {
-                const Blk B = make_blk(A.G, 0, R.sx[i], R.sy[j], R.sz[k], R.lx[i], R.ly[j], R.lz[k]);
+    const uint64_t c0 = (uint64_t)blockIdx.x * per_cta, c1 = c0 + per_cta;
+    uint64_t start = 0;
+    for (int k = 0; k < R.nz && start < c1; k++)
+        for (int j = 0; j < R.ny && start < c1; j++)
+            for (int i = 0; i < R.nx && start < c1; i++) {
                 const uint32_t n = block_cubes(R.lx[i], R.ly[j], R.lz[k]);
-                for (uint32_t base = 0; base < n; base += blockDim.x) {
-                    const uint32_t o = base + threadIdx.x;
-                    const bool valid = o < n;
-                    uint32_t id = 0;
-                    int lv = 0;
-                    if (valid) id = cube_node(A.G, A.I, B, o, lv);
-                    accumulate<FP, AT>(A.P, H, valid, id, lv);
+                const uint64_t lo = max(start, c0), hi = min(start + n, c1);
+                if (lo < hi) {
+                    const Blk B = make_blk(A.G, 0, R.sx[i], R.sy[j], R.sz[k], R.lx[i], R.ly[j], R.lz[k]);
+                    for (uint64_t base = lo - start; base < hi - start; base += blockDim.x) {
+                        const uint32_t o = (uint32_t)base + threadIdx.x;
+                        const bool valid = o < hi - start;
+                        uint32_t id = 0;
+                        int lv = 0;
+                        if (valid) id = cube_node(A.G, A.I, B, o, lv);
+                        accumulate<FP, AT>(A.P, H, valid, id, lv);
+                    }
                 }
+                start += n;
             }
     __syncthreads();
     flush<FP>(H, S, q, A.acc, A.accf);
 }
 
-// Naive baseline: one CTA per box counts every level-0 voxel of the clipped
-// box into a shared histogram (rows read x-fastest, whole-warp runs of one
-// segment added once).  No mipmap, no graph: the brute force the footprint
-// assembly is measured against.
-template <bool FP>
-__global__ void __launch_bounds__(256) query_naive_kernel(Geom G, const void* __restrict__ ids0,
+// Naive baseline (MG_SCHED_NAIVE): no mipmap and no graph, every level-0
+// voxel of the clipped box counted.  Work items are slabs of consecutive rows
+// (x runs) of one box, about kNaiveSlab voxels each, taken from a global
+// ticket by persistent CTAs; each CTA counts its slab into a shared histogram
+// and adds it to the box's row.  A warp reads a row as 16-byte vectors
+// (8 uint16 or 4 uint32 IDs) from the vector holding its first voxel on,
+// masking the IDs outside the row, and keeps one run per lane.
+constexpr uint32_t kNaiveSlab = 1u << 16;
+
+__device__ __forceinline__ void naive_extent(const int32_t* b, const Geom& G, int64_t& dx, int64_t& dy, int64_t& dz) {
+    dx = min((int64_t)b[0] + b[3], (int64_t)G.dims[0][0]) - b[0];
+    dy = min((int64_t)b[1] + b[4], (int64_t)G.dims[0][1]) - b[1];
+    dz = min((int64_t)b[2] + b[5], (int64_t)G.dims[0][2]) - b[2];
+}
+
+// slabs of every box (0 for a malformed box, whose row stays zero)
+__global__ void naive_count_kernel(Geom G, const int32_t* __restrict__ boxes, int64_t Q, uint64_t* __restrict__ items,
+                                   unsigned* __restrict__ status) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
+    int32_t b[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
+    if (!box_ok(b, G)) {
+        set_status(status, kStatBadInput);
+        items[q] = 0;
+        return;
+    }
+    int64_t dx, dy, dz;
+    naive_extent(b, G, dx, dy, dz);
+    const int64_t rows_per = max((int64_t)1, (int64_t)kNaiveSlab / dx);
+    items[q] = (uint64_t)((dy * dz + rows_per - 1) / rows_per);
+}
+
+template <bool FP, typename T>
+__global__ void __launch_bounds__(256) query_naive_kernel(Geom G, const T* __restrict__ ids0,
                                                           const int32_t* __restrict__ boxes, int64_t Q,
-                                                          uint32_t* __restrict__ acc, float* __restrict__ accf,
-                                                          unsigned* __restrict__ status) {
+                                                          const uint64_t* __restrict__ item_off,
+                                                          unsigned long long* __restrict__ ticket,
+                                                          uint32_t* __restrict__ acc, float* __restrict__ accf) {
     extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ unsigned long long s_item;
     uint32_t* h = reinterpret_cast<uint32_t*>(smem);
     const uint32_t S = G.S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t q = blockIdx.x; q < Q; q += gridDim.x) {
-        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) h[i] = 0;
+    constexpr int E = 16 / (int)sizeof(T);   // IDs per 16-byte vector
+    const unsigned long long total = item_off[Q];
+    for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) h[i] = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1ull);
         __syncthreads();
+        const unsigned long long w = s_item;
+        if (w >= total) break;
+        int64_t lo = 0, hi = Q;   // item_off[lo] <= w < item_off[hi]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (item_off[mid] <= w) lo = mid;
+            else hi = mid;
+        }
+        const int64_t q = lo;
         int32_t b[6];
 #pragma unroll
         for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
-        if (box_ok(b, G)) {
-            const int64_t nx = G.dims[0][0], ny = G.dims[0][1];
-            const int dx = (int)(min((int64_t)b[0] + b[3], nx) - b[0]);
-            const int dy = (int)(min((int64_t)b[1] + b[4], ny) - b[1]);
-            const int dz = (int)(min((int64_t)b[2] + b[5], (int64_t)G.dims[0][2]) - b[2]);
-            // warps take rows (y, z); lanes read along x; each lane keeps a run
-            for (int r = warp; r < dy * dz; r += nw) {
-                const int64_t row = ((int64_t)(b[2] + r / dy) * ny + b[1] + r % dy) * nx + b[0];
-                uint32_t rid = kNone, rcnt = 0;
-                for (int x = lane; x < dx; x += 32) {
-                    const uint32_t id = G.id0_bytes == 2 ? (uint32_t)__ldg(static_cast<const uint16_t*>(ids0) + row + x)
-                                                         : __ldg(static_cast<const uint32_t*>(ids0) + row + x);
-                    if (id != rid) {
+        int64_t dx, dy, dz;
+        naive_extent(b, G, dx, dy, dz);
+        const int64_t rows_per = max((int64_t)1, (int64_t)kNaiveSlab / dx);
+        const int64_t r0 = (int64_t)(w - item_off[q]) * rows_per, r1 = min(r0 + rows_per, dy * dz);
+        const int64_t nx = G.dims[0][0], ny = G.dims[0][1];
+        for (int64_t r = r0 + warp; r < r1; r += nw) {
+            const int64_t e0 = ((int64_t)(b[2] + r / dy) * ny + b[1] + r % dy) * nx + b[0], e1 = e0 + dx;
+            uint32_t rid = kNone, rcnt = 0;
+            for (int64_t v = e0 / E + lane; v * E < e1; v += 32) {
+                const uint4 u = __ldg(reinterpret_cast<const uint4*>(ids0) + v);
+                const T* x = reinterpret_cast<const T*>(&u);
+                const int64_t p0 = v * E;
+                const bool whole = p0 >= e0 && p0 + E <= e1;
+                bool uni = whole;
+#pragma unroll
+                for (int k = 1; k < E; k++) uni = uni && x[k] == x[0];
+                if (uni) {
+                    if (rcnt && rid == (uint32_t)x[0]) {
+                        rcnt += E;
+                    } else {
+                        if (rcnt) atomicAdd(h + rid, rcnt);
+                        rid = (uint32_t)x[0];
+                        rcnt = E;
+                    }
+                    continue;
+                }
+#pragma unroll
+                for (int k = 0; k < E; k++) {
+                    if (p0 + k < e0 || p0 + k >= e1) continue;
+                    const uint32_t id = (uint32_t)x[k];
+                    if (rcnt && id == rid) {
+                        rcnt++;
+                    } else {
                         if (rcnt) atomicAdd(h + rid, rcnt);
                         rid = id;
                         rcnt = 1;
-                    } else {
-                        rcnt++;
                     }
                 }
-                if (rcnt) atomicAdd(h + rid, rcnt);
             }
-        } else if (threadIdx.x == 0) {
-            set_status(status, kStatBadInput);
+            if (rcnt) atomicAdd(h + rid, rcnt);
         }
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
-            if (FP) accf[q * S + i] = (float)h[i];
-            else acc[q * S + i] = h[i];
+            const uint32_t c = h[i];
+            if (c) {
+                h[i] = 0;
+                if (FP) atomicAdd(accf + q * S + i, (float)c);
+                else atomicAdd(acc + q * S + i, c);
+            }
         }
-        __syncthreads();
     }
 }
 
@@ -1676,23 +1800,54 @@ mg_status prepare_kernel(K kernel, size_t smem) {
 // CTAs start while the plan kernel finishes and wait for it on the device)
 template <bool FP, typename AT>
 mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts& o, const int32_t* boxes,
-                      size_t smem, int threads, cudaStream_t s, bool pdl = false) {
+                      size_t smem, int threads, cudaStream_t s, bool pdl = false, const Alloc* scratch = nullptr) {
     if (o.schedule == MG_SCHED_NAIVE) {
-        auto k = query_naive_kernel<FP>;
-        const size_t sm = (size_t)g->S * 4;
-        MG_TRY(prepare_kernel(k, sm));
-        int per_sm = 0;
-        MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, sm));
-        const int64_t grid = std::min<int64_t>(A.Q, (int64_t)std::max(per_sm, 1) * sm_count(g->device));
-        k<<<(unsigned)grid, 256, sm, s>>>(A.G, A.I.l0[0], boxes, A.Q, A.acc, A.accf, A.P.status);
+        // slabs per box, their offsets, then one persistent launch
+        if (!scratch) return fail(MG_ERR_INVALID_ARG, "naive schedule without scratch");
+        Buf items, off, ticket;
+        MG_TRY(items.alloc(scratch, (size_t)A.Q * 8, s));
+        MG_TRY(off.alloc(scratch, (size_t)(A.Q + 1) * 8, s));
+        MG_TRY(ticket.alloc(scratch, 8, s));
+        naive_count_kernel<<<grid_for(A.Q, 256), 256, 0, s>>>(A.G, boxes, A.Q, items.as<uint64_t>(), A.P.status);
         MG_CUDA(cudaGetLastError());
-        return MG_OK;
+        MG_TRY(scan_exclusive_u64(items.as<uint64_t>(), off.as<uint64_t>(), A.Q, off.as<uint64_t>() + A.Q, *scratch,
+                                  s));
+        MG_CUDA(cudaMemsetAsync(ticket.p, 0, 8, s));
+        const size_t sm = (size_t)g->S * 4;
+        auto launch = [&](auto k, const void* ids) -> mg_status {
+            MG_TRY(prepare_kernel(k, sm));
+            int per_sm = 0;
+            MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, sm));
+            const int grid = std::max(per_sm, 1) * sm_count(g->device);
+            using T = std::conditional_t<std::is_same<decltype(k), decltype(&query_naive_kernel<FP, uint16_t>)>::value,
+                                         uint16_t, uint32_t>;
+            k<<<grid, 256, sm, s>>>(A.G, static_cast<const T*>(ids), boxes, A.Q, off.as<uint64_t>(),
+                                    ticket.as<unsigned long long>(), A.acc, A.accf);
+            MG_CUDA(cudaGetLastError());
+            return MG_OK;
+        };
+        if (g->id0_bytes == 2) return launch(&query_naive_kernel<FP, uint16_t>, g->mip0.p);
+        return launch(&query_naive_kernel<FP, uint32_t>, g->mip0.p);
     }
     if (o.schedule == MG_SCHED_PLAIN) {
+        // footprint cubes of every box, read back to size each box's launch
+        if (!scratch) return fail(MG_ERR_INVALID_ARG, "plain schedule without scratch");
+        Buf cubes;
+        MG_TRY(cubes.alloc(scratch, (size_t)A.Q * 8, s));
+        plan_count_kernel<<<grid_for(A.Q * 32, kPlanThreads), kPlanThreads, 0, s>>>(
+            A.G, boxes, A.Q, 1, nullptr, cubes.as<uint64_t>(), nullptr, A.P.status, Lim{nullptr, 0, 0});
+        MG_CUDA(cudaGetLastError());
+        std::vector<uint64_t> nc((size_t)A.Q);
+        MG_CUDA(cudaMemcpyAsync(nc.data(), cubes.p, (size_t)A.Q * 8, cudaMemcpyDeviceToHost, s));
+        MG_CUDA(cudaStreamSynchronize(s));
         auto k = query_plain_kernel<FP, AT>;
         MG_TRY(prepare_kernel(k, smem));
+        const uint64_t max_ctas = 4ull * sm_count(g->device);
         for (int64_t q = 0; q < A.Q; q++) {
-            k<<<1, 256, smem, s>>>(A, boxes, q);
+            const uint64_t n = std::max<uint64_t>(nc[q], 1);
+            const uint64_t ctas = std::min<uint64_t>(max_ctas, (n + 4095) / 4096);
+            const uint32_t per = (uint32_t)((n + ctas - 1) / ctas);
+            k<<<(unsigned)ctas, 256, smem, s>>>(A, boxes, q, per);
         }
         MG_CUDA(cudaGetLastError());
         return MG_OK;
@@ -1881,11 +2036,14 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
     MG_CUDA(cudaMemsetAsync(acc, 0, cells * 4, s));
     if (timed) MG_CUDA(cudaEventRecord(gm->qev[1], s));
     if (FP) {
-        if (o.alpha_dtype == MG_F16) MG_TRY((launch_main<true, __half>(g, A, o, boxes, smem, threads, s)));
-        else if (o.alpha_dtype == MG_BF16) MG_TRY((launch_main<true, __nv_bfloat16>(g, A, o, boxes, smem, threads, s)));
-        else MG_TRY((launch_main<true, float>(g, A, o, boxes, smem, threads, s)));
+        if (o.alpha_dtype == MG_F16)
+            MG_TRY((launch_main<true, __half>(g, A, o, boxes, smem, threads, s, false, &al)));
+        else if (o.alpha_dtype == MG_BF16)
+            MG_TRY((launch_main<true, __nv_bfloat16>(g, A, o, boxes, smem, threads, s, false, &al)));
+        else
+            MG_TRY((launch_main<true, float>(g, A, o, boxes, smem, threads, s, false, &al)));
     } else {
-        MG_TRY((launch_main<false, float>(g, A, o, boxes, smem, threads, s)));
+        MG_TRY((launch_main<false, float>(g, A, o, boxes, smem, threads, s, false, &al)));
     }
 
     if (timed) MG_CUDA(cudaEventRecord(gm->qev[2], s));
