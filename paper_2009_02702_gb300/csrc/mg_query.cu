@@ -992,7 +992,7 @@ constexpr int kTable = 256;                  // slots per warp (a power of two)
 constexpr uint32_t kTableFill = 96;          // distinct nodes that trigger an expansion
 constexpr int kProbes = 16;                  // probes before a push bypasses the table
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;  // never a node ID (N < 2^32)
-constexpr size_t kQueueBytes = (size_t)kTable * 8 + 16;   // keys, weights, counter
+constexpr size_t kQueueBytes = (size_t)kTable * 10 + 16;  // keys, weights, occupied-slot list, counter
 
 // chunks of the launch: known on the host, or (plans) read on the device,
 // zero when the batch overflows the plan's buffers
@@ -1006,6 +1006,7 @@ struct Queue {
     uint32_t* n;       // node of every slot (kEmptyKey: free)
     uint32_t* w;       // summed weight of every slot
     uint32_t* count;   // occupied slots
+    uint16_t* used;    // the occupied slots, in order of first use
 };
 
 __device__ __forceinline__ Queue carve_queue(uint8_t* p) {
@@ -1013,6 +1014,7 @@ __device__ __forceinline__ Queue carve_queue(uint8_t* p) {
     Qu.n = reinterpret_cast<uint32_t*>(p);
     Qu.w = Qu.n + kTable;
     Qu.count = Qu.w + kTable;
+    Qu.used = reinterpret_cast<uint16_t*>(Qu.count + 4);
     return Qu;
 }
 
@@ -1034,7 +1036,7 @@ __device__ __forceinline__ bool table_add(const Queue& Qu, uint32_t n, uint32_t 
     for (int i = 0; i < kProbes; i++) {
         const uint32_t old = atomicCAS(Qu.n + h, kEmptyKey, n);
         if (old == kEmptyKey || old == n) {
-            if (old == kEmptyKey) atomicAdd(Qu.count, 1u);
+            if (old == kEmptyKey) Qu.used[atomicAdd(Qu.count, 1u)] = (uint16_t)h;
             atomicAdd(Qu.w + h, w);
             return true;
         }
@@ -1092,22 +1094,24 @@ __device__ __forceinline__ void push_lanes(const PushArgs& P, const Hist<FP>& H,
     __syncwarp();
 }
 
-// expand every node of the warp's table (32 slots at a time) and free the slots
+// expand every node of the warp's table, 32 occupied slots at a time from
+// the list of occupied slots, and free the slots
 template <bool FP, typename AT>
 __device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Queue& Qu) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
-    if (*Qu.count == 0u) return;
-    for (int b = 0; b < kTable; b += 32) {
-        const uint32_t n = Qu.n[b + lane];
-        const bool v = n != kEmptyKey;
-        uint32_t w = 0u;
+    const uint32_t cnt = *Qu.count;
+    for (uint32_t b = 0; b < cnt; b += 32) {
+        const bool v = b + lane < cnt;
+        uint32_t n = 0u, w = 0u;
         if (v) {
-            w = Qu.w[b + lane];
-            Qu.n[b + lane] = kEmptyKey;
-            Qu.w[b + lane] = 0u;
+            const uint32_t slot = Qu.used[b + lane];
+            n = Qu.n[slot];
+            w = Qu.w[slot];
+            Qu.n[slot] = kEmptyKey;
+            Qu.w[slot] = 0u;
         }
-        if (__any_sync(0xffffffffu, v)) push_lanes<FP, AT>(P, H, v, n, w);
+        push_lanes<FP, AT>(P, H, v, n, w);
     }
     __syncwarp();
     if (lane == 0) *Qu.count = 0u;
