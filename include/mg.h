@@ -322,6 +322,49 @@ MG_API mg_status mg_render_lookup_multi(const mg_graph *g, const void *vals, int
                                         const float *samples, const int64_t *offsets, void *out, mg_stream stream);
 
 /*
+ * mg_raymarch -- direct volume rendering from the graph (Sec. 4) into a
+ * headless image.  For pixel (i, j) (row 0 at the top) the ray leaves `eye`
+ * along fwd + ((i + 1/2 - W/2) pix) right + ((H/2 - j - 1/2) pix) up,
+ * normalised, and is clipped to the volume [0, nx] x [0, ny] x [0, nz]
+ * (level-0 voxel units, voxel v covering [v, v+1)).  Samples lie on the
+ * lattice t_k = t_start + k * base_step.  A sample's LOD is floor(log2(t *
+ * pix)) + lod_bias (pixel coverage linear in depth); it picks level m = the
+ * LOD clamped to [0, L-1] and the step 2^m * base_step (the next sample is
+ * k + 2^m).  The sample's value is trilinear within level m between the 8
+ * voxel centres around it (clamped to the level) and, when the LOD lies
+ * between m and m+1 < L, linear between the two levels by the fractional LOD
+ * (quadrilinear).  Opacity correction for the step: alpha' = 1 - (1 -
+ * alpha)^(2^m).  Compositing is front to back with weight (1 - A) alpha' on
+ * the sample's colour; the ray stops once A >= ert (ert > 1: never) or after
+ * max_steps lattice steps.
+ * Empty-space skipping (opacity not NULL): opacity[n] is node n's opacity
+ * (the TF's alpha propagated through the graph, e.g. mg_propagate_tf with
+ * C = 1); climbing from level m+2 while the voxel around the sample has
+ * opacity exactly 0, the lattice samples inside the largest such voxel
+ * shrunk by 3 * 2^m on every side (the reach of the interpolation), and
+ * before the LOD changes, are skipped.  Each would add exactly nothing, so
+ * the image equals the one without skipping.
+ * Decisions (lattice, level, skips, termination) are taken in fp32 with one
+ * rounding per operation.
+ * vals: N x 4 fp32 node values (mg_propagate_tf, storage MG_F32), 16-byte
+ *   aligned.  cam: host struct.  image: H x W x 4 fp32 (R, G, B, A), 16-byte
+ *   aligned.  steps (may be NULL): H x W int32 samples composited per pixel.
+ */
+typedef struct {
+    float eye[3], fwd[3], right[3], up[3];   /* level-0 voxel units; fwd, right, up orthonormal */
+    float pix;                               /* angle of one pixel (radians) */
+    int32_t width, height;                   /* image size, 1..16384 each */
+    float base_step;                         /* lattice step in level-0 voxels, > 0 */
+    int32_t lod_bias;                        /* added to floor(log2(t * pix)) */
+    float ert;                               /* early-termination opacity; > 1: none */
+    int32_t max_steps;                       /* lattice steps at most, >= 1 */
+    int32_t reserved[4];                     /* zero */
+} mg_camera;
+
+MG_API mg_status mg_raymarch(const mg_graph *g, const float *vals, const float *opacity, const mg_camera *cam,
+                             float *image, int32_t *steps, mg_stream stream);
+
+/*
  * Request loop (serving).  A server keeps the graphs of several volumes
  * resident on one GPU and runs box-histogram requests (Sec. 3.6) and
  * TF-update frames (propagation, Sec. 3.4, then ray-sample lookups, Sec. 4)
@@ -329,7 +372,10 @@ MG_API mg_status mg_render_lookup_multi(const mg_graph *g, const void *vals, int
  * slot is free it takes the oldest queued request; a box request takes with
  * it every queued box of the same volume that still fits the slot's batch
  * (max_batch boxes and the footprint capacity of the slot's captured query
- * plan), and the whole batch runs as one plan launch; a TF frame runs alone.
+ * plan), and the whole batch runs as one plan launch; a TF frame takes with it
+ * the next queued frames of its volume (up to 8, as long as frames * C is a
+ * channel count of mg_propagate_tf_multi), propagated in one pass and looked
+ * up in one launch.
  * Requests that arrive while slots are busy join the next batch, so batches
  * of different volumes overlap on the device (continuous batching).  The
  * paper evaluates single queries; the loop is a deployment layer around its
@@ -377,6 +423,7 @@ typedef struct {
     int64_t cancelled;      /* requests cancelled before launch */
     int64_t failed;         /* requests that completed with an error */
     int64_t memory_admitted; /* bytes the admitted volumes hold (graphs, plans, buffers) */
+    int64_t tf_launches;    /* TF work items launched (each up to 8 frames of one volume) */
 } mg_server_stats;
 
 /* Create a server on the current device.  opts may be NULL (defaults).

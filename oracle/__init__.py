@@ -16,6 +16,8 @@ Functions whose results are pinned by tests other than self-comparison:
   fa_cubes          brute-force tiling of the clipped box; Table 3 arithmetic
   fa_query          equals box_hist exactly
   sample_voxels     hand cases at level and voxel boundaries
+  raymarch          closed form through a uniform volume; exact trilinear
+                    reproduction of a linear field; skipping changes nothing
 """
 from __future__ import annotations
 
@@ -45,7 +47,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fopenmp",
-           "-shared", "-fPIC", _SRC, "-o", tmp]
+           "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -98,10 +100,36 @@ def _load():
         lib.mgo_factor_lists.argtypes = [P, P, P, i64, ctypes.c_uint32, P]
         lib.mgo_factor_lists.restype = P
         lib.mgo_depths.argtypes = [P, P, i64, ctypes.c_uint32, P]
+        lib.mgo_raymarch.argtypes = [P, P, P, ctypes.POINTER(Camera), P, P, P]
         lib.mgo_set_threads.argtypes = [i32]
         lib.mgo_set_threads.restype = i32
         _lib = lib
         return lib
+
+
+class Camera(ctypes.Structure):
+    """Pinhole camera and march settings of raymarch (Sec. 4): eye and an
+    orthonormal basis (fwd, right, up) in level-0 voxel units, the angle of a
+    pixel, the image size, the lattice step (level-0 voxels), an integer LOD
+    bias, the early-termination opacity (> 1: none) and a step cap."""
+    _fields_ = [("eye", ctypes.c_float * 3), ("fwd", ctypes.c_float * 3), ("right", ctypes.c_float * 3),
+                ("up", ctypes.c_float * 3), ("pix", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("base_step", ctypes.c_float), ("lod_bias", ctypes.c_int32),
+                ("ert", ctypes.c_float), ("max_steps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+def camera(cam: dict) -> Camera:
+    c = Camera()
+    for k in ("eye", "fwd", "right", "up"):
+        for i in range(3):
+            getattr(c, k)[i] = float(np.float32(cam[k][i]))
+    c.pix = float(np.float32(cam["pix"]))
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    c.base_step = float(np.float32(cam["base_step"]))
+    c.lod_bias = int(cam["lod_bias"])
+    c.ert = float(np.float32(cam["ert"]))
+    c.max_steps = int(cam["max_steps"])
+    return c
 
 
 def _ptr(a: np.ndarray):
@@ -197,6 +225,20 @@ class Graph:
         out = np.zeros(int(d[0] * d[1] * d[2]), np.uint32)
         self._lib.mgo_graph_mip_copy(self._h, level, _ptr(out))
         return out.reshape(int(d[2]), int(d[1]), int(d[0]))
+
+    def raymarch(self, vals: np.ndarray, cam: dict, opacity: np.ndarray = None):
+        """One RGBA image (H, W, 4) fp32 marched through node values vals
+        (N, 4) fp32 (Sec. 4); with opacity (N,) fp32, empty space is skipped.
+        Returns (image, samples per pixel, smallest |A - ert| per pixel)."""
+        vals = np.ascontiguousarray(vals, np.float32).reshape(self.N, 4)
+        op = None if opacity is None else np.ascontiguousarray(opacity, np.float32).reshape(self.N)
+        c = camera(cam)
+        img = np.zeros((c.height, c.width, 4), np.float32)
+        steps = np.zeros((c.height, c.width), np.int32)
+        margin = np.zeros((c.height, c.width), np.float32)
+        self._lib.mgo_raymarch(self._h, _ptr(vals), None if op is None else _ptr(op), ctypes.byref(c), _ptr(img),
+                               _ptr(steps), _ptr(margin))
+        return img, steps, margin
 
     def fa_query(self, boxes: np.ndarray) -> np.ndarray:
         """Box histograms by footprint assembly + exact push (Algorithm 1)."""

@@ -15,6 +15,9 @@
  *   Sec. 3.4, Fig. 5       topological level of every node
  *   Sec. 3.4, Sec. 4       colour propagation, paletted lookup
  *   Sec. 3.6, Algorithm 1  footprint assembly of a box query
+ *   Sec. 4                 ray marching through the node values (LOD,
+ *                          interpolation, opacity correction, empty-space
+ *                          skipping)
  *
  * Readings of the paper taken here (the paper is silent or ambiguous):
  *   R1 border normalisation: N counts children in support (Eq. 4), so a level
@@ -38,6 +41,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <stdio.h>
+#include <math.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -836,4 +840,197 @@ int mgo_set_threads(int n)
     (void)n;
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4: ray marching through the palette of node values.                  */
+/*                                                                          */
+/* Readings taken here (Sec. 4 names the parts, not their formulas):         */
+/*   F1 the LOD of a sample is floor(log2(t * pixel angle)) + bias (pixel     */
+/*      coverage linear in depth); it picks mip level m = clamp(LOD, 0, L-1) */
+/*      and the step: samples lie on the lattice t_k = t_start + k * base,    */
+/*      and a sample at level m advances k by 2^m (step adjusted to the LOD). */
+/*   F2 "interpolation ... manually": trilinear within level m between the    */
+/*      8 voxel centres around the sample (clamped to the level), and        */
+/*      linear between levels m and m+1 by the fractional LOD (quadrilinear).*/
+/*   F3 opacity correction for a step of 2^e base steps:                     */
+/*      alpha' = 1 - (1 - alpha)^(2^e); front-to-back compositing of the    */
+/*      sample's colour with weight (1 - A) * alpha'; the ray stops once A   */
+/*      reaches the early-termination opacity.                               */
+/*   F4 empty-space skipping: opacities propagated through the graph (the    */
+/*      mixture average of the TF's alpha) give every mip voxel's opacity;   */
+/*      climbing from level m+2 while the voxel around the sample has       */
+/*      opacity exactly 0, the largest such voxel, shrunk by 3 * 2^m on      */
+/*      every side (the reach of the sample's interpolation), is skipped:    */
+/*      the lattice samples inside it and before the next LOD change would   */
+/*      each add exactly nothing.                                            */
+/* Every decision (lattice position, level, skip, termination) is taken in   */
+/* fp32 with one rounding per operation, the precision of the GPU path.      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    float eye[3], fwd[3], right[3], up[3];
+    float pix;
+    int32_t width, height;
+    float base_step;
+    int32_t lod_bias;
+    float ert;
+    int32_t max_steps;
+    int32_t reserved[4];
+} mgo_camera;
+
+static float rm_lerp(float a, float b, float f) { return a + f * (b - a); }
+
+static uint32_t rm_node(const mgo_graph *g, int l, int64_t x, int64_t y, int64_t z)
+{
+    const int64_t *d = g->dims + 3 * l;
+    return g->mip[l][(z * d[1] + y) * d[0] + x];
+}
+
+/* trilinear value (4 channels) of level l at position p (level-0 units) */
+static void rm_tri(const mgo_graph *g, const float *vals, int l, const float *p, float *out)
+{
+    const int64_t *d = g->dims + 3 * l;
+    float scale = ldexpf(1.0f, -l);
+    int64_t i0[3], i1[3];
+    float f[3];
+    for (int c = 0; c < 3; c++) {
+        float u = p[c] * scale - 0.5f;
+        float fl = floorf(u);
+        f[c] = u - fl;
+        int64_t k = (int64_t)fl;
+        i0[c] = k < 0 ? 0 : (k > d[c] - 1 ? d[c] - 1 : k);
+        i1[c] = k + 1 < 0 ? 0 : (k + 1 > d[c] - 1 ? d[c] - 1 : k + 1);
+    }
+    float v[8][4];
+    for (int corner = 0; corner < 8; corner++) {
+        int64_t x = corner & 1 ? i1[0] : i0[0], y = corner & 2 ? i1[1] : i0[1], z = corner & 4 ? i1[2] : i0[2];
+        const float *r = vals + 4 * (int64_t)rm_node(g, l, x, y, z);
+        for (int ch = 0; ch < 4; ch++) v[corner][ch] = r[ch];
+    }
+    for (int ch = 0; ch < 4; ch++) {
+        float x00 = rm_lerp(v[0][ch], v[1][ch], f[0]), x10 = rm_lerp(v[2][ch], v[3][ch], f[0]);
+        float x01 = rm_lerp(v[4][ch], v[5][ch], f[0]), x11 = rm_lerp(v[6][ch], v[7][ch], f[0]);
+        float y0 = rm_lerp(x00, x10, f[1]), y1 = rm_lerp(x01, x11, f[1]);
+        out[ch] = rm_lerp(y0, y1, f[2]);
+    }
+}
+
+/* One image of width x height RGBA (fp32, row 0 at the top).  vals: N x 4
+ * node values; opac: N node opacities (NULL: no skipping).  steps_out (may
+ * be NULL): samples composited per pixel; margin_out (may be NULL): the
+ * smallest |A - ert| seen after a sample (+inf when ert > 1). */
+void mgo_raymarch(const mgo_graph *g, const float *vals, const float *opac, const mgo_camera *cam, float *img,
+                  int32_t *steps_out, float *margin_out)
+{
+    const int L = g->L;
+    const int W = cam->width, H = cam->height;
+    const float inf = 3.0e38f;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t pix_i = 0; pix_i < (int64_t)W * H; pix_i++) {
+        int i = (int)(pix_i % W), j = (int)(pix_i / W);
+        float sx = (((float)i + 0.5f) - 0.5f * (float)W) * cam->pix;
+        float sy = ((0.5f * (float)H - (float)j) - 0.5f) * cam->pix;
+        float d[3];
+        for (int c = 0; c < 3; c++) d[c] = (cam->fwd[c] + sx * cam->right[c]) + sy * cam->up[c];
+        float nrm = sqrtf((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+        for (int c = 0; c < 3; c++) d[c] = d[c] / nrm;
+        float tmin = -inf, tmax = inf;
+        int miss = 0;
+        for (int c = 0; c < 3; c++) {
+            float dim = (float)g->dims[c];
+            if (d[c] == 0.0f) {
+                if (cam->eye[c] < 0.0f || cam->eye[c] > dim) miss = 1;
+                continue;
+            }
+            float t0 = (0.0f - cam->eye[c]) / d[c], t1 = (dim - cam->eye[c]) / d[c];
+            float lo = t0 < t1 ? t0 : t1, hi = t0 < t1 ? t1 : t0;
+            if (lo > tmin) tmin = lo;
+            if (hi < tmax) tmax = hi;
+        }
+        float ts = tmin > 0.0f ? tmin : 0.0f;
+        float C[3] = {0.0f, 0.0f, 0.0f}, A = 0.0f, margin = inf;
+        int32_t taken = 0;
+        if (!miss && tmax > ts) {
+            int64_t k = 0;
+            while (k < cam->max_steps) {
+                float t = ts + (float)k * cam->base_step;
+                if (!(t < tmax)) break;
+                float x = t * cam->pix;
+                int lam = x > 0.0f ? ilogbf(x) + cam->lod_bias : -1000000;
+                int m = lam < 0 ? 0 : (lam > L - 1 ? L - 1 : lam);
+                float fr = 0.0f;
+                if (lam >= 0 && m < L - 1) {
+                    fr = (log2f(x) + (float)cam->lod_bias) - (float)lam;
+                    fr = fr < 0.0f ? 0.0f : (fr > 1.0f ? 1.0f : fr);
+                }
+                float p[3];
+                for (int c = 0; c < 3; c++) p[c] = cam->eye[c] + t * d[c];
+                if (opac) {
+                    int jz = -1;
+                    int64_t bz[3] = {0, 0, 0};
+                    for (int jl = m + 2; jl < L; jl++) {
+                        int64_t b[3];
+                        for (int c = 0; c < 3; c++) {
+                            int64_t v = (int64_t)floorf(p[c]);
+                            v = v < 0 ? 0 : v;
+                            v >>= jl;
+                            b[c] = v > g->dims[3 * jl + c] - 1 ? g->dims[3 * jl + c] - 1 : v;
+                        }
+                        if (opac[rm_node(g, jl, b[0], b[1], b[2])] != 0.0f) break;
+                        jz = jl;
+                        for (int c = 0; c < 3; c++) bz[c] = b[c];
+                    }
+                    if (jz >= 0) {
+                        float size = ldexpf(1.0f, jz), gap = ldexpf(3.0f, m);
+                        float lo[3], hi[3];
+                        int inside = 1;
+                        for (int c = 0; c < 3; c++) {
+                            lo[c] = (float)bz[c] * size + gap;
+                            hi[c] = ((float)bz[c] + 1.0f) * size - gap;
+                            if (!(p[c] > lo[c] && p[c] < hi[c])) inside = 0;
+                        }
+                        if (inside) {
+                            float tout = inf;
+                            for (int c = 0; c < 3; c++) {
+                                float te = d[c] > 0.0f ? (hi[c] - cam->eye[c]) / d[c]
+                                                       : d[c] < 0.0f ? (lo[c] - cam->eye[c]) / d[c] : inf;
+                                if (te < tout) tout = te;
+                            }
+                            float tch = m < L - 1 ? ldexpf(1.0f, lam + 1 - cam->lod_bias) / cam->pix : inf;
+                            float tl = tout < tch ? tout : tch;
+                            float len = (float)((int64_t)1 << m) * cam->base_step;
+                            int64_t n = (int64_t)floorf((tl - t) / len) - 1;
+                            if (n >= 1) {
+                                k += n << m;
+                                continue;
+                            }
+                        }
+                    }
+                }
+                float s[4], s1[4];
+                rm_tri(g, vals, m, p, s);
+                if (fr > 0.0f) {
+                    rm_tri(g, vals, m + 1, p, s1);
+                    for (int ch = 0; ch < 4; ch++) s[ch] = rm_lerp(s[ch], s1[ch], fr);
+                }
+                float q = 1.0f - s[3];
+                for (int e = 0; e < m; e++) q = q * q;
+                float ap = 1.0f - q;
+                float w = (1.0f - A) * ap;
+                for (int c = 0; c < 3; c++) C[c] = C[c] + w * s[c];
+                A = A + w;
+                taken++;
+                if (cam->ert <= 1.0f) {
+                    float dm = A > cam->ert ? A - cam->ert : cam->ert - A;
+                    if (dm < margin) margin = dm;
+                    if (A >= cam->ert) break;
+                }
+                k += (int64_t)1 << m;
+            }
+        }
+        float *o = img + 4 * pix_i;
+        o[0] = C[0]; o[1] = C[1]; o[2] = C[2]; o[3] = A;
+        if (steps_out) steps_out[pix_i] = taken;
+        if (margin_out) margin_out[pix_i] = margin;
+    }
 }

@@ -406,6 +406,19 @@ MG_API mg_status mg_render_lookup_multi(const mg_graph* g, const void* vals, int
     return render_lookup_multi(g, vals, k, C, dtype, samples, offsets, out, reinterpret_cast<cudaStream_t>(stream));
 }
 
+MG_API mg_status mg_raymarch(const mg_graph* g, const float* vals, const float* opacity, const mg_camera* cam,
+                             float* image, int32_t* steps, mg_stream stream) {
+    MG_RANGE("mg_raymarch");
+    if (!g || !vals || !cam || !image) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+        return fail(MG_ERR_INVALID_ARG, "image size must be 1..16384 per side");
+    if (!(cam->pix > 0.0f) || !(cam->base_step > 0.0f) || cam->max_steps < 1)
+        return fail(MG_ERR_INVALID_ARG, "pix and base_step must be > 0 and max_steps >= 1");
+    if (cam->lod_bias < -64 || cam->lod_bias > 64) return fail(MG_ERR_INVALID_ARG, "lod_bias must be in -64..64");
+    DeviceGuard dg(g->device);
+    return raymarch(g, vals, opacity, *cam, image, steps, reinterpret_cast<cudaStream_t>(stream));
+}
+
 MG_API mg_status mg_sync_status(mg_graph* g, mg_stream stream) {
     if (!g) return fail(MG_ERR_INVALID_ARG, "graph is NULL");
     DeviceGuard dg(g->device);

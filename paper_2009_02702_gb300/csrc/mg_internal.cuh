@@ -220,6 +220,8 @@ mg_status render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dt,
                         int64_t P, void* out, cudaStream_t s);
 mg_status render_lookup_multi(const mg_graph* g, const void* vals, int k, int C, mg_dtype dt, const float* samples,
                               const int64_t* offsets, void* out, cudaStream_t s);
+mg_status raymarch(const mg_graph* g, const float* vals, const float* opacity, const mg_camera& cam, float* image,
+                   int32_t* steps, cudaStream_t s);
 
 // A query plan's own buffers, executable graph and footprint capacities, for
 // the request loop, which stages boxes straight into them: a run is the boxes

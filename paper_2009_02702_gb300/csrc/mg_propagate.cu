@@ -6,15 +6,13 @@
 // (p, q) as one 8-byte load, alpha as 4 (or 2) bytes; value rows are gathered
 // as one vector load per predecessor.
 //
-// One persistent launch covers all levels: warps take tiles of 128 nodes from
-// a global ticket in level order, and a tile of level d first waits until
-// every tile of level d-1 has signalled (a per-level counter).  Tiles are
-// handed out in order, so every tile waited on belongs to a warp that is
-// already running: the wait always ends.  It is bounded all the same; past
-// the bound the kernel records MG_ERR_TIMEOUT and returns.  Warps never wait
-// for each other inside a CTA (no block barriers), so one warp's level wait or
-// gathers never stall the rest.  Rows written in this launch are read through
-// L2 (ld.global.cg), never through the read-only cache.
+// One persistent launch covers all levels: CTAs take tiles of nodes from a
+// global ticket in level order, and a tile of level d first waits until every
+// tile of level d-1 has signalled (a per-level counter).  Tiles are handed out
+// in order, so every tile waited on belongs to a CTA that is already running:
+// the wait always ends.  It is bounded all the same; past the bound the
+// kernel records MG_ERR_TIMEOUT and returns.  Rows written in this launch are
+// read through L2 (ld.global.cg), never through the read-only cache.
 #include "mg_internal.cuh"
 
 #include <algorithm>
@@ -161,7 +159,7 @@ __global__ void level_kernel(const uint2* __restrict__ pq, const typename Weight
 }
 
 constexpr int kPropThreads = 256;
-constexpr int kPropTile = 128;                  // nodes per warp tile (4 per lane)
+constexpr int kPropTile = 1024;                 // nodes per tile
 constexpr unsigned kSpinLimit = 1u << 22;       // polls before a wait gives up
 
 struct PropTiles {
@@ -178,13 +176,12 @@ __device__ __forceinline__ int tile_level(const PropTiles& T, long long t) {
     return d;
 }
 
-// this lane's edges and weights of tile t: nodes lo + lane + k * 32
+// this thread's edges and weights of tile t: nodes lo + threadIdx.x + k * kPropThreads
 template <typename ST, int NT>
 __device__ __forceinline__ void tile_edges(const PropTiles& T, long long t, long long total,
                                            const uint2* __restrict__ pq,
                                            const typename Weight<ST>::T* __restrict__ alpha, uint2 (&e)[NT],
                                            float (&al)[NT]) {
-    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < NT; k++) {
         e[k] = make_uint2(0u, 0u);
@@ -197,7 +194,7 @@ __device__ __forceinline__ void tile_edges(const PropTiles& T, long long t, long
     const int64_t hi = min(lo + kPropTile, T.first[d] + T.count[d]);
 #pragma unroll
     for (int k = 0; k < NT; k++) {
-        const int64_t n = lo + lane + (int64_t)k * 32;
+        const int64_t n = lo + threadIdx.x + (int64_t)k * kPropThreads;
         if (n < hi) {
             e[k] = __ldg(pq + n);
             al[k] = Cvt<typename Weight<ST>::T>::to(alpha[n]);
@@ -205,31 +202,32 @@ __device__ __forceinline__ void tile_edges(const PropTiles& T, long long t, long
     }
 }
 
-// rows of up to 8 channels fit 3 CTAs per SM uncapped; wider rows are held to 2
-template <int C> struct PropBound {
-    static constexpr int blocks = C <= 8 ? 1 : 2;
-};
-
 template <typename ST, int C>
-__global__ void __launch_bounds__(kPropThreads, PropBound<C>::blocks)
-    warp_pass_kernel(PropTiles T, const uint2* __restrict__ pq, const typename Weight<ST>::T* __restrict__ alpha,
-                     const float* __restrict__ tf, int cin, ST* __restrict__ vals, unsigned* __restrict__ done,
-                     unsigned long long* __restrict__ ticket, unsigned* __restrict__ status) {
-    constexpr int NT = kPropTile / 32;                // nodes of a tile per lane
+__global__ void __launch_bounds__(kPropThreads) single_pass_kernel(PropTiles T, const uint2* __restrict__ pq,
+                                                                   const typename Weight<ST>::T* __restrict__ alpha,
+                                                                   const float* __restrict__ tf, int cin,
+                                                                   ST* __restrict__ vals, unsigned* __restrict__ done,
+                                                                   unsigned long long* __restrict__ ticket,
+                                                                   unsigned* __restrict__ status) {
+    constexpr int NT = kPropTile / kPropThreads;      // nodes of a tile per thread
     constexpr int NPT = C <= 4 ? 4 : C <= 8 ? 2 : 1;  // of them gathered at once
-    const int lane = threadIdx.x & 31;
+    __shared__ long long s_next;
+    __shared__ int s_abort;
     const long long total = T.tile0[T.levels];
-    // lane 0 holds the ticket after next, taken two tiles ahead so that the
+    // thread 0 holds the ticket after next, taken two tiles ahead so that the
     // atomic's round trip is never waited on
-    long long t = 0, ahead = 0;
-    int seen = 0;   // lane 0: every level below this one is known to be complete
-    if (lane == 0) {
-        t = (long long)atomicAdd(ticket, 1ull);
+    long long ahead = 0;
+    int seen = 0;   // thread 0: every level below this one is known to be complete
+    if (threadIdx.x == 0) {
+        s_next = (long long)atomicAdd(ticket, 1ull);
         ahead = (long long)atomicAdd(ticket, 1ull);
     }
-    t = __shfl_sync(0xffffffffu, t, 0);
+    __syncthreads();
+    long long t = s_next;
     // Software pipeline over tiles: the next tile's ticket is known and its
     // (static) edges and weights are loaded while this tile waits and runs.
+    // Tickets are taken in order and a tile only waits for smaller ones, so
+    // the smallest unfinished ticket is always some CTA's current tile.
     uint2 e[NT];
     float al[NT];
     tile_edges<ST, NT>(T, t, total, pq, alpha, e, al);
@@ -237,25 +235,25 @@ __global__ void __launch_bounds__(kPropThreads, PropBound<C>::blocks)
         const int d = tile_level(T, t);
         const int64_t lo = T.first[d] + (t - T.tile0[d]) * kPropTile;
         const int64_t hi = min(lo + kPropTile, T.first[d] + T.count[d]);
-        long long tn = 0;
-        int ok = 1;
-        if (lane == 0) {
-            tn = ahead;
+        __syncthreads();   // every thread has read s_next
+        if (threadIdx.x == 0) {
+            s_next = ahead;
             ahead = (long long)atomicAdd(ticket, 1ull);
+            s_abort = 0;
             if (d > seen) {   // level d-1 not yet seen complete
                 const unsigned need = (unsigned)(T.tile0[d] - T.tile0[d - 1]);
                 if (bounded_wait_geq(done + d - 1, need, kSpinLimit, status)) seen = d;
-                else ok = 0;
+                else s_abort = 1;
             }
         }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        tn = __shfl_sync(0xffffffffu, tn, 0);
-        if (!ok) break;
+        __syncthreads();
+        if (s_abort) break;
+        const long long tn = s_next;
         uint2 en[NT];
         float aln[NT];
         tile_edges<ST, NT>(T, tn, total, pq, alpha, en, aln);
         if (d == 0) {
-            for (int64_t n = lo + lane; n < hi; n += 32) {
+            for (int64_t n = lo + threadIdx.x; n < hi; n += kPropThreads) {
                 float out[C];
 #pragma unroll
                 for (int c = 0; c < C; c++) out[c] = tf_value(tf, n, c, cin, T.count[0] * cin);
@@ -269,7 +267,7 @@ __global__ void __launch_bounds__(kPropThreads, PropBound<C>::blocks)
                 float vp[NPT][C], vq[NPT][C];
 #pragma unroll
                 for (int k = 0; k < NPT; k++) {
-                    const int64_t n = lo + lane + (int64_t)(k0 + k) * 32;
+                    const int64_t n = lo + threadIdx.x + (int64_t)(k0 + k) * kPropThreads;
                     if (n < hi) {
                         uint32_t p = e[k0 + k].x, q = e[k0 + k].y;
                         if (al[k0 + k] < 0.f) {   // 16-bit weights: sign = p and q swapped
@@ -282,7 +280,7 @@ __global__ void __launch_bounds__(kPropThreads, PropBound<C>::blocks)
                 }
 #pragma unroll
                 for (int k = 0; k < NPT; k++) {
-                    const int64_t n = lo + lane + (int64_t)(k0 + k) * 32;
+                    const int64_t n = lo + threadIdx.x + (int64_t)(k0 + k) * kPropThreads;
                     if (n < hi) {
                         const float a = fabsf(al[k0 + k]);
                         float out[C];
@@ -293,9 +291,8 @@ __global__ void __launch_bounds__(kPropThreads, PropBound<C>::blocks)
                 }
             }
         }
-        // every lane's rows are stored; one fence and the level's count
-        __syncwarp();
-        if (lane == 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(done + d, 1u);
         }
@@ -352,11 +349,10 @@ mg_status run_single_pass(mg_graph* g, const float* tf, int cin, const void* alp
     auto* ticket = reinterpret_cast<unsigned long long*>(sync.as<unsigned char>() + (MG_MAX_DEPTH + 2) * sizeof(unsigned) +
                                                         (8 - ((MG_MAX_DEPTH + 2) * sizeof(unsigned)) % 8) % 8);
     using W = typename Weight<ST>::T;
-    auto k = warp_pass_kernel<ST, C>;
+    auto k = single_pass_kernel<ST, C>;
     int per_sm = 0;
     MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kPropThreads, 0));
-    const int64_t warps = (int64_t)std::max(per_sm, 1) * sm_count_prop(g->device) * (kPropThreads / 32);
-    const int64_t grid = (std::min<int64_t>(tiles, warps) + kPropThreads / 32 - 1) / (kPropThreads / 32);
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)std::max(per_sm, 1) * sm_count_prop(g->device));
     k<<<(unsigned)std::max<int64_t>(grid, 1), kPropThreads, 0, s>>>(T, g->pq.as<uint2>(), static_cast<const W*>(alpha),
                                                                     tf, cin, vals, done, ticket,
                                                                     g->status.as<unsigned>());

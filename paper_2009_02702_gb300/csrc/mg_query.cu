@@ -983,16 +983,13 @@ __device__ __forceinline__ void main_out(const MainArgs& A, uint32_t*& acc, floa
     }
 }
 
-// A warp's pending internal-node pushes: an open-addressing table in shared
-// memory keyed by node ID, so runs of one node in a chunk are summed and the
-// node is expanded (mixture table row or lerp tree) once, when the table has
-// kTableFill distinct nodes between two unit steps or when the chunk ends.
-// Weights are box volumes' parts, so the sums stay below 2^32.
-constexpr int kTable = 256;                  // slots per warp (a power of two)
-constexpr uint32_t kTableFill = 96;          // distinct nodes that trigger an expansion
-constexpr int kProbes = 16;                  // probes before a push bypasses the table
-constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;  // never a node ID (N < 2^32)
-constexpr size_t kQueueBytes = (size_t)kTable * 10 + 16;  // keys, weights, occupied-slot list, counter
+// A warp's pending internal-node pushes: the unit loop appends (node, weight)
+// to a queue in shared memory, and the queue is pushed 32 entries at a time
+// (a measured alternative that summed the entries of one node in a hash
+// table first was slower on every workload: its probes cost more than the
+// expansions it saved).
+constexpr int kQueue = 320;   // queued entries at most (drained at >= 32)
+constexpr size_t kQueueBytes = (size_t)kQueue * 8 + 16;   // nodes, weights, counter
 
 // chunks of the launch: known on the host, or (plans) read on the device,
 // zero when the batch overflows the plan's buffers
@@ -1003,46 +1000,23 @@ __device__ __forceinline__ unsigned long long main_total(const MainArgs& A) {
 }
 
 struct Queue {
-    uint32_t* n;       // node of every slot (kEmptyKey: free)
-    uint32_t* w;       // summed weight of every slot
-    uint32_t* count;   // occupied slots
-    uint16_t* used;    // the occupied slots, in order of first use
+    uint32_t* n;       // queued nodes
+    uint32_t* w;       // queued weights
+    uint32_t* count;   // queued entries
 };
 
 __device__ __forceinline__ Queue carve_queue(uint8_t* p) {
     Queue Qu;
     Qu.n = reinterpret_cast<uint32_t*>(p);
-    Qu.w = Qu.n + kTable;
-    Qu.count = Qu.w + kTable;
-    Qu.used = reinterpret_cast<uint16_t*>(Qu.count + 4);
+    Qu.w = Qu.n + kQueue;
+    Qu.count = Qu.w + kQueue;
     return Qu;
 }
 
-// every slot free (one warp)
+// empty queue (one warp)
 __device__ __forceinline__ void clear_queue(const Queue& Qu) {
-    const int lane = threadIdx.x & 31;
-    for (int i = lane; i < kTable; i += 32) {
-        Qu.n[i] = kEmptyKey;
-        Qu.w[i] = 0u;
-    }
-    if (lane == 0) *Qu.count = 0u;
+    if ((threadIdx.x & 31) == 0) *Qu.count = 0u;
     __syncwarp();
-}
-
-// add weight w to node n's slot (one lane); false when every probed slot
-// holds another node
-__device__ __forceinline__ bool table_add(const Queue& Qu, uint32_t n, uint32_t w) {
-    uint32_t h = (n * 0x9E3779B1u) >> 24;   // top 8 bits: kTable = 256
-    for (int i = 0; i < kProbes; i++) {
-        const uint32_t old = atomicCAS(Qu.n + h, kEmptyKey, n);
-        if (old == kEmptyKey || old == n) {
-            if (old == kEmptyKey) Qu.used[atomicAdd(Qu.count, 1u)] = (uint16_t)h;
-            atomicAdd(Qu.w + h, w);
-            return true;
-        }
-        h = (h + 1) & (kTable - 1);
-    }
-    return false;
 }
 
 // push one (node, weight) per lane where `valid`.  With the mixture table the
@@ -1094,27 +1068,32 @@ __device__ __forceinline__ void push_lanes(const PushArgs& P, const Hist<FP>& H,
     __syncwarp();
 }
 
-// expand every node of the warp's table, 32 occupied slots at a time from
-// the list of occupied slots, and free the slots
+// push queued entries 32 at a time until fewer than 32 (none if `all`)
+// remain, then move the rest to the front
 template <bool FP, typename AT>
-__device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Queue& Qu) {
+__device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Queue& Qu, bool all) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
-    const uint32_t cnt = *Qu.count;
-    for (uint32_t b = 0; b < cnt; b += 32) {
-        const bool v = b + lane < cnt;
-        uint32_t n = 0u, w = 0u;
-        if (v) {
-            const uint32_t slot = Qu.used[b + lane];
-            n = Qu.n[slot];
-            w = Qu.w[slot];
-            Qu.n[slot] = kEmptyKey;
-            Qu.w[slot] = 0u;
-        }
-        push_lanes<FP, AT>(P, H, v, n, w);
+    const uint32_t qc = *Qu.count;
+    uint32_t done = 0;
+    while (qc - done >= 32 || (all && qc > done)) {
+        const uint32_t take = min(qc - done, 32u);
+        const bool v = (uint32_t)lane < take;
+        push_lanes<FP, AT>(P, H, v, v ? Qu.n[done + lane] : 0u, v ? Qu.w[done + lane] : 0u);
+        done += take;
+    }
+    const uint32_t rest = qc - done;
+    uint32_t tn = 0, tw = 0;
+    if ((uint32_t)lane < rest) {
+        tn = Qu.n[done + lane];
+        tw = Qu.w[done + lane];
     }
     __syncwarp();
-    if (lane == 0) *Qu.count = 0u;
+    if ((uint32_t)lane < rest) {
+        Qu.n[lane] = tn;
+        Qu.w[lane] = tw;
+    }
+    if (lane == 0) *Qu.count = rest;
     __syncwarp();
 }
 
@@ -1147,8 +1126,10 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
         const uint32_t W = rcnt << (3 * rl);
         if (rl == 0 || rid < S) {
             H.add_int(rid, W);
-        } else if (!table_add(Qu, rid, W)) {
-            push_one<FP, AT>(A.P, H, rid, W);
+        } else {
+            const uint32_t pos = atomicAdd(Qu.count, 1u);
+            Qu.n[pos] = rid;
+            Qu.w[pos] = W;
         }
     };
     auto feed = [&](uint32_t x, int l) {
@@ -1321,7 +1302,7 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
                     }
                 }
                 __syncwarp();
-                if (*Qu.count >= kTableFill) drain<FP, AT>(A.P, H, Qu);
+                if (*Qu.count >= 32) drain<FP, AT>(A.P, H, Qu, false);
             }
         };
         if (__any_sync(0xffffffffu, wide)) run_units(std::integral_constant<int, 1>{});
@@ -1372,7 +1353,7 @@ __global__ void __launch_bounds__(256, 5) query_warp_kernel(MainArgs A) {
         const uint32_t c0 = (uint32_t)(c - A.chunk_off[q]) * A.chunk;
         const uint32_t c1 = min(c0 + A.chunk, ncube);
         process_span<FP, AT>(A, H, Qu, c0, c1, __ldg(A.chunk_b + c), A.blk_off[q + 1], ncube);
-        drain<FP, AT>(A.P, H, Qu);
+        drain<FP, AT>(A.P, H, Qu, true);
         for (uint32_t s = lane; s < S; s += 32) {
             const uint32_t v = H.h[s];
             if (v) {
@@ -1456,7 +1437,7 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
             bhint = b;
             process_span<FP, AT>(A, H, Qu, w0, w1, b, b1, ncube);
         }
-        drain<FP, AT>(A.P, H, Qu);
+        drain<FP, AT>(A.P, H, Qu, true);
         __syncthreads();
         flush<FP>(H, S, q, acc, accf);
         __syncthreads();

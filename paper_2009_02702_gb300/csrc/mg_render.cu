@@ -176,3 +176,212 @@ mg_status render_lookup(const mg_graph* g, const void* vals, int C, mg_dtype dt,
 }
 
 }  // namespace mg
+
+// ---------------------------------------------------------------------------
+// Ray marching through the node values (Sec. 4): for every pixel a ray from
+// the camera through the volume, samples on the lattice t_k = t_start +
+// k * base; a sample's LOD, floor(log2(t * pixel angle)) + bias, picks level m
+// (clamped to the pyramid) and the step 2^m * base (the step adjusted to the
+// LOD, with opacity correction alpha' = 1 - (1 - alpha)^(2^m)); its value is
+// trilinear within level m between the 8 voxel centres around it and linear
+// between levels m and m+1 by the fractional LOD; front-to-back compositing
+// stops at the early-termination opacity.  With node opacities (the TF's
+// alpha propagated through the graph), empty space is skipped: climbing from
+// level m+2 while the voxel around the sample has opacity exactly 0, the
+// lattice samples inside the largest such voxel shrunk by the reach of the
+// interpolation (3 * 2^m: levels m and m+1 read voxels within 1.5 of their
+// widths of the sample), and before the next LOD change, are skipped; each
+// would add exactly nothing, so the image is the same with and without it.
+// Decisions (lattice, level, skip, termination) use one rounding per fp32
+// operation (no contraction), so they are reproducible off the GPU.
+// ---------------------------------------------------------------------------
+namespace mg {
+namespace {
+
+struct MarchArgs {
+    Geom G;
+    const void* mip0;
+    const uint32_t* mip;
+    const float4* vals;
+    const float* opac;
+    mg_camera cam;
+    float4* img;
+    int32_t* steps;
+};
+
+__device__ __forceinline__ uint32_t march_node(const MarchArgs& A, int l, int64_t x, int64_t y, int64_t z) {
+    const int64_t idx = (z * A.G.dims[l][1] + y) * A.G.dims[l][0] + x;
+    if (l == 0)
+        return A.G.id0_bytes == 2 ? (uint32_t)__ldg(static_cast<const uint16_t*>(A.mip0) + idx)
+                                  : __ldg(static_cast<const uint32_t*>(A.mip0) + idx);
+    return __ldg(A.mip + A.G.off[l] + idx);
+}
+
+__device__ __forceinline__ float rn_lerp(float a, float b, float f) { return __fadd_rn(a, __fmul_rn(f, __fsub_rn(b, a))); }
+
+__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float f) {
+    return make_float4(rn_lerp(a.x, b.x, f), rn_lerp(a.y, b.y, f), rn_lerp(a.z, b.z, f), rn_lerp(a.w, b.w, f));
+}
+
+// trilinear value of level l at p (level-0 units), voxel centres clamped to the level
+__device__ float4 march_tri(const MarchArgs& A, int l, const float (&p)[3]) {
+    const float scale = ldexpf(1.0f, -l);
+    int64_t i0[3], i1[3];
+    float f[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float u = __fsub_rn(__fmul_rn(p[c], scale), 0.5f);
+        const float fl = floorf(u);
+        f[c] = __fsub_rn(u, fl);
+        const int64_t k = (int64_t)fl, d = A.G.dims[l][c];
+        i0[c] = k < 0 ? 0 : (k > d - 1 ? d - 1 : k);
+        i1[c] = k + 1 < 0 ? 0 : (k + 1 > d - 1 ? d - 1 : k + 1);
+    }
+    uint32_t n[8];
+#pragma unroll
+    for (int corner = 0; corner < 8; corner++)
+        n[corner] = march_node(A, l, corner & 1 ? i1[0] : i0[0], corner & 2 ? i1[1] : i0[1], corner & 4 ? i1[2] : i0[2]);
+    float4 v[8];
+#pragma unroll
+    for (int corner = 0; corner < 8; corner++) v[corner] = __ldg(A.vals + n[corner]);
+    const float4 x00 = lerp4(v[0], v[1], f[0]), x10 = lerp4(v[2], v[3], f[0]);
+    const float4 x01 = lerp4(v[4], v[5], f[0]), x11 = lerp4(v[6], v[7], f[0]);
+    return lerp4(lerp4(x00, x10, f[1]), lerp4(x01, x11, f[1]), f[2]);
+}
+
+__global__ void __launch_bounds__(128) march_kernel(MarchArgs A) {
+    const mg_camera& cam = A.cam;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= cam.width || j >= cam.height) return;
+    const int L = A.G.L;
+    const float inf = 3.0e38f;
+    const float sx = __fmul_rn(__fsub_rn(__fadd_rn((float)i, 0.5f), __fmul_rn(0.5f, (float)cam.width)), cam.pix);
+    const float sy = __fmul_rn(__fsub_rn(__fsub_rn(__fmul_rn(0.5f, (float)cam.height), (float)j), 0.5f), cam.pix);
+    float d[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        d[c] = __fadd_rn(__fadd_rn(cam.fwd[c], __fmul_rn(sx, cam.right[c])), __fmul_rn(sy, cam.up[c]));
+    const float nrm = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2])));
+#pragma unroll
+    for (int c = 0; c < 3; c++) d[c] = __fdiv_rn(d[c], nrm);
+    float tmin = -inf, tmax = inf;
+    bool miss = false;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float dim = (float)A.G.dims[0][c];
+        if (d[c] == 0.0f) {
+            if (cam.eye[c] < 0.0f || cam.eye[c] > dim) miss = true;
+            continue;
+        }
+        const float t0 = __fdiv_rn(__fsub_rn(0.0f, cam.eye[c]), d[c]), t1 = __fdiv_rn(__fsub_rn(dim, cam.eye[c]), d[c]);
+        const float lo = t0 < t1 ? t0 : t1, hi = t0 < t1 ? t1 : t0;
+        if (lo > tmin) tmin = lo;
+        if (hi < tmax) tmax = hi;
+    }
+    const float ts = tmin > 0.0f ? tmin : 0.0f;
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Aacc = 0.0f;
+    int32_t taken = 0;
+    if (!miss && tmax > ts) {
+        int64_t k = 0;
+        while (k < cam.max_steps) {
+            const float t = __fadd_rn(ts, __fmul_rn((float)k, cam.base_step));
+            if (!(t < tmax)) break;
+            const float x = __fmul_rn(t, cam.pix);
+            const int lam = x > 0.0f ? ilogbf(x) + cam.lod_bias : -1000000;
+            const int m = lam < 0 ? 0 : (lam > L - 1 ? L - 1 : lam);
+            float fr = 0.0f;
+            if (lam >= 0 && m < L - 1) {
+                fr = __fsub_rn(__fadd_rn(log2f(x), (float)cam.lod_bias), (float)lam);
+                fr = fr < 0.0f ? 0.0f : (fr > 1.0f ? 1.0f : fr);
+            }
+            float p[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) p[c] = __fadd_rn(cam.eye[c], __fmul_rn(t, d[c]));
+            if (A.opac) {
+                int jz = -1;
+                int64_t bz[3] = {0, 0, 0};
+                for (int jl = m + 2; jl < L; jl++) {
+                    int64_t b[3];
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        int64_t v = (int64_t)floorf(p[c]);
+                        v = v < 0 ? 0 : v;
+                        v >>= jl;
+                        b[c] = v > A.G.dims[jl][c] - 1 ? A.G.dims[jl][c] - 1 : v;
+                    }
+                    if (__ldg(A.opac + march_node(A, jl, b[0], b[1], b[2])) != 0.0f) break;
+                    jz = jl;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) bz[c] = b[c];
+                }
+                if (jz >= 0) {
+                    const float size = ldexpf(1.0f, jz), gap = ldexpf(3.0f, m);
+                    float lo[3], hi[3];
+                    bool inside = true;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        lo[c] = __fadd_rn(__fmul_rn((float)bz[c], size), gap);
+                        hi[c] = __fsub_rn(__fmul_rn(__fadd_rn((float)bz[c], 1.0f), size), gap);
+                        if (!(p[c] > lo[c] && p[c] < hi[c])) inside = false;
+                    }
+                    if (inside) {
+                        float tout = inf;
+#pragma unroll
+                        for (int c = 0; c < 3; c++) {
+                            const float te = d[c] > 0.0f ? __fdiv_rn(__fsub_rn(hi[c], cam.eye[c]), d[c])
+                                             : d[c] < 0.0f ? __fdiv_rn(__fsub_rn(lo[c], cam.eye[c]), d[c]) : inf;
+                            if (te < tout) tout = te;
+                        }
+                        const float tch = m < L - 1 ? __fdiv_rn(ldexpf(1.0f, lam + 1 - cam.lod_bias), cam.pix) : inf;
+                        const float tl = tout < tch ? tout : tch;
+                        const float len = __fmul_rn((float)((int64_t)1 << m), cam.base_step);
+                        const int64_t n = (int64_t)floorf(__fdiv_rn(__fsub_rn(tl, t), len)) - 1;
+                        if (n >= 1) {
+                            k += n << m;
+                            continue;
+                        }
+                    }
+                }
+            }
+            float4 s = march_tri(A, m, p);
+            if (fr > 0.0f) s = lerp4(s, march_tri(A, m + 1, p), fr);
+            float q = __fsub_rn(1.0f, s.w);
+            for (int e = 0; e < m; e++) q = __fmul_rn(q, q);
+            const float ap = __fsub_rn(1.0f, q);
+            const float w = __fmul_rn(__fsub_rn(1.0f, Aacc), ap);
+            C0 = __fadd_rn(C0, __fmul_rn(w, s.x));
+            C1 = __fadd_rn(C1, __fmul_rn(w, s.y));
+            C2 = __fadd_rn(C2, __fmul_rn(w, s.z));
+            Aacc = __fadd_rn(Aacc, w);
+            taken++;
+            if (cam.ert <= 1.0f && Aacc >= cam.ert) break;
+            k += (int64_t)1 << m;
+        }
+    }
+    const int64_t o = (int64_t)j * cam.width + i;
+    A.img[o] = make_float4(C0, C1, C2, Aacc);
+    if (A.steps) A.steps[o] = taken;
+}
+
+}  // namespace
+
+mg_status raymarch(const mg_graph* g, const float* vals, const float* opacity, const mg_camera& cam, float* image,
+                   int32_t* steps, cudaStream_t s) {
+    if (!aligned(vals, 16) || !aligned(image, 16)) return fail(MG_ERR_INVALID_ARG, "vals and image must be 16-byte aligned");
+    MarchArgs A;
+    A.G = render_geom(g);
+    A.mip0 = g->mip0.p;
+    A.mip = g->mip.as<uint32_t>();
+    A.vals = reinterpret_cast<const float4*>(vals);
+    A.opac = opacity;
+    A.cam = cam;
+    A.img = reinterpret_cast<float4*>(image);
+    A.steps = steps;
+    const dim3 block(16, 8);
+    const dim3 grid((unsigned)((cam.width + 15) / 16), (unsigned)((cam.height + 7) / 8));
+    march_kernel<<<grid, block, 0, s>>>(A);
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+}  // namespace mg

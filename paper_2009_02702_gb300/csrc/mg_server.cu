@@ -6,10 +6,12 @@
 // (one CUDA stream), a captured query plan and staging buffers, so nothing is
 // allocated while serving.  Requests enter one FIFO.  A worker thread polls
 // the slots' completion events and, whenever a slot is free, takes the oldest
-// request: a TF frame alone, or a box together with every queued box of the
-// same volume that fits the slot's batch -- max_batch boxes whose footprint
-// blocks and work chunks (counted on the host at submission, with the same
-// decomposition the plan kernel uses) fit the plan's capacities.  The batch
+// request: a TF frame together with the queued frames of the same volume (up
+// to `frames` of them: one multi-TF propagation and one lookup launch for
+// all), or a box together with every queued box of the same volume that fits
+// the slot's batch -- max_batch boxes whose footprint blocks and work chunks
+// (counted on the host at submission, in closed form as the plan kernel does)
+// fit the plan's capacities.  The batch
 // is staged straight into the plan's input buffers and run as one graph
 // launch; results come back through pinned memory and are copied into the
 // callers' buffers when the slot's event fires, which also ends each
@@ -34,15 +36,19 @@ using Clock = std::chrono::steady_clock;
 constexpr int kMaxRunsHost = 40;   // runs per axis, as in the plan kernels
 
 // Footprint size of one box (Algorithm 1): per axis the aligned power-of-two
-// runs of the clipped range; the blocks are their tensor product, a block of
-// run levels (lx, ly, lz) holds 2^(lx+ly+lz-3 min) cubes.
+// runs of the clipped range; the blocks are their tensor product.  The cubes
+// follow in closed form, as in the plan kernel: with F(m) the sum over an
+// axis's runs of level >= m of 2^(level - m) and P(m) = Fx Fy Fz, the blocks
+// hold P(0) - 7 * sum over m >= 1 of P(m) cubes; an axis's steps rise and then
+// fall, so a level occurs at most twice and two bit masks give F(m).
 void box_work(const int32_t* b, const int32_t* dims, uint32_t chunk, uint64_t* blocks, uint64_t* chunks) {
-    int lv[3][kMaxRunsHost];
-    int n[3];
+    uint64_t once[3], twice[3];
+    uint64_t n[3];
     for (int a = 0; a < 3; a++) {
         int64_t i = b[a], di = std::min<int64_t>((int64_t)b[a] + b[3 + a], dims[a]) - b[a];
+        once[a] = twice[a] = 0;
         n[a] = 0;
-        while (di > 0 && n[a] < kMaxRunsHost) {
+        while (di > 0 && n[a] < (uint64_t)kMaxRunsHost) {
             int hi = 63;
             while (!((di >> hi) & 1)) hi--;
             int lo = 63;
@@ -51,20 +57,23 @@ void box_work(const int32_t* b, const int32_t* dims, uint32_t chunk, uint64_t* b
                 while (!((i >> lo) & 1)) lo++;
             }
             const int l = std::min(hi, lo);
-            lv[a][n[a]++] = l;
+            const uint64_t bit = 1ull << l;
+            if (once[a] & bit) twice[a] |= bit;
+            else once[a] |= bit;
+            n[a]++;
             di -= (int64_t)1 << l;
             i += (int64_t)1 << l;
         }
     }
-    uint64_t cubes = 0;
-    for (int k = 0; k < n[2]; k++)
-        for (int j = 0; j < n[1]; j++)
-            for (int i = 0; i < n[0]; i++) {
-                const int lx = lv[0][i], ly = lv[1][j], lz = lv[2][k];
-                const int m = std::min(lx, std::min(ly, lz));
-                cubes += (uint64_t)1 << (lx + ly + lz - 3 * m);
-            }
-    *blocks = (uint64_t)n[0] * n[1] * n[2];
+    auto P = [&](int m) {
+        uint64_t v = 1;
+        for (int a = 0; a < 3; a++) v *= (once[a] >> m) + (twice[a] >> m);
+        return v;
+    };
+    uint64_t rest = 0;
+    for (int m = 1; m < 64 && (once[0] >> m) && (once[1] >> m) && (once[2] >> m); m++) rest += P(m);
+    const uint64_t cubes = P(0) - 7 * rest;
+    *blocks = n[0] * n[1] * n[2];
     *chunks = (cubes + chunk - 1) / chunk;
 }
 
@@ -75,6 +84,7 @@ struct Req {
     uint64_t ticket = 0;
     Clock::time_point arrival;
     uint64_t blocks = 0, chunks = 0;   // footprint of a box request
+    int64_t frame_off = 0;             // TF frame: first sample in its work item's lookup
 };
 
 struct Rec {
@@ -110,6 +120,7 @@ struct Slot {
 struct Volume {
     mg_graph* g = nullptr;
     int C = 0;
+    int frames = 1;   // TF frames one work item propagates together (frames * C channels)
     int32_t dims[3] = {0, 0, 0};
     uint32_t chunk = 2048;
     uint64_t cap_blocks = 0, cap_chunks = 0;
@@ -144,9 +155,19 @@ struct mg_server {
 namespace mg {
 namespace {
 
-size_t pinned_bytes(size_t Q, size_t S, int C, size_t ms, size_t esize) {
-    return round_up(8) + round_up(4) + round_up(Q * 24) + round_up(Q * S * 4) + round_up(S * C * 4) +
-           round_up(ms * 16) + round_up(ms * C * esize);
+size_t pinned_bytes(size_t Q, size_t S, int C, int F, size_t ms, size_t esize) {
+    return round_up(8) + round_up(4) + round_up(Q * 24) + round_up(Q * S * 4) + round_up((size_t)F * S * C * 4) +
+           round_up((size_t)F * ms * 16) + round_up((size_t)F * ms * C * esize);
+}
+
+// TF frames propagated together: the most, up to 8, whose k * C channels a
+// multi-TF propagation supports
+int frames_for(int C) {
+    for (int k = 8; k > 1; k--) {
+        const int t = k * C;
+        if (t <= 8 || t == 12 || t == 16 || t == 20 || t == 24 || t == 28 || t == 32) return k;
+    }
+    return 1;
 }
 
 // complete the requests of a finished slot (lock held by the caller)
@@ -160,7 +181,8 @@ void finish_locked(mg_server* sv, Slot& sl, Clock::time_point now, mg_status st,
                 std::memcpy(q.r.result, static_cast<const char*>(vs.pin_out) + i * (size_t)v.g->S * 4,
                             (size_t)v.g->S * 4);
             else if (q.r.P > 0)
-                std::memcpy(q.r.result, vs.pin_render, (size_t)q.r.P * v.C * sv->esize);
+                std::memcpy(q.r.result, static_cast<const char*>(vs.pin_render) + q.frame_off * v.C * sv->esize,
+                            (size_t)q.r.P * v.C * sv->esize);
         }
         Rec& rec = sv->recs[q.ticket];
         rec.state = kDone;
@@ -181,7 +203,22 @@ std::vector<Req> take_locked(mg_server* sv) {
     std::vector<Req> w;
     if (sv->queue.empty()) return w;
     const Req& head = sv->queue.front();
-    if (head.r.kind == MG_REQ_TF || sv->o.plain) {
+    if (head.r.kind == MG_REQ_TF) {
+        // the oldest frame and the next queued frames of its volume
+        const int v = head.r.volume;
+        const int F = sv->vols[v].frames;
+        int scanned = 0;
+        for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)w.size() < F && scanned < 4096; scanned++) {
+            if (it->r.kind == MG_REQ_TF && it->r.volume == v) {
+                w.push_back(*it);
+                it = sv->queue.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        return w;
+    }
+    if (sv->o.plain) {
         w.push_back(head);
         sv->queue.pop_front();
         return w;
@@ -206,7 +243,7 @@ std::vector<Req> take_locked(mg_server* sv) {
 mg_status cuda_ok(cudaError_t e, const char* what) { return e == cudaSuccess ? MG_OK : cuda_fail(e, what); }
 
 // stage and enqueue one work item on a free slot
-mg_status launch(mg_server* sv, Slot& sl, const std::vector<Req>& w) {
+mg_status launch(mg_server* sv, Slot& sl, std::vector<Req>& w) {
     const Req& head = w[0];
     MG_RANGE(head.r.kind == MG_REQ_TF ? "mg_server frame" : "mg_server box batch");
     const Volume& vol = sv->vols[head.r.volume];
@@ -215,16 +252,27 @@ mg_status launch(mg_server* sv, Slot& sl, const std::vector<Req>& w) {
     const size_t S = g->S;
     cudaStream_t s = sl.s;
     if (head.r.kind == MG_REQ_TF) {
-        std::memcpy(vs.pin_tf, head.r.tf, S * vol.C * 4);
-        MG_TRY(cuda_ok(cudaMemcpyAsync(vs.tf_dev.p, vs.pin_tf, S * vol.C * 4, cudaMemcpyHostToDevice, s), "TF upload"));
-        MG_TRY(propagate(g, vs.tf_dev.as<float>(), vol.C, (mg_dtype)sv->o.storage, vs.vals_dev.p, s));
-        const int64_t P = head.r.P;
+        // k frames: k TFs through one multi-TF propagation, every frame's
+        // samples looked up against its slice in one launch
+        const int k = (int)w.size();
+        const size_t tf_bytes = S * vol.C * 4;
+        int64_t off[33];
+        off[0] = 0;
+        for (int j = 0; j < k; j++) {
+            std::memcpy(reinterpret_cast<char*>(vs.pin_tf) + j * tf_bytes, w[j].r.tf, tf_bytes);
+            if (w[j].r.P > 0)
+                std::memcpy(vs.pin_samples + 4 * off[j], w[j].r.samples, (size_t)w[j].r.P * 16);
+            w[j].frame_off = off[j];
+            off[j + 1] = off[j] + w[j].r.P;
+        }
+        MG_TRY(cuda_ok(cudaMemcpyAsync(vs.tf_dev.p, vs.pin_tf, k * tf_bytes, cudaMemcpyHostToDevice, s), "TF upload"));
+        MG_TRY(propagate_multi(g, vs.tf_dev.as<float>(), k, vol.C, (mg_dtype)sv->o.storage, vs.vals_dev.p, s));
+        const int64_t P = off[k];
         if (P > 0) {
-            std::memcpy(vs.pin_samples, head.r.samples, (size_t)P * 16);
             MG_TRY(cuda_ok(cudaMemcpyAsync(vs.samples_dev.p, vs.pin_samples, (size_t)P * 16, cudaMemcpyHostToDevice, s),
                            "sample upload"));
-            MG_TRY(render_lookup(g, vs.vals_dev.p, vol.C, (mg_dtype)sv->o.storage, vs.samples_dev.as<float>(), P,
-                                 vs.render_dev.p, s));
+            MG_TRY(render_lookup_multi(g, vs.vals_dev.p, k, vol.C, (mg_dtype)sv->o.storage, vs.samples_dev.as<float>(),
+                                       off, vs.render_dev.p, s));
             MG_TRY(cuda_ok(cudaMemcpyAsync(vs.pin_render, vs.render_dev.p, (size_t)P * vol.C * sv->esize,
                                            cudaMemcpyDeviceToHost, s),
                            "frame readback"));
@@ -298,6 +346,8 @@ void worker_loop(mg_server* sv) {
             if (w[0].r.kind == MG_REQ_BOX) {
                 sv->stats.box_launches++;
                 sv->stats.max_batch_seen = std::max<int64_t>(sv->stats.max_batch_seen, (int64_t)w.size());
+            } else {
+                sv->stats.tf_launches++;
             }
             sl.busy = true;
             // stage outside the lock: submissions continue meanwhile
@@ -442,8 +492,10 @@ MG_API mg_status mg_server_add_volume(mg_server* sv, mg_graph* g, int C, int* vo
     const size_t ms = (size_t)sv->o.max_samples;
     const size_t cap_blocks = std::max<size_t>(Q * 1024, 1 << 20), cap_chunks = std::max<size_t>(Q * 256, 1 << 18);
     // per slot: the plan (or the plain form's buffers and scratch) and the TF frame buffers
-    const size_t tf_bytes = round_up(S * C * 4) + round_up(N * C * sv->esize) + round_up(ms * 16) +
-                            round_up(ms * C * sv->esize);
+    const int F = frames_for(C);
+    v.frames = F;
+    const size_t tf_bytes = round_up((size_t)F * S * C * 4) + round_up(N * F * C * sv->esize) +
+                            round_up((size_t)F * ms * 16) + round_up((size_t)F * ms * C * sv->esize);
     const size_t query_bytes =
         sv->o.plain ? round_up(Q * 24) + round_up(Q * S * 4) + 2 * Q * S * 4
                     : Q * 24 + Q * S * 4 * (sv->o.hist_type == MG_HIST_F32 ? 2 : 1) + Q * 64 + cap_blocks * 12 +
@@ -454,7 +506,7 @@ MG_API mg_status mg_server_add_volume(mg_server* sv, mg_graph* g, int C, int* vo
                                          std::to_string((sv->o.memory_budget - sv->budget_used) >> 20) +
                                          " MiB of the budget remain");
     if (sv->o.storage != MG_F32) MG_TRY(ensure_alpha16(g, (mg_dtype)sv->o.storage, nullptr));
-    const size_t pin_bytes = pinned_bytes(Q, S, C, ms, sv->esize);
+    const size_t pin_bytes = pinned_bytes(Q, S, C, F, ms, sv->esize);
     std::vector<VolSlot> made(sv->slots.size());
     mg_status st = MG_OK;
     for (size_t k = 0; k < made.size() && st == MG_OK; k++) {
@@ -468,10 +520,10 @@ MG_API mg_status mg_server_add_volume(mg_server* sv, mg_graph* g, int C, int* vo
             st = mg_query_plan_create(g, (int64_t)Q, &qo, (int64_t)cap_blocks, (int64_t)cap_chunks, &vs.plan);
             if (st == MG_OK) vs.pp = plan_parts(vs.plan);
         }
-        if (st == MG_OK) st = vs.tf_dev.alloc(&g->al, S * C * 4, nullptr);
-        if (st == MG_OK) st = vs.vals_dev.alloc(&g->al, N * C * sv->esize, nullptr);
-        if (st == MG_OK) st = vs.samples_dev.alloc(&g->al, ms * 16, nullptr);
-        if (st == MG_OK) st = vs.render_dev.alloc(&g->al, ms * C * sv->esize, nullptr);
+        if (st == MG_OK) st = vs.tf_dev.alloc(&g->al, (size_t)F * S * C * 4, nullptr);
+        if (st == MG_OK) st = vs.vals_dev.alloc(&g->al, N * F * C * sv->esize, nullptr);
+        if (st == MG_OK) st = vs.samples_dev.alloc(&g->al, (size_t)F * ms * 16, nullptr);
+        if (st == MG_OK) st = vs.render_dev.alloc(&g->al, (size_t)F * ms * C * sv->esize, nullptr);
         for (Buf* b : {&vs.boxes_dev, &vs.out_dev, &vs.tf_dev, &vs.vals_dev, &vs.samples_dev, &vs.render_dev})
             b->s = nullptr;
         if (st == MG_OK) st = cuda_ok(cudaMallocHost(&vs.pin, pin_bytes), "cudaMallocHost");
@@ -486,9 +538,9 @@ MG_API mg_status mg_server_add_volume(mg_server* sv, mg_graph* g, int C, int* vo
             vs.pin_out = p;
             p += round_up(Q * S * 4);
             vs.pin_tf = reinterpret_cast<float*>(p);
-            p += round_up(S * C * 4);
+            p += round_up((size_t)F * S * C * 4);
             vs.pin_samples = reinterpret_cast<float*>(p);
-            p += round_up(ms * 16);
+            p += round_up((size_t)F * ms * 16);
             vs.pin_render = p;
         }
     }
@@ -497,9 +549,9 @@ MG_API mg_status mg_server_add_volume(mg_server* sv, mg_graph* g, int C, int* vo
     for (size_t k = 0; k < made.size() && st == MG_OK; k++) {
         VolSlot& vs = made[k];
         cudaStream_t s = sv->slots[k].s;
-        st = cuda_ok(cudaMemsetAsync(vs.tf_dev.p, 0, S * C * 4, s), "admission");
+        st = cuda_ok(cudaMemsetAsync(vs.tf_dev.p, 0, (size_t)F * S * C * 4, s), "admission");
         for (int rep = 0; rep < 2 && st == MG_OK; rep++) {
-            st = propagate(g, vs.tf_dev.as<float>(), C, (mg_dtype)sv->o.storage, vs.vals_dev.p, s);
+            st = propagate_multi(g, vs.tf_dev.as<float>(), F, C, (mg_dtype)sv->o.storage, vs.vals_dev.p, s);
             if (st == MG_OK && sv->o.plain) {
                 const int32_t unit[6] = {0, 0, 0, 1, 1, 1};
                 st = cuda_ok(cudaMemcpyAsync(vs.boxes_dev.p, unit, 24, cudaMemcpyHostToDevice, s), "admission");

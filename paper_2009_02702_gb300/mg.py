@@ -38,7 +38,7 @@ EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_cop
            "mg_query_plan_create", "mg_query_plan_run", "mg_query_plan_timing", "mg_query_plan_free",
            "mg_query_autotune",
            "mg_query_set_tuning", "mg_count_cubes", "mg_render_lookup", "mg_propagate_tf_multi",
-           "mg_render_lookup_multi",
+           "mg_render_lookup_multi", "mg_raymarch",
            "mg_server_create", "mg_server_add_volume", "mg_server_start", "mg_server_submit", "mg_server_cancel",
            "mg_server_wait", "mg_server_replay", "mg_server_stats_get", "mg_server_free",
            "mg_graph_export_size", "mg_graph_export", "mg_graph_import",
@@ -77,6 +77,26 @@ class mg_query_opts(ctypes.Structure):
                 ("timing", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
+class mg_camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("fwd", ctypes.c_float * 3), ("right", ctypes.c_float * 3),
+                ("up", ctypes.c_float * 3), ("pix", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("base_step", ctypes.c_float), ("lod_bias", ctypes.c_int32),
+                ("ert", ctypes.c_float), ("max_steps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+def camera(cam: dict) -> mg_camera:
+    """mg_camera from a dict (eye, fwd, right, up, pix, width, height,
+    base_step, lod_bias, ert, max_steps), e.g. synth.orbit_camera()."""
+    c = mg_camera()
+    for k in ("eye", "fwd", "right", "up"):
+        for i in range(3):
+            getattr(c, k)[i] = float(cam[k][i])
+    c.pix, c.width, c.height = float(cam["pix"]), int(cam["width"]), int(cam["height"])
+    c.base_step, c.lod_bias, c.ert, c.max_steps = float(cam["base_step"]), int(cam["lod_bias"]), float(cam["ert"]), \
+        int(cam["max_steps"])
+    return c
+
+
 class mg_server_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("max_batch", ctypes.c_int), ("hist_type", ctypes.c_int),
                 ("storage", ctypes.c_int), ("max_samples", ctypes.c_int64), ("memory_budget", ctypes.c_int64),
@@ -91,7 +111,7 @@ class mg_request(ctypes.Structure):
 
 class mg_server_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("box_requests", "tf_requests", "box_launches", "max_batch_seen",
-                                              "cancelled", "failed", "memory_admitted")]
+                                              "cancelled", "failed", "memory_admitted", "tf_launches")]
 
 
 _lib = None
@@ -123,6 +143,8 @@ def lib():
         L.mg_propagate_tf_multi.restype = st
         L.mg_render_lookup_multi.argtypes = [P, P, i32, i32, i32, P, P, P, P]
         L.mg_render_lookup_multi.restype = st
+        L.mg_raymarch.argtypes = [P, P, P, ctypes.POINTER(mg_camera), P, P, P]
+        L.mg_raymarch.restype = st
         L.mg_query_boxes.argtypes = [P, P, i64, ctypes.POINTER(mg_query_opts), P, ctypes.c_size_t, P, P,
                                      ctypes.POINTER(ctypes.c_size_t), P]
         L.mg_query_boxes.restype = st
@@ -563,6 +585,27 @@ def mg_render_lookup(g: Graph, vals: torch.Tensor, samples: torch.Tensor, out: t
     _check(lib().mg_render_lookup(g.handle, vals.data_ptr(), C, _TORCH_TO_MG[vals.dtype], samples.data_ptr(),
                                   samples.shape[0], out.data_ptr(), _stream(stream)))
     return out
+
+
+def mg_raymarch(g: Graph, vals: torch.Tensor, cam: dict, opacity: torch.Tensor = None, image: torch.Tensor = None,
+                steps: bool = False, stream=None):
+    """RGBA image (H, W, 4) fp32 ray-marched through node values vals (N, 4)
+    fp32; with opacity (N,) fp32 empty space is skipped.  steps=True also
+    returns the samples composited per pixel (H, W) int32."""
+    if vals.dtype != torch.float32 or tuple(vals.shape) != (g.N, 4) or not vals.is_contiguous():
+        raise ValueError("vals must be a contiguous float32 tensor of shape (N, 4)")
+    if opacity is not None and (opacity.dtype != torch.float32 or tuple(opacity.shape) != (g.N,)
+                                or not opacity.is_contiguous()):
+        raise ValueError("opacity must be a contiguous float32 tensor of shape (N,)")
+    c = camera(cam)
+    if image is None:
+        image = torch.empty((c.height, c.width, 4), dtype=torch.float32, device=vals.device)
+    _check_out(image, (c.height, c.width, 4), torch.float32, vals.device, "image")
+    st = torch.empty((c.height, c.width), dtype=torch.int32, device=vals.device) if steps else None
+    _check(lib().mg_raymarch(g.handle, vals.data_ptr(), opacity.data_ptr() if opacity is not None else None,
+                             ctypes.byref(c), image.data_ptr(), st.data_ptr() if st is not None else None,
+                             _stream(stream)))
+    return (image, st) if steps else image
 
 
 def mg_sync_status(g: Graph, stream=None):

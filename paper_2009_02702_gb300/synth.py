@@ -248,6 +248,31 @@ def make_attribute_tf(cfg_index: int, S: int, frame: int = 0) -> np.ndarray:
     return np.ascontiguousarray(tf)
 
 
+def orbit_camera(cfg_index: int, dims=None, width: int = 1920, height: int = 1080, frame: int = 0,
+                 base_step: float = 0.5, lod_bias: int = 0, ert: float = 0.99, max_steps: int = 1 << 20) -> dict:
+    """The seeded orbit camera of make_samples as a pinhole camera for the ray
+    marcher: eye, orthonormal (fwd, right, up), pixel angle, image size, and
+    the march settings (lattice step in level-0 voxels, integer LOD bias,
+    early-termination opacity, step cap).  Same draws as make_samples."""
+    cfg = CONFIGS[cfg_index]
+    dims = np.array(dims if dims is not None else cfg["dims"], dtype=np.float64)
+    rng = rng_for(cfg_index, _STREAM_SAMPLES + 16 * frame)
+    centre = dims / 2.0
+    R = 1.5 * dims.max()
+    phi = rng.random() * 2 * math.pi
+    eye = centre + R * np.array([math.cos(phi), math.sin(phi), 0.35])
+    fwd = centre - eye
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, np.array([0.0, 0.0, 1.0]))
+    right /= np.linalg.norm(right)
+    up = np.cross(right, fwd)
+    pix = 2 * math.tan(math.radians(45.0) / 2) / height
+    f32 = lambda v: [float(np.float32(x)) for x in v]
+    return dict(eye=f32(eye), fwd=f32(fwd), right=f32(right), up=f32(up), pix=float(np.float32(pix)),
+                width=int(width), height=int(height), base_step=float(base_step), lod_bias=int(lod_bias),
+                ert=float(ert), max_steps=int(max_steps))
+
+
 def make_samples(cfg_index: int, dims=None, width: int = 1920, height: int = 1080, frame: int = 0,
                  lod_bias: float = 0.0) -> np.ndarray:
     """(width*height, 4) float32 ray samples (x, y, z, lod) for one frame.

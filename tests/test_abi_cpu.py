@@ -116,12 +116,12 @@ def test_server_struct_layout_matches_header():
     with open(src, "w") as f:
         f.write('#include <stdio.h>\n#include "mg.h"\nint main(void){printf("%zu %zu %zu %zu %zu",'
                 "sizeof(mg_server_opts),sizeof(mg_request),sizeof(mg_server_stats),sizeof(mg_query_opts),"
-                "sizeof(mg_graph_info));return 0;}\n")
+                "sizeof(mg_graph_info));printf(\" %zu\",sizeof(mg_camera));return 0;}\n")
     subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), src, "-o", exe])
     sizes = [int(x) for x in subprocess.check_output([exe]).split()]
     assert sizes == [ctypes.sizeof(mg.mg_server_opts), ctypes.sizeof(mg.mg_request),
                      ctypes.sizeof(mg.mg_server_stats), ctypes.sizeof(mg.mg_query_opts),
-                     ctypes.sizeof(mg.mg_graph_info)]
+                     ctypes.sizeof(mg.mg_graph_info), ctypes.sizeof(mg.mg_camera)]
 
 
 def test_selftest_wait_argument_checks(lib):

@@ -314,3 +314,59 @@ def test_render_lookup_multi(mg):
                                       torch.from_numpy(frames[j]).to(dev())).cpu()
             assert torch.equal(out[off[j]:off[j + 1]], one), (storage, j)
     g.close()
+
+
+# the ray marcher (Sec. 4): decisions in fp32 as the oracle takes them, so the
+# samples per pixel match exactly; colours differ only through the node values
+# (fp32 lerps here, fp64 lerps rounded to fp32 in the oracle) and log2 of the
+# level fraction: a few fp32 ulps per sample over at most a few hundred samples
+MARCH_TOL = 2e-5
+MARCH_CASES = [
+    ("voronoi-lod4", 1, (48, 40, 36), 30, dict(lod_bias=4, ert=2.0, base_step=0.5)),
+    ("voronoi-lod0-ert", 2, (45, 33, 27), 40, dict(lod_bias=0, ert=0.95, base_step=0.25)),
+    ("cylinders-lod0", 4, (64, 64, 64), 4, dict(lod_bias=0, ert=2.0, base_step=0.5)),
+    ("cylinders-lod-2", 4, (64, 64, 64), 12, dict(lod_bias=-2, ert=0.99, base_step=0.5)),
+]
+
+
+@pytest.mark.parametrize("name,cfg,dims,S,kw", MARCH_CASES, ids=[c[0] for c in MARCH_CASES])
+def test_raymarch_matches_oracle(mg, name, cfg, dims, S, kw):
+    vol = synth.make_volume(cfg, dims=dims, S=S)
+    g, og = build_pair(mg, vol, S)
+    tf = synth.make_attribute_tf(cfg, S) if cfg == 4 else synth.make_tf(cfg, S, 4)
+    vals = mg.mg_propagate_tf(g, torch.from_numpy(tf).to(dev()))
+    ref_vals = oracle.propagate(og.p, og.q, og.a, og.b, S, tf.astype(np.float64)).astype(np.float32)
+    cam = synth.orbit_camera(cfg, dims=dims, width=96, height=64, **kw)
+    img, steps = mg.mg_raymarch(g, vals, cam, steps=True)
+    opac = vals[:, 3].contiguous()
+    img_ess, steps_ess = mg.mg_raymarch(g, vals, cam, opacity=opac, steps=True)
+    mg.mg_sync_status(g)
+    # skipping passes over samples of zero opacity only: the same image
+    assert torch.equal(img.cpu(), img_ess.cpu())
+    assert bool((steps_ess <= steps).all())
+    ref, ref_steps, margin = og.raymarch(ref_vals, cam)
+    ref_e, ref_steps_e, _ = og.raymarch(ref_vals, cam, opacity=ref_vals[:, 3].copy())
+    # pixels whose early termination was decided within 1e-4 of the threshold
+    # may stop one sample apart; every other pixel takes the same samples
+    ok = margin >= 1e-4
+    assert ok.mean() > 0.95
+    got, got_steps = img.cpu().numpy(), steps.cpu().numpy()
+    assert np.array_equal(got_steps[ok], ref_steps[ok])
+    assert np.array_equal(steps_ess.cpu().numpy()[ok], ref_steps_e[ok])
+    assert np.abs(got[ok] - ref[ok]).max() <= MARCH_TOL
+    assert (got[..., 3] <= 1.0 + 1e-6).all() and (got >= 0).all()
+    g.close()
+
+
+def test_raymarch_argument_checks(mg):
+    vol = synth.make_volume(1, dims=(16, 16, 16), S=8)
+    g = mg.mg_build(torch.from_numpy(vol).to(dev()), 8)
+    vals = mg.mg_propagate_tf(g, torch.from_numpy(synth.make_tf(1, 8, 4)).to(dev()))
+    cam = synth.orbit_camera(1, dims=(16, 16, 16), width=8, height=8)
+    for bad in (dict(width=0), dict(pix=0.0), dict(base_step=-1.0), dict(max_steps=0), dict(lod_bias=100)):
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_raymarch(g, vals, dict(cam, **bad))
+        assert e.value.status == mg.MG_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        mg.mg_raymarch(g, vals[:, :3], cam)
+    g.close()

@@ -238,3 +238,29 @@ def test_cancel_timeout_and_request_checks(env):
     st = srv.stats()
     assert st["cancelled"] == 1 and st["box_requests"] == 4
     srv.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_tf_frames_are_coalesced_and_exact(env, storage):
+    """Frames queued together go out up to 8 per work item (one multi-TF
+    propagation, one lookup launch) and each equals the frame run alone."""
+    mg, vols, graphs = env
+    srv = mg.Server(slots=2, max_batch=32, hist="u32", storage=storage, max_samples=4096)
+    for g in graphs:
+        srv.add_volume(g, 4)
+    frames = []
+    for i in range(21):
+        v = i % 2   # two volumes interleaved in the queue
+        tf = synth.make_tf(5, vols[v]["S"], 4, frame=100 + i)
+        smp = synth.make_samples(vols[v]["cfg"], dims=vols[v]["dims"], width=8 + i, height=5, frame=i)
+        frames.append((v, tf, smp, srv.submit_tf(v, tf, smp)))
+    srv.start()
+    for _, _, _, (t, _) in frames:
+        srv.wait(t, timeout=60.0)
+    st = srv.stats()
+    srv.close()
+    assert st["tf_requests"] == 21 and st["failed"] == 0
+    assert st["tf_launches"] <= 6          # 11 and 10 frames of the two volumes, 8 per item
+    for v, tf, smp, (_, out) in frames:
+        alone = alone_frame(mg, graphs[v], tf, smp, storage).numpy()
+        assert np.array_equal(out, alone)

@@ -407,3 +407,127 @@ def test_sec4_sample_lookup_hand_cases():
         nx, ny, _ = dims[l]
         x, y, z = s["voxel"]
         assert v == (z * ny + y) * nx + x, s
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4: the ray marcher
+# ---------------------------------------------------------------------------
+def _march_cam(eye, width=24, height=16, base=0.5, bias=-64, ert=2.0, max_steps=1 << 20, target=None):
+    eye = np.array(eye, np.float64)
+    target = np.array(target if target is not None else eye + [1.0, 0.3, 0.2], np.float64)
+    fwd = target - eye
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, [0.0, 0.0, 1.0])
+    right /= np.linalg.norm(right)
+    up = np.cross(right, fwd)
+    f32 = lambda v: [float(np.float32(x)) for x in v]
+    return dict(eye=f32(eye), fwd=f32(fwd), right=f32(right), up=f32(up), pix=float(np.float32(0.01)),
+                width=width, height=height, base_step=base, lod_bias=bias, ert=ert, max_steps=max_steps)
+
+
+def _ray_dirs(cam):
+    """fp64 pixel directions of the camera (independent of the march)."""
+    W, H = cam["width"], cam["height"]
+    i, j = np.meshgrid(np.arange(W), np.arange(H))
+    sx = (i + 0.5 - W / 2) * cam["pix"]
+    sy = (H / 2 - j - 0.5) * cam["pix"]
+    d = (np.array(cam["fwd"])[None, None] + sx[..., None] * np.array(cam["right"])[None, None]
+         + sy[..., None] * np.array(cam["up"])[None, None])
+    return d / np.linalg.norm(d, axis=-1, keepdims=True)
+
+
+def test_raymarch_uniform_volume_closed_form():
+    """One segment of colour (r, g, b, a): every sample has that value, so
+    after the march A = 1 - (1 - a)^K and C = (r, g, b) * A, where K is the
+    number of base steps covered, the ray's length in the volume over the
+    base step (the lattice ends within one step of the exit)."""
+    dims = (20, 14, 9)
+    vol = np.zeros(dims[::-1], np.uint16)
+    g = oracle.Graph(vol, 1)
+    rgba = np.array([[0.2, 0.5, 0.9, 0.01]], np.float32)
+    vals = np.repeat(rgba, g.N, axis=0)
+    cam = _march_cam([-15.0, 3.0, 2.0], target=[10.0, 7.0, 4.5])
+    img, steps, _ = g.raymarch(vals, cam)
+    d = _ray_dirs(cam)
+    eye = np.array(cam["eye"], np.float64)
+    with np.errstate(divide="ignore"):
+        t0 = (0.0 - eye) / d
+        t1 = (np.array(dims, np.float64) - eye) / d
+    tmin = np.minimum(t0, t1).max(axis=-1)
+    tmax = np.maximum(t0, t1).min(axis=-1)
+    hit = tmax > np.maximum(tmin, 0)
+    assert hit.sum() > 50
+    A = img[..., 3].astype(np.float64)
+    assert (A[~hit] == 0).all() and (steps[~hit] == 0).all()
+    # level 0 only (LOD bias -64): one sample per base step
+    n = np.ceil((tmax - np.maximum(tmin, 0)) / cam["base_step"] - 1e-4)
+    assert (np.abs(steps[hit] - n[hit]) <= 1).all()
+    K = np.log1p(-A[hit]) / np.log1p(-0.01)
+    assert np.allclose(K, steps[hit], atol=1e-2)
+    for c in range(3):
+        assert np.allclose(img[..., c][hit], rgba[0, c] * A[hit], rtol=1e-5)
+
+
+def test_raymarch_opacity_correction_with_lod_steps():
+    """With the LOD bias raised the march takes steps of 2^m base steps and
+    corrects each sample's opacity to 1 - (1 - a)^(2^m): the total is still
+    1 - (1 - a)^K with K the base steps covered."""
+    dims = (64, 64, 64)
+    vol = np.zeros(dims[::-1], np.uint16)
+    g = oracle.Graph(vol, 1)
+    vals = np.repeat(np.array([[0.3, 0.3, 0.3, 0.004]], np.float32), g.N, axis=0)
+    cam0 = _march_cam([-40.0, 30.0, 31.0], target=[32.0, 32.0, 32.0], bias=-64)
+    cam1 = dict(cam0, lod_bias=9)
+    img0, st0, _ = g.raymarch(vals, cam0)
+    img1, st1, _ = g.raymarch(vals, cam1)
+    hit = st0 > 0
+    assert (st1[hit] < st0[hit]).all()          # fewer, longer steps
+    K0 = np.log1p(-img0[..., 3][hit].astype(np.float64)) / np.log1p(-0.004)
+    K1 = np.log1p(-img1[..., 3][hit].astype(np.float64)) / np.log1p(-0.004)
+    # the coarse march covers the same length up to its last (longest) step
+    assert (np.abs(K1 - K0) <= 2 ** 6 + 1).all()
+    assert np.allclose(K0, np.round(K0), atol=2e-2)
+    assert np.allclose(K1, np.round(K1), atol=2e-1)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("bias", [-64, 9])
+def test_raymarch_interpolation_reproduces_a_linear_field(axis, bias):
+    """Segment ID = the voxel's coordinate along one axis, TF red = (ID + 1/2)
+    / n: the field is linear in the voxel centres, every mip level holds its
+    block averages (linear again), so trilinear and level interpolation give
+    red = p / n exactly at interior points.  A single sample at the eye (ray
+    parameter 0) reads that point; red / A recovers it."""
+    dims = [16, 16, 16]
+    n = dims[axis]
+    coords = np.indices(dims[::-1])[2 - axis]
+    vol = coords.astype(np.uint16)
+    g = oracle.Graph(vol, n)
+    tf = np.zeros((n, 4), np.float64)
+    tf[:, 0] = (np.arange(n) + 0.5) / n
+    tf[:, 3] = 0.5
+    vals = oracle.propagate(g.p, g.q, g.a, g.b, n, tf).astype(np.float32)
+    rng = np.random.default_rng(axis)
+    for _ in range(6):
+        eye = rng.uniform(5.0, 11.0, 3)
+        cam = _march_cam(eye, width=2, height=2, bias=bias, max_steps=1)
+        img, steps, _ = g.raymarch(vals, cam)
+        assert (steps == 1).all()
+        red = img[..., 0] / img[..., 3]
+        assert np.allclose(red, np.float32(eye[axis]) / n, atol=2e-6), (eye, red)
+
+
+def test_raymarch_skipping_changes_nothing():
+    """Empty-space skipping only passes over samples of exactly zero opacity:
+    the image is identical with and without it, and fewer samples are taken."""
+    dims = (64, 64, 64)
+    S = 4
+    vol = synth.make_volume(4, dims=dims, S=S)   # three cylinders in a background (ID 0)
+    g = oracle.Graph(vol, S)
+    tf = synth.make_attribute_tf(4, S)           # background fully transparent
+    vals = oracle.propagate(g.p, g.q, g.a, g.b, S, tf.astype(np.float64)).astype(np.float32)
+    cam = synth.orbit_camera(4, dims=dims, width=48, height=32, base_step=0.5, lod_bias=0, ert=2.0)
+    a, sa, _ = g.raymarch(vals, cam)
+    b, sb, _ = g.raymarch(vals, cam, opacity=vals[:, 3].copy())
+    assert np.array_equal(a, b)
+    assert (sb <= sa).all() and sb.sum() < sa.sum()
