@@ -502,6 +502,61 @@ MG_API mg_status mg_graph_export(const mg_graph *g, void *host, size_t bytes, mg
 MG_API mg_status mg_graph_import(const void *host, size_t bytes, const mg_allocator *allocator, mg_stream stream,
                                  mg_graph **out);
 
+/*
+ * Bitstream (Sec. 3.3, Table 1, Eq. 14-15): the graph as the paper's fixed-
+ * rate stream.  Bit i of the stream is bit i % 8 of byte i / 8 and every
+ * field is written least significant bit first, in Table 1's order:
+ *   (1) sources, 32 bits;  (2) fractional input, 1 bit (0);  (3) bits per node
+ *   ID nb = ceil(log2 N), stored minus one in 6 bits;  (4) sigma_max, 32 bits
+ *   (0: no quantiser);  (5) resolution, 3 x 32 bits;  (6) quantisation
+ *   bitrate minus one, 4 bits (0);  (7) internal nodes N - S, nb bits;
+ *   lossless extension (Table 1 has no exact form): 1 bit "exact weights" (1)
+ *   and the weight width w minus one in 6 bits;
+ *   per level l = 0..L-1: (8) voxel bits r(l) = ceil(log2(i_max(l) - i_min(l)
+ *   + 1)) and (9) i_min(l), nb bits each;
+ *   (A) every level's voxels x fastest: node ID - i_min(l) at r(l) bits;
+ *   (B) every internal node S..N-1: p and q at nb bits, the coprime weights a
+ *   and b at w bits (in place of a codebook index);  (C) empty;
+ *   zero padding to a multiple of 8 bytes.
+ * mg_bitstream_size: the stream's bytes (synchronises: the per-level ID
+ *   ranges are reduced on the device).
+ * mg_bitstream_write: the stream into `dst` (device, 8-byte aligned, at
+ *   least that many bytes); synchronises `stream`.
+ * mg_bitstream_parse: the layout from the stream's first bytes (host; the
+ *   header is at most ~600 bytes): MG_ERR_INVALID_ARG for a short or
+ *   inconsistent header, MG_ERR_UNSUPPORTED for a fractional or quantised one.
+ * mg_bitstream_decode_mip / _nodes: a level's node IDs (dims[level], x
+ *   fastest) / the node table (as mg_graph_copy_nodes, any pointer may be
+ *   NULL), decoded on the device from the stream (device) into device buffers.
+ * mg_bitstream_lookup: mg_render_lookup with every sample's node ID read by
+ *   bit address from the stream (Sec. 4: voxel data addressed by bit), vals
+ *   from a propagation of the same graph.
+ */
+typedef struct {
+    uint32_t num_segments;                   /* S */
+    int levels;                              /* L */
+    int node_bits;                           /* nb */
+    int weight_bits;                         /* w */
+    int64_t num_nodes;                       /* N */
+    int64_t dims[MG_MAX_LEVELS][3];
+    int32_t voxel_bits[MG_MAX_LEVELS];       /* r(l) */
+    int64_t imin[MG_MAX_LEVELS];             /* i_min(l) */
+    int64_t level_bit[MG_MAX_LEVELS];        /* bit offset of each level's section (A) */
+    int64_t node_bit;                        /* bit offset of section (B) */
+    int64_t header_bits;                     /* bits before section (A) */
+    int64_t bytes;                           /* stream size */
+} mg_bitstream_info;
+
+MG_API mg_status mg_bitstream_size(const mg_graph *g, size_t *bytes);
+MG_API mg_status mg_bitstream_write(const mg_graph *g, void *dst, size_t bytes, mg_stream stream);
+MG_API mg_status mg_bitstream_parse(const void *host, size_t bytes, mg_bitstream_info *info);
+MG_API mg_status mg_bitstream_decode_mip(const void *stream_dev, const mg_bitstream_info *info, int level,
+                                         uint32_t *out, mg_stream stream);
+MG_API mg_status mg_bitstream_decode_nodes(const void *stream_dev, const mg_bitstream_info *info, uint32_t *p,
+                                           uint32_t *q, uint64_t *a, uint64_t *b, mg_stream stream);
+MG_API mg_status mg_bitstream_lookup(const void *stream_dev, const mg_bitstream_info *info, const void *vals, int C,
+                                     mg_dtype dtype, const float *samples, int64_t P, void *out, mg_stream stream);
+
 /* Self-test of failure handling: one GPU thread waits, with the same bounded
  * wait the single-pass propagation uses between topological levels (Sec. 3.4),
  * on a device flag that is already set (satisfied = 1: returns MG_OK) or that

@@ -18,6 +18,11 @@ Functions whose results are pinned by tests other than self-comparison:
   sample_voxels     hand cases at level and voxel boundaries
   raymarch          closed form through a uniform volume; exact trilinear
                     reproduction of a linear field; skipping changes nothing
+  bitstream         read back by an independent reader of Table 1's layout;
+                    section sizes from Eq. 15
+  greedy            hand-worked picks (phi_1 and phi_2 differ); exact mode
+                    expands to every mixture; quantisation error within its
+                    bound; codewords and sigma by definition
 """
 from __future__ import annotations
 
@@ -101,6 +106,13 @@ def _load():
         lib.mgo_factor_lists.restype = P
         lib.mgo_depths.argtypes = [P, P, i64, ctypes.c_uint32, P]
         lib.mgo_raymarch.argtypes = [P, P, P, ctypes.POINTER(Camera), P, P, P]
+        lib.mgo_build_greedy.argtypes = [P, i32, i64, i64, i64, ctypes.c_uint32, i32, i32, i32, P, P, P, i64, P]
+        lib.mgo_build_greedy.restype = P
+        lib.mgo_greedy_lists.argtypes = [P, P, P, i64, ctypes.c_uint32, i32, i32, i32, P, P, i64, P]
+        lib.mgo_greedy_lists.restype = P
+        lib.mgo_quantised_mixture.argtypes = [P, P, ctypes.c_uint32, P]
+        lib.mgo_bitstream.argtypes = [P, P, i64]
+        lib.mgo_bitstream.restype = i64
         lib.mgo_set_threads.argtypes = [i32]
         lib.mgo_set_threads.restype = i32
         _lib = lib
@@ -240,6 +252,14 @@ class Graph:
                                _ptr(steps), _ptr(margin))
         return img, steps, margin
 
+    def bitstream(self) -> bytes:
+        """The graph as the bitstream of Table 1 (Sec. 3.3, Eq. 14-15), exact
+        weights in the extension field (see mg_oracle.c for the readings)."""
+        n = int(self._lib.mgo_bitstream(self._h, None, 0))
+        out = np.zeros(max(n, 8), np.uint8)
+        self._lib.mgo_bitstream(self._h, _ptr(out), out.nbytes)
+        return out[:n].tobytes()
+
     def fa_query(self, boxes: np.ndarray) -> np.ndarray:
         """Box histograms by footprint assembly + exact push (Algorithm 1)."""
         boxes = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 6)
@@ -282,6 +302,60 @@ def factor_lists(lists, num_segments: int):
     if not h:
         raise MemoryError("oracle factorisation failed")
     return Graph(None, num_segments, _handle=h), roots[: len(lists)]
+
+
+STRATEGIES = {"occurrence": 1, "reduction": 2}   # phi_1 max-occurrence, phi_2 max-reduction (Eq. 10-13)
+
+
+def greedy(vol: np.ndarray, num_segments: int, strategy: str = "reduction", tau: int = 3, bitrate: int = 9,
+           max_picks: int = 1 << 16):
+    """Greedy factorisation of a volume's mipmap (Sec. 3.3, Sec. 3.7): returns
+    (Graph, codebook (2^b,), sigma (2^b,), stage-1 picks (n, 2)).  bitrate 0
+    keeps exact ratios (then a, b are the exact weights); otherwise a node's
+    `a` is its quantiser bin and b = 0."""
+    vol, nb, nx, ny, nz = _vol_args(vol)
+    nbins = (1 << bitrate) if bitrate else 1
+    cb = np.zeros(nbins, np.float64)
+    sg = np.zeros(nbins, np.float64)
+    picks = np.zeros((max_picks, 2), np.uint32)
+    n = ctypes.c_int64(0)
+    h = _load().mgo_build_greedy(_ptr(vol), nb, nx, ny, nz, num_segments, STRATEGIES[strategy], tau, bitrate,
+                                 _ptr(cb), _ptr(sg), _ptr(picks), max_picks, ctypes.byref(n))
+    if not h:
+        raise ValueError("oracle greedy build failed")
+    g = Graph(None, num_segments, _handle=h)
+    return g, cb, sg, picks[: min(n.value, max_picks)].copy()
+
+
+def greedy_lists(lists, num_segments: int, strategy: str = "reduction", tau: int = 3, bitrate: int = 0,
+                 max_picks: int = 1024):
+    """Greedy factorisation of given mixtures [(id, weight), ...] ascending by
+    id: returns (Graph, roots, stage-1 picks)."""
+    off = [0]
+    ids, cnt = [], []
+    for lst in lists:
+        for sid, w in lst:
+            ids.append(int(sid)); cnt.append(int(w))
+        off.append(len(ids))
+    off = np.array(off, np.uint64)
+    ids = np.array(ids if ids else [0], np.uint32)
+    cnt = np.array(cnt if cnt else [0], np.uint64)
+    roots = np.zeros(max(len(lists), 1), np.uint32)
+    picks = np.zeros((max_picks, 2), np.uint32)
+    n = ctypes.c_int64(0)
+    h = _load().mgo_greedy_lists(_ptr(off), _ptr(ids), _ptr(cnt), len(lists), num_segments, STRATEGIES[strategy],
+                                 tau, bitrate, _ptr(roots), _ptr(picks), max_picks, ctypes.byref(n))
+    if not h:
+        raise ValueError("oracle greedy failed")
+    return Graph(None, num_segments, _handle=h), roots[: len(lists)], picks[: min(n.value, max_picks)].copy()
+
+
+def quantised_mixture(g, codebook: np.ndarray, node: int) -> np.ndarray:
+    """The mixture (S,) a quantised graph reconstructs for one node."""
+    cb = np.ascontiguousarray(codebook, np.float64)
+    out = np.zeros(g.S, np.float64)
+    _load().mgo_quantised_mixture(g._h, _ptr(cb), int(node), _ptr(out))
+    return out
 
 
 def depths(p, q, S: int) -> np.ndarray:

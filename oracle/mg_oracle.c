@@ -311,12 +311,9 @@ static uint64_t gcd_u64(uint64_t x, uint64_t y)
     return x;
 }
 
-/* Eq. 5-6: the lerp of the entries (p, wp) and (q, wq) with the reduced ratio
- * a:b = wp:wq; an identical key already in the table is re-used (Sec. 3.3). */
-static int64_t table_get(mgo_table *t, uint32_t p, uint64_t wp, uint32_t q, uint64_t wq)
+/* The node with key (p, q, a, b), created if new (Sec. 3.3 re-use). */
+static int64_t table_get_key(mgo_table *t, uint32_t p, uint32_t q, uint64_t a, uint64_t b)
 {
-    uint64_t g = gcd_u64(wp, wq);
-    uint64_t a = wp / g, b = wq / g;
     uint64_t h = key_hash(p, q, a, b);
     int64_t m = t->nslot - 1;
     int64_t i = (int64_t)(h & (uint64_t)m);
@@ -337,6 +334,14 @@ static int64_t table_get(mgo_table *t, uint32_t p, uint64_t wp, uint32_t q, uint
         for (int64_t j = 0; j < t->n; j++) if (t->p[j] != MGO_NONE) table_insert_slot(t, j);
     }
     return k;
+}
+
+/* Eq. 5-6: the lerp of the entries (p, wp) and (q, wq) with the reduced ratio
+ * a:b = wp:wq; an identical key already in the table is re-used (Sec. 3.3). */
+static int64_t table_get(mgo_table *t, uint32_t p, uint64_t wp, uint32_t q, uint64_t wq)
+{
+    uint64_t g = gcd_u64(wp, wq);
+    return table_get_key(t, p, q, wp / g, wq / g);
 }
 
 /* Reading R3: factorise one mixture (entries sorted by id) with the balanced
@@ -1033,4 +1038,428 @@ void mgo_raymarch(const mgo_graph *g, const float *vals, const float *opac, cons
         if (steps_out) steps_out[pix_i] = taken;
         if (margin_out) margin_out[pix_i] = margin;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.3, Table 1, Eq. 14-15: the bitstream of a graph.                   */
+/*                                                                          */
+/* Readings taken here:                                                      */
+/*   B1 bit order: every field is written least significant bit first, and  */
+/*      bit i of the stream is bit (i mod 8) of byte i / 8.                  */
+/*   B2 ranges [1..64] and [1..16] (fields (3) and (6)) are stored minus one.*/
+/*   B3 Table 1 has no lossless form: the exact graph's weights a:b (no     */
+/*      quantiser) go into an extension after field (7): one bit "exact"    */
+/*      (1 here) and six bits holding w - 1, w the width of the larger of a  */
+/*      and b; then every node of (B) stores p, q at field (3)'s width and   */
+/*      a, b at w bits instead of a codebook index, and (C) is empty.  Field */
+/*      (6) holds 1 and field (4) holds 0.                                   */
+/*   B4 field (3) is ceil(log2 N) (at least 1); field (7) is N - S; levels   */
+/*      go from 0 (the input) to L - 1, and (A) lists each level's voxels    */
+/*      x fastest, as ID - i_min(l) at r(l) = ceil(log2(i_max - i_min + 1))  */
+/*      bits (Eq. 15; 0 bits when the level holds one ID).                   */
+/*   B5 the stream is padded with zero bytes to a multiple of 8 bytes.       */
+/* ------------------------------------------------------------------------ */
+typedef struct { uint8_t *buf; int64_t cap; int64_t bit; } bs_writer;
+
+static void bs_put(bs_writer *w, uint64_t v, int nbits)
+{
+    for (int i = 0; i < nbits; i++) {
+        if ((v >> i) & 1u) {
+            int64_t byte = (w->bit + i) >> 3;
+            if (byte < w->cap) w->buf[byte] |= (uint8_t)(1u << ((w->bit + i) & 7));
+        }
+    }
+    w->bit += nbits;
+}
+
+static int bits_for(uint64_t range)   /* ceil(log2(range)), range >= 1 */
+{
+    int b = 0;
+    while (b < 64 && ((uint64_t)1 << b) < range) b++;
+    return b;
+}
+
+/* Writes the stream into out (cap bytes, zeroed here); returns its size in
+ * bytes (call with out = NULL for the size alone). */
+int64_t mgo_bitstream(const mgo_graph *g, uint8_t *out, int64_t cap)
+{
+    int nb = bits_for((uint64_t)g->N);
+    if (nb < 1) nb = 1;
+    uint64_t wmax = 1;
+    for (int64_t n = g->S; n < g->N; n++) {
+        if (g->a[n] > wmax) wmax = g->a[n];
+        if (g->b[n] > wmax) wmax = g->b[n];
+    }
+    int wbits = bits_for(wmax + 1);
+    if (wbits < 1) wbits = 1;
+    uint32_t imin[MGO_MAX_LEVELS], rl[MGO_MAX_LEVELS];
+    for (int l = 0; l < g->L; l++) {
+        int64_t nv = g->dims[3 * l] * g->dims[3 * l + 1] * g->dims[3 * l + 2];
+        uint32_t lo = g->mip[l][0], hi = g->mip[l][0];
+        for (int64_t v = 1; v < nv; v++) {
+            if (g->mip[l][v] < lo) lo = g->mip[l][v];
+            if (g->mip[l][v] > hi) hi = g->mip[l][v];
+        }
+        imin[l] = lo;
+        rl[l] = (uint32_t)bits_for((uint64_t)(hi - lo) + 1);
+    }
+    bs_writer w = {out, out ? cap : 0, 0};
+    if (out) memset(out, 0, (size_t)cap);
+    bs_put(&w, g->S, 32);                       /* (1) sources */
+    bs_put(&w, 0, 1);                           /* (2) fractional input: no */
+    bs_put(&w, (uint64_t)(nb - 1), 6);          /* (3) bits per node */
+    bs_put(&w, 0, 32);                          /* (4) sigma_max (no quantiser) */
+    for (int k = 0; k < 3; k++) bs_put(&w, (uint64_t)g->dims[k], 32);   /* (5) resolution */
+    bs_put(&w, 0, 4);                           /* (6) quantisation bitrate 1 (unused) */
+    bs_put(&w, (uint64_t)(g->N - g->S), nb);    /* (7) internal nodes */
+    bs_put(&w, 1, 1);                           /* extension: exact weights */
+    bs_put(&w, (uint64_t)(wbits - 1), 6);       /*            their width */
+    for (int l = 0; l < g->L; l++) {
+        bs_put(&w, rl[l], nb);                  /* (8) voxel bits */
+        bs_put(&w, imin[l], nb);                /* (9) i_min(l) */
+    }
+    for (int l = 0; l < g->L; l++) {           /* (A) one mixture ID per voxel */
+        int64_t nv = g->dims[3 * l] * g->dims[3 * l + 1] * g->dims[3 * l + 2];
+        for (int64_t v = 0; v < nv; v++) bs_put(&w, g->mip[l][v] - imin[l], (int)rl[l]);
+    }
+    for (int64_t n = g->S; n < g->N; n++) {    /* (B) description of mixtures */
+        bs_put(&w, g->p[n], nb);
+        bs_put(&w, g->q[n], nb);
+        bs_put(&w, g->a[n], wbits);
+        bs_put(&w, g->b[n], wbits);
+    }
+    int64_t bytes = (w.bit + 7) >> 3;
+    return (bytes + 7) & ~(int64_t)7;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.3 (Eq. 10-13) and Sec. 3.7: greedy factorisation.                  */
+/*                                                                          */
+/* Readings taken here:                                                      */
+/*   G1 H is every mixture of levels 1..L-1 (level-0 voxels are sources).   */
+/*      Components are node IDs with exact integer weights (8^l H, R1).     */
+/*   G2 stage 1 (Sec. 3.7): only mixtures with more than tau components are */
+/*      scored and factored.  A round scores every pair i < j of components */
+/*      that occur together in such a mixture h, phi_1 adding 1 per h and   */
+/*      phi_2 adding |h| - 1 if |h| > 2, else 2 (Eq. 10-13); the pick is the */
+/*      highest score, ties to the smallest (i, j); every such mixture that */
+/*      holds both is factored (all occurrences).  Stage 1 ends when no      */
+/*      mixture has more than tau components.                               */
+/*   G3 stage 2: every mixture left with 2..tau components, levels in order */
+/*      and voxels x fastest, lerps its two lowest-numbered components until */
+/*      one remains.                                                         */
+/*   G4 a lerp of components p < q with weights c_p, c_q gives q the weight */
+/*      w = c_q / (c_p + c_q).  bitrate b >= 1: w falls in bin k = floor(w   */
+/*      2^b) of the 2^b equal bins of (0, 1), decided exactly in integers;   */
+/*      the node is the key (p, q, k), so all lerps of one pair in one bin   */
+/*      are one node; the bin's codeword is its centre (2k + 1) / 2^(b+1)    */
+/*      and its sigma the rms of w - codeword over the lerps in the bin.     */
+/*      The bins are symmetric about 1/2, so the symmetry of Sec. 3.7         */
+/*      ((i, j, w) = (j, i, 1 - w)) never lowers the error: orientation p<q.*/
+/*      b = 0: exact, the node is the key (p, q, a, b) of the reduced ratio  */
+/*      a:b = c_p:c_q as in the pairwise graph.                              */
+/*   G5 the merged component keeps the exact weight c_p + c_q.  Node IDs are */
+/*      canonical (R5); a quantised node holds its bin in `a` and 0 in `b`.  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t M;            /* mixtures (levels 1..L-1, level by level, x fastest) */
+    int64_t *off;         /* first entry of every mixture (M + 1) */
+    int32_t *len;         /* current number of components */
+    uint32_t *comp;       /* component node IDs, ascending within a mixture */
+    uint64_t *wt;         /* their exact weights */
+} gr_lists;
+
+static void gr_free(gr_lists *x)
+{
+    free(x->off); free(x->len); free(x->comp); free(x->wt);
+    memset(x, 0, sizeof(*x));
+}
+
+/* lerp of (p, cp), (q, cq), p < q: the node, and the quantiser's record */
+static int64_t gr_node(mgo_table *t, uint32_t p, uint64_t cp, uint32_t q, uint64_t cq, int bitrate,
+                       double *ssq, int64_t *cnt)
+{
+    if (bitrate == 0) return table_get(t, p, cp, q, cq);
+    uint64_t s = cp + cq;
+    uint64_t k = (cq << bitrate) / s;      /* floor(w 2^b), w in (0, 1) */
+    uint64_t nb = (uint64_t)1 << bitrate;
+    if (k >= nb) k = nb - 1;
+    double w = (double)cq / (double)s, c = ((double)(2 * k + 1)) / (double)(2 * nb);
+    ssq[k] += (w - c) * (w - c);
+    cnt[k]++;
+    return table_get_key(t, p, q, k, 0);
+}
+
+/* replace components i, j (both present, i < j) of mixture m by node n with
+ * weight ci + cj, keeping the list ascending */
+static void gr_merge(gr_lists *x, int64_t m, int32_t ii, int32_t jj, uint32_t n, uint64_t w)
+{
+    uint32_t *c = x->comp + x->off[m];
+    uint64_t *v = x->wt + x->off[m];
+    int32_t L = x->len[m], o = 0;
+    for (int32_t e = 0; e < L; e++) {
+        if (e == ii || e == jj) continue;
+        c[o] = c[e]; v[o] = v[e]; o++;
+    }
+    int32_t pos = o;
+    while (pos > 0 && c[pos - 1] > n) { c[pos] = c[pos - 1]; v[pos] = v[pos - 1]; pos--; }
+    c[pos] = n; v[pos] = w;
+    x->len[m] = o + 1;
+}
+
+static int32_t gr_find(const gr_lists *x, int64_t m, uint32_t id)
+{
+    const uint32_t *c = x->comp + x->off[m];
+    int32_t lo = 0, hi = x->len[m];
+    while (lo < hi) {
+        int32_t mid = (lo + hi) / 2;
+        if (c[mid] < id) lo = mid + 1; else hi = mid;
+    }
+    return lo < x->len[m] && c[lo] == id ? lo : -1;
+}
+
+typedef struct { uint32_t i, j; uint64_t score; int used; } gr_pair;
+
+/* Stages 1 and 2 on the mixtures x (G2, G3), nodes into t; the quantiser's
+ * records into ssq / cnt; the stage-1 picks into picks (room for max_picks). */
+static void gr_run(gr_lists *x, mgo_table *t, int strategy, int tau, int bitrate, double *ssq, int64_t *cnt,
+                   uint32_t *picks, int64_t max_picks, int64_t *n_picks)
+{
+    int64_t npick = 0;
+    const int64_t M = x->M;
+
+    /* stage 1: greedy picks over the mixtures with more than tau components */
+    int64_t pcap = 1024, pn = 0;
+    gr_pair *pairs = (gr_pair *)malloc((size_t)pcap * sizeof(gr_pair));
+    int64_t hcap = 1;
+    int64_t *hslot = NULL;
+    for (;;) {
+        /* scores: an open-addressing map (i, j) -> index into pairs */
+        pn = 0;
+        int64_t need = 16;
+        for (int64_t m = 0; m < M; m++)
+            if (x->len[m] > tau) need += (int64_t)x->len[m] * (x->len[m] - 1) / 2;
+        if (need <= 16) break;
+        while (hcap < 2 * need) hcap *= 2;
+        hslot = (int64_t *)realloc(hslot, (size_t)hcap * sizeof(int64_t));
+        for (int64_t i = 0; i < hcap; i++) hslot[i] = -1;
+        for (int64_t m = 0; m < M; m++) {
+            int32_t n = x->len[m];
+            if (n <= tau) continue;
+            uint64_t add = strategy == 1 ? 1 : (n > 2 ? (uint64_t)(n - 1) : 2);
+            const uint32_t *c = x->comp + x->off[m];
+            for (int32_t a = 0; a < n; a++)
+                for (int32_t b2 = a + 1; b2 < n; b2++) {
+                    uint64_t h = mix64(((uint64_t)c[a] << 32) | c[b2]) & (uint64_t)(hcap - 1);
+                    while (hslot[h] >= 0 && !(pairs[hslot[h]].i == c[a] && pairs[hslot[h]].j == c[b2]))
+                        h = (h + 1) & (uint64_t)(hcap - 1);
+                    if (hslot[h] < 0) {
+                        if (pn == pcap) { pcap *= 2; pairs = (gr_pair *)realloc(pairs, (size_t)pcap * sizeof(gr_pair)); }
+                        pairs[pn].i = c[a]; pairs[pn].j = c[b2]; pairs[pn].score = 0;
+                        hslot[h] = pn++;
+                    }
+                    pairs[hslot[h]].score += add;
+                }
+        }
+        int64_t best = -1;
+        for (int64_t k = 0; k < pn; k++) {
+            if (best < 0 || pairs[k].score > pairs[best].score ||
+                (pairs[k].score == pairs[best].score &&
+                 (pairs[k].i < pairs[best].i || (pairs[k].i == pairs[best].i && pairs[k].j < pairs[best].j))))
+                best = k;
+        }
+        if (best < 0) break;
+        uint32_t bi = pairs[best].i, bj = pairs[best].j;
+        if (picks && npick < max_picks) { picks[2 * npick] = bi; picks[2 * npick + 1] = bj; }
+        npick++;
+        /* factor every occurrence among the mixtures with more than tau components */
+        for (int64_t m = 0; m < M; m++) {
+            if (x->len[m] <= tau) continue;
+            int32_t ii = gr_find(x, m, bi), jj = gr_find(x, m, bj);
+            if (ii < 0 || jj < 0) continue;
+            uint64_t ci = x->wt[x->off[m] + ii], cj = x->wt[x->off[m] + jj];
+            int64_t nd = gr_node(t, bi, ci, bj, cj, bitrate, ssq, cnt);
+            gr_merge(x, m, ii, jj, (uint32_t)nd, ci + cj);
+        }
+    }
+    free(pairs); free(hslot);
+
+    /* stage 2: the rest in scanline order, the two lowest components first */
+    for (int64_t m = 0; m < M; m++) {
+        while (x->len[m] > 1) {
+            const uint32_t *c = x->comp + x->off[m];
+            uint32_t p = c[0], q = c[1];
+            uint64_t cp = x->wt[x->off[m]], cq = x->wt[x->off[m] + 1];
+            int64_t nd = gr_node(t, p, cp, q, cq, bitrate, ssq, cnt);
+            gr_merge(x, m, 0, 1, (uint32_t)nd, cp + cq);
+        }
+    }
+
+    *n_picks = npick;
+}
+
+/* The greedy graph of a volume; codebook / sigma (2^bitrate each, may be
+ * NULL) receive the codewords and rms errors, picks (may be NULL, room for
+ * max_picks pairs) the stage-1 picks in order, *n_picks their number. */
+mgo_graph *mgo_build_greedy(const void *vol, int id_bytes, int64_t nx, int64_t ny, int64_t nz, uint32_t S,
+                            int strategy, int tau, int bitrate, double *codebook, double *sigma,
+                            uint32_t *picks, int64_t max_picks, int64_t *n_picks)
+{
+    if (strategy != 1 && strategy != 2) return NULL;
+    if (bitrate < 0 || bitrate > 16 || tau < 1) return NULL;
+    mgo_graph *g = (mgo_graph *)calloc(1, sizeof(mgo_graph));
+    if (!g) return NULL;
+    g->S = S;
+    g->L = mgo_level_dims(nx, ny, nz, g->dims, MGO_MAX_LEVELS);
+    int64_t V0 = nx * ny * nz;
+    for (int64_t i = 0; i < V0; i++) if (vol_id(vol, id_bytes, i) >= S) { free(g); return NULL; }
+    g->mip = (uint32_t **)calloc((size_t)g->L, sizeof(uint32_t *));
+    g->mip[0] = (uint32_t *)malloc((size_t)V0 * sizeof(uint32_t));
+    for (int64_t i = 0; i < V0; i++) g->mip[0][i] = vol_id(vol, id_bytes, i);
+
+    /* H: the mixtures of levels 1..L-1 */
+    int64_t M = 0, E = 0;
+    mgo_lists lv[MGO_MAX_LEVELS];
+    memset(lv, 0, sizeof(lv));
+    lists_level0(vol, id_bytes, nx, ny, nz, &lv[0]);
+    for (int l = 1; l < g->L; l++) {
+        if (lists_next(&lv[l - 1], &lv[l])) {
+            for (int k = 0; k <= l; k++) lists_free(&lv[k]);
+            mgo_graph_free(g);
+            return NULL;
+        }
+        if (l == 1) lists_free(&lv[0]);
+        M += lv[l].nv;
+        E += lv[l].nnz;
+    }
+    if (g->L == 1) lists_free(&lv[0]);
+    gr_lists x;
+    x.M = M;
+    x.off = (int64_t *)malloc((size_t)(M + 1) * sizeof(int64_t));
+    x.len = (int32_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int32_t));
+    x.comp = (uint32_t *)malloc((size_t)(E > 0 ? E : 1) * sizeof(uint32_t));
+    x.wt = (uint64_t *)malloc((size_t)(E > 0 ? E : 1) * sizeof(uint64_t));
+    {
+        int64_t m = 0, e = 0;
+        for (int l = 1; l < g->L; l++) {
+            for (int64_t v = 0; v < lv[l].nv; v++, m++) {
+                x.off[m] = e;
+                x.len[m] = (int32_t)(lv[l].off[v + 1] - lv[l].off[v]);
+                for (uint64_t k = lv[l].off[v]; k < lv[l].off[v + 1]; k++, e++) {
+                    x.comp[e] = lv[l].ids[k];
+                    x.wt[e] = lv[l].cnt[k];
+                }
+            }
+            if (lv[l].nv) {
+                int64_t nv = lv[l].nv;
+                for (int64_t v = 0; v < nv; v++) {
+                    int64_t n = (int64_t)(lv[l].off[v + 1] - lv[l].off[v]);
+                    if (n > g->max_nnz) g->max_nnz = n;
+                    g->pairs += n - 1;
+                }
+            }
+            lists_free(&lv[l]);
+        }
+        x.off[M] = e;
+    }
+    if (g->max_nnz < 1) g->max_nnz = 1;
+
+    mgo_table t;
+    table_init(&t, S);
+    int64_t nbins = bitrate ? ((int64_t)1 << bitrate) : 1;
+    double *ssq = (double *)calloc((size_t)nbins, sizeof(double));
+    int64_t *cnt = (int64_t *)calloc((size_t)nbins, sizeof(int64_t));
+    int64_t npick = 0;
+    gr_run(&x, &t, strategy, tau, bitrate, ssq, cnt, picks, max_picks, &npick);
+
+    /* mip IDs (temporary numbers), then the canonical numbering */
+    {
+        int64_t m = 0;
+        for (int l = 1; l < g->L; l++) {
+            int64_t nv = g->dims[3 * l] * g->dims[3 * l + 1] * g->dims[3 * l + 2];
+            g->mip[l] = (uint32_t *)malloc((size_t)nv * sizeof(uint32_t));
+            for (int64_t v = 0; v < nv; v++, m++) g->mip[l][v] = x.comp[x.off[m]];
+        }
+    }
+    gr_free(&x);
+    if (relabel(g, &t)) { table_free(&t); mgo_graph_free(g); free(ssq); free(cnt); return NULL; }
+    for (int l = 1; l < g->L; l++) {
+        int64_t nv = g->dims[3 * l] * g->dims[3 * l + 1] * g->dims[3 * l + 2];
+        for (int64_t v = 0; v < nv; v++) g->mip[l][v] = (uint32_t)g->canon[g->mip[l][v]];
+    }
+    free(g->canon); g->canon = NULL;
+    table_free(&t);
+    for (int64_t k = 0; k < nbins && bitrate; k++) {
+        if (codebook) codebook[k] = ((double)(2 * k + 1)) / (double)(2 * nbins);
+        if (sigma) sigma[k] = cnt[k] ? sqrt(ssq[k] / (double)cnt[k]) : 0.0;
+    }
+    free(ssq); free(cnt);
+    if (n_picks) *n_picks = npick;
+    return g;
+}
+
+/* The mixture a quantised graph reconstructs for one node: 1 pushed from the
+ * node to the sources, q receiving the codeword of the node's bin (a) and p
+ * the rest.  out: S doubles (dense). */
+void mgo_quantised_mixture(const mgo_graph *g, const double *codebook, uint32_t node, double *out)
+{
+    size_t cap = 64, n = 0;
+    uint32_t *sn = (uint32_t *)malloc(cap * sizeof(uint32_t));
+    double *sw = (double *)malloc(cap * sizeof(double));
+    sn[n] = node; sw[n] = 1.0; n++;
+    while (n) {
+        n--;
+        uint32_t k = sn[n];
+        double w = sw[n];
+        if (k < g->S) { out[k] += w; continue; }
+        double c = codebook[g->a[k]];
+        if (n + 2 > cap) {
+            cap *= 2;
+            sn = (uint32_t *)realloc(sn, cap * sizeof(uint32_t));
+            sw = (double *)realloc(sw, cap * sizeof(double));
+        }
+        sn[n] = g->p[k]; sw[n] = w * (1.0 - c); n++;
+        sn[n] = g->q[k]; sw[n] = w * c; n++;
+    }
+    free(sn); free(sw);
+}
+
+/* The greedy factorisation of given mixtures (CSR lists ascending by ID,
+ * integer weights), as mgo_build_greedy does for a volume's mipmap; roots[m]
+ * receives the canonical node of mixture m.  For the paper's worked examples. */
+mgo_graph *mgo_greedy_lists(const uint64_t *off, const uint32_t *ids, const uint64_t *cnt_in, int64_t M, uint32_t S,
+                            int strategy, int tau, int bitrate, uint32_t *roots, uint32_t *picks, int64_t max_picks,
+                            int64_t *n_picks)
+{
+    if ((strategy != 1 && strategy != 2) || bitrate < 0 || bitrate > 16 || tau < 1) return NULL;
+    mgo_graph *g = (mgo_graph *)calloc(1, sizeof(mgo_graph));
+    if (!g) return NULL;
+    g->S = S;
+    g->L = 0;
+    gr_lists x;
+    x.M = M;
+    int64_t E = (int64_t)off[M];
+    x.off = (int64_t *)malloc((size_t)(M + 1) * sizeof(int64_t));
+    x.len = (int32_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int32_t));
+    x.comp = (uint32_t *)malloc((size_t)(E > 0 ? E : 1) * sizeof(uint32_t));
+    x.wt = (uint64_t *)malloc((size_t)(E > 0 ? E : 1) * sizeof(uint64_t));
+    for (int64_t m = 0; m <= M; m++) x.off[m] = (int64_t)off[m];
+    for (int64_t m = 0; m < M; m++) x.len[m] = (int32_t)(off[m + 1] - off[m]);
+    for (int64_t e = 0; e < E; e++) { x.comp[e] = ids[e]; x.wt[e] = cnt_in[e]; }
+    mgo_table t;
+    table_init(&t, S);
+    int64_t nbins = bitrate ? ((int64_t)1 << bitrate) : 1;
+    double *ssq = (double *)calloc((size_t)nbins, sizeof(double));
+    int64_t *cnt = (int64_t *)calloc((size_t)nbins, sizeof(int64_t));
+    gr_run(&x, &t, strategy, tau, bitrate, ssq, cnt, picks, max_picks, n_picks);
+    uint32_t *tmp = (uint32_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(uint32_t));
+    for (int64_t m = 0; m < M; m++) tmp[m] = x.comp[x.off[m]];
+    gr_free(&x);
+    free(ssq); free(cnt);
+    if (relabel(g, &t)) { free(tmp); table_free(&t); mgo_graph_free(g); return NULL; }
+    for (int64_t m = 0; m < M; m++) roots[m] = (uint32_t)g->canon[tmp[m]];
+    free(tmp);
+    free(g->canon); g->canon = NULL;
+    table_free(&t);
+    return g;
 }

@@ -12,19 +12,6 @@ namespace mg {
 namespace {
 thread_local std::string t_err;
 
-struct DeviceGuard {
-    int prev = -1;
-    bool changed = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
-            changed = cudaSetDevice(dev) == cudaSuccess;
-        }
-    }
-    ~DeviceGuard() {
-        if (changed) cudaSetDevice(prev);
-    }
-};
-
 }  // namespace
 
 mg_status status_from_bits(unsigned bits) {

@@ -290,6 +290,20 @@ __device__ __forceinline__ bool bounded_wait_geq(const unsigned* p, unsigned nee
     return true;
 }
 
+// makes `dev` current for the scope of a call and restores the caller's device
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
 inline unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 30) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;

@@ -1248,20 +1248,10 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
                     if (k == 0) {
                         feed(x.x, l);
                     } else if (k == 1 || k == 3) {
-                        // a vector of one node: extend the lane's run or start a new one
-                        const uint32_t f = x.x;
-                        const bool uni = x.y == f && x.z == f && x.w == f &&
-                                         (k == 1 || (y.x == f && y.y == f && y.z == f && y.w == f));
-                        if (uni) {
-                            const uint32_t nn = k == 1 ? 4u : 8u;
-                            if (rcnt && rl == l && rid == f) {
-                                rcnt += nn;
-                            } else {
-                                finish();
-                                rid = f;
-                                rl = l;
-                                rcnt = nn;
-                            }
+                        const bool same = rcnt && rl == l && x.x == rid && x.y == rid && x.z == rid && x.w == rid &&
+                                          (k == 1 || (y.x == rid && y.y == rid && y.z == rid && y.w == rid));
+                        if (same) {
+                            rcnt += k == 1 ? 4 : 8;
                         } else {
                             feed(x.x, l);
                             feed(x.y, l);
@@ -1275,20 +1265,11 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
                             }
                         }
                     } else if (k == 2 || k == 4) {
-                        const uint32_t f = x.x & 0xffffu;   // the vector's first ID
-                        const uint32_t pr = f * 0x10001u;
+                        const uint32_t pr = rid * 0x10001u;
                         uint32_t diff = (x.x ^ pr) | (x.y ^ pr) | (x.z ^ pr) | (x.w ^ pr);
                         if (k == 4) diff |= (y.x ^ pr) | (y.y ^ pr) | (y.z ^ pr) | (y.w ^ pr);
-                        if (diff == 0u) {
-                            const uint32_t nn = k == 2 ? 8u : 16u;
-                            if (rcnt && rl == 0 && rid == f) {
-                                rcnt += nn;
-                            } else {
-                                finish();
-                                rid = f;
-                                rl = 0;
-                                rcnt = nn;
-                            }
+                        if (rcnt && rl == 0 && diff == 0u) {
+                            rcnt += k == 2 ? 8 : 16;
                         } else {
                             const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll

@@ -38,7 +38,8 @@ EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_cop
            "mg_query_plan_create", "mg_query_plan_run", "mg_query_plan_timing", "mg_query_plan_free",
            "mg_query_autotune",
            "mg_query_set_tuning", "mg_count_cubes", "mg_render_lookup", "mg_propagate_tf_multi",
-           "mg_render_lookup_multi", "mg_raymarch",
+           "mg_render_lookup_multi", "mg_raymarch", "mg_bitstream_size", "mg_bitstream_write", "mg_bitstream_parse",
+           "mg_bitstream_decode_mip", "mg_bitstream_decode_nodes", "mg_bitstream_lookup",
            "mg_server_create", "mg_server_add_volume", "mg_server_start", "mg_server_submit", "mg_server_cancel",
            "mg_server_wait", "mg_server_replay", "mg_server_stats_get", "mg_server_free",
            "mg_graph_export_size", "mg_graph_export", "mg_graph_import",
@@ -97,6 +98,14 @@ def camera(cam: dict) -> mg_camera:
     return c
 
 
+class mg_bitstream_info(ctypes.Structure):
+    _fields_ = [("num_segments", ctypes.c_uint32), ("levels", ctypes.c_int), ("node_bits", ctypes.c_int),
+                ("weight_bits", ctypes.c_int), ("num_nodes", ctypes.c_int64),
+                ("dims", (ctypes.c_int64 * 3) * MG_MAX_LEVELS), ("voxel_bits", ctypes.c_int32 * MG_MAX_LEVELS),
+                ("imin", ctypes.c_int64 * MG_MAX_LEVELS), ("level_bit", ctypes.c_int64 * MG_MAX_LEVELS),
+                ("node_bit", ctypes.c_int64), ("header_bits", ctypes.c_int64), ("bytes", ctypes.c_int64)]
+
+
 class mg_server_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("max_batch", ctypes.c_int), ("hist_type", ctypes.c_int),
                 ("storage", ctypes.c_int), ("max_samples", ctypes.c_int64), ("memory_budget", ctypes.c_int64),
@@ -144,6 +153,15 @@ def lib():
         L.mg_render_lookup_multi.argtypes = [P, P, i32, i32, i32, P, P, P, P]
         L.mg_render_lookup_multi.restype = st
         L.mg_raymarch.argtypes = [P, P, P, ctypes.POINTER(mg_camera), P, P, P]
+        L.mg_bitstream_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.mg_bitstream_write.argtypes = [P, P, ctypes.c_size_t, P]
+        L.mg_bitstream_parse.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(mg_bitstream_info)]
+        L.mg_bitstream_decode_mip.argtypes = [P, ctypes.POINTER(mg_bitstream_info), i32, P, P]
+        L.mg_bitstream_decode_nodes.argtypes = [P, ctypes.POINTER(mg_bitstream_info), P, P, P, P, P]
+        L.mg_bitstream_lookup.argtypes = [P, ctypes.POINTER(mg_bitstream_info), P, i32, i32, P, i64, P, P]
+        for f in ("mg_bitstream_size", "mg_bitstream_write", "mg_bitstream_parse", "mg_bitstream_decode_mip",
+                  "mg_bitstream_decode_nodes", "mg_bitstream_lookup"):
+            getattr(L, f).restype = st
         L.mg_raymarch.restype = st
         L.mg_query_boxes.argtypes = [P, P, i64, ctypes.POINTER(mg_query_opts), P, ctypes.c_size_t, P, P,
                                      ctypes.POINTER(ctypes.c_size_t), P]
@@ -606,6 +624,54 @@ def mg_raymarch(g: Graph, vals: torch.Tensor, cam: dict, opacity: torch.Tensor =
                              ctypes.byref(c), image.data_ptr(), st.data_ptr() if st is not None else None,
                              _stream(stream)))
     return (image, st) if steps else image
+
+
+class Bitstream:
+    """A graph's bitstream (Table 1) in device memory with its parsed layout."""
+
+    def __init__(self, data: torch.Tensor):
+        self.data = data
+        head = data[:1024].cpu().numpy()
+        self.info = mg_bitstream_info()
+        _check(lib().mg_bitstream_parse(head.ctypes.data, head.nbytes, ctypes.byref(self.info)))
+
+    def decode_mip(self, level: int, stream=None) -> torch.Tensor:
+        """Node IDs of one level, (z, y, x) uint32, decoded on the device."""
+        d = self.info.dims[level]
+        out = torch.empty((d[2], d[1], d[0]), dtype=torch.uint32, device=self.data.device)
+        _check(lib().mg_bitstream_decode_mip(self.data.data_ptr(), ctypes.byref(self.info), level, out.data_ptr(),
+                                             _stream(stream)))
+        return out
+
+    def decode_nodes(self, stream=None):
+        """(p, q, a, b) device tensors of the node table."""
+        N, dev = self.info.num_nodes, self.data.device
+        p = torch.empty(N, dtype=torch.uint32, device=dev)
+        q = torch.empty(N, dtype=torch.uint32, device=dev)
+        a = torch.empty(N, dtype=torch.uint64, device=dev)
+        b = torch.empty(N, dtype=torch.uint64, device=dev)
+        _check(lib().mg_bitstream_decode_nodes(self.data.data_ptr(), ctypes.byref(self.info), p.data_ptr(),
+                                               q.data_ptr(), a.data_ptr(), b.data_ptr(), _stream(stream)))
+        return p, q, a, b
+
+    def lookup(self, vals: torch.Tensor, samples: torch.Tensor, stream=None) -> torch.Tensor:
+        """mg_render_lookup with node IDs read from the stream by bit address."""
+        samples = samples.contiguous()
+        C = vals.shape[1]
+        out = torch.empty((samples.shape[0], C), dtype=vals.dtype, device=vals.device)
+        _check(lib().mg_bitstream_lookup(self.data.data_ptr(), ctypes.byref(self.info), vals.data_ptr(), C,
+                                         _TORCH_TO_MG[vals.dtype], samples.data_ptr(), samples.shape[0],
+                                         out.data_ptr(), _stream(stream)))
+        return out
+
+
+def mg_bitstream_write(g: Graph, stream=None) -> Bitstream:
+    """The graph's bitstream (Sec. 3.3, Table 1) encoded on the GPU."""
+    n = ctypes.c_size_t()
+    _check(lib().mg_bitstream_size(g.handle, ctypes.byref(n)))
+    data = torch.empty(n.value, dtype=torch.uint8, device=torch.device("cuda", g.device))
+    _check(lib().mg_bitstream_write(g.handle, data.data_ptr(), n.value, _stream(stream)))
+    return Bitstream(data)
 
 
 def mg_sync_status(g: Graph, stream=None):

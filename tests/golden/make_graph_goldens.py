@@ -8,7 +8,8 @@ here runs on or reads from the GPU path.  For each configuration the record
 holds the sizes (N, S, D, L, per-level dims), the depth bucket offsets, the
 longest mixture and the pair count, and sha256 digests of the node table
 (p, q uint32; a, b uint64, canonical order) and of the node ID of every voxel
-of every mip level (uint32, x fastest), all little-endian.
+of every mip level (uint32, x fastest), all little-endian, and the size and
+sha256 of the graph's bitstream (Table 1, oracle.Graph.bitstream).
 
     python tests/golden/make_graph_goldens.py 2 4 [3]
 """
@@ -48,8 +49,11 @@ def record(cfg_index: int) -> dict:
         "max_list": g.max_nnz, "pairs": g.pairs,
         "sha256": {"p": digest(g.p[:N]), "q": digest(g.q[:N]), "a": digest(g.a[:N]), "b": digest(g.b[:N]),
                    "mip": [digest(g.mip(l)) for l in range(g.L)]},
+        "bitstream": {},
         "source": "oracle.Graph on synth.make_volume(%d) (host generator)" % cfg_index,
     }
+    stream = g.bitstream()
+    rec["bitstream"] = {"bytes": len(stream), "sha256": hashlib.sha256(stream).hexdigest()}
     g.close()
     print("cfg %d: volume %.1f s, oracle build %.1f s, N=%d D=%d" % (cfg_index, t1 - t0, t2 - t1, N, rec["D"]),
           flush=True)

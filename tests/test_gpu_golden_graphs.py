@@ -61,3 +61,21 @@ def test_graph_matches_oracle_record(mg, cfg):
     for level in range(rec["L"]):
         assert digest(mg.mg_graph_copy_mip(g, level)) == rec["sha256"]["mip"][level], level
     g.close()
+
+
+@pytest.mark.parametrize("cfg", [2, 4, 3])
+def test_bitstream_matches_oracle_record(mg, cfg):
+    """The GPU-encoded bitstream (Table 1) of each benchmarked graph has the
+    size and sha256 of the oracle's stream of the same volume."""
+    with open(os.path.join(GOLDEN, "graph_cfg%d.json" % cfg)) as f:
+        rec = json.load(f)
+    c = synth.CONFIGS[cfg]
+    vol = synth.make_volume(cfg, device="cuda") if c["kind"] == "voronoi" else \
+        torch.from_numpy(synth.make_volume(cfg)).cuda()
+    g = mg.mg_build(vol, c["S"])
+    del vol
+    bs = mg.mg_bitstream_write(g)
+    data = bs.data.cpu().numpy()
+    assert data.nbytes == rec["bitstream"]["bytes"]
+    assert hashlib.sha256(data.tobytes()).hexdigest() == rec["bitstream"]["sha256"]
+    g.close()

@@ -370,3 +370,26 @@ def test_raymarch_argument_checks(mg):
     with pytest.raises(ValueError):
         mg.mg_raymarch(g, vals[:, :3], cam)
     g.close()
+
+
+# the bitstream (Table 1): encoded on the GPU byte for byte as the oracle
+# writes it, decoded on the GPU back to the graph, looked up in place
+@pytest.mark.parametrize("dims,S", [((37, 29, 23), 24), ((64, 64, 64), 64), ((16, 16, 16), 1), ((130, 7, 3), 50)])
+def test_bitstream_matches_oracle_and_decodes(mg, dims, S):
+    vol = synth.make_volume(1, dims=dims, S=S) if S > 1 else np.zeros(dims[::-1], np.uint16)
+    g, og = build_pair(mg, vol, S)
+    bs = mg.mg_bitstream_write(g)
+    ref = og.bitstream()
+    assert bs.data.cpu().numpy().tobytes() == ref
+    assert bs.info.bytes == len(ref) and bs.info.num_nodes == og.N
+    for level in range(og.L):
+        assert np.array_equal(bs.decode_mip(level).cpu().numpy(), og.mip(level)), level
+    p, q, a, b = (t.cpu().numpy() for t in bs.decode_nodes())
+    assert (p == og.p[:og.N]).all() and (q == og.q[:og.N]).all()
+    assert (a == og.a[:og.N]).all() and (b == og.b[:og.N]).all()
+    tf = torch.from_numpy(synth.make_tf(1, S, 4)).to(dev())
+    for storage in ("f32", "bf16"):
+        vals = mg.mg_propagate_tf(g, tf, storage=storage)
+        smp = torch.from_numpy(synth.make_samples(1, dims=dims, width=64, height=40)).to(dev())
+        assert torch.equal(bs.lookup(vals, smp).cpu(), mg.mg_render_lookup(g, vals, smp).cpu())
+    g.close()

@@ -531,3 +531,153 @@ def test_raymarch_skipping_changes_nothing():
     b, sb, _ = g.raymarch(vals, cam, opacity=vals[:, 3].copy())
     assert np.array_equal(a, b)
     assert (sb <= sa).all() and sb.sum() < sa.sum()
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.3, Table 1: the bitstream
+# ---------------------------------------------------------------------------
+class _BitReader:
+    """Fields least significant bit first, bit i of the stream = bit i % 8 of
+    byte i / 8 (a reader written from Table 1's field list)."""
+
+    def __init__(self, data):
+        self.x = int.from_bytes(data, "little")
+        self.pos = 0
+
+    def get(self, n):
+        v = (self.x >> self.pos) & ((1 << n) - 1)
+        self.pos += n
+        return v
+
+
+def _read_stream(data, L):
+    r = _BitReader(data)
+    h = dict(S=r.get(32), fractional=r.get(1), nb=r.get(6) + 1, sigma_max=r.get(32),
+             dims=[r.get(32) for _ in range(3)], bitrate=r.get(4) + 1)
+    h["internal"] = r.get(h["nb"])
+    h["exact"] = r.get(1)
+    h["wbits"] = r.get(6) + 1
+    h["r"], h["imin"] = [], []
+    for _ in range(L):
+        h["r"].append(r.get(h["nb"]))
+        h["imin"].append(r.get(h["nb"]))
+    h["header_bits"] = r.pos
+    return h, r
+
+
+@pytest.mark.parametrize("dims,S", [((37, 29, 23), 24), ((16, 16, 16), 1), ((9, 5, 3), 40)])
+def test_bitstream_reads_back_the_graph(dims, S):
+    vol = synth.make_volume(1, dims=dims, S=S) if S > 1 else np.zeros(dims[::-1], np.uint16)
+    g = oracle.Graph(vol, S)
+    data = g.bitstream()
+    assert len(data) % 8 == 0
+    h, r = _read_stream(data, g.L)
+    assert h["S"] == S and h["fractional"] == 0 and h["exact"] == 1 and h["sigma_max"] == 0
+    assert h["dims"] == list(dims) and h["internal"] == g.N - S
+    assert h["nb"] == max(1, int(np.ceil(np.log2(g.N))))
+    total = h["header_bits"]
+    for l in range(g.L):
+        ids = g.mip(l).ravel().astype(np.int64)
+        lo, hi = ids.min(), ids.max()
+        # Eq. 14-15: the smallest ID referenced and the bits of the range
+        assert h["imin"][l] == lo
+        assert h["r"][l] == int(np.ceil(np.log2(hi - lo + 1))) if hi > lo else h["r"][l] == 0
+        got = np.array([r.get(h["r"][l]) for _ in range(ids.size)], np.int64) + lo
+        assert np.array_equal(got, ids), l
+        total += ids.size * h["r"][l]
+    wmax = int(max(g.a[S:g.N].max(initial=1), g.b[S:g.N].max(initial=1)))
+    assert h["wbits"] == max(1, wmax.bit_length())
+    for n in range(S, g.N):
+        assert (r.get(h["nb"]), r.get(h["nb"]), r.get(h["wbits"]), r.get(h["wbits"])) == \
+            (g.p[n], g.q[n], g.a[n], g.b[n])
+    total += (g.N - S) * 2 * (h["nb"] + h["wbits"])
+    assert r.pos == total and len(data) == ((total + 7) // 8 + 7) // 8 * 8
+    assert int.from_bytes(data, "little") >> total == 0    # zero padding
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.3 (Eq. 10-13), Sec. 3.7: greedy factorisation and the quantiser
+# ---------------------------------------------------------------------------
+def test_greedy_hand_worked_phi1():
+    """Mixtures A = {1:1, 2:1, 3:2}, B = {1:1, 2:1}, C = {2:1, 3:1}.  phi_1:
+    (1,2) and (2,3) occur in two mixtures each -> the smaller (1,2) first, and
+    both occurrences give the same 1:1 lerp n4; then (2,3) and (3,n4) tie at
+    one -> (2,3) (n5), then (3,n4) (n6, 2:2)."""
+    g, roots, picks = oracle.greedy_lists([[(1, 1), (2, 1), (3, 2)], [(1, 1), (2, 1)], [(2, 1), (3, 1)]], 4,
+                                          "occurrence", tau=1, bitrate=0)
+    assert picks.tolist() == [[1, 2], [2, 3], [3, 4]]
+    assert g.N == 7 and g.D == 2
+    assert list(zip(g.p[4:7], g.q[4:7], g.a[4:7], g.b[4:7])) == [(1, 2, 1, 1), (2, 3, 1, 1), (3, 4, 1, 1)]
+    assert roots.tolist() == [6, 4, 5]
+
+
+def test_greedy_strategies_differ():
+    """Two mixtures of five components and three of the pair {1, 2}: phi_1
+    counts (1,2) three times against two for any pair of the large ones;
+    phi_2 weighs each large mixture |h| - 1 = 4 (8 per pair) against 2 per
+    small one (6): max-occurrence picks (1,2), max-reduction (3,4)."""
+    big = [(i, 1) for i in range(3, 8)]
+    lists = [big, big, [(1, 1), (2, 1)], [(1, 1), (2, 1)], [(1, 1), (2, 1)]]
+    _, _, p1 = oracle.greedy_lists(lists, 8, "occurrence", tau=1)
+    _, _, p2 = oracle.greedy_lists(lists, 8, "reduction", tau=1)
+    assert p1[0].tolist() == [1, 2] and p2[0].tolist() == [3, 4]
+
+
+def test_greedy_tau_skips_small_mixtures():
+    vol = synth.make_volume(1, dims=(20, 17, 13), S=12)
+    g, _, _, picks = oracle.greedy(vol, 12, "reduction", tau=64, bitrate=0)
+    assert len(picks) == 0                       # nothing has more than 64 components
+    g3, _, _, picks3 = oracle.greedy(vol, 12, "reduction", tau=3, bitrate=0)
+    assert len(picks3) > 0
+
+
+@pytest.mark.parametrize("strategy", ["occurrence", "reduction"])
+def test_greedy_exact_mode_expands_to_every_mixture(strategy):
+    """Without the quantiser every voxel's node expands exactly to its Eq. 4
+    mixture, whatever the pick order."""
+    dims = (21, 14, 11)
+    vol = synth.make_volume(2, dims=dims, S=15)
+    g, _, _, picks = oracle.greedy(vol, 15, strategy, tau=3, bitrate=0)
+    assert len(picks) > 0
+    for l in range(1, g.L):
+        off, ids, cnt = oracle.mixtures(vol, l)
+        mip = g.mip(l).ravel()
+        for v in range(len(mip)):
+            total = int(cnt[off[v]:off[v + 1]].sum())
+            e = oracle.expand(g.p, g.q, g.a, g.b, 15, int(mip[v]), total)
+            want = np.zeros(15, np.uint64)
+            want[ids[off[v]:off[v + 1]]] = cnt[off[v]:off[v + 1]]
+            assert np.array_equal(e, want), (l, v)
+
+
+@pytest.mark.parametrize("bitrate", [3, 6, 9])
+def test_greedy_quantiser_error_bound(bitrate):
+    """Each lerp's weight is off by at most half a bin (2^-(b+1)); pushing a
+    unit of mass through a tree moves at most twice that per level, so every
+    reconstructed mixture is within D * 2^-b of Eq. 4 in l1, and still sums
+    to 1.  Codewords are the bin centres; sigma lies within half a bin."""
+    dims = (24, 20, 16)
+    vol = synth.make_volume(1, dims=dims, S=20)
+    g, cb, sg, _ = oracle.greedy(vol, 20, "reduction", tau=3, bitrate=bitrate)
+    nb = 1 << bitrate
+    assert np.allclose(cb, (2 * np.arange(nb) + 1) / (2.0 * nb))
+    assert (sg >= 0).all() and (sg <= 0.5 / nb + 1e-12).all() and (sg > 0).any()
+    assert (g.a[20:g.N] < nb).all() and (g.b[20:g.N] == 0).all()
+    worst = 0.0
+    for l in range(1, g.L):
+        off, ids, cnt = oracle.mixtures(vol, l)
+        mip = g.mip(l).ravel()
+        for v in range(0, len(mip), 7):
+            rec = oracle.quantised_mixture(g, cb, int(mip[v]))
+            h = np.zeros(20)
+            c = cnt[off[v]:off[v + 1]].astype(np.float64)
+            h[ids[off[v]:off[v + 1]]] = c / c.sum()
+            assert abs(rec.sum() - 1.0) < 1e-12
+            worst = max(worst, np.abs(rec - h).sum())
+    assert worst <= g.D * 2.0 ** -bitrate
+
+
+def test_greedy_coarser_bins_reuse_more():
+    vol = synth.make_volume(1, dims=(32, 32, 32), S=24)
+    n = [oracle.greedy(vol, 24, "reduction", tau=3, bitrate=b)[0].N for b in (3, 9, 0)]
+    assert n[0] <= n[1] <= n[2]
