@@ -557,6 +557,63 @@ MG_API mg_status mg_bitstream_decode_nodes(const void *stream_dev, const mg_bits
 MG_API mg_status mg_bitstream_lookup(const void *stream_dev, const mg_bitstream_info *info, const void *vals, int C,
                                      mg_dtype dtype, const float *samples, int64_t P, void *out, mg_stream stream);
 
+/*
+ * Greedy factorisation (Sec. 3.3, Eq. 10-13; Sec. 3.7): the paper's encoder,
+ * on the GPU.  H is every mixture of levels 1..L-1 (Eq. 4, integer weights
+ * 8^l H).  Stage 1 repeats rounds: every pair i < j of components that occur
+ * together in a mixture with more than tau components is scored -- phi_1
+ * (max-occurrence) adds 1 per mixture, phi_2 (max-reduction) adds |h| - 1
+ * if |h| > 2, else 2 -- the highest score wins (ties to the smallest (i,
+ * j)) and every such mixture holding both has i and j replaced by their
+ * lerp with the summed weight.  Stage 2 runs in waves: every mixture left
+ * with two or more components lerps its two lowest-numbered ones.  A lerp of
+ * p < q with weights c_p, c_q is the node (p, q, a, b) of the reduced ratio
+ * a:b = c_p:c_q (bitrate 0: exact), or (p, q, k, 0) with k = floor(c_q 2^b /
+ * (c_p + c_q)) (a b-bit scalar quantiser of equal bins over (0, 1); the
+ * codeword of bin k is its centre (2k + 1) / 2^(b+1), its sigma the rms of
+ * the weights' distance to it; lerps of one pair in one bin are one node).
+ * New nodes are numbered in creation order, a round's or wave's in the scan
+ * order of the first mixture making them; the result is renumbered as
+ * mg_build's graph (level, p, q, a, b).
+ * ids: device, as for mg_build (opts->id_bytes; NULL: uint16).  Synchronises
+ * `stream` once per round and wave; device memory from cudaMallocAsync.  The
+ * result lives in host memory until mg_greedy_free.
+ * MG_ERR_UNSUPPORTED when the pair table would exceed 2^30 entries.
+ */
+typedef struct mg_greedy mg_greedy;   /* opaque */
+typedef struct {
+    int strategy;      /* 1: phi_1 max-occurrence; 2: phi_2 max-reduction */
+    int tau;           /* stage-1 cutoff, >= 1 (the paper uses 3) */
+    int bitrate;       /* 0: exact ratios; 1..16: quantiser bits */
+    int reserved[5];   /* zero */
+} mg_greedy_opts;
+typedef struct {
+    uint32_t num_segments;
+    int levels;
+    int depth;
+    int reserved0;
+    int64_t num_nodes;     /* N, sources included */
+    int64_t picks;         /* stage-1 rounds */
+    int64_t waves;         /* stage-2 waves */
+    double ms;             /* wall time of mg_factor_greedy */
+} mg_greedy_info;
+
+MG_API mg_status mg_factor_greedy(const void *ids, int64_t nx, int64_t ny, int64_t nz, uint32_t num_segments,
+                                  const mg_build_opts *opts, const mg_greedy_opts *gopts, mg_stream stream,
+                                  mg_greedy **out);
+MG_API mg_status mg_greedy_info_get(const mg_greedy *r, mg_greedy_info *info);
+/* host buffers of N entries (any may be NULL): p, q predecessors (MG_NO_NODE
+ * for sources); a, b the exact coprime weights, or for a quantised graph the
+ * bin in a and 0 in b */
+MG_API mg_status mg_greedy_copy_nodes(const mg_greedy *r, uint32_t *p, uint32_t *q, uint64_t *a, uint64_t *b);
+/* host buffer of dims[level] node IDs, x fastest */
+MG_API mg_status mg_greedy_copy_mip(const mg_greedy *r, int level, uint32_t *dst);
+/* host buffer of 2 * picks uint32: the stage-1 picks (i, j) in creation numbering */
+MG_API mg_status mg_greedy_copy_picks(const mg_greedy *r, uint32_t *picks);
+/* host buffers of 2^bitrate doubles (quantised graphs) */
+MG_API mg_status mg_greedy_copy_codebook(const mg_greedy *r, double *codebook, double *sigma);
+MG_API void mg_greedy_free(mg_greedy *r);
+
 /* Self-test of failure handling: one GPU thread waits, with the same bounded
  * wait the single-pass propagation uses between topological levels (Sec. 3.4),
  * on a device flag that is already set (satisfied = 1: returns MG_OK) or that

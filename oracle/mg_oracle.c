@@ -1145,9 +1145,12 @@ int64_t mgo_bitstream(const mgo_graph *g, uint8_t *out, int64_t cap)
 /*      highest score, ties to the smallest (i, j); every such mixture that */
 /*      holds both is factored (all occurrences).  Stage 1 ends when no      */
 /*      mixture has more than tau components.                               */
-/*   G3 stage 2: every mixture left with 2..tau components, levels in order */
-/*      and voxels x fastest, lerps its two lowest-numbered components until */
-/*      one remains.                                                         */
+/*   G3 stage 2: the mixtures left with 2..tau components are factorised in */
+/*      waves: in each, every such mixture, levels in order and voxels x     */
+/*      fastest, lerps its two lowest-numbered components.  Nodes are        */
+/*      numbered in order of creation, so a wave's new nodes follow the scan */
+/*      position of the first mixture that made them (as a parallel build   */
+/*      numbers them).                                                       */
 /*   G4 a lerp of components p < q with weights c_p, c_q gives q the weight */
 /*      w = c_q / (c_p + c_q).  bitrate b >= 1: w falls in bin k = floor(w   */
 /*      2^b) of the 2^b equal bins of (0, 1), decided exactly in integers;   */
@@ -1284,14 +1287,18 @@ static void gr_run(gr_lists *x, mgo_table *t, int strategy, int tau, int bitrate
     }
     free(pairs); free(hslot);
 
-    /* stage 2: the rest in scanline order, the two lowest components first */
-    for (int64_t m = 0; m < M; m++) {
-        while (x->len[m] > 1) {
+    /* stage 2: waves over the rest in scanline order, each mixture lerping
+     * its two lowest components per wave */
+    for (int any = 1; any;) {
+        any = 0;
+        for (int64_t m = 0; m < M; m++) {
+            if (x->len[m] < 2) continue;
             const uint32_t *c = x->comp + x->off[m];
             uint32_t p = c[0], q = c[1];
             uint64_t cp = x->wt[x->off[m]], cq = x->wt[x->off[m] + 1];
             int64_t nd = gr_node(t, p, cp, q, cq, bitrate, ssq, cnt);
             gr_merge(x, m, 0, 1, (uint32_t)nd, cp + cq);
+            any = 1;
         }
     }
 

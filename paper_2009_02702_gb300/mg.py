@@ -40,6 +40,8 @@ EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_cop
            "mg_query_set_tuning", "mg_count_cubes", "mg_render_lookup", "mg_propagate_tf_multi",
            "mg_render_lookup_multi", "mg_raymarch", "mg_bitstream_size", "mg_bitstream_write", "mg_bitstream_parse",
            "mg_bitstream_decode_mip", "mg_bitstream_decode_nodes", "mg_bitstream_lookup",
+           "mg_factor_greedy", "mg_greedy_info_get", "mg_greedy_copy_nodes", "mg_greedy_copy_mip",
+           "mg_greedy_copy_picks", "mg_greedy_copy_codebook", "mg_greedy_free",
            "mg_server_create", "mg_server_add_volume", "mg_server_start", "mg_server_submit", "mg_server_cancel",
            "mg_server_wait", "mg_server_replay", "mg_server_stats_get", "mg_server_free",
            "mg_graph_export_size", "mg_graph_export", "mg_graph_import",
@@ -106,6 +108,17 @@ class mg_bitstream_info(ctypes.Structure):
                 ("node_bit", ctypes.c_int64), ("header_bits", ctypes.c_int64), ("bytes", ctypes.c_int64)]
 
 
+class mg_greedy_opts(ctypes.Structure):
+    _fields_ = [("strategy", ctypes.c_int), ("tau", ctypes.c_int), ("bitrate", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
+class mg_greedy_info(ctypes.Structure):
+    _fields_ = [("num_segments", ctypes.c_uint32), ("levels", ctypes.c_int), ("depth", ctypes.c_int),
+                ("reserved0", ctypes.c_int), ("num_nodes", ctypes.c_int64), ("picks", ctypes.c_int64),
+                ("waves", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
 class mg_server_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("max_batch", ctypes.c_int), ("hist_type", ctypes.c_int),
                 ("storage", ctypes.c_int), ("max_samples", ctypes.c_int64), ("memory_budget", ctypes.c_int64),
@@ -153,6 +166,18 @@ def lib():
         L.mg_render_lookup_multi.argtypes = [P, P, i32, i32, i32, P, P, P, P]
         L.mg_render_lookup_multi.restype = st
         L.mg_raymarch.argtypes = [P, P, P, ctypes.POINTER(mg_camera), P, P, P]
+        L.mg_factor_greedy.argtypes = [P, i64, i64, i64, ctypes.c_uint32, ctypes.POINTER(mg_build_opts),
+                                       ctypes.POINTER(mg_greedy_opts), P, ctypes.POINTER(P)]
+        L.mg_greedy_info_get.argtypes = [P, ctypes.POINTER(mg_greedy_info)]
+        L.mg_greedy_copy_nodes.argtypes = [P, P, P, P, P]
+        L.mg_greedy_copy_mip.argtypes = [P, i32, P]
+        L.mg_greedy_copy_picks.argtypes = [P, P]
+        L.mg_greedy_copy_codebook.argtypes = [P, P, P]
+        for f in ("mg_factor_greedy", "mg_greedy_info_get", "mg_greedy_copy_nodes", "mg_greedy_copy_mip",
+                  "mg_greedy_copy_picks", "mg_greedy_copy_codebook"):
+            getattr(L, f).restype = st
+        L.mg_greedy_free.argtypes = [P]
+        L.mg_greedy_free.restype = None
         L.mg_bitstream_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
         L.mg_bitstream_write.argtypes = [P, P, ctypes.c_size_t, P]
         L.mg_bitstream_parse.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(mg_bitstream_info)]
@@ -672,6 +697,52 @@ def mg_bitstream_write(g: Graph, stream=None) -> Bitstream:
     data = torch.empty(n.value, dtype=torch.uint8, device=torch.device("cuda", g.device))
     _check(lib().mg_bitstream_write(g.handle, data.data_ptr(), n.value, _stream(stream)))
     return Bitstream(data)
+
+
+_STRATEGY = {"occurrence": 1, "reduction": 2}
+
+
+def mg_factor_greedy(ids: torch.Tensor, num_segments: int, strategy: str = "reduction", tau: int = 3,
+                     bitrate: int = 9, stream=None) -> dict:
+    """Greedy factorisation (phi_1 'occurrence' or phi_2 'reduction') of a
+    (nz, ny, nx) uint16/uint32 CUDA volume on the GPU.  Returns a dict with
+    the node table (p, q, a, b numpy), the mip IDs of every level, the
+    stage-1 picks, the codebook and sigma (bitrate > 0) and the counts."""
+    import numpy as np
+    if not ids.is_cuda or ids.dim() != 3:
+        raise ValueError("ids must be a 3-D CUDA tensor (z, y, x)")
+    ids = ids.contiguous()
+    nb = 2 if ids.dtype == torch.uint16 else 4
+    nz, ny, nx = ids.shape
+    o = mg_greedy_opts(_STRATEGY[strategy], tau, bitrate)
+    h = ctypes.c_void_p()
+    with torch.cuda.device(ids.device):
+        _check(lib().mg_factor_greedy(ids.data_ptr(), nx, ny, nz, num_segments, ctypes.byref(mg_build_opts(nb)),
+                                      ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+    try:
+        info = mg_greedy_info()
+        _check(lib().mg_greedy_info_get(h, ctypes.byref(info)))
+        N, L = info.num_nodes, info.levels
+        p = np.zeros(N, np.uint32); q = np.zeros(N, np.uint32)
+        a = np.zeros(N, np.uint64); b = np.zeros(N, np.uint64)
+        _check(lib().mg_greedy_copy_nodes(h, p.ctypes.data, q.ctypes.data, a.ctypes.data, b.ctypes.data))
+        dims, mips = [], []
+        d = [nx, ny, nz]
+        for l in range(L):
+            out = np.zeros((d[2], d[1], d[0]), np.uint32)
+            _check(lib().mg_greedy_copy_mip(h, l, out.ctypes.data))
+            mips.append(out)
+            dims.append(tuple(d))
+            d = [(v + 1) // 2 for v in d]
+        picks = np.zeros((max(info.picks, 1), 2), np.uint32)
+        _check(lib().mg_greedy_copy_picks(h, picks.ctypes.data))
+        nbins = (1 << bitrate) if bitrate else 1
+        cb = np.zeros(nbins); sg = np.zeros(nbins)
+        _check(lib().mg_greedy_copy_codebook(h, cb.ctypes.data, sg.ctypes.data))
+        return dict(N=N, D=info.depth, L=L, p=p, q=q, a=a, b=b, mip=mips, dims=dims,
+                    picks=picks[:info.picks], codebook=cb, sigma=sg, waves=info.waves, ms=info.ms)
+    finally:
+        lib().mg_greedy_free(h)
 
 
 def mg_sync_status(g: Graph, stream=None):

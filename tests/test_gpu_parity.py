@@ -393,3 +393,27 @@ def test_bitstream_matches_oracle_and_decodes(mg, dims, S):
         smp = torch.from_numpy(synth.make_samples(1, dims=dims, width=64, height=40)).to(dev())
         assert torch.equal(bs.lookup(vals, smp).cpu(), mg.mg_render_lookup(g, vals, smp).cpu())
     g.close()
+
+
+# greedy factorisation (Sec. 3.3, Sec. 3.7): integer decisions throughout, so
+# the GPU graph equals the oracle's bit for bit; sigma is an fp64 sum
+@pytest.mark.parametrize("strategy,tau,bitrate,cfg,dims,S", [
+    ("reduction", 3, 9, 1, (24, 20, 16), 20),
+    ("occurrence", 3, 9, 1, (24, 20, 16), 20),
+    ("reduction", 3, 0, 2, (21, 14, 11), 15),
+    ("reduction", 1, 5, 3, (33, 17, 9), 12),
+    ("occurrence", 2, 16, 1, (32, 32, 32), 24),
+])
+def test_greedy_matches_oracle(mg, strategy, tau, bitrate, cfg, dims, S):
+    vol = synth.make_volume(cfg, dims=dims, S=S)
+    r = mg.mg_factor_greedy(torch.from_numpy(vol).to(dev()), S, strategy=strategy, tau=tau, bitrate=bitrate)
+    og, cb, sg, picks = oracle.greedy(vol, S, strategy, tau=tau, bitrate=bitrate)
+    assert r["N"] == og.N and r["D"] == og.D and r["L"] == og.L
+    assert np.array_equal(r["picks"], picks)
+    for k in "pqab":
+        assert np.array_equal(r[k], getattr(og, k)[:og.N]), k
+    for l in range(og.L):
+        assert np.array_equal(r["mip"][l], og.mip(l)), l
+    if bitrate:
+        assert np.array_equal(r["codebook"], cb)
+        assert np.allclose(r["sigma"], sg, rtol=1e-9, atol=1e-15)
