@@ -614,6 +614,43 @@ MG_API mg_status mg_greedy_copy_picks(const mg_greedy *r, uint32_t *picks);
 MG_API mg_status mg_greedy_copy_codebook(const mg_greedy *r, double *codebook, double *sigma);
 MG_API void mg_greedy_free(mg_greedy *r);
 
+/* A graph from a quantised greedy result (bitrate >= 1), on the current
+ * device (memory from `allocator`, NULL = cudaMallocAsync): node weights are
+ * the codewords of their bins, so propagation, lookups, ray marching, fp32
+ * box queries and the mixture table below work on it as on mg_build's
+ * graphs; exact-count queries (MG_HIST_U32) return MG_ERR_UNSUPPORTED, as
+ * do the bitstream and the export.  Synchronises `stream`.  The result may be
+ * freed afterwards. */
+MG_API mg_status mg_graph_from_greedy(const mg_greedy *r, const mg_allocator *allocator, mg_stream stream,
+                                      mg_graph **out);
+
+/*
+ * The mixture lookup table with uncertainties (Sec. 3.5, Eq. 16-17; Sec. 3.6).
+ * Row n lists the sources under node n (ascending) with mu, their share of
+ * n's mixture, and dmu, its uncertainty: for n the lerp of p and q with
+ * weight w of q and uncertainty dw,
+ *   mu_i(n) = (1 - w) mu_i(p) + w mu_i(q),
+ *   dmu_i(n)^2 = mu_i(n)^2 ((dmu_i(p)/mu_i(p))^2 + (dmu_i(q)/mu_i(q))^2
+ *                + 2 (dw/w)^2)   (Eq. 17),
+ * a ratio term being 0 for a component absent from that input; sources have
+ * mu = 1, dmu = 0.  w = b/(a+b) and dw = 0 for exact graphs; the bin's
+ * codeword and sigma for quantised ones.  fp64.
+ * mg_error_table_build: builds the table once (synchronises); *entries (may
+ *   be NULL) = its entries.  MG_ERR_UNSUPPORTED above 2^31 entries.
+ * mg_error_table_copy: the table into host or device buffers (any NULL):
+ *   off[N+1] (int64), src/mu/dmu[entries]; unused slack entries (none for
+ *   graphs whose lerps join disjoint sources) hold source 2^32 - 1.
+ * mg_query_lut: box histograms summed from the table (the paper's query,
+ *   Sec. 3.6): hist[q][s] = sum over the box's footprint cubes c (Algorithm
+ *   1) of 8^l mu_s(node_c); err[q][s] = sqrt(sum_c (8^l dmu_s(node_c))^2)
+ *   (Eq. 16), the error bar.  Boxes as for mg_query_boxes; hist and err
+ *   (may be NULL) Q x S fp64, device.  One CTA per box; S <= 12800.
+ */
+MG_API mg_status mg_error_table_build(mg_graph *g, int64_t *entries, mg_stream stream);
+MG_API mg_status mg_error_table_copy(const mg_graph *g, int64_t *off, uint32_t *src, double *mu, double *dmu);
+MG_API mg_status mg_query_lut(const mg_graph *g, const int32_t *boxes, int64_t Q, double *hist, double *err,
+                              mg_stream stream);
+
 /* Self-test of failure handling: one GPU thread waits, with the same bounded
  * wait the single-pass propagation uses between topological levels (Sec. 3.4),
  * on a device flag that is already set (satisfied = 1: returns MG_OK) or that

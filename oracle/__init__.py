@@ -20,6 +20,9 @@ Functions whose results are pinned by tests other than self-comparison:
                     reproduction of a linear field; skipping changes nothing
   bitstream         read back by an independent reader of Table 1's layout;
                     section sizes from Eq. 15
+  error_rows        a lerp's closed form (Eq. 17); rows equal the tree pushes;
+                    zero uncertainty for exact weights
+  lut_query         equals box_hist for exact graphs; error bars by Eq. 16
   greedy            hand-worked picks (phi_1 and phi_2 differ); exact mode
                     expands to every mixture; quantisation error within its
                     bound; codewords and sigma by definition
@@ -111,6 +114,9 @@ def _load():
         lib.mgo_greedy_lists.argtypes = [P, P, P, i64, ctypes.c_uint32, i32, i32, i32, P, P, i64, P]
         lib.mgo_greedy_lists.restype = P
         lib.mgo_quantised_mixture.argtypes = [P, P, ctypes.c_uint32, P]
+        lib.mgo_error_rows.argtypes = [P, P, P, P, i64, ctypes.c_uint32, P, P, P, P]
+        lib.mgo_error_rows.restype = i32
+        lib.mgo_lut_query.argtypes = [P, P, P, P, P, P, i64, P, P]
         lib.mgo_bitstream.argtypes = [P, P, i64]
         lib.mgo_bitstream.restype = i64
         lib.mgo_set_threads.argtypes = [i32]
@@ -356,6 +362,50 @@ def quantised_mixture(g, codebook: np.ndarray, node: int) -> np.ndarray:
     out = np.zeros(g.S, np.float64)
     _load().mgo_quantised_mixture(g._h, _ptr(cb), int(node), _ptr(out))
     return out
+
+
+def node_weights(g, codebook=None, sigma=None):
+    """(w, dw) of every node (Sec. 3.5): the weight of q and its uncertainty;
+    exact graphs b/(a+b) and 0, quantised graphs their bin's codeword and
+    sigma.  Sources get 0, 0."""
+    N, S = g.N, g.S
+    w = np.zeros(N, np.float64)
+    dw = np.zeros(N, np.float64)
+    if codebook is None:
+        a = g.a[S:N].astype(np.float64); b = g.b[S:N].astype(np.float64)
+        w[S:] = b / (a + b)
+    else:
+        k = g.a[S:N].astype(np.int64)
+        w[S:] = np.asarray(codebook, np.float64)[k]
+        dw[S:] = np.asarray(sigma, np.float64)[k]
+    return w, dw
+
+
+def error_rows(g, w, dw):
+    """Every node's mixture with its Eq. 17 uncertainty: (off (N+1,), src,
+    mu, dmu); row n is [off[n], off[n+1]), sources ascending (unused slack
+    entries hold source 2^32 - 1)."""
+    P_, Q_ = np.ascontiguousarray(g.p[:g.N]), np.ascontiguousarray(g.q[:g.N])
+    w = np.ascontiguousarray(w, np.float64); dw = np.ascontiguousarray(dw, np.float64)
+    off = np.zeros(g.N + 1, np.int64)
+    lib = _load()
+    if lib.mgo_error_rows(_ptr(P_), _ptr(Q_), _ptr(w), _ptr(dw), g.N, g.S, _ptr(off), None, None, None):
+        raise ValueError("malformed node table")
+    E = int(off[-1])
+    src = np.zeros(max(E, 1), np.uint32); mu = np.zeros(max(E, 1)); dmu = np.zeros(max(E, 1))
+    lib.mgo_error_rows(_ptr(P_), _ptr(Q_), _ptr(w), _ptr(dw), g.N, g.S, _ptr(off), _ptr(src), _ptr(mu), _ptr(dmu))
+    return off, src[:E], mu[:E], dmu[:E]
+
+
+def lut_query(g, rows, boxes):
+    """Box histograms summed from the mixture table (Sec. 3.6) and their
+    error bars (Sec. 3.5): ((Q, S) expected counts, (Q, S) error bars)."""
+    off, src, mu, dmu = (np.ascontiguousarray(x) for x in rows)
+    boxes = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 6)
+    hist = np.zeros((boxes.shape[0], g.S)); err = np.zeros((boxes.shape[0], g.S))
+    _load().mgo_lut_query(g._h, _ptr(off), _ptr(src), _ptr(mu), _ptr(dmu), _ptr(boxes), boxes.shape[0], _ptr(hist),
+                          _ptr(err))
+    return hist, err
 
 
 def depths(p, q, S: int) -> np.ndarray:

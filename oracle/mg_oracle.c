@@ -1470,3 +1470,83 @@ mgo_graph *mgo_greedy_lists(const uint64_t *off, const uint32_t *ids, const uint
     table_free(&t);
     return g;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.5 (Eq. 16-17) and Sec. 3.6: every node's mixture with its          */
+/* uncertainty (the mixture lookup table), and box histograms summed from   */
+/* it with error bars.                                                       */
+/*                                                                          */
+/* Readings taken here:                                                      */
+/*   E1 node n's weight w_n is that of q (b/(a+b) exact, or the codeword of  */
+/*      its bin), its uncertainty dw_n (0 exact, or the bin's sigma).        */
+/*   E2 Eq. 17 per component i: mu_i(n) = (1 - w) mu_i(p) + w mu_i(q) and    */
+/*      dmu_i(n)^2 = mu_i(n)^2 ((dmu_i(p)/mu_i(p))^2 + (dmu_i(q)/mu_i(q))^2  */
+/*      + 2 (dw/w)^2), a ratio term being 0 when the component is absent     */
+/*      from that input.  Sources: mu = e_s, dmu = 0.                        */
+/*   E3 a box's histogram from the table: h_s = sum over its footprint       */
+/*      cubes c (Algorithm 1) of W_c mu_s(node_c), W_c = 8^l; the error bar  */
+/*      dh_s = sqrt(sum_c (W_c dmu_s(node_c))^2) (Eq. 16, independent sums). */
+/* ------------------------------------------------------------------------ */
+/* Rows of every node, sources ascending.  With src == NULL only off (N + 1)
+ * is filled (sizes); returns 0, or -1 on a malformed table. */
+int mgo_error_rows(const uint32_t *p, const uint32_t *q, const double *w, const double *dw, int64_t N, uint32_t S,
+                   int64_t *off, uint32_t *src, double *mu, double *dmu)
+{
+    off[0] = 0;
+    for (int64_t n = 0; n < N; n++) {
+        if (n < S) { off[n + 1] = off[n] + 1; continue; }
+        if (p[n] >= n || q[n] >= n) return -1;
+        /* an upper bound (disjoint sources give exactly the sum) */
+        off[n + 1] = off[n] + (off[p[n] + 1] - off[p[n]]) + (off[q[n] + 1] - off[q[n]]);
+    }
+    if (!src) return 0;
+    for (int64_t n = 0; n < N; n++) {
+        int64_t o = off[n];
+        if (n < S) { src[o] = (uint32_t)n; mu[o] = 1.0; dmu[o] = 0.0; continue; }
+        int64_t a = off[p[n]], ae = off[p[n] + 1], b = off[q[n]], be = off[q[n] + 1];
+        double wq = w[n], wp = 1.0 - w[n];
+        double rw = wq > 0 ? dw[n] / wq : 0.0;
+        int64_t k = o;
+        while (a < ae || b < be) {
+            int from_a = b >= be || (a < ae && src[a] <= src[b]);
+            int from_b = a >= ae || (b < be && src[b] <= src[a]);
+            uint32_t s = from_a ? src[a] : src[b];
+            double m = 0.0, r2 = 2.0 * rw * rw;
+            if (from_a) { m += wp * mu[a]; if (mu[a] > 0) r2 += (dmu[a] / mu[a]) * (dmu[a] / mu[a]); a++; }
+            if (from_b) { m += wq * mu[b]; if (mu[b] > 0) r2 += (dmu[b] / mu[b]) * (dmu[b] / mu[b]); b++; }
+            src[k] = s; mu[k] = m; dmu[k] = sqrt(m * m * r2);
+            k++;
+        }
+        for (; k < off[n + 1]; k++) { src[k] = 0xFFFFFFFFu; mu[k] = 0.0; dmu[k] = 0.0; }   /* unused slack */
+    }
+    return 0;
+}
+
+/* hist, err: Q x S (err may be NULL) */
+void mgo_lut_query(const mgo_graph *g, const int64_t *off, const uint32_t *src, const double *mu, const double *dmu,
+                   const int32_t *boxes, int64_t Q, double *hist, double *err)
+{
+    const int64_t nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < Q; i++) {
+        double *h = hist + i * (int64_t)g->S, *e = err ? err + i * (int64_t)g->S : NULL;
+        for (uint32_t s = 0; s < g->S; s++) { h[s] = 0.0; if (e) e[s] = 0.0; }
+        int64_t n = mgo_fa_cubes(boxes + 6 * i, nx, ny, nz, NULL, 0);
+        if (n <= 0) continue;
+        int32_t *cubes = (int32_t *)malloc((size_t)n * 4 * sizeof(int32_t));
+        mgo_fa_cubes(boxes + 6 * i, nx, ny, nz, cubes, n);
+        for (int64_t c = 0; c < n; c++) {
+            int l = cubes[4 * c];
+            const int64_t *d = g->dims + 3 * l;
+            uint32_t node = g->mip[l][((int64_t)cubes[4 * c + 3] * d[1] + cubes[4 * c + 2]) * d[0] + cubes[4 * c + 1]];
+            double W = ldexp(1.0, 3 * l);
+            for (int64_t k = off[node]; k < off[node + 1]; k++) {
+                if (src[k] == 0xFFFFFFFFu) continue;
+                h[src[k]] += W * mu[k];
+                if (e) e[src[k]] += (W * dmu[k]) * (W * dmu[k]);
+            }
+        }
+        if (e) for (uint32_t s = 0; s < g->S; s++) e[s] = sqrt(e[s]);
+        free(cubes);
+    }
+}

@@ -147,7 +147,8 @@ mg_status sync_status(mg_graph* g, cudaStream_t s) {
 int64_t mg_graph::device_bytes() const {
     return (int64_t)(mip0.bytes + mip.bytes + mip0x[0].bytes + mip0x[1].bytes + mip0x[2].bytes + mipx[0].bytes +
                      mipx[1].bytes + mipx[2].bytes + pq.bytes + ab.bytes + ab32.bytes + alpha.bytes + alpha16.bytes +
-                     alphab16.bytes + status.bytes + lut_meta.bytes + lut.bytes);
+                     alphab16.bytes + status.bytes + lut_meta.bytes + lut.bytes + wq.bytes + dw.bytes +
+                     err_off.bytes + err_src.bytes + err_mu.bytes + err_dmu.bytes);
 }
 
 using namespace mg;
@@ -324,6 +325,8 @@ MG_API mg_status mg_query_boxes(const mg_graph* g, const int32_t* boxes, int64_t
         return fail(MG_ERR_INVALID_ARG, "alpha_dtype must be MG_F32, MG_F16 or MG_BF16");
     if (o.hist_type == MG_HIST_U32 && o.alpha_dtype != MG_F32)
         return fail(MG_ERR_INVALID_ARG, "16-bit weights apply to the fp32 push only");
+    if (g->quantised && o.hist_type == MG_HIST_U32)
+        return fail(MG_ERR_UNSUPPORTED, "a quantised graph has no exact weights: use MG_HIST_F32");
     if (o.schedule != MG_SCHED_BATCHED && o.schedule != MG_SCHED_PLAIN && o.schedule != MG_SCHED_NAIVE)
         return fail(MG_ERR_INVALID_ARG, "schedule must be MG_SCHED_BATCHED, MG_SCHED_PLAIN or MG_SCHED_NAIVE");
     if (o.chunk_cubes < 0 || o.block_threads < 0) return fail(MG_ERR_INVALID_ARG, "negative tuning option");

@@ -370,6 +370,7 @@ extern "C" {
 MG_API mg_status mg_bitstream_size(const mg_graph* g, size_t* bytes) {
     MG_RANGE("mg_bitstream_size");
     if (!g || !bytes) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    if (g->quantised) return fail(MG_ERR_UNSUPPORTED, "the stream holds exact weights; this graph is quantised");
     DeviceGuard dg(g->device);
     Layout Y;
     MG_TRY(layout_of(g, Y, nullptr));
@@ -381,6 +382,7 @@ MG_API mg_status mg_bitstream_write(const mg_graph* g, void* dst, size_t bytes, 
     MG_RANGE("mg_bitstream_write");
     if (!g || !dst) return fail(MG_ERR_INVALID_ARG, "NULL argument");
     if (reinterpret_cast<uintptr_t>(dst) % 8) return fail(MG_ERR_INVALID_ARG, "dst must be 8-byte aligned");
+    if (g->quantised) return fail(MG_ERR_UNSUPPORTED, "the stream holds exact weights; this graph is quantised");
     DeviceGuard dg(g->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Layout Y;

@@ -830,3 +830,95 @@ MG_API mg_status mg_greedy_copy_codebook(const mg_greedy* r, double* codebook, d
 MG_API void mg_greedy_free(mg_greedy* r) { delete r; }
 
 }  // extern "C"
+
+extern "C" MG_API mg_status mg_graph_from_greedy(const mg_greedy* r, const mg_allocator* allocator, mg_stream stream,
+                                                mg_graph** out) {
+    MG_RANGE("mg_graph_from_greedy");
+    using namespace mg;
+    if (!r || !out) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (r->codebook.empty()) return fail(MG_ERR_INVALID_ARG, "an exact greedy result: build with mg_build instead");
+    if (r->D + 1 > MG_MAX_DEPTH) return fail(MG_ERR_UNSUPPORTED, "graph deeper than MG_MAX_DEPTH");
+    std::unique_ptr<mg_graph> g(new (std::nothrow) mg_graph());
+    if (!g) return fail(MG_ERR_OOM, "host allocation failed");
+    if (allocator) {
+        if (!allocator->alloc || !allocator->free) return fail(MG_ERR_INVALID_ARG, "allocator needs alloc and free");
+        g->al.a = *allocator;
+        g->al.custom = true;
+    }
+    MG_CUDA(cudaGetDevice(&g->device));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t N = r->N;
+    const uint32_t S = r->S;
+    g->S = S;
+    g->N = N;
+    g->L = r->L;
+    g->D = r->D;
+    g->quantised = true;
+    g->geom.L = r->L;
+    int64_t hi = 0;
+    for (int l = 0; l < r->L; l++) {
+        for (int k = 0; k < 3; k++) g->geom.dims[l][k] = (int32_t)r->dims[l][k];
+        if (l >= 1) {
+            g->geom.off[l] = hi;
+            hi += (int64_t)r->mip[l].size();
+        }
+    }
+    // depth buckets of the canonical numbering
+    std::vector<int> depth((size_t)N, 0);
+    for (int64_t n = S; n < N; n++) depth[n] = std::max(depth[r->p[n]], depth[r->q[n]]) + 1;
+    g->bucket[0] = 0;
+    for (int d = 0; d <= r->D; d++) {
+        int64_t c = 0;
+        for (int64_t n = 0; n < N; n++) c += depth[n] == d;
+        g->bucket[d + 1] = g->bucket[d] + c;
+    }
+    g->id0_bytes = S <= 65536u ? 2 : 4;
+    const size_t V0 = r->mip[0].size();
+    MG_TRY(g->mip0.alloc(&g->al, V0 * g->id0_bytes, s));
+    if (g->id0_bytes == 2) {
+        std::vector<uint16_t> v16(V0);
+        for (size_t i = 0; i < V0; i++) v16[i] = (uint16_t)r->mip[0][i];
+        MG_CUDA(cudaMemcpyAsync(g->mip0.p, v16.data(), V0 * 2, cudaMemcpyHostToDevice, s));
+        MG_CUDA(cudaStreamSynchronize(s));
+    } else {
+        MG_CUDA(cudaMemcpyAsync(g->mip0.p, r->mip[0].data(), V0 * 4, cudaMemcpyHostToDevice, s));
+    }
+    if (hi > 0) {
+        MG_TRY(g->mip.alloc(&g->al, (size_t)hi * 4, s));
+        for (int l = 1; l < r->L; l++)
+            MG_CUDA(cudaMemcpyAsync(g->mip.as<uint32_t>() + g->geom.off[l], r->mip[l].data(), r->mip[l].size() * 4,
+                                    cudaMemcpyHostToDevice, s));
+    }
+    std::vector<uint2> pq((size_t)N);
+    std::vector<float> alpha((size_t)N, 0.f);
+    std::vector<double> wq((size_t)N, 0.0), dw((size_t)N, 0.0);
+    for (int64_t n = 0; n < N; n++) {
+        pq[n] = make_uint2(r->p[n], r->q[n]);
+        if (n >= (int64_t)S) {
+            wq[n] = r->codebook[r->a[n]];
+            dw[n] = r->sigma[r->a[n]];
+            alpha[n] = (float)wq[n];
+        }
+    }
+    MG_TRY(g->pq.alloc(&g->al, (size_t)N * 8, s));
+    MG_TRY(g->ab.alloc(&g->al, (size_t)N * 16, s));
+    MG_TRY(g->ab32.alloc(&g->al, (size_t)N * 8, s));
+    MG_TRY(g->alpha.alloc(&g->al, (size_t)N * 4, s));
+    MG_TRY(g->wq.alloc(&g->al, (size_t)N * 8, s));
+    MG_TRY(g->dw.alloc(&g->al, (size_t)N * 8, s));
+    MG_TRY(g->status.alloc(&g->al, 4, s));
+    MG_CUDA(cudaMemcpyAsync(g->pq.p, pq.data(), (size_t)N * 8, cudaMemcpyHostToDevice, s));
+    MG_CUDA(cudaMemsetAsync(g->ab.p, 0, (size_t)N * 16, s));
+    MG_CUDA(cudaMemsetAsync(g->ab32.p, 0, (size_t)N * 8, s));
+    MG_CUDA(cudaMemcpyAsync(g->alpha.p, alpha.data(), (size_t)N * 4, cudaMemcpyHostToDevice, s));
+    MG_CUDA(cudaMemcpyAsync(g->wq.p, wq.data(), (size_t)N * 8, cudaMemcpyHostToDevice, s));
+    MG_CUDA(cudaMemcpyAsync(g->dw.p, dw.data(), (size_t)N * 8, cudaMemcpyHostToDevice, s));
+    MG_CUDA(cudaMemsetAsync(g->status.p, 0, 4, s));
+    MG_TRY(build_query_copies(g.get(), s));
+    MG_CUDA(cudaStreamSynchronize(s));   // the host staging above is freed on return
+    for (Buf* b : {&g->mip0, &g->mip, &g->pq, &g->ab, &g->ab32, &g->alpha, &g->wq, &g->dw, &g->status}) b->s = nullptr;
+    for (int c = 0; c < 3; c++) g->mip0x[c].s = g->mipx[c].s = nullptr;
+    *out = g.release();
+    return MG_OK;
+}

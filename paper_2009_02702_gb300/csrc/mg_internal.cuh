@@ -161,6 +161,15 @@ struct mg_graph {
     mg::Buf lut_meta;
     mg::Buf lut;
     int64_t lut_entries = 0;
+    // quantised graph (from the greedy factorisation): a node's weight is its
+    // bin's codeword, no exact weights (a = b = 0), so only fp32 pushes apply
+    bool quantised = false;
+    mg::Buf wq;        // double: weight of q of every node (quantised graphs)
+    mg::Buf dw;        // double: its uncertainty (the bin's sigma)
+    // mixture table with uncertainties (Sec. 3.5), built on request:
+    // node n's row is [err_off[n], err_off[n+1]) of (source, mu, dmu)
+    mg::Buf err_off, err_src, err_mu, err_dmu;
+    int64_t err_entries = 0;
     // launch shape chosen by mg_query_autotune, per histogram type (0 = none yet)
     int tuned_chunk[2] = {0, 0};
     int tuned_threads[2] = {0, 0};
@@ -203,6 +212,8 @@ mg_status propagate_multi(mg_graph* g, const float* tf, int k, int C, mg_dtype s
 mg_status build_lut(mg_graph* g, cudaStream_t s);
 // the padded axis-major copies of the box queries, from mip0 and mip
 mg_status build_query_copies(mg_graph* g, cudaStream_t s);
+// box histograms summed from the mixture table, with error bars (Sec. 3.5-3.6)
+mg_status query_lut(const mg_graph* g, const int32_t* boxes, int64_t Q, double* hist, double* err, cudaStream_t s);
 mg_status ensure_alpha16(mg_graph* g, mg_dtype dt, cudaStream_t s);
 mg_status query_boxes(const mg_graph* g, const int32_t* boxes, int64_t Q, const mg_query_opts& o,
                       void* out, size_t cap, uint32_t* seg, uint64_t* offsets, size_t* required,

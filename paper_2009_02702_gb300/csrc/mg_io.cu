@@ -52,6 +52,7 @@ extern "C" {
 
 MG_API mg_status mg_graph_export_size(const mg_graph* g, size_t* bytes) {
     if (!g || !bytes) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    if (g->quantised) return fail(MG_ERR_UNSUPPORTED, "quantised graphs are not exported");
     uint64_t b[kArrays];
     for (int k = 0; k < kArrays; k++) b[k] = arrays(const_cast<mg_graph*>(g), k)->bytes;
     *bytes = image_bytes(b);
@@ -61,6 +62,7 @@ MG_API mg_status mg_graph_export_size(const mg_graph* g, size_t* bytes) {
 MG_API mg_status mg_graph_export(const mg_graph* g, void* host, size_t bytes, mg_stream stream) {
     MG_RANGE("mg_graph_export");
     if (!g || !host) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+    if (g->quantised) return fail(MG_ERR_UNSUPPORTED, "quantised graphs are not exported");
     mg_graph* gm = const_cast<mg_graph*>(g);
     Header h;
     std::memset(&h, 0, sizeof(h));

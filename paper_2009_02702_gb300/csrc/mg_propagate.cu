@@ -322,6 +322,22 @@ __global__ void alpha16_kernel(const ulonglong2* __restrict__ ab, int64_t N, uin
     }
 }
 
+// the same from fp32 weights (quantised graphs: no exact a, b)
+__global__ void alpha16_from_f32_kernel(const float* __restrict__ alpha, int64_t N, uint32_t S, int bf16,
+                                        void* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (i >= (int64_t)S) {
+            const float w = alpha[i];
+            v = w <= 0.5f ? w : -(1.0f - w);
+        }
+        if (bf16)
+            static_cast<__nv_bfloat16*>(out)[i] = __float2bfloat16_rn(v);
+        else
+            static_cast<__half*>(out)[i] = __float2half_rn(v);
+    }
+}
+
 int sm_count_prop(int dev) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
@@ -407,8 +423,12 @@ mg_status ensure_alpha16(mg_graph* g, mg_dtype dt, cudaStream_t s) {
     Buf& b = dt == MG_BF16 ? g->alphab16 : g->alpha16;
     if (b.p) return MG_OK;
     MG_TRY(b.alloc(&g->al, (size_t)g->N * 2, s));
-    alpha16_kernel<<<grid_for(g->N, 256, 152 * 32), 256, 0, s>>>(g->ab.as<ulonglong2>(), g->N, g->S, dt == MG_BF16,
-                                                                b.p);
+    if (g->quantised)
+        alpha16_from_f32_kernel<<<grid_for(g->N, 256, 152 * 32), 256, 0, s>>>(g->alpha.as<float>(), g->N, g->S,
+                                                                              dt == MG_BF16, b.p);
+    else
+        alpha16_kernel<<<grid_for(g->N, 256, 152 * 32), 256, 0, s>>>(g->ab.as<ulonglong2>(), g->N, g->S,
+                                                                    dt == MG_BF16, b.p);
     MG_CUDA(cudaGetLastError());
     MG_CUDA(cudaStreamSynchronize(s));
     b.s = nullptr;

@@ -1847,7 +1847,72 @@ mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts&
     return MG_OK;
 }
 
+// Box histograms summed from the mixture table (Sec. 3.6) with error bars
+// (Sec. 3.5): one CTA per box walks its footprint blocks; every cube adds
+// 8^l mu and (8^l dmu)^2 of each entry of its node's row into shared fp64
+// accumulators; the row's error bars are the square roots.
+__global__ void __launch_bounds__(256) query_lut_kernel(Geom G, Ids I, const int32_t* __restrict__ boxes,
+                                                        const uint64_t* __restrict__ off,
+                                                        const uint32_t* __restrict__ src, const double* __restrict__ mu,
+                                                        const double* __restrict__ dmu, double* __restrict__ hist,
+                                                        double* __restrict__ err, unsigned* __restrict__ status) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ Runs R;
+    const uint32_t S = G.S;
+    double* h = reinterpret_cast<double*>(smem);
+    double* e2 = h + S;
+    const int64_t q = blockIdx.x;
+    for (uint32_t i = threadIdx.x; i < 2 * S; i += blockDim.x) h[i] = 0.0;
+    int32_t b[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) b[k] = boxes[q * 6 + k];
+    const bool ok = box_ok(b, G);
+    if (threadIdx.x == 0) {
+        if (ok) make_runs(b, G, R);
+        else set_status(status, kStatBadInput);
+    }
+    __syncthreads();
+    if (ok) {
+        for (int k = 0; k < R.nz; k++)
+            for (int j = 0; j < R.ny; j++)
+                for (int i = 0; i < R.nx; i++) {
+                    const Blk B = make_blk(G, 0, R.sx[i], R.sy[j], R.sz[k], R.lx[i], R.ly[j], R.lz[k]);
+                    const uint32_t n = block_cubes(R.lx[i], R.ly[j], R.lz[k]);
+                    for (uint32_t o = threadIdx.x; o < n; o += blockDim.x) {
+                        int lv = 0;
+                        const uint32_t node = cube_node(G, I, B, o, lv);
+                        const double W = ldexp(1.0, 3 * lv);
+                        for (uint64_t t = off[node]; t < off[node + 1]; t++) {
+                            const uint32_t s = src[t];
+                            if (s >= S) continue;
+                            atomicAdd(h + s, W * mu[t]);
+                            const double x = W * dmu[t];
+                            if (x != 0.0) atomicAdd(e2 + s, x * x);
+                        }
+                    }
+                }
+    }
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
+        hist[q * S + s] = h[s];
+        if (err) err[q * S + s] = sqrt(e2[s]);
+    }
+}
+
 }  // namespace
+
+mg_status query_lut(const mg_graph* g, const int32_t* boxes, int64_t Q, double* hist, double* err, cudaStream_t s) {
+    if (!g->err_off.p) return fail(MG_ERR_INVALID_ARG, "build the mixture table first (mg_error_table_build)");
+    const size_t sm = (size_t)g->S * 16;
+    if (sm > 200 * 1024) return fail(MG_ERR_UNSUPPORTED, "too many segments for the shared fp64 accumulators");
+    if (Q == 0) return MG_OK;
+    MG_CUDA(cudaFuncSetAttribute(query_lut_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    query_lut_kernel<<<(unsigned)Q, 256, sm, s>>>(make_geom(g), make_ids(g), boxes, g->err_off.as<uint64_t>(),
+                                                   g->err_src.as<uint32_t>(), g->err_mu.as<double>(),
+                                                   g->err_dmu.as<double>(), hist, err, g->status.as<unsigned>());
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
 
 mg_status count_cubes(const mg_graph* g, const int32_t* boxes, int64_t Q, uint64_t* cubes, cudaStream_t s) {
     const Geom G = make_geom(g);
@@ -2150,6 +2215,7 @@ extern "C" MG_API mg_status mg_query_boxes_noalloc(const mg_graph* g, const int3
     if (!boxes || !out) return fail(MG_ERR_INVALID_ARG, "NULL argument");
     if ((uint64_t)out_capacity < (uint64_t)Q * g->S) return fail(MG_ERR_INVALID_ARG, "out_capacity must be >= Q*S");
     if (g->S > kMaxSharedSegments) return fail(MG_ERR_UNSUPPORTED, "more than 32768 segments");
+    if (g->quantised) return fail(MG_ERR_UNSUPPORTED, "a quantised graph has no exact weights");
     if (per_box_scratch(Q) > kNoAllocBytes / 2) {
         int64_t qmax = 1;
         while (per_box_scratch(qmax * 2) <= kNoAllocBytes / 2) qmax *= 2;
@@ -2328,6 +2394,8 @@ MG_API mg_status mg_query_plan_create(mg_graph* g, int64_t max_Q, const mg_query
     if (o.layout != MG_LAYOUT_DENSE || o.schedule != MG_SCHED_BATCHED)
         return fail(MG_ERR_UNSUPPORTED, "plans hold the dense layout and the batched schedule");
     if (o.hist_type != MG_HIST_U32 && o.hist_type != MG_HIST_F32) return fail(MG_ERR_INVALID_ARG, "bad hist_type");
+    if (g->quantised && o.hist_type == MG_HIST_U32)
+        return fail(MG_ERR_UNSUPPORTED, "a quantised graph has no exact weights: use MG_HIST_F32");
     if (o.alpha_dtype != MG_F32 && (o.hist_type == MG_HIST_U32 || (o.alpha_dtype != MG_F16 && o.alpha_dtype != MG_BF16)))
         return fail(MG_ERR_INVALID_ARG, "bad alpha_dtype");
     if (o.block_threads && o.block_threads != 128 && o.block_threads != 256 && o.block_threads != 512)
@@ -2486,6 +2554,8 @@ extern "C" MG_API mg_status mg_query_autotune(mg_graph* g, const int32_t* boxes,
     if (!g || !opts) return fail(MG_ERR_INVALID_ARG, "NULL argument");
     if (Q < 1 || !boxes) return fail(MG_ERR_INVALID_ARG, "autotuning needs a non-empty batch");
     if (opts->hist_type != MG_HIST_U32 && opts->hist_type != MG_HIST_F32) return fail(MG_ERR_INVALID_ARG, "bad hist_type");
+    if (g->quantised && opts->hist_type == MG_HIST_U32)
+        return fail(MG_ERR_UNSUPPORTED, "a quantised graph has no exact weights: use MG_HIST_F32");
     const bool FP = opts->hist_type == MG_HIST_F32;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int prev = -1;

@@ -41,7 +41,8 @@ EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_cop
            "mg_render_lookup_multi", "mg_raymarch", "mg_bitstream_size", "mg_bitstream_write", "mg_bitstream_parse",
            "mg_bitstream_decode_mip", "mg_bitstream_decode_nodes", "mg_bitstream_lookup",
            "mg_factor_greedy", "mg_greedy_info_get", "mg_greedy_copy_nodes", "mg_greedy_copy_mip",
-           "mg_greedy_copy_picks", "mg_greedy_copy_codebook", "mg_greedy_free",
+           "mg_greedy_copy_picks", "mg_greedy_copy_codebook", "mg_greedy_free", "mg_graph_from_greedy",
+           "mg_error_table_build", "mg_error_table_copy", "mg_query_lut",
            "mg_server_create", "mg_server_add_volume", "mg_server_start", "mg_server_submit", "mg_server_cancel",
            "mg_server_wait", "mg_server_replay", "mg_server_stats_get", "mg_server_free",
            "mg_graph_export_size", "mg_graph_export", "mg_graph_import",
@@ -176,6 +177,14 @@ def lib():
         for f in ("mg_factor_greedy", "mg_greedy_info_get", "mg_greedy_copy_nodes", "mg_greedy_copy_mip",
                   "mg_greedy_copy_picks", "mg_greedy_copy_codebook"):
             getattr(L, f).restype = st
+        L.mg_graph_from_greedy.argtypes = [P, ctypes.POINTER(mg_allocator), P, ctypes.POINTER(P)]
+        L.mg_graph_from_greedy.restype = st
+        L.mg_error_table_build.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P]
+        L.mg_error_table_build.restype = st
+        L.mg_error_table_copy.argtypes = [P, P, P, P, P]
+        L.mg_error_table_copy.restype = st
+        L.mg_query_lut.argtypes = [P, P, i64, P, P, P]
+        L.mg_query_lut.restype = st
         L.mg_greedy_free.argtypes = [P]
         L.mg_greedy_free.restype = None
         L.mg_bitstream_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
@@ -703,7 +712,7 @@ _STRATEGY = {"occurrence": 1, "reduction": 2}
 
 
 def mg_factor_greedy(ids: torch.Tensor, num_segments: int, strategy: str = "reduction", tau: int = 3,
-                     bitrate: int = 9, stream=None) -> dict:
+                     bitrate: int = 9, graph: bool = False, stream=None) -> dict:
     """Greedy factorisation (phi_1 'occurrence' or phi_2 'reduction') of a
     (nz, ny, nx) uint16/uint32 CUDA volume on the GPU.  Returns a dict with
     the node table (p, q, a, b numpy), the mip IDs of every level, the
@@ -739,10 +748,49 @@ def mg_factor_greedy(ids: torch.Tensor, num_segments: int, strategy: str = "redu
         nbins = (1 << bitrate) if bitrate else 1
         cb = np.zeros(nbins); sg = np.zeros(nbins)
         _check(lib().mg_greedy_copy_codebook(h, cb.ctypes.data, sg.ctypes.data))
-        return dict(N=N, D=info.depth, L=L, p=p, q=q, a=a, b=b, mip=mips, dims=dims,
-                    picks=picks[:info.picks], codebook=cb, sigma=sg, waves=info.waves, ms=info.ms)
+        res = dict(N=N, D=info.depth, L=L, p=p, q=q, a=a, b=b, mip=mips, dims=dims,
+                   picks=picks[:info.picks], codebook=cb, sigma=sg, waves=info.waves, ms=info.ms)
+        if graph:
+            # mg_graph_from_greedy: the quantised graph, usable by every fp32 entry point
+            dev = ids.device.index if ids.device.index is not None else torch.cuda.current_device()
+            alloc = torch_allocator(dev)
+            gh = ctypes.c_void_p()
+            with torch.cuda.device(dev):
+                _check(lib().mg_graph_from_greedy(h, ctypes.byref(alloc), _stream(stream), ctypes.byref(gh)))
+            res["graph"] = Graph(gh.value, dev, alloc)
+        return res
     finally:
         lib().mg_greedy_free(h)
+
+
+def mg_error_table(g: Graph, stream=None):
+    """mg_error_table_build + mg_error_table_copy: the mixture table with
+    its Eq. 17 uncertainties as numpy (off, src, mu, dmu)."""
+    import numpy as np
+    e = ctypes.c_int64()
+    with torch.cuda.device(g.device):
+        _check(lib().mg_error_table_build(g.handle, ctypes.byref(e), _stream(stream)))
+    off = np.zeros(g.N + 1, np.int64)
+    src = np.zeros(max(e.value, 1), np.uint32); mu = np.zeros(max(e.value, 1)); dmu = np.zeros(max(e.value, 1))
+    _check(lib().mg_error_table_copy(g.handle, off.ctypes.data, src.ctypes.data, mu.ctypes.data, dmu.ctypes.data))
+    return off, src[:e.value], mu[:e.value], dmu[:e.value]
+
+
+def mg_query_lut(g: Graph, boxes: torch.Tensor, errors: bool = True, stream=None):
+    """Box histograms summed from the mixture table and their error bars,
+    (Q, S) float64 each (errors=False: error bars None).  Builds the table on
+    first use."""
+    if not boxes.is_cuda or boxes.dtype != torch.int32 or boxes.dim() != 2 or boxes.shape[1] != 6:
+        raise ValueError("boxes must be a CUDA int32 tensor of shape (Q, 6)")
+    boxes = boxes.contiguous()
+    with torch.cuda.device(g.device):
+        _check(lib().mg_error_table_build(g.handle, None, _stream(stream)))
+    Q = boxes.shape[0]
+    hist = torch.empty((Q, g.S), dtype=torch.float64, device=boxes.device)
+    err = torch.empty((Q, g.S), dtype=torch.float64, device=boxes.device) if errors else None
+    _check(lib().mg_query_lut(g.handle, boxes.data_ptr(), Q, hist.data_ptr(), err.data_ptr() if errors else None,
+                              _stream(stream)))
+    return hist, err
 
 
 def mg_sync_status(g: Graph, stream=None):

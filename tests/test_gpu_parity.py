@@ -417,3 +417,56 @@ def test_greedy_matches_oracle(mg, strategy, tau, bitrate, cfg, dims, S):
     if bitrate:
         assert np.array_equal(r["codebook"], cb)
         assert np.allclose(r["sigma"], sg, rtol=1e-9, atol=1e-15)
+
+
+# mixture table with uncertainties (Sec. 3.5) and the table-summed query
+def _rows_close(got, ref):
+    off, src, mu, dmu = got
+    roff, rsrc, rmu, rdmu = ref
+    assert np.array_equal(off, roff) and np.array_equal(src, rsrc)
+    assert np.allclose(mu, rmu, rtol=1e-12, atol=1e-15) and np.allclose(dmu, rdmu, rtol=1e-9, atol=1e-15)
+
+
+def test_error_table_and_lut_query_exact_graph(mg):
+    dims, S = (37, 29, 23), 24
+    vol = synth.make_volume(1, dims=dims, S=S)
+    g, og = build_pair(mg, vol, S)
+    _rows_close(mg.mg_error_table(g), oracle.error_rows(og, *oracle.node_weights(og)))
+    boxes = synth.make_boxes(1, Q=300, dims=dims, box_max=40)
+    h, e = mg.mg_query_lut(g, torch.from_numpy(boxes).to(dev()))
+    mg.mg_sync_status(g)
+    assert np.allclose(h.cpu().numpy(), oracle.box_hist(vol, S, boxes), rtol=1e-12, atol=1e-9)
+    assert (e.cpu().numpy() == 0).all()
+    g.close()
+
+
+@pytest.mark.parametrize("bitrate", [4, 9])
+def test_quantised_graph_table_queries_and_colours(mg, bitrate):
+    dims, S = (24, 20, 16), 20
+    vol = synth.make_volume(1, dims=dims, S=S)
+    r = mg.mg_factor_greedy(torch.from_numpy(vol).to(dev()), S, "reduction", tau=3, bitrate=bitrate, graph=True)
+    g = r["graph"]
+    og, cb, sg, _ = oracle.greedy(vol, S, "reduction", tau=3, bitrate=bitrate)
+    rows = oracle.error_rows(og, *oracle.node_weights(og, cb, sg))
+    _rows_close(mg.mg_error_table(g), rows)
+    boxes = synth.make_boxes(1, Q=200, dims=dims, box_max=24)
+    bt = torch.from_numpy(boxes).to(dev())
+    h, e = mg.mg_query_lut(g, bt)
+    hr, er = oracle.lut_query(og, rows, boxes)
+    assert np.allclose(h.cpu().numpy(), hr, rtol=1e-10, atol=1e-9)
+    assert np.allclose(e.cpu().numpy(), er, rtol=1e-9, atol=1e-12) and (er > 0).any()
+    # the fp32 push through the codeword weights gives the same expectations
+    hf = mg.mg_query_boxes(g, bt, hist="f32").cpu().numpy()
+    assert np.allclose(hf, hr, rtol=1e-4, atol=1e-2)
+    with pytest.raises(mg.MGError) as ex:
+        mg.mg_query_boxes(g, bt)
+    assert ex.value.status == mg.MG_ERR_UNSUPPORTED
+    # colours: the codeword lerps of Sec. 3.4 = sum over a node's row of mu * TF
+    tf = synth.make_tf(1, S, 4)
+    vals = mg.mg_propagate_tf(g, torch.from_numpy(tf).to(dev())).cpu().numpy()
+    off, src, mu, _ = rows
+    ref = np.stack([mu[off[n]:off[n + 1]] @ tf[src[off[n]:off[n + 1]]].astype(np.float64) for n in range(og.N)])
+    ok, err_ = fp32_close(vals, ref)
+    assert ok, err_
+    mg.mg_sync_status(g)
+    g.close()

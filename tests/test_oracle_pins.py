@@ -681,3 +681,65 @@ def test_greedy_coarser_bins_reuse_more():
     vol = synth.make_volume(1, dims=(32, 32, 32), S=24)
     n = [oracle.greedy(vol, 24, "reduction", tau=3, bitrate=b)[0].N for b in (3, 9, 0)]
     assert n[0] <= n[1] <= n[2]
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.5 (Eq. 16-17): error propagation through the mixture table
+# ---------------------------------------------------------------------------
+def test_error_rows_closed_form_of_two_lerps():
+    """n4 = lerp(e0, e1; w = 1/4), n5 = lerp(n4, e2; w = 1/2), weight
+    uncertainties 0.01 and 0.02.  Eq. 17: n4's components carry relative
+    error sqrt(2) * 0.01 / (1/4); n5 adds 2 (0.02 / (1/2))^2 to the squared
+    relative error of the components from n4, and e2 gets that term alone."""
+    g, _ = oracle.factor_lists([[(0, 3), (1, 1)], [(0, 3), (1, 1), (2, 4)]], 3)
+    # the pairwise rule: n3 = (e0, e1, 3:1), n4 = (n3, e2, 4:4)
+    assert g.N == 5 and list(g.p[3:5]) == [0, 3] and list(g.q[3:5]) == [1, 2]
+    w = np.array([0, 0, 0, 0.25, 0.5]); dw = np.array([0, 0, 0, 0.01, 0.02])
+    off, src, mu, dmu = oracle.error_rows(g, w, dw)
+    r3 = slice(off[3], off[4]); r4 = slice(off[4], off[5])
+    assert src[r3].tolist() == [0, 1] and np.allclose(mu[r3], [0.75, 0.25])
+    rel3 = np.sqrt(2) * 0.01 / 0.25
+    assert np.allclose(dmu[r3], np.array([0.75, 0.25]) * rel3)
+    assert src[r4].tolist() == [0, 1, 2] and np.allclose(mu[r4], [0.375, 0.125, 0.5])
+    rel4 = np.sqrt(rel3 ** 2 + 2 * (0.02 / 0.5) ** 2)
+    assert np.allclose(dmu[r4], [0.375 * rel4, 0.125 * rel4, 0.5 * np.sqrt(2) * 0.04])
+
+
+def test_error_rows_match_the_tree_pushes_and_exact_graphs_have_none():
+    vol = synth.make_volume(1, dims=(24, 20, 16), S=20)
+    gq, cb, sg, _ = oracle.greedy(vol, 20, "reduction", tau=3, bitrate=6)
+    off, src, mu, dmu = oracle.error_rows(gq, *oracle.node_weights(gq, cb, sg))
+    for n in range(20, gq.N, 37):
+        dense = np.zeros(20)
+        sl = slice(off[n], off[n + 1])
+        dense[src[sl]] = mu[sl]
+        assert np.allclose(dense, oracle.quantised_mixture(gq, cb, n), rtol=1e-12, atol=1e-15)
+    assert (dmu[off[20]:] > 0).any()
+    ge = oracle.Graph(vol, 20)
+    _, _, _, dmu_e = oracle.error_rows(ge, *oracle.node_weights(ge))
+    assert (dmu_e == 0).all()
+
+
+def test_lut_query_exact_counts_and_error_bars():
+    """Exact graphs: the table's sums are the brute-force counts.  Quantised
+    graphs: the sums still add up to the box volume (convex lerps), and the
+    error bar of a one-cube box is its node's Eq. 17 uncertainty times 8^l."""
+    dims = (24, 20, 16)
+    vol = synth.make_volume(1, dims=dims, S=20)
+    boxes = synth.make_boxes(1, Q=60, dims=dims, box_max=24)
+    ge = oracle.Graph(vol, 20)
+    h, e = oracle.lut_query(ge, oracle.error_rows(ge, *oracle.node_weights(ge)), boxes)
+    assert np.allclose(h, oracle.box_hist(vol, 20, boxes), rtol=1e-12, atol=1e-9) and (e == 0).all()
+    gq, cb, sg, _ = oracle.greedy(vol, 20, "reduction", tau=3, bitrate=5)
+    rows = oracle.error_rows(gq, *oracle.node_weights(gq, cb, sg))
+    hq, eq = oracle.lut_query(gq, rows, boxes)
+    vq = np.prod(np.minimum(boxes[:, :3] + boxes[:, 3:], dims) - boxes[:, :3], axis=1)
+    assert np.allclose(hq.sum(axis=1), vq, rtol=1e-12)
+    one = np.array([[8, 4, 4, 4, 4, 4]], np.int32)          # a single level-2 cube
+    h1, e1 = oracle.lut_query(gq, rows, one)
+    off, src, mu, dmu = rows
+    node = int(gq.mip(2)[1, 1, 2])
+    sl = slice(off[node], off[node + 1])
+    want = np.zeros(20)
+    want[src[sl]] = 64 * dmu[sl]
+    assert np.allclose(e1[0], want)
