@@ -431,15 +431,24 @@ typedef struct {
 MG_API mg_status mg_server_create(const mg_server_opts *opts, mg_server **out);
 
 /* Admit a volume: its graph g (built with mg_build, owned by the caller and
- * kept alive until mg_server_free) and the channel count C (1-8, 12 or 16) of
- * its TF frames.  Only before mg_server_start.  Allocates the volume's
- * per-slot plans and buffers from g's allocator, runs each slot's scratch up
- * to size (serving then allocates nothing) and synchronises the device.
- * MG_ERR_CAPACITY if the budget does not hold it (nothing is kept).
- * *volume = its index. */
+ * kept alive until it is removed or the server freed) and the channel count C
+ * (1-8, 12 or 16) of its TF frames -- before or while serving (from one
+ * thread at a time).  Allocates the volume's per-slot plans and buffers from
+ * g's allocator, runs each slot's scratch up to size (serving then allocates
+ * nothing for it) and synchronises the device.  MG_ERR_CAPACITY if the
+ * budget's remainder does not hold it (nothing is kept) or 1024 volumes were
+ * admitted.  *volume = its index (indices are never reused). */
 MG_API mg_status mg_server_add_volume(mg_server *sv, mg_graph *g, int C, int *volume);
 
-/* Start the worker thread.  Volumes cannot be added afterwards. */
+/* Remove (evict) a volume: new requests for it fail; before the start its
+ * queued requests are cancelled, after it the call waits (up to timeout_s, 0
+ * = no limit: else MG_ERR_TIMEOUT and the volume stays) until no queued or
+ * running work refers to it; then its per-slot plans and buffers are freed
+ * and their bytes return to the budget.  The graph stays the caller's; it
+ * can be admitted again (under a new index). */
+MG_API mg_status mg_server_remove_volume(mg_server *sv, int volume, double timeout_s);
+
+/* Start the worker thread. */
 MG_API mg_status mg_server_start(mg_server *sv);
 
 /* Queue a request (thread-safe; before mg_server_start requests wait in the

@@ -117,9 +117,12 @@ struct Slot {
     std::vector<VolSlot> vols;
 };
 
+constexpr int kMaxVolumes = 1024;   // admitted over a server's life (slots reserved up front)
+
 struct Volume {
     mg_graph* g = nullptr;
     int C = 0;
+    bool removed = false;   // mg_server_remove_volume: no new requests, resources released
     int frames = 1;   // TF frames one work item propagates together (frames * C channels)
     int32_t dims[3] = {0, 0, 0};
     uint32_t chunk = 2048;
@@ -389,6 +392,7 @@ void worker_loop(mg_server* sv) {
 mg_status check_request(const mg_server* sv, const mg_request& r, Req* q) {
     if (r.volume < 0 || r.volume >= (int)sv->vols.size()) return fail(MG_ERR_INVALID_ARG, "unknown volume");
     const Volume& v = sv->vols[r.volume];
+    if (v.removed) return fail(MG_ERR_INVALID_ARG, "volume removed from the server");
     q->blocks = q->chunks = 0;
     if (r.kind == MG_REQ_BOX) {
         const int32_t* b = r.box;
@@ -415,9 +419,10 @@ mg_status submit(mg_server* sv, const mg_request& r, Clock::time_point arrival, 
     Req q;
     q.r = r;
     q.arrival = arrival;
-    MG_TRY(check_request(sv, r, &q));
     {
+        // checked under the lock: volumes may be admitted or removed meanwhile
         std::lock_guard<std::mutex> lk(sv->mu);
+        MG_TRY(check_request(sv, r, &q));
         if (sv->stop.load()) return fail(MG_ERR_INVALID_ARG, "server is stopping");
         q.ticket = sv->next_ticket++;
         sv->recs.emplace(q.ticket, Rec{});
@@ -464,6 +469,8 @@ MG_API mg_status mg_server_create(const mg_server_opts* opts, mg_server** out) {
     sv->esize = o.storage == MG_F32 ? 4 : 2;
     MG_CUDA(cudaGetDevice(&sv->device));
     sv->slots.resize((size_t)o.slots);
+    sv->vols.reserve(kMaxVolumes);
+    for (Slot& sl : sv->slots) sl.vols.reserve(kMaxVolumes);
     mg_status st = MG_OK;
     for (Slot& sl : sv->slots) {
         if (st == MG_OK) st = cuda_ok(cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -479,7 +486,7 @@ MG_API mg_status mg_server_create(const mg_server_opts* opts, mg_server** out) {
 
 MG_API mg_status mg_server_add_volume(mg_server* sv, mg_graph* g, int C, int* volume) {
     if (!sv || !g || !volume) return fail(MG_ERR_INVALID_ARG, "NULL argument");
-    if (sv->started) return fail(MG_ERR_INVALID_ARG, "volumes are admitted before mg_server_start");
+    if ((int)sv->vols.size() >= kMaxVolumes) return fail(MG_ERR_CAPACITY, "at most 1024 volumes per server");
     if (!((C >= 1 && C <= 8) || C == 12 || C == 16)) return fail(MG_ERR_INVALID_ARG, "C must be 1-8, 12 or 16");
     if (g->device != sv->device) return fail(MG_ERR_INVALID_ARG, "graph lives on another device");
     if (g->L < 1) return fail(MG_ERR_INVALID_ARG, "empty volume");
@@ -578,10 +585,65 @@ MG_API mg_status mg_server_add_volume(mg_server* sv, mg_graph* g, int C, int* vo
         v.cap_blocks = v.cap_chunks = ~0ull;
     }
     v.bytes = need;
-    for (size_t k = 0; k < sv->slots.size(); k++) sv->slots[k].vols.push_back(std::move(made[k]));
-    sv->vols.push_back(v);
-    sv->budget_used += need;
-    *volume = (int)sv->vols.size() - 1;
+    {
+        // capacity is reserved: no element moves while the worker reads them
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (size_t k = 0; k < sv->slots.size(); k++) sv->slots[k].vols.push_back(std::move(made[k]));
+        sv->vols.push_back(v);
+        sv->budget_used += need;
+        *volume = (int)sv->vols.size() - 1;
+    }
+    return MG_OK;
+}
+
+MG_API mg_status mg_server_remove_volume(mg_server* sv, int volume, double timeout_s) {
+    if (!sv) return fail(MG_ERR_INVALID_ARG, "server is NULL");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    if (volume < 0 || volume >= (int)sv->vols.size() || sv->vols[volume].removed)
+        return fail(MG_ERR_INVALID_ARG, "unknown or removed volume");
+    Volume& v = sv->vols[volume];
+    v.removed = true;   // submissions now fail
+    if (!sv->started) {
+        // nothing runs before the start: its queued requests are cancelled
+        for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+            if (it->r.volume == volume) {
+                Rec& rec = sv->recs[it->ticket];
+                rec.state = kDone;
+                rec.status = MG_ERR_CANCELLED;
+                rec.error = "volume removed before the request was launched";
+                sv->stats.cancelled++;
+                it = sv->queue.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        sv->done_cv.notify_all();
+    }
+    // wait until no queued or running work refers to the volume
+    auto busy = [&]() {
+        for (const Req& q : sv->queue)
+            if (q.r.volume == volume) return true;
+        for (const Slot& sl : sv->slots)
+            if (sl.busy && !sl.work.empty() && sl.work[0].r.volume == volume) return true;
+        return false;
+    };
+    const auto until = Clock::now() + std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 1e9);
+    while (busy()) {
+        if (sv->done_cv.wait_until(lk, until) == std::cv_status::timeout && busy()) {
+            v.removed = false;
+            return fail(MG_ERR_TIMEOUT, "the volume's requests did not finish in time");
+        }
+    }
+    // its per-slot plans and buffers go back to the graph's allocator
+    for (Slot& sl : sv->slots) {
+        cudaStreamSynchronize(sl.s);
+        arena_drop(v.g, sl.s);
+        release_slot_volume(sl.vols[volume]);
+        VolSlot empty;
+        std::swap(sl.vols[volume], empty);
+    }
+    sv->budget_used -= v.bytes;
+    v.bytes = 0;
     return MG_OK;
 }
 

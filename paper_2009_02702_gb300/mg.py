@@ -43,7 +43,7 @@ EXPORTS = ("mg_build", "mg_graph_info_get", "mg_graph_copy_nodes", "mg_graph_cop
            "mg_factor_greedy", "mg_greedy_info_get", "mg_greedy_copy_nodes", "mg_greedy_copy_mip",
            "mg_greedy_copy_picks", "mg_greedy_copy_codebook", "mg_greedy_free", "mg_graph_from_greedy",
            "mg_error_table_build", "mg_error_table_copy", "mg_query_lut",
-           "mg_server_create", "mg_server_add_volume", "mg_server_start", "mg_server_submit", "mg_server_cancel",
+           "mg_server_create", "mg_server_add_volume", "mg_server_remove_volume", "mg_server_start", "mg_server_submit", "mg_server_cancel",
            "mg_server_wait", "mg_server_replay", "mg_server_stats_get", "mg_server_free",
            "mg_graph_export_size", "mg_graph_export", "mg_graph_import",
            "mg_selftest_bounded_wait", "mg_sync_status", "mg_free", "mg_last_error", "mg_version")
@@ -224,6 +224,8 @@ def lib():
         L.mg_server_create.restype = st
         L.mg_server_add_volume.argtypes = [P, P, i32, ctypes.POINTER(ctypes.c_int)]
         L.mg_server_add_volume.restype = st
+        L.mg_server_remove_volume.argtypes = [P, i32, ctypes.c_double]
+        L.mg_server_remove_volume.restype = st
         L.mg_server_start.argtypes = [P]
         L.mg_server_start.restype = st
         L.mg_server_submit.argtypes = [P, ctypes.POINTER(mg_request), ctypes.POINTER(ctypes.c_uint64)]
@@ -871,6 +873,10 @@ class Server:
             _check(lib().mg_server_add_volume(self.handle, g.handle, C, ctypes.byref(v)))
         self.volumes.append((g, C))
         return v.value
+
+    def remove_volume(self, volume: int, timeout: float = 0.0):
+        """Evict a volume once its queued and running requests are done."""
+        _check(lib().mg_server_remove_volume(self.handle, volume, timeout))
 
     def start(self):
         _check(lib().mg_server_start(self.handle))

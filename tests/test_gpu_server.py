@@ -264,3 +264,34 @@ def test_tf_frames_are_coalesced_and_exact(env, storage):
     for v, tf, smp, (_, out) in frames:
         alone = alone_frame(mg, graphs[v], tf, smp, storage).numpy()
         assert np.array_equal(out, alone)
+
+
+def test_volumes_admitted_and_removed_while_serving(env):
+    """A volume admitted after the start serves at once; a removed one refuses
+    new requests, its memory returns to the budget, and it can come back."""
+    mg, vols, graphs = env
+    srv = mg.Server(slots=2, max_batch=64, hist="u32")
+    v0 = srv.add_volume(graphs[0], 4)
+    srv.start()
+    base = srv.stats()["memory_admitted"]
+    v1 = srv.add_volume(graphs[1], 4)                 # while serving
+    assert srv.stats()["memory_admitted"] > base
+    box = [1, 2, 3, 9, 8, 7]
+    t1, out1 = srv.submit_box(v1, box)
+    t0, out0 = srv.submit_box(v0, box)
+    srv.wait(t1, timeout=60.0)
+    srv.wait(t0, timeout=60.0)
+    b = np.array([box], np.int32)
+    assert np.array_equal(out1, oracle.box_hist(vols[1]["vol"], vols[1]["S"], b)[0])
+    assert np.array_equal(out0, oracle.box_hist(vols[0]["vol"], vols[0]["S"], b)[0])
+    srv.remove_volume(v1, timeout=60.0)
+    assert srv.stats()["memory_admitted"] == base
+    with pytest.raises(mg.MGError) as e:
+        srv.submit_box(v1, box)
+    assert e.value.status == mg.MG_ERR_INVALID_ARG
+    v2 = srv.add_volume(graphs[1], 4)                 # admitted again, new index
+    assert v2 != v1
+    t2, out2 = srv.submit_box(v2, box)
+    srv.wait(t2, timeout=60.0)
+    assert np.array_equal(out2, out1)
+    srv.close()
