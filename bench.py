@@ -65,6 +65,8 @@ def parse(argv=None):
     ap.add_argument("--no-forms", action="store_true", help="skip the plain/naive/16-bit extra measurements")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving mix) measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the cylinder graph measurements")
+    ap.add_argument("--no-ext", action="store_true",
+                    help="skip ray marching, bitstream, greedy factorisation and error-table measurements")
     ap.add_argument("--serve-requests", type=int, default=0)
     ap.add_argument("--serve-rate", type=float, default=0.0)
     return ap.parse_args(argv)
@@ -595,14 +597,17 @@ def run_ours(args):
     head["graph"]["volume_generation_s"] = gen_s
     boxes = torch.from_numpy(boxes_h).to(dev)
 
+    cpu, ref = None, {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg_i, boxes_h, args.cpu_boxes, keep=ref)
+
     forms = None
     if not args.no_forms:
-        forms = other_forms(mg, g, boxes, boxes_h, Q, S, dims, cfg_i, flush, stream, peak)
+        forms = other_forms(mg, g, boxes, boxes_h, Q, S, dims, cfg_i, flush, stream, peak, ref=ref)
         forms["storage_types"] = storage_forms(mg, g, cfg_i, flush, stream, peak)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(cfg_i, boxes_h, args.cpu_boxes)
+        if not args.no_ext:
+            forms["raymarch"] = raymarch_forms(mg, g, cfg_i, dev, flush, stream)
+            forms["bitstream"] = bitstream_forms(mg, g, cfg_i, dev, flush, stream)
 
     secondary = None
     graphs = {cfg_i: g}
@@ -617,13 +622,23 @@ def run_ours(args):
         if not args.no_cpu_baseline:
             secondary["cpu_baseline"] = cpu_baseline(c2, b2, args.cpu_boxes, tf=synth.make_tf(c2, synth.CONFIGS[c2]["S"], 4))
 
+    ext = None
+    if not args.no_ext and rank == 0:
+        ext = {}
+        if secondary is not None:
+            ext["error_table_" + synth.CONFIGS[args.secondary]["name"]] = \
+                error_table_forms(mg, graphs[args.secondary], args.secondary, dev, flush, stream)
+            ext["bitstream_" + synth.CONFIGS[args.secondary]["name"]] = \
+                bitstream_forms(mg, graphs[args.secondary], args.secondary, dev, flush, stream)
+        ext["greedy"] = greedy_forms(mg, dev, cpu=world == 1 and not args.no_cpu_baseline)
+
     served = None
     if not args.no_serve and rank == 0:
         served = serving(mg, graphs, args, dev)
 
     large = None
     if not args.no_large and rank == 0:
-        large = cylinder_workload(mg, dev, flush, stream, peak)
+        large = cylinder_workload(mg, dev, flush, stream, peak, march=not args.no_ext)
 
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -641,6 +656,7 @@ def run_ours(args):
     line["secondary"] = secondary
     line["serving"] = served
     line["cylinders"] = large
+    line["extensions"] = ext
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -712,33 +728,42 @@ def error_sample(boxes_h, dims, n, seed):
     return np.sort(pick), vol
 
 
-def other_forms(mg, g, boxes, boxes_h, Q, S, dims, cfg_i, flush, stream, peak, n_err=500):
+def exact_vs_oracle(hist_u32, ref):
+    """The GPU's exact histograms (host copy) of the CPU baseline's sampled
+    boxes against the oracle's counts of the same boxes (ref: the dict
+    cpu_baseline fills)."""
+    if not ref:
+        return None
+    got = hist_u32[ref["pick"]].astype(np.int64)
+    return {"boxes": int(len(ref["pick"])), "equal": bool(np.array_equal(got, ref["counts"].astype(np.int64)))}
+
+
+def other_forms(mg, g, boxes, boxes_h, Q, S, dims, cfg_i, flush, stream, peak, n_err=5000, ref=None):
     """The batch in the other forms: direct calls (u32, f32, f32 with 16-bit
-    weights) with their error against the oracle's brute-force counts on
-    n_err boxes across the size range, the plain one-launch-per-box form and
-    the naive level-0 count."""
+    weights), the f32 forms with their relative l1 error against the exact
+    counts on n_err boxes across the size range, the plain one-launch-per-box
+    form and the naive level-0 count.  The exact counts themselves are
+    checked against the oracle on the CPU baseline's sample (ref)."""
     import torch
-    import oracle
     out = {}
     hist = torch.empty((Q, S), dtype=torch.uint32, device=boxes.device)
     histf = torch.empty((Q, S), dtype=torch.float32, device=boxes.device)
     ms = _time(lambda: mg.mg_query_boxes(g, boxes, out=hist), 5, flush, stream)
-    out["batched_direct_u32"] = {"queries_per_s": Q / (ms / 1e3), "ms": ms}
+    hist_h = hist.cpu().numpy()
+    out["batched_direct_u32"] = {"queries_per_s": Q / (ms / 1e3), "ms": ms,
+                                 "exact_vs_oracle": exact_vs_oracle(hist_h, ref)}
     pick, vol = error_sample(boxes_h, dims, n_err, 21)
-    vol_h = synth.make_volume(cfg_i)
-    ref = oracle.box_hist(vol_h, S, boxes_h[pick]).astype(np.float64)
-    del vol_h
-    hu = hist.cpu().numpy()[pick]
-    out["batched_direct_u32"]["exact_vs_oracle"] = {"boxes": int(len(pick)), "equal": bool(np.array_equal(hu, ref))}
+    exact = hist_h[pick].astype(np.float64)
+    del hist_h
     for name, alpha in (("batched_direct_f32", "f32"), ("batched_direct_f32_alpha_f16", "f16"),
                         ("batched_direct_f32_alpha_bf16", "bf16")):
         ms = _time(lambda: mg.mg_query_boxes(g, boxes, out=histf, hist="f32", alpha=alpha), 5, flush, stream)
         h = histf.cpu().numpy()[pick].astype(np.float64)
-        rel = np.abs(h - ref).sum(axis=1) / vol[pick]
+        rel = np.abs(h - exact).sum(axis=1) / vol[pick]
         out[name] = {"queries_per_s": Q / (ms / 1e3), "ms": ms,
-                     "rel_l1_error_vs_oracle": {"max": float(rel.max()), "mean": float(rel.mean()),
-                                                "boxes": int(len(pick)),
-                                                "box_voxels": [int(vol[pick].min()), int(vol[pick].max())]}}
+                     "rel_l1_error_vs_exact": {"max": float(rel.max()), "mean": float(rel.mean()),
+                                               "boxes": int(len(pick)),
+                                               "box_voxels": [int(vol[pick].min()), int(vol[pick].max())]}}
     n = min(Q, 1000)
     sub = boxes[:n].contiguous()
     hs = torch.empty((n, S), dtype=torch.float32, device=boxes.device)
@@ -776,6 +801,20 @@ def storage_forms(mg, g, cfg_i, flush, stream, peak, nsample=400):
         r["propagate_" + st] = {"ms": ms_p, "gbs": pb / ms_p / 1e6, "frac": pb / ms_p / 1e6 / peak, "bytes": pb}
         r["lookup_" + st] = {"ms": ms_l, "samples_per_s": P / (ms_l / 1e3), "gbs": lb / ms_l / 1e6,
                              "frac": lb / ms_l / 1e6 / peak}
+    # k transfer functions in one pass (one read of the node table, k*C
+    # values written per node) against k single passes
+    k = 8
+    tfs_h = np.stack([synth.make_attribute_tf(cfg_i, S, frame=j) if cfg_i == 4 else synth.make_tf(cfg_i, S, 4, frame=j)
+                      for j in range(k)])
+    tfs = torch.from_numpy(tfs_h).to(dev)
+    for st, dt, esz in (("f32", torch.float32, 4), ("f16", torch.float16, 2)):
+        vk = torch.empty((g.N, k * 4), dtype=dt, device=dev)
+        ms = _time(lambda: mg.mg_propagate_tf_multi(g, tfs, storage=st, out=vk), 10, flush, stream)
+        pb = NI * (8 + (4 if st == "f32" else 2) + k * 4 * esz) + S * k * (16 + 4 * esz)
+        r["propagate_multi_k8_" + st] = {"ms": ms, "ms_per_tf": ms / k, "tfs": k, "gbs": pb / ms / 1e6,
+                                         "frac": pb / ms / 1e6 / peak, "bytes": pb,
+                                         "speedup_vs_k_single": k * r["propagate_" + st]["ms"] / ms}
+        del vk
     vol_h = synth.make_volume(cfg_i)
     r["storage_error_vs_fp64"] = storage_errors(mg, g, tf, vol_h, c["dims"], S, nsample=nsample, seed=11,
                                                 max_level=4)
@@ -783,9 +822,186 @@ def storage_forms(mg, g, cfg_i, flush, stream, peak, nsample=400):
 
 
 # --------------------------------------------------------------------------
+# ray marching, the bitstream, greedy factorisation and error bars
+# --------------------------------------------------------------------------
+def selection_tf(cfg_i, S, frac=0.02, seed=31):
+    """The config's RGBA TF with all but a seeded fraction of the segments
+    made fully transparent (a selection of a few segments, as a user
+    highlighting them would set it)."""
+    tf = synth.make_tf(cfg_i, S, 4).copy()
+    keep = np.random.default_rng(seed).random(S) < frac
+    tf[~keep, 3] = 0.0
+    return tf
+
+
+def raymarch_forms(mg, g, cfg_i, dev, flush, stream, reps=3):
+    """1920x1080 frames ray-marched through the propagated node values
+    (Sec. 4: LOD steps, opacity correction, early termination at 0.99),
+    with and without empty-space skipping through the propagated opacity;
+    frame time, composited samples per second, and that skipping leaves
+    the image bit for bit unchanged."""
+    import torch
+    c = synth.CONFIGS[cfg_i]
+    S = c["S"]
+    cam = synth.orbit_camera(cfg_i)
+    W, H = cam["width"], cam["height"]
+    tfs = {"attribute_tf": synth.make_attribute_tf(cfg_i, S)} if cfg_i == 4 else \
+        {"uniform_tf": synth.make_tf(cfg_i, S, 4), "selection_tf_2pct": selection_tf(cfg_i, S)}
+    out = {"image": "%dx%d RGBA fp32" % (W, H),
+           "camera": "seeded orbit frame 0, 45 deg vertical fov, lattice step 0.5 voxel, lod bias 0, "
+                     "early termination at opacity 0.99"}
+    img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    for name, tf_h in tfs.items():
+        vals = mg.mg_propagate_tf(g, torch.from_numpy(tf_h).to(dev))
+        opac = vals[:, 3].contiguous()
+        row, ref = {}, None
+        for ess in (False, True):
+            op = opac if ess else None
+            ms = _time(lambda: mg.mg_raymarch(g, vals, cam, opacity=op, image=img), reps, flush, stream)
+            im, st = mg.mg_raymarch(g, vals, cam, opacity=op, steps=True)
+            n = int(st.sum().item())
+            row["skip" if ess else "plain"] = {"frame_ms": ms, "frames_per_s": 1e3 / ms, "composited_samples": n,
+                                               "samples_per_s": n / (ms / 1e3),
+                                               "rays_hit": int((st > 0).sum().item())}
+            if ref is None:
+                ref = im
+            else:
+                row["skip_image_identical"] = bool(torch.equal(ref, im))
+        mg.mg_sync_status(g)
+        row["skip_speedup"] = row["plain"]["frame_ms"] / row["skip"]["frame_ms"]
+        row["transparent_segments"] = int((tf_h[:, 3] == 0).sum())
+        out[name] = row
+        del vals, opac, ref, im, st
+    return out
+
+
+def bitstream_forms(mg, g, cfg_i, dev, flush, stream, reps=5):
+    """The graph's bitstream (Sec. 3.3, Table 1): bytes and bits per level-0
+    voxel against the raw 16-bit volume and the in-memory graph, GPU encode
+    and node-table decode time, and the palette lookup reading node IDs from
+    the stream by bit address against the plain lookup (same colours)."""
+    import torch
+    c = synth.CONFIGS[cfg_i]
+    S = c["S"]
+    bs = mg.mg_bitstream_write(g)
+    n = bs.data.numel()
+    vox = int(np.prod(c["dims"]))
+    lib = mg.lib()
+    enc = _time(lambda: mg._check(lib.mg_bitstream_write(g.handle, bs.data.data_ptr(), n, mg._stream(stream))),
+                reps, flush, stream)
+    dec = _time(lambda: bs.decode_nodes(stream=stream), reps, flush, stream)
+    tf = torch.from_numpy(synth.make_tf(cfg_i, S, 4)).to(dev)
+    vals = mg.mg_propagate_tf(g, tf)
+    smp = torch.from_numpy(synth.make_samples(cfg_i)).to(dev)
+    P = smp.shape[0]
+    look = torch.empty((P, 4), dtype=torch.float32, device=dev)
+    ms_plain = _time(lambda: mg.mg_render_lookup(g, vals, smp, out=look), reps, flush, stream)
+    ms_bs = _time(lambda: bs.lookup(vals, smp, stream=stream), reps, flush, stream)
+    same = bool(torch.equal(look, bs.lookup(vals, smp)))
+    mg.mg_sync_status(g)
+    out = {"bytes": n, "bits_per_voxel": 8.0 * n / vox, "raw_u16_volume_bytes": 2 * vox,
+           "ratio_vs_raw_u16": 2.0 * vox / n, "graph_device_bytes": g.info["device_bytes"],
+           "encode_ms": enc, "encode_gbs": n / enc / 1e6, "decode_nodes_ms": dec,
+           "lookup_plain_ms": ms_plain, "lookup_bitstream_ms": ms_bs,
+           "lookup_bitstream_samples_per_s": P / (ms_bs / 1e3), "lookup_same_colours": same, "samples": P}
+    del bs, vals, smp, look
+    return out
+
+
+def _hist_rel_l1(h, exact, vox):
+    rel = np.abs(h - exact).sum(axis=1) / np.maximum(vox, 1)
+    return {"max": float(rel.max()), "mean": float(rel.mean())}
+
+
+def greedy_forms(mg, dev, cpu=True):
+    """Greedy factorisation on the GPU (Sec. 3.3, Sec. 3.7) on the 64^3
+    Voronoi config: nodes N and depth D of phi_1 and phi_2 at b = 0 (exact)
+    and b = 5, 7, 9 bits against the pairwise graph; the quantised graphs'
+    box histograms (fp32 push) against the exact counts; their table-summed
+    histograms with Eq. 17 error bars against the realised error; GPU time
+    against the oracle's on the host cores (cpu).  Then the same for phi_2,
+    b = 9 on the 512x512x384 config (GPU only)."""
+    import torch
+    out = {}
+    for ci, bits, strategies in ((1, (0, 5, 7, 9), ("occurrence", "reduction")), (2, (9,), ("reduction",))):
+        c = synth.CONFIGS[ci]
+        S = c["S"]
+        vol = synth.make_volume(ci, device=dev)
+        torch.cuda.synchronize()
+        g = mg.mg_build(vol, S)
+        info = g.info
+        boxes_h = synth.make_boxes(ci)[:1000]
+        boxes = torch.from_numpy(boxes_h).to(dev)
+        exact = mg.mg_query_boxes(g, boxes).cpu().numpy().astype(np.float64)
+        d = np.array(c["dims"], np.int64)
+        vox = (np.minimum(boxes_h[:, :3].astype(np.int64) + boxes_h[:, 3:], d) - boxes_h[:, :3]).prod(axis=1)
+        res = {"pairwise": {"nodes": info["num_nodes"], "depth": info["depth"], "build_ms": info["build_ms"]},
+               "boxes": int(len(boxes_h))}
+        for strategy in strategies:
+            for b in bits:
+                key = "%s_b%d" % ("phi1" if strategy == "occurrence" else "phi2", b)
+                try:
+                    t0 = time.perf_counter()
+                    r = mg.mg_factor_greedy(vol, S, strategy=strategy, tau=3, bitrate=b, graph=b > 0)
+                    wall = time.perf_counter() - t0
+                except mg.MGError as e:
+                    res[key] = {"error": str(e)}
+                    continue
+                row = {"nodes": r["N"], "depth": r["D"], "nodes_vs_pairwise": r["N"] / info["num_nodes"],
+                       "stage1_picks": int(len(r["picks"])), "stage2_waves": r["waves"], "gpu_ms": r["ms"],
+                       "wall_s": wall}
+                if b > 0:
+                    gq = r["graph"]
+                    hf = mg.mg_query_boxes(gq, boxes, hist="f32").cpu().numpy().astype(np.float64)
+                    row["box_rel_l1_error_fp32_push"] = _hist_rel_l1(hf, exact, vox)
+                    hl, el = mg.mg_query_lut(gq, boxes)
+                    hl, el = hl.cpu().numpy(), el.cpu().numpy()
+                    dev_ = np.abs(hl - exact)
+                    row["box_rel_l1_error_table"] = _hist_rel_l1(hl, exact, vox)
+                    nz = el > 0
+                    row["error_bars"] = {"mean_bar_over_box_voxels": float((el.sum(axis=1) / vox).mean()),
+                                         "realised_within_1_bar": float((dev_ <= el + 1e-9).mean()),
+                                         "realised_within_2_bars": float((dev_ <= 2 * el + 1e-9).mean()),
+                                         "bins_with_bar": float(nz.mean())}
+                    mg.mg_sync_status(gq)
+                    gq.close()
+                res[key] = row
+        if ci == 1 and cpu:
+            res["cpu_baseline"] = greedy_cpu_baseline(ci)
+        out[c["name"]] = res
+        g.close()
+        del vol
+    return out
+
+
+def error_table_forms(mg, g, cfg_i, dev, flush, stream, reps=5):
+    """The mixture table of an exact graph (Sec. 3.5-3.6): entries, GPU
+    build time, and the table-summed fp64 box query against the exact u32
+    query on the config's boxes."""
+    import torch
+    c = synth.CONFIGS[cfg_i]
+    S = c["S"]
+    t0 = time.perf_counter()
+    off, src, mu, dmu = mg.mg_error_table(g)
+    build_s = time.perf_counter() - t0
+    boxes_h = synth.make_boxes(cfg_i)
+    boxes = torch.from_numpy(boxes_h).to(dev)
+    Q = boxes_h.shape[0]
+    ms_lut = _time(lambda: mg.mg_query_lut(g, boxes, errors=False, stream=stream), reps, flush, stream)
+    hist = torch.empty((Q, S), dtype=torch.uint32, device=dev)
+    ms_u32 = _time(lambda: mg.mg_query_boxes(g, boxes, out=hist), reps, flush, stream)
+    hl, _ = mg.mg_query_lut(g, boxes, errors=False)
+    diff = float(np.abs(hl.cpu().numpy() - hist.cpu().numpy().astype(np.float64)).max())
+    mg.mg_sync_status(g)
+    return {"entries": int(off[-1]), "entries_per_node": float(off[-1]) / g.N, "build_and_copy_s": build_s,
+            "query_table_f64_ms": ms_lut, "query_table_queries_per_s": Q / (ms_lut / 1e3),
+            "query_u32_ms": ms_u32, "table_max_abs_diff_vs_exact": diff, "boxes": Q}
+
+
+# --------------------------------------------------------------------------
 # the cylinder graph: many segments, attribute TF, bf16 frames
 # --------------------------------------------------------------------------
-def cylinder_workload(mg, dev, flush, stream, peak):
+def cylinder_workload(mg, dev, flush, stream, peak, march=True):
     """The cylinder graph (15,917 segments, 8.9 M nodes): propagation and
     lookup per storage type against the HBM peak, errors against fp64 on
     sampled voxels, and a 10,000-box batch through the CTA-shared histogram
@@ -824,6 +1040,8 @@ def cylinder_workload(mg, dev, flush, stream, peak):
                                  "achieved": qb / main_ms / 1e6, "peak": peak, "unit": "GB/s",
                                  "frac": qb / main_ms / 1e6 / peak, "algorithmic_bytes_per_launch": qb,
                                  "cubes_per_launch": cubes, "traffic": measured_traffic(kernel, cfg_i, Q)}}
+    if march:
+        r["raymarch"] = raymarch_forms(mg, g, cfg_i, dev, flush, stream)
     g.close()
     return r
 
@@ -876,24 +1094,34 @@ def serving(mg, have, args, dev):
     out = {"workload": c5["name"], "requests": n, "offered_rate_hz": rate, "tf_fraction": c5["tf_frac"],
            "frame_samples": side * side, "volumes": [synth.CONFIGS[m["cfg"]]["name"] for m in meta],
            "hist": "f32 (both forms)", "volume_build_s": build_s}
+    # the same requests at other offered rates (arrival times scaled) and as
+    # one burst; the sweep shows where each form saturates
+    sweep = [("offered", reqs)]
+    for r in (200000.0, 2000000.0):
+        if r > rate:
+            sweep.append(("rate_%d" % int(r), [dict(q, arrival=q["arrival"] * rate / r) for q in reqs]))
+    sweep.append(("burst", burst))
     for form, plain in (("batched", False), ("plain", True)):
         srv = mg.Server(slots=4, max_batch=1024, hist="f32", storage="f32", max_samples=side * side, plain=plain)
         for g in graphs:
             srv.add_volume(g, 4)
         srv.start()
         res = {}
-        for mode, stream in (("offered", reqs), ("burst", burst)):
+        for mode, stream in sweep:
             before = srv.stats()
             results, lat, wall = srv.replay(stream)
             after = srv.stats()
             launches = after["box_launches"] - before["box_launches"]
+            tfl = after["tf_launches"] - before["tf_launches"]
             nb = int(is_box.sum())
-            res[mode] = {"wall_s": wall, "queries_per_s": nb / wall, "requests_per_s": n / wall,
-                         "tf_frames_per_s": (n - nb) / wall,
+            offered = None if mode == "burst" else n / max(stream[-1]["arrival"], 1e-9)
+            res[mode] = {"offered_requests_per_s": offered, "wall_s": wall, "queries_per_s": nb / wall,
+                         "requests_per_s": n / wall, "tf_frames_per_s": (n - nb) / wall,
                          "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
                          "box_p50_ms": _pct(lat[is_box], 50), "box_p99_ms": _pct(lat[is_box], 99),
                          "tf_p50_ms": _pct(lat[~is_box], 50), "tf_p99_ms": _pct(lat[~is_box], 99),
                          "mean_batch": nb / max(launches, 1), "box_launches": launches,
+                         "tf_launches": tfl, "tf_frames_per_launch": (n - nb) / max(tfl, 1),
                          "failed": after["failed"] - before["failed"]}
             if form == "batched" and mode == "offered":
                 # served results against the same boxes queried alone (fp32 tolerance)
@@ -912,7 +1140,7 @@ def serving(mg, have, args, dev):
         srv.close()
         out[form] = res
     out["batched_over_plain_queries_per_s"] = {m: out["batched"][m]["queries_per_s"] / out["plain"][m]["queries_per_s"]
-                                               for m in ("offered", "burst")}
+                                               for m, _ in sweep}
     for g in graphs:
         if all(g is not h for h in have.values()):
             g.close()
@@ -946,11 +1174,13 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
-def cpu_baseline(cfg_i, boxes, n_boxes, vol=None, tf=None):
+def cpu_baseline(cfg_i, boxes, n_boxes, vol=None, tf=None, keep=None):
     """The oracle's brute-force counting timed on the host cores on a seeded
     sample of the step's boxes (n_boxes of them on all cores, a tenth on one
     core); with tf, also the oracle's TF propagation as the direct per-voxel
-    sum over levels 1-3 (the paper's 'revisiting every voxel')."""
+    sum over levels 1-3 (the paper's 'revisiting every voxel').  keep (a
+    dict) receives the sample's indices and counts, against which the GPU's
+    histograms of the same boxes are checked."""
     import oracle
     cfg = synth.CONFIGS[cfg_i]
     if vol is None:
@@ -958,9 +1188,10 @@ def cpu_baseline(cfg_i, boxes, n_boxes, vol=None, tf=None):
     all_threads = oracle.set_threads(0)
     rng = np.random.default_rng(1000 + cfg_i)
     n = min(n_boxes, len(boxes))
-    smp = boxes[np.sort(rng.choice(len(boxes), size=n, replace=False))]
+    pick = np.sort(rng.choice(len(boxes), size=n, replace=False))
+    smp = boxes[pick]
     t0 = time.perf_counter()
-    oracle.box_hist(vol, cfg["S"], smp)
+    counts = oracle.box_hist(vol, cfg["S"], smp)
     t_all = time.perf_counter() - t0
     oracle.set_threads(1)
     n1 = max(1, n // 10)
@@ -973,6 +1204,8 @@ def cpu_baseline(cfg_i, boxes, n_boxes, vol=None, tf=None):
                      "(OpenMP over boxes), %.1f s" % (n, len(boxes), t_all),
            "single_thread": {"value": n1 / t_one, "unit": UNIT, "boxes": n1, "seconds": t_one},
            "cpu_model": cpu_model()}
+    if keep is not None:
+        keep["pick"], keep["counts"] = pick, counts
     if tf is not None:
         dims = oracle.level_dims(*cfg["dims"])
         vox_all = int(np.prod(dims[1:], axis=1).sum())
@@ -985,6 +1218,20 @@ def cpu_baseline(cfg_i, boxes, n_boxes, vol=None, tf=None):
         res["propagation"] = {"voxels_per_s": n_vox / t_vox, "sample": "levels 1-3 (%d voxels), %.1f s"
                               % (n_vox, t_vox), "full_mip_estimate_s": vox_all / (n_vox / t_vox)}
     return res
+
+
+def greedy_cpu_baseline(cfg_i, reps=20):
+    """The oracle's greedy factorisation (phi_2, tau 3, b = 9) of the config's
+    volume timed on the host cores (single-threaded C), reps repetitions."""
+    import oracle
+    c = synth.CONFIGS[cfg_i]
+    vol = _host_volume(cfg_i)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        og, _, _, _ = oracle.greedy(vol, c["S"], "reduction", tau=3, bitrate=9)
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": 1.0 / dt, "unit": "factorisations/s", "seconds": dt, "cores": 1, "kind": "oracle",
+            "sample": "%d repetitions of the whole %s volume" % (reps, c["name"]), "nodes": og.N}
 
 
 def run_reference(args):
