@@ -237,7 +237,7 @@ def load_peak():
 def query_kernel_name(S, threads, hist="u32"):
     """The histogram kernel the library launches for S segments and a CTA size
     (a private histogram per warp when it fits, else one per CTA)."""
-    per_warp = S * 4 * (2 if hist == "f32" else 1) + 320 * 8 + 16   # histogram and push queue
+    per_warp = S * 4 * (2 if hist == "f32" else 1) + 64 * 8 + 16   # histogram and push queue
     warp_mode = S <= 2048 and threads <= 256 and per_warp * (threads // 32) <= 96 * 1024
     return "query_warp_kernel" if warp_mode else "query_batched_kernel"
 

@@ -343,7 +343,9 @@ MG_API mg_status mg_render_lookup_multi(const mg_graph *g, const void *vals, int
  * opacity exactly 0, the lattice samples inside the largest such voxel
  * shrunk by 3 * 2^m on every side (the reach of the interpolation), and
  * before the LOD changes, are skipped.  Each would add exactly nothing, so
- * the image equals the one without skipping.
+ * the image equals the one without skipping.  Opacities must be >= 0 (a
+ * voxel of opacity 0 then has only zero voxels below it, which lets a ray
+ * reuse its last climb while it stays inside the same voxel).
  * Decisions (lattice, level, skips, termination) are taken in fp32 with one
  * rounding per operation.
  * vals: N x 4 fp32 node values (mg_propagate_tf, storage MG_F32), 16-byte
@@ -370,9 +372,10 @@ MG_API mg_status mg_raymarch(const mg_graph *g, const float *vals, const float *
  * TF-update frames (propagation, Sec. 3.4, then ray-sample lookups, Sec. 4)
  * as they arrive.  A worker thread owns `slots` CUDA streams.  Whenever a
  * slot is free it takes the oldest queued request; a box request takes with
- * it every queued box of the same volume that still fits the slot's batch
- * (max_batch boxes and the footprint capacity of the slot's captured query
- * plan), and the whole batch runs as one plan launch; a TF frame takes with it
+ * it the next queued boxes of the same volume, in arrival order, while they
+ * fit the slot's batch (max_batch boxes and the footprint capacity of the
+ * slot's captured query plan), and the whole batch runs as one plan launch;
+ * a TF frame takes with it
  * the next queued frames of its volume (up to 8, as long as frames * C is a
  * channel count of mg_propagate_tf_multi), propagated in one pass and looked
  * up in one launch.

@@ -969,6 +969,7 @@ struct MainArgs {
     uint32_t* acc;
     float* accf;
     void* const* io;             // plans: io[1] is the output (acc for u32, accf for fp32)
+    uint32_t qcap;               // entries of each warp's push queue (set by launch_main)
 };
 
 // the output a main kernel accumulates into: fixed, or (plans) the caller's
@@ -988,8 +989,14 @@ __device__ __forceinline__ void main_out(const MainArgs& A, uint32_t*& acc, floa
 // (a measured alternative that summed the entries of one node in a hash
 // table first was slower on every workload: its probes cost more than the
 // expansions it saved).
-constexpr int kQueue = 320;   // queued entries at most (drained at >= 32)
-constexpr size_t kQueueBytes = (size_t)kQueue * 8 + 16;   // nodes, weights, counter
+// The queue is drained once it holds 32 entries; a step of the unit loop can
+// add up to 8 per lane, and an entry that finds the queue full is pushed by
+// its own lane at once (divergent, slower).  The launch takes the long queue
+// unless a short one fits more CTAs on an SM: the loop is bound by load
+// latency, so resident warps count for more where shared memory limits them.
+constexpr uint32_t kQueueLong = 320, kQueueShort = 64;   // entries
+constexpr size_t queue_bytes(uint32_t cap) { return (size_t)cap * 8 + 16; }   // nodes, weights, counter
+constexpr size_t kMaxDynSmem = 227 * 1024;   // dynamic shared memory of one CTA at most
 
 // chunks of the launch: known on the host, or (plans) read on the device,
 // zero when the batch overflows the plan's buffers
@@ -1003,13 +1010,15 @@ struct Queue {
     uint32_t* n;       // queued nodes
     uint32_t* w;       // queued weights
     uint32_t* count;   // queued entries
+    uint32_t cap;      // room
 };
 
-__device__ __forceinline__ Queue carve_queue(uint8_t* p) {
+__device__ __forceinline__ Queue carve_queue(uint8_t* p, uint32_t cap) {
     Queue Qu;
     Qu.n = reinterpret_cast<uint32_t*>(p);
-    Qu.w = Qu.n + kQueue;
-    Qu.count = Qu.w + kQueue;
+    Qu.w = Qu.n + cap;
+    Qu.count = Qu.w + cap;
+    Qu.cap = cap;
     return Qu;
 }
 
@@ -1074,7 +1083,7 @@ template <bool FP, typename AT>
 __device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Queue& Qu, bool all) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
-    const uint32_t qc = *Qu.count;
+    const uint32_t qc = min(*Qu.count, Qu.cap);   // entries past the end were pushed at once
     uint32_t done = 0;
     while (qc - done >= 32 || (all && qc > done)) {
         const uint32_t take = min(qc - done, 32u);
@@ -1128,18 +1137,22 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
             H.add_int(rid, W);
         } else {
             const uint32_t pos = atomicAdd(Qu.count, 1u);
-            Qu.n[pos] = rid;
-            Qu.w[pos] = W;
+            if (pos < Qu.cap) {
+                Qu.n[pos] = rid;
+                Qu.w[pos] = W;
+            } else {
+                push_one<FP, AT>(A.P, H, rid, W);
+            }
         }
     };
-    auto feed = [&](uint32_t x, int l) {
+    auto feed = [&](uint32_t x, int l, uint32_t n = 1) {
         if (x == rid && l == rl) {
-            rcnt++;
+            rcnt += n;
         } else {
             finish();
             rid = x;
             rl = l;
-            rcnt = 1;
+            rcnt = n;
         }
     };
     for (uint64_t bb = b;; bb += 31) {
@@ -1306,14 +1319,14 @@ __global__ void __launch_bounds__(256, 5) query_warp_kernel(MainArgs A) {
     const uint32_t S = A.P.S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t hist_bytes = (size_t)S * 4 * (FP ? 2 : 1);
-    uint8_t* mine = smem + warp * (hist_bytes + kQueueBytes);
+    uint8_t* mine = smem + warp * (hist_bytes + queue_bytes(A.qcap));
     Hist<FP> H;
     H.h = reinterpret_cast<uint32_t*>(mine);
     H.hf = FP ? reinterpret_cast<float*>(H.h + S) : nullptr;
     H.touched = nullptr;
     H.ntouched = nullptr;
     H.track = false;
-    const Queue Qu = carve_queue(mine + hist_bytes);
+    const Queue Qu = carve_queue(mine + hist_bytes, A.qcap);
     for (uint32_t i = lane; i < S; i += 32) {
         H.h[i] = 0;
         if constexpr (FP) H.hf[i] = 0.f;
@@ -1368,7 +1381,7 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
     // per-warp queues follow the touched list
     const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
     uint8_t* qbase = reinterpret_cast<uint8_t*>(H.touched) + ((touched_bytes + 15) & ~(size_t)15);
-    const Queue Qu = carve_queue(qbase + warp * kQueueBytes);
+    const Queue Qu = carve_queue(qbase + warp * queue_bytes(A.qcap), A.qcap);
     for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
         H.h[i] = 0;
         if constexpr (FP) H.hf[i] = 0.f;
@@ -1546,42 +1559,67 @@ __global__ void __launch_bounds__(256) query_naive_kernel(Geom G, const T* __res
         naive_extent(b, G, dx, dy, dz);
         const int64_t rows_per = max((int64_t)1, (int64_t)kNaiveSlab / dx);
         const int64_t r0 = (int64_t)(w - item_off[q]) * rows_per, r1 = min(r0 + rows_per, dy * dz);
-        const int64_t nx = G.dims[0][0], ny = G.dims[0][1];
+        const int64_t nx = G.dims[0][0], ny = G.dims[0][1], V0 = nx * ny * G.dims[0][2];
+        // a warp per row of the slab (row r = (y, z) of the box, advanced
+        // without divisions); lanes read 16-byte vectors of the row, four
+        // per lane in flight
+        int64_t ry = (r0 + warp) % dy, rz = (r0 + warp) / dy;
         for (int64_t r = r0 + warp; r < r1; r += nw) {
-            const int64_t e0 = ((int64_t)(b[2] + r / dy) * ny + b[1] + r % dy) * nx + b[0], e1 = e0 + dx;
+            const int64_t e0 = ((int64_t)(b[2] + rz) * ny + b[1] + ry) * nx + b[0], e1 = e0 + dx;
             uint32_t rid = kNone, rcnt = 0;
-            for (int64_t v = e0 / E + lane; v * E < e1; v += 32) {
-                const uint4 u = __ldg(reinterpret_cast<const uint4*>(ids0) + v);
-                const T* x = reinterpret_cast<const T*>(&u);
-                const int64_t p0 = v * E;
-                const bool whole = p0 >= e0 && p0 + E <= e1;
-                bool uni = whole;
+            for (int64_t v0 = e0 / E; v0 * E < e1; v0 += 128) {
+                uint4 u[4];
 #pragma unroll
-                for (int k = 1; k < E; k++) uni = uni && x[k] == x[0];
-                if (uni) {
-                    if (rcnt && rid == (uint32_t)x[0]) {
-                        rcnt += E;
+                for (int j = 0; j < 4; j++) {
+                    const int64_t v = v0 + lane + 32 * j;
+                    u[j] = make_uint4(0u, 0u, 0u, 0u);
+                    if (v * E >= e1) continue;
+                    if ((v + 1) * E <= V0) {
+                        u[j] = __ldg(reinterpret_cast<const uint4*>(ids0) + v);
                     } else {
-                        if (rcnt) atomicAdd(h + rid, rcnt);
-                        rid = (uint32_t)x[0];
-                        rcnt = E;
+                        // the volume's last vector, cut at its end
+                        T* x = reinterpret_cast<T*>(&u[j]);
+                        for (int k = 0; k < E && v * E + k < V0; k++) x[k] = __ldg(ids0 + v * E + k);
                     }
-                    continue;
                 }
 #pragma unroll
-                for (int k = 0; k < E; k++) {
-                    if (p0 + k < e0 || p0 + k >= e1) continue;
-                    const uint32_t id = (uint32_t)x[k];
-                    if (rcnt && id == rid) {
-                        rcnt++;
-                    } else {
-                        if (rcnt) atomicAdd(h + rid, rcnt);
-                        rid = id;
-                        rcnt = 1;
+                for (int j = 0; j < 4; j++) {
+                    const int64_t p0 = (v0 + lane + 32 * j) * E;
+                    if (p0 >= e1) continue;
+                    const T* x = reinterpret_cast<const T*>(&u[j]);
+                    bool uni = p0 >= e0 && p0 + E <= e1;
+#pragma unroll
+                    for (int k = 1; k < E; k++) uni = uni && x[k] == x[0];
+                    if (uni) {
+                        if (rcnt && rid == (uint32_t)x[0]) {
+                            rcnt += E;
+                        } else {
+                            if (rcnt) atomicAdd(h + rid, rcnt);
+                            rid = (uint32_t)x[0];
+                            rcnt = E;
+                        }
+                        continue;
+                    }
+#pragma unroll
+                    for (int k = 0; k < E; k++) {
+                        if (p0 + k < e0 || p0 + k >= e1) continue;
+                        const uint32_t id = (uint32_t)x[k];
+                        if (rcnt && id == rid) {
+                            rcnt++;
+                        } else {
+                            if (rcnt) atomicAdd(h + rid, rcnt);
+                            rid = id;
+                            rcnt = 1;
+                        }
                     }
                 }
             }
             if (rcnt) atomicAdd(h + rid, rcnt);
+            ry += nw;
+            while (ry >= dy) {
+                ry -= dy;
+                rz++;
+            }
         }
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
@@ -1818,18 +1856,31 @@ mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts&
         MG_CUDA(cudaGetLastError());
         return MG_OK;
     }
-    // few segments: a private histogram per warp; else one per CTA
-    const size_t per_warp = (size_t)g->S * 4 * (FP ? 2 : 1) + kQueueBytes;
-    const bool warp_mode = g->S <= kWarpHistMax && threads <= 256 && per_warp * (threads / 32) <= 96 * 1024;
+    // few segments: a private histogram per warp; else one per CTA (smem
+    // is then the histogram's part, the warps' queues come on top)
+    const int warps = threads / 32;
+    const size_t hist_w = (size_t)g->S * 4 * (FP ? 2 : 1);
+    const bool warp_mode =
+        g->S <= kWarpHistMax && threads <= 256 && (hist_w + queue_bytes(kQueueShort)) * warps <= 96 * 1024;
     auto k = warp_mode ? query_warp_kernel<FP, AT> : query_batched_kernel<FP, AT>;
-    const size_t sm = warp_mode ? per_warp * (threads / 32) : smem;
-    MG_TRY(prepare_kernel(k, sm));
-    int per_sm = 0;
-    MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, sm));
+    auto smem_for = [&](uint32_t cap) {
+        return warp_mode ? (hist_w + queue_bytes(cap)) * warps : smem + warps * queue_bytes(cap);
+    };
+    int per_sm = 0, per_long = 0;
+    if (smem_for(kQueueShort) > kMaxDynSmem) return fail(MG_ERR_UNSUPPORTED, "query kernel does not fit on an SM");
+    MG_TRY(prepare_kernel(k, smem_for(kQueueShort)));
+    MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem_for(kQueueShort)));
     if (per_sm < 1) return fail(MG_ERR_UNSUPPORTED, "query kernel does not fit on an SM");
+    if (smem_for(kQueueLong) <= kMaxDynSmem) {
+        MG_TRY(prepare_kernel(k, smem_for(kQueueLong)));
+        MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_long, k, threads, smem_for(kQueueLong)));
+    }
+    MainArgs A2 = A;
+    A2.qcap = per_long >= per_sm ? kQueueLong : kQueueShort;
+    const size_t sm = smem_for(A2.qcap);
     const int grid = per_sm * sm_count(g->device);
     if (!pdl) {
-        k<<<grid, threads, sm, s>>>(A);
+        k<<<grid, threads, sm, s>>>(A2);
         MG_CUDA(cudaGetLastError());
         return MG_OK;
     }
@@ -1843,7 +1894,7 @@ mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts&
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    MG_CUDA(cudaLaunchKernelEx(&cfg, k, A));
+    MG_CUDA(cudaLaunchKernelEx(&cfg, k, A2));
     return MG_OK;
 }
 
@@ -1873,24 +1924,44 @@ __global__ void __launch_bounds__(256) query_lut_kernel(Geom G, Ids I, const int
     }
     __syncthreads();
     if (ok) {
-        for (int k = 0; k < R.nz; k++)
-            for (int j = 0; j < R.ny; j++)
-                for (int i = 0; i < R.nx; i++) {
-                    const Blk B = make_blk(G, 0, R.sx[i], R.sy[j], R.sz[k], R.lx[i], R.ly[j], R.lz[k]);
-                    const uint32_t n = block_cubes(R.lx[i], R.ly[j], R.lz[k]);
-                    for (uint32_t o = threadIdx.x; o < n; o += blockDim.x) {
-                        int lv = 0;
-                        const uint32_t node = cube_node(G, I, B, o, lv);
-                        const double W = ldexp(1.0, 3 * lv);
-                        for (uint64_t t = off[node]; t < off[node + 1]; t++) {
-                            const uint32_t s = src[t];
-                            if (s >= S) continue;
-                            atomicAdd(h + s, W * mu[t]);
-                            const double x = W * dmu[t];
-                            if (x != 0.0) atomicAdd(e2 + s, x * x);
-                        }
-                    }
+        // warps take the footprint's blocks in turn; a lane takes a contiguous
+        // range of its block's cubes (consecutive cubes of a row) and keeps a
+        // run of equal nodes, so a row of k cubes of node n at level l adds
+        // k 8^l mu(n) and k (8^l dmu(n))^2 with one pass over n's row
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        const int nb = R.nx * R.ny * R.nz;
+        uint32_t rn = 0xffffffffu, rc = 0;
+        int rl = 0;
+        auto flush_run = [&]() {
+            if (!rc) return;
+            const double W = ldexp((double)rc, 3 * rl), W2 = ldexp((double)rc, 6 * rl);
+            for (uint64_t t = off[rn]; t < off[rn + 1]; t++) {
+                const uint32_t s = src[t];
+                if (s >= S) continue;
+                atomicAdd(h + s, W * mu[t]);
+                const double x = dmu[t];
+                if (x != 0.0) atomicAdd(e2 + s, W2 * x * x);
+            }
+        };
+        for (int bi = warp; bi < nb; bi += nwarps) {
+            const int i = bi % R.nx, j = (bi / R.nx) % R.ny, k = bi / (R.nx * R.ny);
+            const Blk B = make_blk(G, 0, R.sx[i], R.sy[j], R.sz[k], R.lx[i], R.ly[j], R.lz[k]);
+            const uint32_t n = block_cubes(R.lx[i], R.ly[j], R.lz[k]);
+            const uint32_t per = (n + 31) / 32, o0 = min(n, lane * per), o1 = min(n, o0 + per);
+            for (uint32_t o = o0; o < o1; o++) {
+                int lv = 0;
+                const uint32_t node = cube_node(G, I, B, o, lv);
+                if (node == rn && lv == rl) {
+                    rc++;
+                } else {
+                    flush_run();
+                    rn = node;
+                    rl = lv;
+                    rc = 1;
                 }
+            }
+        }
+        flush_run();
     }
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
@@ -1997,10 +2068,10 @@ mg_status query_boxes_impl(const mg_graph* g, const int32_t* boxes, int64_t Q, c
     A.lim = Lim{nullptr, 0, 0};
     A.ticket = nullptr;
     A.io = nullptr;
+    A.qcap = kQueueShort;
 
     const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
-    const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + ((touched_bytes + 15) & ~(size_t)15) +
-                        (size_t)(threads / 32) * kQueueBytes + 16;
+    const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + ((touched_bytes + 15) & ~(size_t)15) + 16;
     if (smem > 220 * 1024) return fail(MG_ERR_UNSUPPORTED, "too many segments for the shared-memory histogram");
     Buf nblk, ncube, nchunk, blk_off, chunk_off, blk, ticket, chunk_q, chunk_b;
     if (o.schedule == MG_SCHED_BATCHED) {
@@ -2354,11 +2425,11 @@ mg_status plan_enqueue(mg_query_plan* p, const Alloc& al, cudaStream_t s) {
     A.acc = acc;
     A.accf = accf;
     A.io = p->io;
+    A.qcap = kQueueShort;
     mg_query_opts o{};
     o.hist_type = FP ? MG_HIST_F32 : MG_HIST_U32;
     const size_t touched_bytes = (size_t)S * 2 * (FP ? 2 : 1);
-    const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + ((touched_bytes + 15) & ~(size_t)15) +
-                        (size_t)(p->threads / 32) * kQueueBytes + 16;
+    const size_t smem = (size_t)S * 4 * (FP ? 2 : 1) + ((touched_bytes + 15) & ~(size_t)15) + 16;
     MG_TRY((launch_main<FP, AT>(g, A, o, nullptr, smem, p->threads, s, !p->timed)));
     if (p->timed) MG_CUDA(cudaEventRecordWithFlags(p->ev[2], s, cudaEventRecordExternal));
     if (FP) {

@@ -204,6 +204,8 @@ struct MarchArgs {
     const uint32_t* mip;
     const float4* vals;
     const float* opac;
+    const uint32_t* occ;              // occupancy bits of levels >= 2 (skipping on)
+    int64_t occ_off[MG_MAX_LEVELS];   // first word of every level's bits
     mg_camera cam;
     float4* img;
     int32_t* steps;
@@ -281,6 +283,14 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs A) {
     const float ts = tmin > 0.0f ? tmin : 0.0f;
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Aacc = 0.0f;
     int32_t taken = 0;
+    // Climbs are not repeated while their answer cannot change.  (hl, hv): the
+    // last voxel of level hl the climb found non-zero; a climb that reaches it
+    // stops there.  (zm, zj, zb): the last climb from level zm + 2 ended with
+    // the zero voxel zb of level zj; opacities are >= 0, so every voxel below
+    // it is zero too and its parent is the same, and a climb from the same
+    // level anywhere inside it ends the same way.
+    int hl = -1, zm = -1, zj = -1;
+    int64_t hv[3] = {0, 0, 0}, zb[3] = {0, 0, 0};
     if (!miss && tmax > ts) {
         int64_t k = 0;
         while (k < cam.max_steps) {
@@ -300,7 +310,23 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs A) {
             if (A.opac) {
                 int jz = -1;
                 int64_t bz[3] = {0, 0, 0};
-                for (int jl = m + 2; jl < L; jl++) {
+                if (zj >= 0 && zm == m) {
+                    bool same = true;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        int64_t v = (int64_t)floorf(p[c]);
+                        v = v < 0 ? 0 : v;
+                        v >>= zj;
+                        v = v > A.G.dims[zj][c] - 1 ? A.G.dims[zj][c] - 1 : v;
+                        same = same && v == zb[c];
+                    }
+                    if (same) {
+                        jz = zj;
+#pragma unroll
+                        for (int c = 0; c < 3; c++) bz[c] = zb[c];
+                    }
+                }
+                for (int jl = jz >= 0 ? L : m + 2; jl < L; jl++) {
                     int64_t b[3];
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
@@ -309,10 +335,23 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs A) {
                         v >>= jl;
                         b[c] = v > A.G.dims[jl][c] - 1 ? A.G.dims[jl][c] - 1 : v;
                     }
-                    if (__ldg(A.opac + march_node(A, jl, b[0], b[1], b[2])) != 0.0f) break;
+                    if (jl == hl && b[0] == hv[0] && b[1] == hv[1] && b[2] == hv[2]) break;
+                    const int64_t vi = (b[2] * A.G.dims[jl][1] + b[1]) * A.G.dims[jl][0] + b[0];
+                    if ((__ldg(A.occ + A.occ_off[jl] + (vi >> 5)) >> (vi & 31)) & 1u) {
+                        hl = jl;
+#pragma unroll
+                        for (int c = 0; c < 3; c++) hv[c] = b[c];
+                        break;
+                    }
                     jz = jl;
 #pragma unroll
                     for (int c = 0; c < 3; c++) bz[c] = b[c];
+                }
+                if (jz >= 0 && (jz != zj || zm != m)) {
+                    zm = m;
+                    zj = jz;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) zb[c] = bz[c];
                 }
                 if (jz >= 0) {
                     const float size = ldexpf(1.0f, jz), gap = ldexpf(3.0f, m);
@@ -363,6 +402,19 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs A) {
     if (A.steps) A.steps[o] = taken;
 }
 
+// bit v of a level's words: the opacity of voxel v's node is non-zero (one
+// lane per voxel, a warp's ballot is one word)
+__global__ void occ_bits_kernel(const uint32_t* __restrict__ ids, int64_t n, const float* __restrict__ opac,
+                                uint32_t* __restrict__ words) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        const bool occ = i < n && __ldg(opac + __ldg(ids + i)) != 0.0f;
+        const unsigned w = __ballot_sync(0xffffffffu, occ);
+        if ((threadIdx.x & 31) == 0 && i < n) words[i >> 5] = w;
+    }
+}
+
 }  // namespace
 
 mg_status raymarch(const mg_graph* g, const float* vals, const float* opacity, const mg_camera& cam, float* image,
@@ -374,6 +426,31 @@ mg_status raymarch(const mg_graph* g, const float* vals, const float* opacity, c
     A.mip = g->mip.as<uint32_t>();
     A.vals = reinterpret_cast<const float4*>(vals);
     A.opac = opacity;
+    A.occ = nullptr;
+    for (int l = 0; l < MG_MAX_LEVELS; l++) A.occ_off[l] = 0;
+    if (opacity) {
+        // the climbs of empty-space skipping read one bit per voxel of levels
+        // >= 2 (built here, in the graph's per-stream scratch) instead of a
+        // node ID and its opacity
+        int64_t words = 0;
+        for (int l = 2; l < g->L; l++) {
+            A.occ_off[l] = words;
+            words += ((int64_t)A.G.dims[l][0] * A.G.dims[l][1] * A.G.dims[l][2] + 31) / 32;
+        }
+        if (words > 0) {
+            Arena* arena = nullptr;
+            MG_TRY(arena_begin(const_cast<mg_graph*>(g), s, &arena));
+            Buf bits;
+            MG_TRY(bits.alloc(&arena->view, (size_t)words * 4, s));
+            for (int l = 2; l < g->L; l++) {
+                const int64_t n = (int64_t)A.G.dims[l][0] * A.G.dims[l][1] * A.G.dims[l][2];
+                occ_bits_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(g->mip.as<uint32_t>() + A.G.off[l], n, opacity,
+                                                                           bits.as<uint32_t>() + A.occ_off[l]);
+                MG_CUDA(cudaGetLastError());
+            }
+            A.occ = bits.as<uint32_t>();
+        }
+    }
     A.cam = cam;
     A.img = reinterpret_cast<float4*>(image);
     A.steps = steps;

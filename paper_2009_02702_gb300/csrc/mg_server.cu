@@ -4,14 +4,15 @@
 //
 // Resident volumes are admitted against a memory budget; each gets, per slot
 // (one CUDA stream), a captured query plan and staging buffers, so nothing is
-// allocated while serving.  Requests enter one FIFO.  A worker thread polls
-// the slots' completion events and, whenever a slot is free, takes the oldest
-// request: a TF frame together with the queued frames of the same volume (up
-// to `frames` of them: one multi-TF propagation and one lookup launch for
-// all), or a box together with every queued box of the same volume that fits
-// the slot's batch -- max_batch boxes whose footprint blocks and work chunks
-// (counted on the host at submission, in closed form as the plan kernel does)
-// fit the plan's capacities.  The batch
+// allocated while serving.  Requests enter per-volume FIFOs (boxes and TF
+// frames apart).  A worker thread polls the slots' completion events and,
+// whenever a slot is free, takes the oldest request: a TF frame together with
+// the next queued frames of the same volume (up to `frames` of them: one
+// multi-TF propagation and one lookup launch for all), or a box together with
+// the next queued boxes of the same volume while they fit the slot's batch --
+// max_batch boxes whose footprint blocks and work chunks (counted on the host
+// at submission, in closed form as the plan kernel does) fit the plan's
+// capacities.  The batch
 // is staged straight into the plan's input buffers and run as one graph
 // launch; results come back through pinned memory and are copied into the
 // callers' buffers when the slot's event fires, which also ends each
@@ -130,6 +131,12 @@ struct Volume {
     int64_t bytes = 0;   // admitted memory
 };
 
+// queued requests of one volume, boxes and TF frames apart, each in arrival
+// (ticket) order: a work item takes from the front of one of them
+struct VolQueue {
+    std::deque<Req> box, tf;
+};
+
 size_t round_up(size_t n) { return (n + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -146,7 +153,8 @@ struct mg_server {
     std::mutex mu;
     std::condition_variable work_cv;   // worker: new requests or stop
     std::condition_variable done_cv;   // waiters: completions
-    std::deque<mg::Req> queue;
+    std::vector<mg::VolQueue> vq;   // per volume (reserved like vols)
+    int64_t queued = 0;             // requests in vq
     std::unordered_map<uint64_t, mg::Rec> recs;
     uint64_t next_ticket = 0;
     mg_server_stats stats{};
@@ -173,20 +181,29 @@ int frames_for(int C) {
     return 1;
 }
 
-// complete the requests of a finished slot (lock held by the caller)
+// copy a finished slot's results into the callers' buffers (worker thread,
+// lock not held: the slot's work and the callers' buffers are the worker's
+// until the requests are marked done, and a volume with work in flight is
+// not removed)
+void copy_results(const mg_server* sv, const Slot& sl) {
+    for (size_t i = 0; i < sl.work.size(); i++) {
+        const Req& q = sl.work[i];
+        if (!q.r.result) continue;
+        const Volume& v = sv->vols[q.r.volume];
+        const VolSlot& vs = sl.vols[q.r.volume];
+        if (q.r.kind == MG_REQ_BOX)
+            std::memcpy(q.r.result, static_cast<const char*>(vs.pin_out) + i * (size_t)v.g->S * 4, (size_t)v.g->S * 4);
+        else if (q.r.P > 0)
+            std::memcpy(q.r.result, static_cast<const char*>(vs.pin_render) + q.frame_off * v.C * sv->esize,
+                        (size_t)q.r.P * v.C * sv->esize);
+    }
+}
+
+// complete the requests of a finished slot (lock held by the caller; results
+// already copied when st is MG_OK)
 void finish_locked(mg_server* sv, Slot& sl, Clock::time_point now, mg_status st, const std::string& err) {
     for (size_t i = 0; i < sl.work.size(); i++) {
         const Req& q = sl.work[i];
-        const Volume& v = sv->vols[q.r.volume];
-        const VolSlot& vs = sl.vols[q.r.volume];
-        if (st == MG_OK && q.r.result) {
-            if (q.r.kind == MG_REQ_BOX)
-                std::memcpy(q.r.result, static_cast<const char*>(vs.pin_out) + i * (size_t)v.g->S * 4,
-                            (size_t)v.g->S * 4);
-            else if (q.r.P > 0)
-                std::memcpy(q.r.result, static_cast<const char*>(vs.pin_render) + q.frame_off * v.C * sv->esize,
-                            (size_t)q.r.P * v.C * sv->esize);
-        }
         Rec& rec = sv->recs[q.ticket];
         rec.state = kDone;
         rec.status = st;
@@ -200,46 +217,39 @@ void finish_locked(mg_server* sv, Slot& sl, Clock::time_point now, mg_status st,
     sl.busy = false;
 }
 
-// the next work item: a TF frame alone, or the queued boxes of the oldest
-// request's volume that fit one batch (the plain mode takes one box)
+// the next work item, for the oldest queued request: a TF frame with the
+// next queued frames of its volume (up to `frames`), or a box with the next
+// queued boxes of its volume, in order, while they fit one batch (the plain
+// mode takes one box).  Every take is from the front of a per-volume queue.
 std::vector<Req> take_locked(mg_server* sv) {
     std::vector<Req> w;
-    if (sv->queue.empty()) return w;
-    const Req& head = sv->queue.front();
-    if (head.r.kind == MG_REQ_TF) {
-        // the oldest frame and the next queued frames of its volume
-        const int v = head.r.volume;
-        const int F = sv->vols[v].frames;
-        int scanned = 0;
-        for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)w.size() < F && scanned < 4096; scanned++) {
-            if (it->r.kind == MG_REQ_TF && it->r.volume == v) {
-                w.push_back(*it);
-                it = sv->queue.erase(it);
-            } else {
-                ++it;
-            }
+    if (!sv->queued) return w;
+    std::deque<Req>* best = nullptr;
+    for (VolQueue& q : sv->vq) {
+        if (!q.box.empty() && (!best || q.box.front().ticket < best->front().ticket)) best = &q.box;
+        if (!q.tf.empty() && (!best || q.tf.front().ticket < best->front().ticket)) best = &q.tf;
+    }
+    std::deque<Req>& d = *best;
+    const Volume& vol = sv->vols[d.front().r.volume];
+    if (d.front().r.kind == MG_REQ_TF) {
+        while (!d.empty() && (int)w.size() < vol.frames) {
+            w.push_back(d.front());
+            d.pop_front();
         }
-        return w;
-    }
-    if (sv->o.plain) {
-        w.push_back(head);
-        sv->queue.pop_front();
-        return w;
-    }
-    const int v = head.r.volume;
-    const Volume& vol = sv->vols[v];
-    uint64_t blocks = 0, chunks = 0;
-    for (auto it = sv->queue.begin(); it != sv->queue.end() && (int64_t)w.size() < sv->o.max_batch;) {
-        if (it->r.kind == MG_REQ_BOX && it->r.volume == v && blocks + it->blocks <= vol.cap_blocks &&
-            chunks + it->chunks <= vol.cap_chunks) {
-            blocks += it->blocks;
-            chunks += it->chunks;
-            w.push_back(*it);
-            it = sv->queue.erase(it);
-        } else {
-            ++it;
+    } else if (sv->o.plain) {
+        w.push_back(d.front());
+        d.pop_front();
+    } else {
+        uint64_t blocks = 0, chunks = 0;
+        while (!d.empty() && (int64_t)w.size() < sv->o.max_batch && blocks + d.front().blocks <= vol.cap_blocks &&
+               chunks + d.front().chunks <= vol.cap_chunks) {
+            blocks += d.front().blocks;
+            chunks += d.front().chunks;
+            w.push_back(d.front());
+            d.pop_front();
         }
     }
+    sv->queued -= (int64_t)w.size();
     return w;
 }
 
@@ -336,7 +346,13 @@ void worker_loop(mg_server* sv) {
                     err = mg_last_error();
                 }
             }
-            finish_locked(sv, sl, Clock::now(), st, err);
+            const Clock::time_point now = Clock::now();
+            if (st == MG_OK) {
+                lk.unlock();
+                copy_results(sv, sl);
+                lk.lock();
+            }
+            finish_locked(sv, sl, now, st, err);
             progressed = true;
         }
         if (progressed) sv->done_cv.notify_all();
@@ -378,14 +394,18 @@ void worker_loop(mg_server* sv) {
         }
     }
     // stopping: what is still queued is cancelled
-    for (const Req& q : sv->queue) {
-        Rec& rec = sv->recs[q.ticket];
-        rec.state = kDone;
-        rec.status = MG_ERR_CANCELLED;
-        rec.error = "server stopped before the request was launched";
-        sv->stats.cancelled++;
-    }
-    sv->queue.clear();
+    for (VolQueue& vq : sv->vq)
+        for (std::deque<Req>* d : {&vq.box, &vq.tf}) {
+            for (const Req& q : *d) {
+                Rec& rec = sv->recs[q.ticket];
+                rec.state = kDone;
+                rec.status = MG_ERR_CANCELLED;
+                rec.error = "server stopped before the request was launched";
+                sv->stats.cancelled++;
+            }
+            d->clear();
+        }
+    sv->queued = 0;
     sv->done_cv.notify_all();
 }
 
@@ -426,7 +446,9 @@ mg_status submit(mg_server* sv, const mg_request& r, Clock::time_point arrival, 
         if (sv->stop.load()) return fail(MG_ERR_INVALID_ARG, "server is stopping");
         q.ticket = sv->next_ticket++;
         sv->recs.emplace(q.ticket, Rec{});
-        sv->queue.push_back(q);
+        VolQueue& vq = sv->vq[r.volume];
+        (r.kind == MG_REQ_BOX ? vq.box : vq.tf).push_back(q);
+        sv->queued++;
     }
     sv->work_cv.notify_one();
     if (ticket) *ticket = q.ticket;
@@ -470,6 +492,7 @@ MG_API mg_status mg_server_create(const mg_server_opts* opts, mg_server** out) {
     MG_CUDA(cudaGetDevice(&sv->device));
     sv->slots.resize((size_t)o.slots);
     sv->vols.reserve(kMaxVolumes);
+    sv->vq.reserve(kMaxVolumes);
     for (Slot& sl : sv->slots) sl.vols.reserve(kMaxVolumes);
     mg_status st = MG_OK;
     for (Slot& sl : sv->slots) {
@@ -590,6 +613,7 @@ MG_API mg_status mg_server_add_volume(mg_server* sv, mg_graph* g, int C, int* vo
         std::lock_guard<std::mutex> lk(sv->mu);
         for (size_t k = 0; k < sv->slots.size(); k++) sv->slots[k].vols.push_back(std::move(made[k]));
         sv->vols.push_back(v);
+        sv->vq.emplace_back();
         sv->budget_used += need;
         *volume = (int)sv->vols.size() - 1;
     }
@@ -605,24 +629,22 @@ MG_API mg_status mg_server_remove_volume(mg_server* sv, int volume, double timeo
     v.removed = true;   // submissions now fail
     if (!sv->started) {
         // nothing runs before the start: its queued requests are cancelled
-        for (auto it = sv->queue.begin(); it != sv->queue.end();) {
-            if (it->r.volume == volume) {
-                Rec& rec = sv->recs[it->ticket];
+        for (std::deque<Req>* d : {&sv->vq[volume].box, &sv->vq[volume].tf}) {
+            for (const Req& q : *d) {
+                Rec& rec = sv->recs[q.ticket];
                 rec.state = kDone;
                 rec.status = MG_ERR_CANCELLED;
                 rec.error = "volume removed before the request was launched";
                 sv->stats.cancelled++;
-                it = sv->queue.erase(it);
-            } else {
-                ++it;
             }
+            sv->queued -= (int64_t)d->size();
+            d->clear();
         }
         sv->done_cv.notify_all();
     }
     // wait until no queued or running work refers to the volume
     auto busy = [&]() {
-        for (const Req& q : sv->queue)
-            if (q.r.volume == volume) return true;
+        if (!sv->vq[volume].box.empty() || !sv->vq[volume].tf.empty()) return true;
         for (const Slot& sl : sv->slots)
             if (sl.busy && !sl.work.empty() && sl.work[0].r.volume == volume) return true;
         return false;
@@ -665,17 +687,20 @@ MG_API mg_status mg_server_submit(mg_server* sv, const mg_request* r, uint64_t* 
 MG_API mg_status mg_server_cancel(mg_server* sv, uint64_t ticket) {
     if (!sv) return fail(MG_ERR_INVALID_ARG, "server is NULL");
     std::lock_guard<std::mutex> lk(sv->mu);
-    for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
-        if (it->ticket != ticket) continue;
-        Rec& rec = sv->recs[ticket];
-        rec.state = kDone;
-        rec.status = MG_ERR_CANCELLED;
-        rec.error = "request cancelled";
-        sv->queue.erase(it);
-        sv->stats.cancelled++;
-        sv->done_cv.notify_all();
-        return MG_OK;
-    }
+    for (VolQueue& vq : sv->vq)
+        for (std::deque<Req>* d : {&vq.box, &vq.tf})
+            for (auto it = d->begin(); it != d->end(); ++it) {
+                if (it->ticket != ticket) continue;
+                Rec& rec = sv->recs[ticket];
+                rec.state = kDone;
+                rec.status = MG_ERR_CANCELLED;
+                rec.error = "request cancelled";
+                d->erase(it);
+                sv->queued--;
+                sv->stats.cancelled++;
+                sv->done_cv.notify_all();
+                return MG_OK;
+            }
     return fail(MG_ERR_INVALID_ARG, "request is not queued (already launched, done or unknown)");
 }
 
