@@ -343,9 +343,9 @@ MG_API mg_status mg_render_lookup_multi(const mg_graph *g, const void *vals, int
  * opacity exactly 0, the lattice samples inside the largest such voxel
  * shrunk by 3 * 2^m on every side (the reach of the interpolation), and
  * before the LOD changes, are skipped.  Each would add exactly nothing, so
- * the image equals the one without skipping.  Opacities must be >= 0 (a
- * voxel of opacity 0 then has only zero voxels below it, which lets a ray
- * reuse its last climb while it stays inside the same voxel).
+ * the image equals the one without skipping.  The climbs read a bit mask
+ * of the voxels of levels >= 2 whose opacity is non-zero, built first in the
+ * graph's per-stream scratch (one pass over those levels' IDs).
  * Decisions (lattice, level, skips, termination) are taken in fp32 with one
  * rounding per operation.
  * vals: N x 4 fp32 node values (mg_propagate_tf, storage MG_F32), 16-byte

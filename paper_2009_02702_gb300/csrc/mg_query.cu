@@ -1496,9 +1496,9 @@ __global__ void __launch_bounds__(256) query_plain_kernel(MainArgs A, const int3
 // voxel of the clipped box counted.  Work items are slabs of consecutive rows
 // (x runs) of one box, about kNaiveSlab voxels each, taken from a global
 // ticket by persistent CTAs; each CTA counts its slab into a shared histogram
-// and adds it to the box's row.  A warp reads a row as 16-byte vectors
-// (8 uint16 or 4 uint32 IDs) from the vector holding its first voxel on,
-// masking the IDs outside the row, and keeps one run per lane.
+// and adds it to the box's row.  Rows are read as 16-byte vectors (8 uint16
+// or 4 uint32 IDs) from the vector holding their first voxel on, masking the
+// IDs outside the row; every thread keeps one run.
 constexpr uint32_t kNaiveSlab = 1u << 16;
 
 __device__ __forceinline__ void naive_extent(const int32_t* b, const Geom& G, int64_t& dx, int64_t& dy, int64_t& dz) {
@@ -1536,7 +1536,6 @@ __global__ void __launch_bounds__(256) query_naive_kernel(Geom G, const T* __res
     __shared__ unsigned long long s_item;
     uint32_t* h = reinterpret_cast<uint32_t*>(smem);
     const uint32_t S = G.S;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     constexpr int E = 16 / (int)sizeof(T);   // IDs per 16-byte vector
     const unsigned long long total = item_off[Q];
     for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) h[i] = 0;
@@ -1560,67 +1559,72 @@ __global__ void __launch_bounds__(256) query_naive_kernel(Geom G, const T* __res
         const int64_t rows_per = max((int64_t)1, (int64_t)kNaiveSlab / dx);
         const int64_t r0 = (int64_t)(w - item_off[q]) * rows_per, r1 = min(r0 + rows_per, dy * dz);
         const int64_t nx = G.dims[0][0], ny = G.dims[0][1], V0 = nx * ny * G.dims[0][2];
-        // a warp per row of the slab (row r = (y, z) of the box, advanced
-        // without divisions); lanes read 16-byte vectors of the row, four
-        // per lane in flight
-        int64_t ry = (r0 + warp) % dy, rz = (r0 + warp) / dy;
-        for (int64_t r = r0 + warp; r < r1; r += nw) {
-            const int64_t e0 = ((int64_t)(b[2] + rz) * ny + b[1] + ry) * nx + b[0], e1 = e0 + dx;
-            uint32_t rid = kNone, rcnt = 0;
-            for (int64_t v0 = e0 / E; v0 * E < e1; v0 += 128) {
-                uint4 u[4];
+        // the slab as one flat stream of (row, vector) pairs, vpr vector
+        // slots per row (the most a row of dx IDs can touch), taken by the
+        // CTA's threads in turn, four per thread in flight: long rows are
+        // read by consecutive lanes, short rows by one lane each, so every
+        // lane has loads in flight whatever the box's shape
+        const uint32_t vpr = (uint32_t)((dx + E - 1) / E + 1);
+        const uint32_t nf = (uint32_t)(r1 - r0) * vpr;   // <= 2^16 / E + 2^17, or one row of a wider box
+        uint32_t rid = kNone, rcnt = 0;
+        for (uint32_t f0 = 0; f0 < nf; f0 += 4 * blockDim.x) {
+            uint4 u[4];
+            int64_t e0s[4], p0s[4];
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int64_t v = v0 + lane + 32 * j;
-                    u[j] = make_uint4(0u, 0u, 0u, 0u);
-                    if (v * E >= e1) continue;
-                    if ((v + 1) * E <= V0) {
-                        u[j] = __ldg(reinterpret_cast<const uint4*>(ids0) + v);
-                    } else {
-                        // the volume's last vector, cut at its end
-                        T* x = reinterpret_cast<T*>(&u[j]);
-                        for (int k = 0; k < E && v * E + k < V0; k++) x[k] = __ldg(ids0 + v * E + k);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int64_t p0 = (v0 + lane + 32 * j) * E;
-                    if (p0 >= e1) continue;
-                    const T* x = reinterpret_cast<const T*>(&u[j]);
-                    bool uni = p0 >= e0 && p0 + E <= e1;
-#pragma unroll
-                    for (int k = 1; k < E; k++) uni = uni && x[k] == x[0];
-                    if (uni) {
-                        if (rcnt && rid == (uint32_t)x[0]) {
-                            rcnt += E;
-                        } else {
-                            if (rcnt) atomicAdd(h + rid, rcnt);
-                            rid = (uint32_t)x[0];
-                            rcnt = E;
-                        }
-                        continue;
-                    }
-#pragma unroll
-                    for (int k = 0; k < E; k++) {
-                        if (p0 + k < e0 || p0 + k >= e1) continue;
-                        const uint32_t id = (uint32_t)x[k];
-                        if (rcnt && id == rid) {
-                            rcnt++;
-                        } else {
-                            if (rcnt) atomicAdd(h + rid, rcnt);
-                            rid = id;
-                            rcnt = 1;
-                        }
-                    }
+            for (int j = 0; j < 4; j++) {
+                const uint32_t f = f0 + threadIdx.x + j * blockDim.x;
+                u[j] = make_uint4(0u, 0u, 0u, 0u);
+                p0s[j] = -1;
+                e0s[j] = 0;
+                if (f >= nf) continue;
+                const uint32_t row = f / vpr, vi = f - row * vpr;
+                const int64_t r = r0 + row, rz = r / dy, ry = r - rz * dy;
+                const int64_t e0 = ((int64_t)(b[2] + rz) * ny + b[1] + ry) * nx + b[0];
+                const int64_t v = e0 / E + vi;
+                if (v * E >= e0 + dx) continue;
+                e0s[j] = e0;
+                p0s[j] = v * E;
+                if ((v + 1) * E <= V0) {
+                    u[j] = __ldg(reinterpret_cast<const uint4*>(ids0) + v);
+                } else {
+                    // the volume's last vector, cut at its end
+                    T* x = reinterpret_cast<T*>(&u[j]);
+                    for (int k = 0; k < E && v * E + k < V0; k++) x[k] = __ldg(ids0 + v * E + k);
                 }
             }
-            if (rcnt) atomicAdd(h + rid, rcnt);
-            ry += nw;
-            while (ry >= dy) {
-                ry -= dy;
-                rz++;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int64_t p0 = p0s[j], e0 = e0s[j], e1 = e0 + dx;
+                if (p0 < 0) continue;
+                const T* x = reinterpret_cast<const T*>(&u[j]);
+                bool uni = p0 >= e0 && p0 + E <= e1;
+#pragma unroll
+                for (int k = 1; k < E; k++) uni = uni && x[k] == x[0];
+                if (uni) {
+                    if (rcnt && rid == (uint32_t)x[0]) {
+                        rcnt += E;
+                    } else {
+                        if (rcnt) atomicAdd(h + rid, rcnt);
+                        rid = (uint32_t)x[0];
+                        rcnt = E;
+                    }
+                    continue;
+                }
+#pragma unroll
+                for (int k = 0; k < E; k++) {
+                    if (p0 + k < e0 || p0 + k >= e1) continue;
+                    const uint32_t id = (uint32_t)x[k];
+                    if (rcnt && id == rid) {
+                        rcnt++;
+                    } else {
+                        if (rcnt) atomicAdd(h + rid, rcnt);
+                        rid = id;
+                        rcnt = 1;
+                    }
+                }
             }
         }
+        if (rcnt) atomicAdd(h + rid, rcnt);
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
             const uint32_t c = h[i];

@@ -219,6 +219,18 @@ __device__ __forceinline__ uint32_t march_node(const MarchArgs& A, int l, int64_
     return __ldg(A.mip + A.G.off[l] + idx);
 }
 
+// voxel of level l holding coordinate x of axis c (clamped to the level)
+__device__ __forceinline__ int64_t march_voxel(const MarchArgs& A, int l, float x, int c) {
+    int64_t v = (int64_t)floorf(x);
+    v = v < 0 ? 0 : v;
+    v >>= l;
+    return v > A.G.dims[l][c] - 1 ? A.G.dims[l][c] - 1 : v;
+}
+
+__device__ __forceinline__ int64_t march_index(const MarchArgs& A, int l, const int64_t (&b)[3]) {
+    return (b[2] * A.G.dims[l][1] + b[1]) * A.G.dims[l][0] + b[0];
+}
+
 __device__ __forceinline__ float rn_lerp(float a, float b, float f) { return __fadd_rn(a, __fmul_rn(f, __fsub_rn(b, a))); }
 
 __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float f) {
@@ -250,6 +262,8 @@ __device__ float4 march_tri(const MarchArgs& A, int l, const float (&p)[3]) {
     const float4 x01 = lerp4(v[4], v[5], f[0]), x11 = lerp4(v[6], v[7], f[0]);
     return lerp4(lerp4(x00, x10, f[1]), lerp4(x01, x11, f[1]), f[2]);
 }
+
+constexpr int kPreload = 1;   // climb levels whose bits are loaded up front (1 measured best of 1, 2, 3, 5)
 
 __global__ void __launch_bounds__(128) march_kernel(MarchArgs A) {
     const mg_camera& cam = A.cam;
@@ -283,14 +297,6 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs A) {
     const float ts = tmin > 0.0f ? tmin : 0.0f;
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Aacc = 0.0f;
     int32_t taken = 0;
-    // Climbs are not repeated while their answer cannot change.  (hl, hv): the
-    // last voxel of level hl the climb found non-zero; a climb that reaches it
-    // stops there.  (zm, zj, zb): the last climb from level zm + 2 ended with
-    // the zero voxel zb of level zj; opacities are >= 0, so every voxel below
-    // it is zero too and its parent is the same, and a climb from the same
-    // level anywhere inside it ends the same way.
-    int hl = -1, zm = -1, zj = -1;
-    int64_t hv[3] = {0, 0, 0}, zb[3] = {0, 0, 0};
     if (!miss && tmax > ts) {
         int64_t k = 0;
         while (k < cam.max_steps) {
@@ -307,51 +313,41 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs A) {
             float p[3];
 #pragma unroll
             for (int c = 0; c < 3; c++) p[c] = __fadd_rn(cam.eye[c], __fmul_rn(t, d[c]));
-            if (A.opac) {
-                int jz = -1;
-                int64_t bz[3] = {0, 0, 0};
-                if (zj >= 0 && zm == m) {
-                    bool same = true;
+            // the occupancy bits of the climb's first kPreload levels are
+            // loaded before the sample's own values, so that these loads and
+            // the sample's two dependent ones overlap; most climbs stop
+            // within them
+            uint32_t pre = 0;   // bit j: level m + 2 + j occupied
+            const bool climb = A.occ && m + 2 < L;
+            if (climb) {
 #pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        int64_t v = (int64_t)floorf(p[c]);
-                        v = v < 0 ? 0 : v;
-                        v >>= zj;
-                        v = v > A.G.dims[zj][c] - 1 ? A.G.dims[zj][c] - 1 : v;
-                        same = same && v == zb[c];
-                    }
-                    if (same) {
-                        jz = zj;
-#pragma unroll
-                        for (int c = 0; c < 3; c++) bz[c] = zb[c];
-                    }
-                }
-                for (int jl = jz >= 0 ? L : m + 2; jl < L; jl++) {
+                for (int j = 0; j < kPreload; j++) {
+                    const int jl = m + 2 + j;
+                    if (jl >= L) break;
                     int64_t b[3];
 #pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        int64_t v = (int64_t)floorf(p[c]);
-                        v = v < 0 ? 0 : v;
-                        v >>= jl;
-                        b[c] = v > A.G.dims[jl][c] - 1 ? A.G.dims[jl][c] - 1 : v;
-                    }
-                    if (jl == hl && b[0] == hv[0] && b[1] == hv[1] && b[2] == hv[2]) break;
-                    const int64_t vi = (b[2] * A.G.dims[jl][1] + b[1]) * A.G.dims[jl][0] + b[0];
-                    if ((__ldg(A.occ + A.occ_off[jl] + (vi >> 5)) >> (vi & 31)) & 1u) {
-                        hl = jl;
+                    for (int c = 0; c < 3; c++) b[c] = march_voxel(A, jl, p[c], c);
+                    const int64_t vi = march_index(A, jl, b);
+                    pre |= ((__ldg(A.occ + A.occ_off[jl] + (vi >> 5)) >> (vi & 31)) & 1u) << j;
+                }
+            }
+            float4 s = march_tri(A, m, p);
+            if (fr > 0.0f) s = lerp4(s, march_tri(A, m + 1, p), fr);
+            if (climb) {
+                int jz = -1;
+                int64_t bz[3] = {0, 0, 0};
+                for (int jl = m + 2; jl < L; jl++) {
+                    int64_t b[3];
 #pragma unroll
-                        for (int c = 0; c < 3; c++) hv[c] = b[c];
-                        break;
-                    }
+                    for (int c = 0; c < 3; c++) b[c] = march_voxel(A, jl, p[c], c);
+                    const int64_t vi = march_index(A, jl, b);
+                    const bool occ = jl < m + 2 + kPreload
+                                         ? ((pre >> (jl - m - 2)) & 1u)
+                                         : ((__ldg(A.occ + A.occ_off[jl] + (vi >> 5)) >> (vi & 31)) & 1u);
+                    if (occ) break;
                     jz = jl;
 #pragma unroll
                     for (int c = 0; c < 3; c++) bz[c] = b[c];
-                }
-                if (jz >= 0 && (jz != zj || zm != m)) {
-                    zm = m;
-                    zj = jz;
-#pragma unroll
-                    for (int c = 0; c < 3; c++) zb[c] = bz[c];
                 }
                 if (jz >= 0) {
                     const float size = ldexpf(1.0f, jz), gap = ldexpf(3.0f, m);
@@ -382,8 +378,6 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs A) {
                     }
                 }
             }
-            float4 s = march_tri(A, m, p);
-            if (fr > 0.0f) s = lerp4(s, march_tri(A, m + 1, p), fr);
             float q = __fsub_rn(1.0f, s.w);
             for (int e = 0; e < m; e++) q = __fmul_rn(q, q);
             const float ap = __fsub_rn(1.0f, q);
