@@ -1122,7 +1122,11 @@ __device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Q
 // its own consecutive cubes; a finished run of a source is added to the
 // shared histogram, one of an internal node (levels >= 1) is queued for the
 // warp's pushes.
-template <bool FP, typename AT>
+// RN: units per lane per step in windows without 32-byte units (2 in the
+// per-warp kernel, whose registers are capped for occupancy; 4 in the CTA
+// kernel, which has registers to spare: measured 4.67 -> 4.34 ms on the
+// cylinder batch, while the per-warp kernel spills at 4)
+template <bool FP, typename AT, int RN>
 __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& H, const Queue& Qu, uint32_t w0,
                                              uint32_t w1, uint64_t b, uint64_t b1, uint32_t ncube) {
     const int lane = threadIdx.x & 31;
@@ -1190,8 +1194,8 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t excl = incl - units;
         // R units per lane per step: one (16- or 32-byte) where the window
-        // has 32-byte units, else two, so scalar-heavy windows keep two loads
-        // in flight per lane
+        // has 32-byte units, else RN, so scalar-heavy windows keep several
+        // loads in flight per lane
         auto run_units = [&](auto rc) {
             constexpr int R = decltype(rc)::value;
             for (uint32_t u0 = 0; u0 < total; u0 += 32u * R) {
@@ -1300,7 +1304,7 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
             }
         };
         if (__any_sync(0xffffffffu, wide)) run_units(std::integral_constant<int, 1>{});
-        else run_units(std::integral_constant<int, 2>{});
+        else run_units(std::integral_constant<int, RN>{});
         const uint32_t st31 = __shfl_sync(0xffffffffu, st, 31);
         if (bb + 31 >= b1 || st31 >= w1) break;
     }
@@ -1346,7 +1350,7 @@ __global__ void __launch_bounds__(256, 5) query_warp_kernel(MainArgs A) {
         const uint32_t ncube = (uint32_t)A.ncube[q];
         const uint32_t c0 = (uint32_t)(c - A.chunk_off[q]) * A.chunk;
         const uint32_t c1 = min(c0 + A.chunk, ncube);
-        process_span<FP, AT>(A, H, Qu, c0, c1, __ldg(A.chunk_b + c), A.blk_off[q + 1], ncube);
+        process_span<FP, AT, 2>(A, H, Qu, c0, c1, __ldg(A.chunk_b + c), A.blk_off[q + 1], ncube);
         drain<FP, AT>(A.P, H, Qu, true);
         for (uint32_t s = lane; s < S; s += 32) {
             const uint32_t v = H.h[s];
@@ -1429,7 +1433,7 @@ __global__ void __launch_bounds__(512) query_batched_kernel(MainArgs A) {
             }
             b = __shfl_sync(0xffffffffu, b, 0);
             bhint = b;
-            process_span<FP, AT>(A, H, Qu, w0, w1, b, b1, ncube);
+            process_span<FP, AT, 4>(A, H, Qu, w0, w1, b, b1, ncube);
         }
         drain<FP, AT>(A.P, H, Qu, true);
         __syncthreads();
