@@ -1314,11 +1314,19 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
 
 // Few segments: every warp owns a histogram in shared memory and takes whole
 // chunks from the global ticket, so warps never wait for each other.
-// At most 51 registers (5 CTAs of 256 threads per SM): the loop is bound by
-// load latency, and 40 resident warps per SM beat 32 at 63 registers even
-// with a few spilled values (measured: 0.40 vs 0.42 ms on the 10,000-box batch).
-template <bool FP, typename AT>
-__global__ void __launch_bounds__(256, 5) query_warp_kernel(MainArgs A) {
+// Register budget by CTA size NT: 256 threads, at most 51 registers (5 CTAs
+// per SM): the loop is bound by load latency, and 40 resident warps per SM
+// beat 32 at 63 registers even with a few spilled values (0.40 vs 0.42 ms on
+// the 10,000-box batch).  128 threads, at most 56 registers (9 CTAs): where
+// shared memory holds 9-10 CTAs of 4 warps anyway (1,182 segments), fewer
+// spills beat the tenth CTA (7.04 vs 7.25 ms on the 100,000-box batch; 64
+// registers and 8 CTAs: 7.41 ms).
+template <int NT> struct WarpKernelBounds;
+template <> struct WarpKernelBounds<128> { static constexpr int min_ctas = 9; };
+template <> struct WarpKernelBounds<256> { static constexpr int min_ctas = 5; };
+
+template <bool FP, typename AT, int NT>
+__global__ void __launch_bounds__(NT, WarpKernelBounds<NT>::min_ctas) query_warp_kernel(MainArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t S = A.P.S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1870,7 +1878,8 @@ mg_status launch_main(const mg_graph* g, const MainArgs& A, const mg_query_opts&
     const size_t hist_w = (size_t)g->S * 4 * (FP ? 2 : 1);
     const bool warp_mode =
         g->S <= kWarpHistMax && threads <= 256 && (hist_w + queue_bytes(kQueueShort)) * warps <= 96 * 1024;
-    auto k = warp_mode ? query_warp_kernel<FP, AT> : query_batched_kernel<FP, AT>;
+    auto k = !warp_mode ? query_batched_kernel<FP, AT>
+             : threads <= 128 ? query_warp_kernel<FP, AT, 128> : query_warp_kernel<FP, AT, 256>;
     auto smem_for = [&](uint32_t cap) {
         return warp_mode ? (hist_w + queue_bytes(cap)) * warps : smem + warps * queue_bytes(cap);
     };
