@@ -1284,34 +1284,31 @@ __device__ __forceinline__ void process_span(const MainArgs& A, const Hist<FP>& 
                             }
                         }
                     } else if (k == 2 || k == 4) {
-                        const uint32_t pr = rid * 0x10001u;
-                        uint32_t diff = (x.x ^ pr) | (x.y ^ pr) | (x.z ^ pr) | (x.w ^ pr);
-                        if (k == 4) diff |= (y.x ^ pr) | (y.y ^ pr) | (y.z ^ pr) | (y.w ^ pr);
-                        if (rcnt && rl == 0 && diff == 0u) {
-                            rcnt += k == 2 ? 8 : 16;
-                        } else {
-                            // a uniform vector starts a new run; a mixed one (a
-                            // segment boundary inside) adds each ID to its bin at
-                            // once: level-0 IDs are bins, and the adds are
-                            // independent where a run would chain them
-                            const uint32_t a = x.x & 0xffffu, pa = a * 0x10001u;
-                            uint32_t d2 = (x.x ^ pa) | (x.y ^ pa) | (x.z ^ pa) | (x.w ^ pa);
-                            if (k == 4) d2 |= (y.x ^ pa) | (y.y ^ pa) | (y.z ^ pa) | (y.w ^ pa);
-                            if (d2 == 0u) {
+                        // uniform vector (every ID equals the first): it extends
+                        // the lane's run or starts a new one.  Mixed vector (a
+                        // segment boundary inside): each ID is added to its bin
+                        // at once -- level-0 IDs are bins, and the adds are
+                        // independent where a run would chain them
+                        const uint32_t a = x.x & 0xffffu, pa = a * 0x10001u;
+                        uint32_t d = (x.x ^ pa) | (x.y ^ pa) | (x.z ^ pa) | (x.w ^ pa);
+                        if (k == 4) d |= (y.x ^ pa) | (y.y ^ pa) | (y.z ^ pa) | (y.w ^ pa);
+                        if (d == 0u) {
+                            if (rcnt && rl == 0 && rid == a) {
+                                rcnt += k == 2 ? 8 : 16;
+                            } else {
                                 finish();
                                 rid = a;
                                 rl = 0;
                                 rcnt = k == 2 ? 8 : 16;
-                            } else {
-                                const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+                            }
+                        } else {
+                            const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-                                for (int q = 0; q < 8; q++) H.add_int((w4[q >> 1] >> (16 * (q & 1))) & 0xffffu, 1u);
-                                if (k == 4) {
-                                    const uint32_t x4[4] = {y.x, y.y, y.z, y.w};
+                            for (int q = 0; q < 8; q++) H.add_int((w4[q >> 1] >> (16 * (q & 1))) & 0xffffu, 1u);
+                            if (k == 4) {
+                                const uint32_t x4[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
-                                    for (int q = 0; q < 8; q++)
-                                        H.add_int((x4[q >> 1] >> (16 * (q & 1))) & 0xffffu, 1u);
-                                }
+                                for (int q = 0; q < 8; q++) H.add_int((x4[q >> 1] >> (16 * (q & 1))) & 0xffffu, 1u);
                             }
                         }
                     }
