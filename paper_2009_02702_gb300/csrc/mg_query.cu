@@ -1028,10 +1028,12 @@ __device__ __forceinline__ void clear_queue(const Queue& Qu) {
     __syncwarp();
 }
 
-// push one (node, weight) per lane where `valid`.  With the mixture table the
-// rows of all of them are flattened: entry e goes to lane e % 32, which finds
-// its row by a binary search over the inclusive sums of the row lengths;
-// nodes without a row (and 16-bit weights) walk their lerp trees.
+// push one (node, weight) per lane where `valid`.  With the mixture table each
+// lane adds the first two entries of its node's row itself (rows average about
+// two entries: two independent loads right after the row header); the rest of
+// longer rows is flattened: entry e goes to lane e % 32, which finds its row by
+// a binary search over the inclusive sums of the remaining lengths.  Nodes
+// without a row (and 16-bit weights) walk their lerp trees.
 template <bool FP, typename AT>
 __device__ __forceinline__ void push_lanes(const PushArgs& P, const Hist<FP>& H, bool valid, uint32_t n,
                                            uint32_t w) {
@@ -1046,6 +1048,19 @@ __device__ __forceinline__ void push_lanes(const PushArgs& P, const Hist<FP>& H,
             }
         }
         __syncwarp();
+        if (len) {
+            const uint2 e0 = __ldg(P.lut + off);
+            const uint2 e1 = len > 1 ? __ldg(P.lut + off + 1) : make_uint2(0u, 0u);
+            H.add_int(e0.x, k * e0.y);
+            if (len > 1) H.add_int(e1.x, k * e1.y);
+            const uint32_t h = len > 1 ? 2u : 1u;
+            off += h;
+            len -= h;
+        }
+        if (!__any_sync(0xffffffffu, len != 0u)) {
+            __syncwarp();
+            return;
+        }
         uint32_t incl = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
