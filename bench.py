@@ -462,23 +462,26 @@ def end_to_end(mg, g, boxes_h, tf_h, smp_h, storage, Q, S, P, esz, args, dev, st
                qkw):
     """The step through the public API with host buffers: every step copies its
     boxes, TF and samples in from pinned memory and its histograms and colours
-    out.  Pipelined: three lanes take steps in turn, so a step's copies overlap
-    the other lanes' kernels.  Serial: one lane, each step on its own with the
-    L2 flushed before it (the footing of `value`)."""
+    out.  Pipelined: a copy-in stream, a query stream (the steps' query
+    batches in step order, so no two share the GPU), a frame stream beside it
+    (propagation and lookup, as in `value`) and a copy-out stream, over two
+    slots of device buffers, ordered by events, so a step's copies overlap
+    its neighbours' kernels.
+    Serial: one slot, each step on its own with the L2 flushed before it (the
+    footing of `value`)."""
     import torch
     from paper_2009_02702_gb300 import mg as _mg
     dt = _mg._DTYPES[storage][1]
     boxes_p = torch.from_numpy(boxes_h).pin_memory()
     tf_p = torch.from_numpy(tf_h).pin_memory()
     smp_p = torch.from_numpy(smp_h).pin_memory()
+    cin, cq, cf, cout = (torch.cuda.Stream(dev) for _ in range(4))
 
-    class Lane:
-        """Boxes -> queries -> histograms on its query stream, TF and samples ->
-        propagation -> lookup -> colours on its frame stream, each with its own
-        buffers (and query plan, whose buffers a run owns until it ends)."""
+    class Slot:
+        """Device buffers of one step in flight (and its own query plan, whose
+        buffers a run owns until it ends), with pinned host results."""
 
         def __init__(self):
-            self.qs, self.fs = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
             self.boxes = torch.empty((Q, 6), dtype=torch.int32, device=dev)
             self.tf = torch.empty((S, 4), dtype=torch.float32, device=dev)
             self.smp = torch.empty((P, 4), dtype=torch.float32, device=dev)
@@ -489,82 +492,92 @@ def end_to_end(mg, g, boxes_h, tf_h, smp_h, storage, Q, S, P, esz, args, dev, st
             self.look_p = torch.empty((P, 4), dtype=dt).pin_memory()
             self.plan = mg.QueryPlan(g, max_Q=Q, chunk_cubes=args.chunk,
                                      block_threads=args.threads) if use_plan else None
+            self.ev_in, self.ev_q, self.ev_f, self.ev_out = (torch.cuda.Event() for _ in range(4))
+            self.used = False
 
         def step(self):
-            with torch.cuda.stream(self.fs):
+            # inputs: once this slot's previous kernels have read them
+            if self.used:
+                cin.wait_event(self.ev_q)
+                cin.wait_event(self.ev_f)
+            with torch.cuda.stream(cin):
+                self.boxes.copy_(boxes_p, non_blocking=True)
                 self.tf.copy_(tf_p, non_blocking=True)
                 self.smp.copy_(smp_p, non_blocking=True)
-            mg.mg_propagate_tf(g, self.tf, storage=storage, out=self.vals, stream=self.fs)
-            mg.mg_render_lookup(g, self.vals, self.smp, out=self.look, stream=self.fs)
-            with torch.cuda.stream(self.fs):
-                self.look_p.copy_(self.look, non_blocking=True)
-            with torch.cuda.stream(self.qs):
-                self.boxes.copy_(boxes_p, non_blocking=True)
+            self.ev_in.record(cin)
+            # kernels: after the inputs, and once the previous results are out
+            for st_ in (cq, cf):
+                st_.wait_event(self.ev_in)
+                if self.used:
+                    st_.wait_event(self.ev_out)
             if self.plan is not None:
-                self.plan.run(self.boxes, out=self.hist, stream=self.qs)
+                self.plan.run(self.boxes, out=self.hist, stream=cq)
             else:
-                mg.mg_query_boxes(g, self.boxes, out=self.hist, stream=self.qs, **qkw)
-            with torch.cuda.stream(self.qs):
+                mg.mg_query_boxes(g, self.boxes, out=self.hist, stream=cq, **qkw)
+            self.ev_q.record(cq)
+            mg.mg_propagate_tf(g, self.tf, storage=storage, out=self.vals, stream=cf)
+            mg.mg_render_lookup(g, self.vals, self.smp, out=self.look, stream=cf)
+            self.ev_f.record(cf)
+            # results out
+            cout.wait_event(self.ev_q)
+            cout.wait_event(self.ev_f)
+            with torch.cuda.stream(cout):
                 self.hist_p.copy_(self.hist, non_blocking=True)
-
-        def streams(self):
-            return (self.qs, self.fs)
+                self.look_p.copy_(self.look, non_blocking=True)
+            self.ev_out.record(cout)
+            self.used = True
 
         def close(self):
             if self.plan is not None:
                 self.plan.close()
 
-    def window(lanes, steps, flushed):
+    def window(slots, steps, flushed):
         e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e_start.record(stream)
-        for ln in lanes:
-            for st_ in ln.streams():
-                st_.wait_event(e_start)
+        for st_ in (cin, cq, cf, cout):
+            st_.wait_event(e_start)
         ms = 0.0
         for k in range(steps):
-            ln = lanes[k % len(lanes)]
+            sl = slots[k % len(slots)]
             if flushed:
                 # each step alone: flush the L2, then time from its first copy to its last
                 flush.zero_()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                for st_ in ln.streams():
+                for st_ in (cin, cq, cf, cout):
                     st_.wait_event(a)
-            ln.step()
+            sl.step()
             if flushed:
-                for st_ in ln.streams():
-                    ev_ = torch.cuda.Event()
-                    ev_.record(st_)
-                    stream.wait_event(ev_)
+                stream.wait_event(sl.ev_out)
                 b.record(stream)
                 torch.cuda.synchronize()
                 ms += a.elapsed_time(b)
-        for ln in lanes:
-            for st_ in ln.streams():
-                ev_ = torch.cuda.Event()
-                ev_.record(st_)
-                stream.wait_event(ev_)
+        for st_ in (cin, cq, cf, cout):
+            ev_ = torch.cuda.Event()
+            ev_.record(st_)
+            stream.wait_event(ev_)
         e_end.record(stream)
         torch.cuda.synchronize()
         return ms if flushed else float(e_start.elapsed_time(e_end))
 
-    lanes = [Lane() for _ in range(3)]
-    for k in range(6):
-        lanes[k % 3].step()
+    slots = [Slot() for _ in range(2)]
+    for k in range(4):
+        slots[k % 2].step()
     torch.cuda.synchronize()
-    e_ms = max_over_ranks(window(lanes, args.steps, False), world, dev)
-    s_ms = max_over_ranks(window(lanes[:1], args.steps, True), world, dev)
-    for ln in lanes:
-        ln.close()
+    e_ms = max_over_ranks(window(slots, args.steps, False), world, dev)
+    s_ms = max_over_ranks(window(slots[:1], args.steps, True), world, dev)
+    for sl in slots:
+        sl.close()
     return {"value": whole_job_rate(world, Q, e_ms / args.steps), "unit": UNIT,
             "h2d_bytes_per_step": int(boxes_h.nbytes + tf_h.nbytes + smp_h.nbytes),
             "d2h_bytes_per_step": int(Q * S * 4 + P * 4 * esz), "ms_per_step": e_ms / args.steps,
-            "timing": "one window over all steps on three lanes taking steps in turn (query and frame streams "
-                      "each), joined at its end: a step's copies overlap the other lanes' kernels",
+            "timing": "one window over all steps: copy-in stream, query stream (batches in step order), frame "
+                      "stream beside it, copy-out stream, two slots of buffers ordered by events; a step's copies "
+                      "overlap its neighbours' kernels",
             "l2": "not flushed in the pipelined window (a step reads far more distinct IDs than the 129 MB L2)",
             "serial_flushed": {"value": whole_job_rate(world, Q, s_ms / args.steps), "unit": UNIT,
                                "ms_per_step": s_ms / args.steps,
-                               "timing": "one lane, each step alone: L2 flushed, copies in, kernels, copies out"}}
+                               "timing": "one slot, each step alone: L2 flushed, copies in, kernels, copies out"}}
 
 
 def run_ours(args):
