@@ -1093,9 +1093,11 @@ __device__ __forceinline__ void push_lanes(const PushArgs& P, const Hist<FP>& H,
 }
 
 // push queued entries 32 at a time until fewer than 32 (none if `all`)
-// remain, then move the rest to the front
+// remain, then move the rest to the front.  Inlined: as a call it made the
+// main loop save and restore its live registers around every drain (100,000-box
+// batch 5.79 -> 5.48 ms)
 template <bool FP, typename AT>
-__device__ __noinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Queue& Qu, bool all) {
+__device__ __forceinline__ void drain(const PushArgs& P, const Hist<FP>& H, const Queue& Qu, bool all) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
     const uint32_t qc = min(*Qu.count, Qu.cap);   // entries past the end were pushed at once
